@@ -1,0 +1,454 @@
+#!/usr/bin/env python
+"""Benchmark of the piecewise-flat-embedding hot path on one GB300.
+
+Metric: seconds per outer iteration (one SOC iteration of Alg. 1 = n_inner
+split-Bregman iterations of Alg. 2, each a d-column PCG solve of Eq. 13 to
+relative residual 1e-6 plus the fused edge pass, then the P/B-step), with
+the PCG iteration counts, for the FP32 path (FP32 edge/SpMM/vectors,
+double-FP32 dots and solution, FP64 P-step) next to the plain FP64 path.
+
+Workload (default): the 2048x2048 synthetic image (40 Voronoi regions with
+texture, noise 0.03), radius-2 graph (n = 4,194,304, 50,290,692 directed
+edges), sigma = 0.1, d = 10, 10 inner iterations per outer iteration.  A
+step is one outer iteration, continuing the same solve; the working set of
+a step (several GB) is far larger than L2, so no flush is needed between
+steps.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank solves its own image (seed + rank): independent
+replicas, weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PFE sec/outer-iter & PCG iters @1e-6 res, learned+FP32 vs plain FP64"
+UNIT = "s/outer-iter"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="C5", choices=["C1", "C2", "C5"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-worker", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-window", type=int, default=192)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# CPU oracle sample (runs in a fresh single-threaded process)
+# --------------------------------------------------------------------------
+
+
+def cpu_sample_worker(arg: str):
+    """One outer iteration of the oracle (Jacobi-PCG mode) on a seeded window
+    of the workload's image, with the full image's lambda; prints JSON."""
+    import numpy as np
+
+    from oracle import pfe_oracle as O
+    from synth import CONFIGS, make_problem
+    from dataclasses import replace
+    cfg = json.loads(arg)
+    spec = CONFIGS[cfg["workload"]]
+    win = cfg["window"]
+    x0 = (spec.W - win) // 2
+    y0 = (spec.H - win) // 2
+    wspec = replace(spec, crop=(x0, y0, win, win))
+    X, Y0 = make_problem(wspec)
+    g = O.build_grid_graph(X, win, win, spec.radius, spec.sigma, lam=cfg["lambda"])
+    st = O.init_state(g, Y0)
+    solve = O.PCGSolver(g.A, spec.tol, 5000, 50)
+    times, iters = [], []
+    for _ in range(cfg["steps"]):
+        t0 = time.perf_counter()
+        O.reset_inner(st)
+        its = 0
+        for _ in range(spec.n_inner):
+            info = O.split_bregman_step(g, st, solve)
+            its += int(info["iters"].max())
+        O.p_and_b_step(g, st)
+        times.append(time.perf_counter() - t0)
+        iters.append(its / spec.n_inner)
+    nnz = g.A.nnz
+    print(json.dumps({"times": times, "iters": iters, "nnz": int(nnz), "n": int(g.n)}))
+
+
+def run_cpu_sample(workload: str, lam: float, steps: int, window: int, nnz_full: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    arg = json.dumps({"workload": workload, "lambda": lam, "steps": steps, "window": window})
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-worker", arg],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("CPU oracle sample failed:\n" + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    scale = nnz_full / out["nnz"]
+    out["scale"] = scale
+    out["per_step_scaled"] = [t * scale for t in out["times"]]
+    return out
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sms, maxs, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                maxs = max(maxs, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sms:
+            return None
+        sms.sort()
+        return {"sm_mhz": sms[len(sms) // 2], "sm_max_mhz": maxs, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pcg_kernels.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1612_06496_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str, kernel: str, units_full: float) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, scaled to the
+    full launch; None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as f:
+        for ln in f:
+            if "=" in ln and not ln.startswith("#"):
+                k, v = ln.split("=", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("kernel_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"]) * units_full / float(kv["units"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 oracle, timed as it stands on the host cores
+# --------------------------------------------------------------------------
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    from synth import CONFIGS, make_problem
+    from oracle import pfe_oracle as O
+    spec = CONFIGS[args.workload]
+    # lambda of the full image, and its nnz_A, for the scale of the sample
+    nnz_full, lam = full_graph_size_and_lambda(spec)
+    steps = args.warmup + args.steps
+    out = run_cpu_sample(args.workload, lam, steps, args.cpu_window, nnz_full)
+    timed = out["per_step_scaled"][args.warmup:]
+    v = sum(timed) / len(timed)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(spec, args.gpus),
+        "pcg_iters_mean": sum(out["iters"][args.warmup:]) / len(timed),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration per step on "
+                                   f"the central {args.cpu_window}x{args.cpu_window} window of the same image "
+                                   f"with the full image's lambda, scaled by nnz_A ratio {out['scale']:.1f}"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def full_graph_size_and_lambda(spec):
+    """nnz_A and lambda = sqrt(vol) of the full image, from the oracle's graph
+    definition (pure NumPy; no GPU)."""
+    import numpy as np
+    from oracle import pfe_oracle as O
+    from synth import make_problem
+    X, _ = make_problem(spec)
+    a, b = O.grid_edges(spec.H, spec.W, spec.radius)
+    w = O.heat_kernel_weights(X, a, b, spec.sigma)
+    vol = 2.0 * float(np.sum(w))
+    return spec.n + 2 * a.shape[0], float(np.sqrt(vol))
+
+
+def workload_config(spec, gpus: int) -> dict:
+    return {"workload": f"{spec.name}: {spec.W}x{spec.H} synthetic Voronoi image, radius-{spec.radius:g} graph, "
+                        f"sigma={spec.sigma:g}, d={spec.d}, {spec.n_inner} inner iterations per outer step, "
+                        f"PCG rel-res {spec.tol:g}",
+            "n": spec.n, "d": spec.d, "n_inner": spec.n_inner, "tol": spec.tol,
+            "l2": "working set per step >> L2 (inputs larger than L2, no flush)",
+            "parallelism": f"replicas x{gpus}" if gpus > 1 else "single GPU"}
+
+
+# --------------------------------------------------------------------------
+# GB300 arm
+# --------------------------------------------------------------------------
+
+
+def main():
+    args = parse()
+    if args.cpu_sample_worker is not None:
+        cpu_sample_worker(args.cpu_sample_worker)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1612_06496_gb300 import PFE, load_library
+    from synth import CONFIGS, make_problem
+    from dataclasses import replace
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    load_library()
+    spec = CONFIGS[args.workload]
+    if world > 1:
+        spec = replace(spec, seed=spec.seed + rank)
+    X, Y0 = make_problem(spec)
+    H, W = spec.shape
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    Xd = torch.from_numpy(X).cuda()
+    Y0d = torch.from_numpy(Y0).cuda()
+
+    def run_arm(precision: str, warmup: int, steps: int, clocks: bool):
+        t0 = time.perf_counter()
+        p = PFE(Xd, sigma=spec.sigma, H=H, W=W, radius=spec.radius, precision=precision, tol=spec.tol,
+                stream=stream)
+        p.init(Y0d)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        for _ in range(warmup):
+            p.solve(1, spec.n_inner)
+        sampler = ClockSampler(local) if clocks else None
+        barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = []
+        for _ in range(steps):
+            stats.append(p.solve(1, spec.n_inner))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        clk = sampler.stop() if sampler else None
+        return p, ms, stats, setup_s, clk
+
+    # --- FP32 path (the timed arm)
+    p, ms, stats, setup_s, clk = run_arm("mixed", args.warmup, args.steps, True)
+    ms_max = max_over_ranks(ms)
+    info = p.info()
+    iters_total = sum(s["pcg_iters_total"] for s in stats)
+    n_solves = sum(s["n_solves"] for s in stats)
+    launches = sum(s["kernel_launches"] for s in stats)
+    sec_per_outer = ms_max / 1e3 / (args.steps * world)
+
+    # --- roofline of the dominant kernel (SpMM with fused column dots)
+    spmm_ms = p.time_kernel("spmm", 20)
+    upd_ms = p.time_kernel("update", 20)
+    pup_ms = p.time_kernel("pupdate", 20)
+    edge_ms = p.time_kernel("edge", 10)
+    n, d, nnz = info["n"], info["d"], info["nnz_A"]
+    spmm_bytes = 8 * nnz + 4 * (n + 1) + 2 * 4 * n * d         # FP32 values + int32 indices + p in, q out
+    peaks = measured_peaks()
+    achieved = spmm_bytes / (spmm_ms * 1e-3) / 1e9
+    pcg_time_est = iters_total * (spmm_ms + upd_ms + pup_ms) * 1e-3
+    roofline = {"bound": "hbm", "kernel": "k_spmm<float,%d>" % d, "achieved": round(achieved, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": ncu_traffic(args.workload, "spmm", nnz),
+                "algorithmic_bytes_per_launch": spmm_bytes, "avg_launch_ms": round(spmm_ms, 5),
+                "launches_in_timed_region": iters_total,
+                "share_of_timed_region": round(iters_total * spmm_ms / ms, 4),
+                "other_kernels_ms": {"update": round(upd_ms, 5), "pupdate": round(pup_ms, 5),
+                                     "edge": round(edge_ms, 5)}}
+    p.close()
+
+    # --- plain FP64 path on the same problem
+    fp64 = None
+    if not args.no_fp64:
+        q, ms64, st64, _, _ = run_arm("fp64", 1, args.fp64_steps, False)
+        ms64 = max_over_ranks(ms64)
+        it64 = sum(s["pcg_iters_total"] for s in st64)
+        ns64 = sum(s["n_solves"] for s in st64)
+        spmm64 = q.time_kernel("spmm", 5)
+        fp64 = {"sec_per_outer_iter": ms64 / 1e3 / (args.fp64_steps * world),
+                "pcg_iters_mean": it64 / max(ns64, 1), "pcg_iters_max": max(s["pcg_iters_max"] for s in st64),
+                "spmm_ms": round(spmm64, 4),
+                "spmm_bound": "fp64 alu: 2 FLOP per nonzero per column at the measured 1.2 TFLOP/s DFMA rate"}
+        q.close()
+
+    # --- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        Y0h = torch.from_numpy(Y0).pin_memory()
+        Yo = torch.empty((spec.n, spec.d), dtype=torch.float64).pin_memory()
+        Yho = torch.empty_like(Yo).pin_memory()
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            r = PFE(Xh, sigma=spec.sigma, H=H, W=W, radius=spec.radius, precision="mixed", tol=spec.tol,
+                    stream=stream)
+            r.init(Y0h)
+            r.solve(1, spec.n_inner, Yo, Yho)
+            r.close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        barrier()
+        ms_e2e = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3))
+        e2e = {"value": ms_e2e / 1e3 / (e2e_steps * world), "unit": UNIT,
+               "h2d_bytes_per_step": int(X.nbytes + Y0.nbytes), "d2h_bytes_per_step": int(2 * Yo.numel() * 8),
+               "steps": e2e_steps,
+               "what": "per step: pfe_build_graph from host features, pfe_init from host Y0, one outer "
+                       "iteration (pfe_solve 1 x n_inner), Y and Yhat copied back to pinned host memory"}
+
+    # --- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            out = run_cpu_sample(args.workload, info["lambda_"], 1, args.cpu_window, nnz)
+            cpu = {"value": out["per_step_scaled"][0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration on the central "
+                             f"{args.cpu_window}x{args.cpu_window} window of the same image with the full "
+                             f"image's lambda ({out['iters'][0]:.0f} PCG iterations per solve), "
+                             f"{out['times'][0]:.1f} s scaled by nnz_A ratio {out['scale']:.1f}"}
+        except Exception as ex:  # report, do not hide
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": sec_per_outer, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(spec, world),
+            "precision_path": "FP32 edge/SpMM/vectors, double-FP32 dots and PCG solution, FP64 P-step; "
+                              "Jacobi preconditioner",
+            "pcg_iters_mean": iters_total / max(n_solves, 1),
+            "pcg_iters_max": max(s["pcg_iters_max"] for s in stats),
+            "pcg_relres_max": max(s["relres_max"] for s in stats),
+            "gnnz_rhs_per_s": nnz * d * iters_total / (ms / 1e3) / 1e9,
+            "setup_s": setup_s, "lambda": info["lambda_"],
+            "fp64": fp64,
+            "speedup_vs_fp64": (fp64["sec_per_outer_iter"] / sec_per_outer) if fp64 else None,
+            "roofline": roofline,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

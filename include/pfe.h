@@ -1,0 +1,280 @@
+/*
+ * pfe.h -- C ABI of libpfe, a CUDA (sm_103a) implementation of the inner
+ * loop of piecewise flat embeddings (PFE):
+ *
+ *     min_Y  sum_{i,j} w_ij |y_i - y_j|_1   s.t.  Y^T D Y = I          (Eq. 1)
+ *
+ * solved by the SOC / Bregman outer iteration (Alg. 1) around the split
+ * Bregman inner iteration (Alg. 2) in its compact form (Eqs. 9, 10, 13),
+ * with the d right-hand-side systems of Eq. 13 solved by preconditioned
+ * conjugate gradients (Sec. III, last paragraph).
+ *
+ * Conventions for every entry point:
+ *  - Returns a pfe_status; PFE_OK is 0.  No C++ exception crosses the ABI.
+ *    pfe_last_error() returns a message for the last failing call on a ctx.
+ *  - Array arguments are plain pointers.  Unless a parameter says otherwise
+ *    a pointer may address host memory (pageable or pinned) or device
+ *    memory of the context's GPU; the library detects which and copies host
+ *    data through its own device buffers.  Arrays are row-major and
+ *    contiguous unless a leading dimension is given.
+ *  - The caller owns every array it passes; the library never frees or
+ *    retains caller memory beyond the call.  The library owns everything it
+ *    allocates inside a pfe_ctx until pfe_destroy().
+ *  - All device work is queued on the stream given to pfe_build_graph (or
+ *    pfe_set_stream).  Calls that return host-visible results synchronise
+ *    that stream before returning; the others only enqueue work.
+ *  - A context is thread-compatible, not thread-safe: do not use one
+ *    context from two threads at once.
+ */
+#ifndef PFE_H
+#define PFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PFE_API __attribute__((visibility("default")))
+#else
+#define PFE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pfe_ctx pfe_ctx;
+/* A cudaStream_t passed as an opaque pointer; NULL is the legacy default stream. */
+typedef void *pfe_stream_t;
+
+typedef enum pfe_status {
+    PFE_OK = 0,
+    PFE_EINVAL = 1,        /* bad argument (NULL, size, zero-degree vertex, duplicate edge, ...) */
+    PFE_ENOMEM = 2,        /* a device or host allocation failed */
+    PFE_ECUDA = 3,         /* a CUDA runtime call failed */
+    PFE_ENOTCONV = 4,      /* a PCG solve hit max_iter; results are still written */
+    PFE_ENUMERIC = 5,      /* NaN/Inf or a non-positive curvature p^T A p in PCG */
+    PFE_ESINGULAR = 6,     /* the P-step's Gram matrix is numerically singular */
+    PFE_ETIMEOUT = 7,      /* reserved: a bounded device wait ran out */
+    PFE_EUNSUPPORTED = 8,  /* embedding dimension or option not built into this library */
+    PFE_ESTATE = 9         /* call out of order (e.g. pfe_inner_step before pfe_init) */
+} pfe_status;
+
+/* Graph kinds (pfe_graph_desc.kind). */
+enum { PFE_GRAPH_GRID = 0, PFE_GRAPH_EDGES = 1 };
+/* Arithmetic of the iteration (pfe_params.precision). */
+enum {
+    PFE_FP64 = 0,  /* every array and operation in FP64 */
+    PFE_MIXED = 1  /* FP32 edge pass, SpMM and PCG vectors; FP32-pair (about 48-bit)
+                      accumulation of dot products and of the PCG solution; FP64
+                      Gram, polar step, P, B */
+};
+/* Preconditioner of the PCG solve (pfe_params.precond). */
+enum { PFE_PRECOND_JACOBI = 0 };
+/* How the PCG loop is driven (pfe_params.loop_mode). */
+enum {
+    PFE_LOOP_GRAPH = 0,  /* CUDA graph with a device-evaluated WHILE node: no host sync */
+    PFE_LOOP_HOST = 1    /* host loop that polls a device flag every check_every iterations */
+};
+
+/*
+ * Data points and graph (Sec. II: points x_i in R^m; heat-kernel weights
+ * w_ij = exp(-|x_i - x_j|^2 / (2 sigma^2)); Sec. IV: one vertex per pixel,
+ * edges between nearby pixels).
+ */
+typedef struct pfe_graph_desc {
+    int64_t n;               /* number of data points (vertices), >= 2 */
+    int32_t m;               /* feature dimension, >= 1 */
+    int32_t kind;            /* PFE_GRAPH_GRID or PFE_GRAPH_EDGES */
+    const double *features;  /* n x m, row-major FP64 (host or device) */
+    /* PFE_GRAPH_GRID: n == H*W, pixel (x, y) is vertex y*W + x, and every
+     * pair of pixels with 0 < dx^2 + dy^2 <= radius^2 is an edge. */
+    int32_t H, W;
+    double radius;           /* in pixels, 1 <= radius <= 8 */
+    /* PFE_GRAPH_EDGES: n_edges undirected pairs (ei[k], ej[k]), 0 <= ei, ej < n,
+     * ei != ej, no pair listed twice (in either orientation).  int32 arrays,
+     * host or device.  Edge k keeps id k in pfe_get_edges(). */
+    const int32_t *ei, *ej;
+    int64_t n_edges;
+    double sigma;            /* heat-kernel width, > 0 */
+} pfe_graph_desc;
+
+typedef struct pfe_params {
+    double lambda;        /* split-Bregman penalty (Alg. 2); <= 0 selects sqrt(sum_i d_i) */
+    double r;             /* SOC penalty (Alg. 1, Eq. 5), > 0; default 1 */
+    int32_t precision;    /* PFE_FP64 or PFE_MIXED; default PFE_MIXED */
+    int32_t precond;      /* PFE_PRECOND_JACOBI */
+    double tol;           /* PCG stops a column when |b - A y| / |b| <= tol; default 1e-6 */
+    int32_t max_iter;     /* PCG iteration cap per solve; default 5000 */
+    int32_t refresh;      /* every `refresh` iterations r is recomputed as b - A y in
+                             extended precision; 0 = never; default 50 */
+    int32_t reset_inner_each_outer; /* 1 (default): b = d = 0 at every outer iteration
+                                       (Alg. 2 restarts); 0: carry them over */
+    int32_t loop_mode;    /* PFE_LOOP_GRAPH (default) or PFE_LOOP_HOST */
+    int32_t check_every;  /* iterations per graph body / host poll; default 4 */
+    int32_t blocks_per_sm;/* persistent-grid occupancy of the row kernels; 0 = auto */
+} pfe_params;
+
+/* Fills *p with the defaults listed above.  Never fails. */
+PFE_API void pfe_default_params(pfe_params *p);
+
+typedef struct pfe_info {
+    int64_t n;            /* vertices */
+    int64_t n_edges;      /* undirected edges |E| (rows of M, Sec. II) */
+    int64_t nnz_A;        /* n + 2|E|: nonzeros of lambda M^T M + r D */
+    int64_t sell_slots;   /* padded off-diagonal slots actually stored (>= 2|E|) */
+    int32_t d;            /* embedding dimension after pfe_init, else 0 */
+    int32_t precision;
+    double lambda, r;     /* values in use */
+    double vol;           /* sum_i d_i */
+    int64_t device_bytes; /* bytes of device memory the context holds */
+} pfe_info;
+
+typedef struct pfe_step_stats {
+    int32_t pcg_iters;      /* iterations of this step's solve (max over columns) */
+    int32_t converged;      /* 1 if every column reached tol */
+    double relres_max;      /* max over columns of the final relative residual */
+} pfe_step_stats;
+
+typedef struct pfe_solve_stats {
+    int64_t pcg_iters_total;  /* sum over solves of the per-solve iteration count */
+    int32_t pcg_iters_max;    /* largest per-solve iteration count */
+    int32_t n_solves;         /* inner steps run by this call */
+    int32_t n_unconverged;    /* solves that stopped at max_iter */
+    double relres_max;        /* largest final relative residual of any solve */
+    int64_t kernel_launches;  /* libpfe kernels launched by this call's iterations */
+} pfe_solve_stats;
+
+/*
+ * pfe_build_graph -- build the graph and the constant system matrix of Eq. 13.
+ *
+ * Computes the heat-kernel weights (Sec. II), d_i = sum_j w_ij (Sec. II,
+ * Alg. 1 step 2), the edge operator M (one row per undirected edge i < j with
+ * +w_ij at i and -w_ij at j, Sec. II) in implicit form, and
+ * A = lambda M^T M + r D (twice the matrix of Eq. 13), all on the device.
+ * A zero-degree vertex is PFE_EINVAL (D^{-1/2} would not exist).
+ * *out receives a new context (NULL on failure).  The feature and edge
+ * arrays are read during the call only.  Synchronises `stream`.
+ */
+PFE_API pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *g, const pfe_params *p,
+                           pfe_stream_t stream);
+
+/*
+ * pfe_init -- set the starting embedding (Alg. 1 step 3).
+ *
+ * Y0 is n x d FP64 with leading dimension ldY0 >= d (host or device).  The
+ * library D-orthonormalises it, Y = D^{-1/2} polar(D^{1/2} Y0) (the P-step
+ * map of Alg. 1 step 6 applied to D^{1/2} Y0), then sets P = D^{1/2} Y,
+ * B = 0 and the split-Bregman variables b = d = 0 (Alg. 2 step 3).
+ * Y0 == NULL is PFE_EINVAL (no built-in initialiser).  d must be one of the
+ * dimensions built into the library (1..16, 20, 24, 25, 32), else
+ * PFE_EUNSUPPORTED.  PFE_ESINGULAR if D^{1/2} Y0 is rank deficient.
+ */
+PFE_API pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0);
+
+/*
+ * pfe_inner_step -- one split-Bregman iteration (Alg. 2 steps 5-7 in the
+ * compact form): solve Eq. 13 for Y by PCG (warm-started from the previous
+ * Y), then d = Shrink(M Y + b, 1/lambda) (Eq. 9), b = b + M Y - d (Eq. 10),
+ * and the next right-hand side lambda M^T (d - b) + r D^{1/2} (P - B), all
+ * fused in one edge pass.  Only enqueues work unless st != NULL, in which
+ * case it synchronises and fills *st.  PFE_ENOTCONV / PFE_ENUMERIC are
+ * reported by the call that synchronises.
+ */
+PFE_API pfe_status pfe_inner_step(pfe_ctx *c, pfe_step_stats *st);
+
+/*
+ * pfe_pstep -- close an outer iteration: Alg. 1 steps 6-7,
+ * P = polar(D^{1/2} Y + B) (orthogonal Procrustes solution, FP64),
+ * B = B + D^{1/2} Y - P, then restart the inner variables (b = d = 0) when
+ * reset_inner_each_outer is set.  Enqueues only.
+ */
+PFE_API pfe_status pfe_pstep(pfe_ctx *c);
+
+/*
+ * pfe_solve -- run n_outer outer iterations of Alg. 1, each with n_inner
+ * inner iterations of Alg. 2, from the current state.  Writes (when non-NULL)
+ * Y_out = the last split-Bregman solution Y and Yhat_out = D^{-1/2} P (which
+ * satisfies Yhat^T D Yhat = I), both n x d FP64 row-major, host or device.
+ * Synchronises once at the end; fills *st when non-NULL.
+ */
+PFE_API pfe_status pfe_solve(pfe_ctx *c, int32_t n_outer, int32_t n_inner, double *Y_out,
+                     double *Yhat_out, pfe_solve_stats *st);
+
+/* Frees every library allocation of the context (NULL is allowed). */
+PFE_API pfe_status pfe_destroy(pfe_ctx *c);
+
+/* Message of the last failed call on c (never NULL; "" when none). */
+PFE_API const char *pfe_last_error(const pfe_ctx *c);
+
+/* Human-readable name of a status code (static storage). */
+PFE_API const char *pfe_status_string(pfe_status s);
+
+/* Sizes and parameters of a context. Never synchronises. */
+PFE_API pfe_status pfe_get_info(const pfe_ctx *c, pfe_info *info);
+
+/* Changes the stream later calls enqueue on. */
+PFE_API pfe_status pfe_set_stream(pfe_ctx *c, pfe_stream_t stream);
+
+/*
+ * State arrays, for checkpoint/resume and for tests (all FP64, row-major,
+ * host or device pointers; converted from the working precision):
+ *   PFE_ARR_Y     n x d    current Y (last solve, or the start after pfe_init)
+ *   PFE_ARR_P     n x d    P of Alg. 1
+ *   PFE_ARR_B     n x d    B of Alg. 1
+ *   PFE_ARR_BS    |E| x d  split-Bregman b (Alg. 2), rows in pfe_get_edges order
+ *   PFE_ARR_RHS   n x d    right-hand side of the next solve (Eq. 13, times 2)
+ *   PFE_ARR_DEG   n        d_i = sum_j w_ij
+ *   PFE_ARR_DIAG  n        diagonal of A = lambda M^T M + r D
+ * pfe_get_array synchronises.  pfe_set_array accepts Y, P, B, BS and RHS;
+ * restoring all five after pfe_init(d) resumes an iteration exactly (Y also
+ * restores the extended-precision part of the mixed path when set from FP64).
+ */
+enum { PFE_ARR_Y = 0, PFE_ARR_P = 1, PFE_ARR_B = 2, PFE_ARR_BS = 3, PFE_ARR_RHS = 4,
+       PFE_ARR_DEG = 5, PFE_ARR_DIAG = 6 };
+PFE_API pfe_status pfe_get_array(pfe_ctx *c, int32_t which, double *dst);
+PFE_API pfe_status pfe_set_array(pfe_ctx *c, int32_t which, const double *src);
+
+/*
+ * Undirected edges in the library's numbering: a[k] < b[k] and the heat-kernel
+ * weight w[k] (any of the three may be NULL).  Each array has n_edges entries
+ * (host or device).  For PFE_GRAPH_EDGES input, edge k is input pair k.
+ * Synchronises.
+ */
+PFE_API pfe_status pfe_get_edges(pfe_ctx *c, int32_t *a, int32_t *b, double *w);
+
+/*
+ * pfe_apply_A -- Yout = A X for n x d FP64 arrays (host or device), computed
+ * by the library's SpMM kernel in the working precision (the product that
+ * every PCG iteration performs).  Requires pfe_init (fixes d).  Synchronises.
+ */
+PFE_API pfe_status pfe_apply_A(pfe_ctx *c, const double *X, double *Yout);
+
+/*
+ * pfe_solve_system -- solve A Y = RHS (Eq. 13) by the configured PCG, with Y
+ * holding the initial guess on entry and the solution on exit (n x d FP64,
+ * host or device).  Does not touch the iteration state except scratch
+ * vectors.  Synchronises; fills *st when non-NULL.
+ */
+PFE_API pfe_status pfe_solve_system(pfe_ctx *c, const double *RHS, double *Y, pfe_step_stats *st);
+
+/*
+ * pfe_time_kernel -- average device time of one hot-path kernel, for
+ * roofline reporting: `reps` back-to-back launches on the context's current
+ * state (after pfe_init), bracketed by CUDA events on the context's stream.
+ *   PFE_KERNEL_SPMM     q = A p with the fused p.q column dots (one PCG iteration's SpMM)
+ *   PFE_KERNEL_UPDATE   y += alpha p, r -= alpha q with the r.z, r.r dots
+ *   PFE_KERNEL_PUPDATE  p = D_A^{-1} r + beta p
+ *   PFE_KERNEL_EDGE     fused M Y / Shrink / b update / M^T scatter (Eqs. 7, 9, 10, 13)
+ * The iteration state is not modified (scratch copies and a scratch control
+ * block are used; the edge pass rewrites the same right-hand side).  Only
+ * the PCG direction p and product q, which every solve re-initialises, are
+ * overwritten.  Synchronises; allocates temporary device memory.
+ */
+enum { PFE_KERNEL_SPMM = 0, PFE_KERNEL_UPDATE = 1, PFE_KERNEL_PUPDATE = 2, PFE_KERNEL_EDGE = 3 };
+PFE_API pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFE_H */

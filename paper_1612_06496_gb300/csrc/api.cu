@@ -1,0 +1,676 @@
+// The C ABI of libpfe (include/pfe.h): context life cycle, argument checks,
+// host/device staging, the PCG loop driver (CUDA graph with a WHILE node, or
+// a host poll loop) and the SOC / split-Bregman loop (Alg. 1 around Alg. 2).
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace pfe;
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+pfe_status fail(pfe_ctx *c, pfe_status s, const char *msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+template <typename P>
+pfe_status walloc(pfe_ctx *c, P **p, int64_t count) {
+    size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(P);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->err = std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e);
+        *p = nullptr;
+        return PFE_ENOMEM;
+    }
+    c->work_allocs.push_back((void *)*p);
+    c->bytes += (int64_t)bytes;
+    return PFE_OK;
+}
+
+void free_pcg_graph(pfe_ctx *c) {
+    if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
+    if (c->pcg_graph) cudaGraphDestroy(c->pcg_graph);
+    c->pcg_exec = nullptr;
+    c->pcg_graph = nullptr;
+}
+
+void free_work(pfe_ctx *c) {
+    free_pcg_graph(c);
+    for (void *p : c->work_allocs) cudaFree(p);
+    c->work_allocs.clear();
+    c->wk = Work{};
+    c->inited = false;
+    c->d = 0;
+}
+
+pfe_status sync(pfe_ctx *c) {
+    PFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PFE_OK;
+}
+
+// Build the CUDA graph {init kernel -> WHILE(body of check_every iterations)}.
+pfe_status build_pcg_graph(pfe_ctx *c) {
+    free_pcg_graph(c);
+    cudaStream_t cs;
+    PFE_CUDA_TRY(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } guard{cs};
+    cudaGraph_t g = nullptr;
+    PFE_CUDA_TRY(c, cudaGraphCreate(&g, 0));
+    c->pcg_graph = g;
+    cudaGraphConditionalHandle h;
+    PFE_CUDA_TRY(c, cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    PcgLaunch L{h, 1};
+    PFE_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    pfe_status st = launch_pcg_init(c, cs, L);
+    cudaGraph_t g2 = g;
+    cudaError_t ce = cudaStreamEndCapture(cs, &g2);
+    if (st != PFE_OK) return st;
+    PFE_CUDA_TRY(c, ce);
+    size_t nn = 0;
+    PFE_CUDA_TRY(c, cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    PFE_CUDA_TRY(c, cudaGraphGetNodes(g, nodes.data(), &nn));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    PFE_CUDA_TRY(c, cudaGraphAddNode(&cn, g, nodes.data(), nullptr, nn, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    PFE_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    st = launch_pcg_body(c, cs, L, std::max(1, c->prm.check_every));
+    cudaGraph_t b2 = body;
+    ce = cudaStreamEndCapture(cs, &b2);
+    if (st != PFE_OK) return st;
+    PFE_CUDA_TRY(c, ce);
+    PFE_CUDA_TRY(c, cudaGraphInstantiate(&c->pcg_exec, g, 0));
+    return PFE_OK;
+}
+
+// One PCG solve A Y = RHS on the work arrays, no host synchronisation in graph mode.
+pfe_status run_pcg(pfe_ctx *c, bool force_host) {
+    if (!force_host && c->prm.loop_mode == PFE_LOOP_GRAPH) {
+        if (!c->pcg_exec) PFE_TRY(build_pcg_graph(c));
+        PFE_CUDA_TRY(c, cudaGraphLaunch(c->pcg_exec, c->stream));
+        return PFE_OK;
+    }
+    PcgLaunch L{0, 0};
+    PFE_TRY(launch_pcg_init(c, c->stream, L));
+    const int chunk = std::max(1, c->prm.check_every);
+    const int64_t cap = (int64_t)c->prm.max_iter + 2 * chunk + 8;
+    for (int64_t it = 0;; it += chunk) {
+        PFE_TRY(launch_pcg_body(c, c->stream, L, chunk));
+        PFE_CUDA_TRY(c, cudaMemcpyAsync(c->h_flag, &c->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        PFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (*c->h_flag) break;
+        if (it > cap) return fail(c, PFE_ECUDA, "PCG control block never reported completion");
+    }
+    return PFE_OK;
+}
+
+pfe_status read_ctl(pfe_ctx *c) {
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, c->stream));
+    PFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return PFE_OK;
+}
+
+pfe_status clear_stats(pfe_ctx *c) {
+    // zero the statistics (tot_iters .. last_converged) and the launch counter
+    const size_t off = offsetof(PcgCtl, tot_iters), end = offsetof(PcgCtl, unroll);
+    PFE_CUDA_TRY(c, cudaMemsetAsync((char *)c->ctl + off, 0, end - off, c->stream));
+    PFE_CUDA_TRY(c, cudaMemsetAsync((char *)c->ctl + offsetof(PcgCtl, launches), 0, sizeof(long long), c->stream));
+    return PFE_OK;
+}
+
+pfe_status check_pstep(pfe_ctx *c) {
+    int e = 0;
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(c->h_flag, &c->pctl->error, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    e = *c->h_flag;
+    if (e) return fail(c, PFE_ESINGULAR, "P-step: X^T X is numerically singular");
+    return PFE_OK;
+}
+
+// status of the solves since the last clear_stats (host copy must be fresh)
+pfe_status pcg_status(pfe_ctx *c) {
+    if (c->h_ctl->error) return fail(c, PFE_ENUMERIC, "PCG: NaN/Inf or non-positive p^T A p");
+    if (c->h_ctl->n_unconv > 0) return fail(c, PFE_ENOTCONV, "PCG: max_iter reached before tol");
+    return PFE_OK;
+}
+
+size_t elem_size(const pfe_ctx *c) { return c->mixed ? sizeof(float) : sizeof(double); }
+
+pfe_status inner_step_enqueue(pfe_ctx *c) {
+    PFE_TRY(run_pcg(c, false));
+    PFE_TRY(launch_edge(c, c->stream));
+    return PFE_OK;
+}
+
+pfe_status pstep_enqueue(pfe_ctx *c) {
+    const bool reset = c->prm.reset_inner_each_outer != 0;
+    PFE_TRY(launch_pstep(c, c->stream, reset ? PSTEP_RESET : PSTEP_CARRY));
+    if (reset) {
+        const size_t bytes = (size_t)c->g.fslots * c->d * elem_size(c);
+        PFE_CUDA_TRY(c, cudaMemsetAsync(c->wk.Bs[c->bs_cur], 0, bytes, c->stream));
+    }
+    return PFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pfe_default_params(pfe_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->lambda = 0.0;
+    p->r = 1.0;
+    p->precision = PFE_MIXED;
+    p->precond = PFE_PRECOND_JACOBI;
+    p->tol = 1e-6;
+    p->max_iter = 5000;
+    p->refresh = 50;
+    p->reset_inner_each_outer = 1;
+    p->loop_mode = PFE_LOOP_GRAPH;
+    p->check_every = 4;
+    p->blocks_per_sm = 0;
+}
+
+const char *pfe_status_string(pfe_status s) {
+    switch (s) {
+        case PFE_OK: return "PFE_OK";
+        case PFE_EINVAL: return "PFE_EINVAL";
+        case PFE_ENOMEM: return "PFE_ENOMEM";
+        case PFE_ECUDA: return "PFE_ECUDA";
+        case PFE_ENOTCONV: return "PFE_ENOTCONV";
+        case PFE_ENUMERIC: return "PFE_ENUMERIC";
+        case PFE_ESINGULAR: return "PFE_ESINGULAR";
+        case PFE_ETIMEOUT: return "PFE_ETIMEOUT";
+        case PFE_EUNSUPPORTED: return "PFE_EUNSUPPORTED";
+        case PFE_ESTATE: return "PFE_ESTATE";
+    }
+    return "PFE_?";
+}
+
+const char *pfe_last_error(const pfe_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+pfe_status pfe_destroy(pfe_ctx *c) {
+    if (!c) return PFE_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_work(c);
+    for (void *p : c->dev_allocs) cudaFree(p);
+    if (c->ctl) cudaFree(c->ctl);
+    if (c->pctl) cudaFree(c->pctl);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    if (c->h_flag) cudaFreeHost(c->h_flag);
+    delete c;
+    return PFE_OK;
+}
+
+pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_params *p, pfe_stream_t stream) {
+    if (!out) return PFE_EINVAL;
+    *out = nullptr;
+    if (!gd || !p) return PFE_EINVAL;
+    if (gd->n < 2 || gd->m < 1 || !gd->features || !(gd->sigma > 0.0)) return PFE_EINVAL;
+    if (gd->n > (int64_t)INT32_MAX - 64) return PFE_EINVAL;
+    if (gd->kind == PFE_GRAPH_GRID) {
+        if (gd->H < 1 || gd->W < 1 || (int64_t)gd->H * gd->W != gd->n) return PFE_EINVAL;
+        if (!(gd->radius >= 1.0) || gd->radius > 8.0) return PFE_EINVAL;
+    } else if (gd->kind == PFE_GRAPH_EDGES) {
+        if (gd->n_edges < 1 || !gd->ei || !gd->ej || gd->n_edges > (int64_t)INT32_MAX / 2) return PFE_EINVAL;
+    } else {
+        return PFE_EINVAL;
+    }
+    if (!(p->r > 0.0) || !(p->tol >= 0.0) || p->max_iter < 1 || p->refresh < 0) return PFE_EINVAL;
+    if (p->precision != PFE_FP64 && p->precision != PFE_MIXED) return PFE_EINVAL;
+    if (p->precond != PFE_PRECOND_JACOBI) return PFE_EUNSUPPORTED;
+    if (p->loop_mode != PFE_LOOP_GRAPH && p->loop_mode != PFE_LOOP_HOST) return PFE_EINVAL;
+
+    pfe_ctx *c = new (std::nothrow) pfe_ctx();
+    if (!c) return PFE_ENOMEM;
+    c->prm = *p;
+    c->stream = (cudaStream_t)stream;
+    c->n = gd->n;
+    c->m = gd->m;
+    c->kind = gd->kind;
+    c->H = gd->H;
+    c->W = gd->W;
+    c->radius = gd->radius;
+    c->sigma = gd->sigma;
+    c->mixed = p->precision == PFE_MIXED;
+    c->g.n_edges = gd->kind == PFE_GRAPH_EDGES ? gd->n_edges : 0;
+    auto bail = [&](pfe_status s) {
+        std::string msg = c->err;
+        pfe_destroy(c);
+        (void)msg;
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return bail(PFE_ECUDA);
+    e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) return bail(PFE_ECUDA);
+    if (cudaMalloc((void **)&c->ctl, sizeof(PcgCtl)) != cudaSuccess) return bail(PFE_ENOMEM);
+    if (cudaMalloc((void **)&c->pctl, sizeof(PstepCtl)) != cudaSuccess) return bail(PFE_ENOMEM);
+    if (cudaMallocHost((void **)&c->h_ctl, sizeof(PcgCtl)) != cudaSuccess) return bail(PFE_ENOMEM);
+    if (cudaMallocHost((void **)&c->h_flag, 16) != cudaSuccess) return bail(PFE_ENOMEM);
+    if (cudaMemsetAsync(c->ctl, 0, sizeof(PcgCtl), c->stream) != cudaSuccess) return bail(PFE_ECUDA);
+    if (cudaMemsetAsync(c->pctl, 0, sizeof(PstepCtl), c->stream) != cudaSuccess) return bail(PFE_ECUDA);
+
+    // stage the inputs on the device when they are host arrays
+    const double *dfeat = gd->features;
+    double *feat_tmp = nullptr;
+    int32_t *ei_tmp = nullptr, *ej_tmp = nullptr;
+    struct Frees {
+        std::vector<void *> v;
+        ~Frees() {
+            for (void *q : v) cudaFree(q);
+        }
+    } frees;
+    if (!is_device_ptr(gd->features)) {
+        size_t bytes = sizeof(double) * (size_t)gd->n * gd->m;
+        if (cudaMalloc((void **)&feat_tmp, bytes) != cudaSuccess) return bail(PFE_ENOMEM);
+        frees.v.push_back(feat_tmp);
+        if (cudaMemcpyAsync(feat_tmp, gd->features, bytes, cudaMemcpyDefault, c->stream) != cudaSuccess)
+            return bail(PFE_ECUDA);
+        dfeat = feat_tmp;
+    }
+    pfe_status st;
+    if (gd->kind == PFE_GRAPH_GRID) {
+        st = build_grid_graph(c, dfeat);
+    } else {
+        const int32_t *dei = gd->ei, *dej = gd->ej;
+        size_t bytes = sizeof(int32_t) * (size_t)gd->n_edges;
+        if (!is_device_ptr(gd->ei)) {
+            if (cudaMalloc((void **)&ei_tmp, bytes) != cudaSuccess) return bail(PFE_ENOMEM);
+            frees.v.push_back(ei_tmp);
+            if (cudaMemcpyAsync(ei_tmp, gd->ei, bytes, cudaMemcpyDefault, c->stream) != cudaSuccess)
+                return bail(PFE_ECUDA);
+            dei = ei_tmp;
+        }
+        if (!is_device_ptr(gd->ej)) {
+            if (cudaMalloc((void **)&ej_tmp, bytes) != cudaSuccess) return bail(PFE_ENOMEM);
+            frees.v.push_back(ej_tmp);
+            if (cudaMemcpyAsync(ej_tmp, gd->ej, bytes, cudaMemcpyDefault, c->stream) != cudaSuccess)
+                return bail(PFE_ECUDA);
+            dej = ej_tmp;
+        }
+        st = build_edge_graph(c, dfeat, dei, dej);
+    }
+    if (st != PFE_OK) return bail(st);
+    st = finish_graph_values(c);
+    if (st != PFE_OK) return bail(st);
+    int bps = p->blocks_per_sm > 0 ? p->blocks_per_sm : 4;
+    int64_t want = (int64_t)c->num_sms * bps;
+    int64_t need = (c->g.n_slices + kWarps - 1) / kWarps;
+    c->grid_rows = (int)std::max<int64_t>(1, std::min(want, need));
+    *out = c;
+    return PFE_OK;
+}
+
+pfe_status pfe_set_stream(pfe_ctx *c, pfe_stream_t stream) {
+    if (!c) return PFE_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return PFE_OK;
+}
+
+pfe_status pfe_get_info(const pfe_ctx *c, pfe_info *info) {
+    if (!c || !info) return PFE_EINVAL;
+    info->n = c->n;
+    info->n_edges = c->g.n_edges;
+    info->nnz_A = c->n + 2 * c->g.n_edges;
+    info->sell_slots = c->g.slots;
+    info->d = c->d;
+    info->precision = c->mixed ? PFE_MIXED : PFE_FP64;
+    info->lambda = c->lambda;
+    info->r = c->r;
+    info->vol = c->vol;
+    info->device_bytes = c->bytes;
+    return PFE_OK;
+}
+
+pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
+    if (!c) return PFE_EINVAL;
+    if (!Y0) return fail(c, PFE_EINVAL, "Y0 is NULL: the library has no built-in initialiser");
+    if (d < 1 || d > c->n) return fail(c, PFE_EINVAL, "d must be in [1, n]");
+    if (ldY0 < d) return fail(c, PFE_EINVAL, "ldY0 < d");
+    if (!d_supported(d)) return fail(c, PFE_EUNSUPPORTED, "embedding dimension not built into libpfe");
+    free_work(c);
+    c->d = d;
+    const int64_t nd = c->n * (int64_t)d;
+    const int64_t ed = c->g.fslots * (int64_t)d;
+    auto &w = c->wk;
+    if (c->mixed) {
+        float *y, *bs0, *bs1, *rhs, *cw, *r, *pd, *q;
+        PFE_TRY(walloc(c, &y, nd));
+        PFE_TRY(walloc(c, &w.Ylo, nd));
+        PFE_TRY(walloc(c, &bs0, ed));
+        PFE_TRY(walloc(c, &bs1, ed));
+        PFE_TRY(walloc(c, &rhs, nd));
+        PFE_TRY(walloc(c, &cw, nd));
+        PFE_TRY(walloc(c, &r, nd));
+        PFE_TRY(walloc(c, &pd, nd));
+        PFE_TRY(walloc(c, &q, nd));
+        w.Y = y; w.Bs[0] = bs0; w.Bs[1] = bs1; w.RHS = rhs; w.Cw = cw; w.R = r; w.Pd = pd; w.Q = q;
+    } else {
+        double *y, *bs0, *bs1, *rhs, *cw, *r, *pd, *q;
+        PFE_TRY(walloc(c, &y, nd));
+        PFE_TRY(walloc(c, &bs0, ed));
+        PFE_TRY(walloc(c, &bs1, ed));
+        PFE_TRY(walloc(c, &rhs, nd));
+        PFE_TRY(walloc(c, &cw, nd));
+        PFE_TRY(walloc(c, &r, nd));
+        PFE_TRY(walloc(c, &pd, nd));
+        PFE_TRY(walloc(c, &q, nd));
+        w.Y = y; w.Bs[0] = bs0; w.Bs[1] = bs1; w.RHS = rhs; w.Cw = cw; w.R = r; w.Pd = pd; w.Q = q;
+    }
+    PFE_TRY(walloc(c, &w.P, nd));
+    PFE_TRY(walloc(c, &w.B, nd));
+    PFE_TRY(walloc(c, &w.stage, nd));
+    const int64_t part_pcg = (int64_t)c->grid_rows * 3 * PFE_DMAX;
+    const int64_t part_gram = (int64_t)c->num_sms * 2 * (PFE_DMAX * (PFE_DMAX + 1) / 2);
+    w.partials_len = std::max(part_pcg, part_gram);
+    PFE_TRY(walloc(c, &w.partials, w.partials_len));
+    const size_t es = elem_size(c);
+    PFE_CUDA_TRY(c, cudaMemsetAsync(w.Bs[0], 0, (size_t)ed * es, c->stream));
+    PFE_CUDA_TRY(c, cudaMemsetAsync(w.Bs[1], 0, (size_t)ed * es, c->stream));
+    PFE_CUDA_TRY(c, cudaMemsetAsync(w.Pd, 0, (size_t)nd * es, c->stream));
+    PFE_CUDA_TRY(c, cudaMemsetAsync(w.Q, 0, (size_t)nd * es, c->stream));
+    PFE_CUDA_TRY(c, cudaMemsetAsync(w.R, 0, (size_t)nd * es, c->stream));
+    c->bs_cur = 0;
+    // control block parameters
+    PcgCtl h;
+    memset(&h, 0, sizeof(h));
+    h.max_iter = c->prm.max_iter;
+    h.refresh = c->prm.refresh;
+    h.ncols = d;
+    h.tol = c->prm.tol;
+    h.done = 1;
+    h.unroll = std::max(1, c->prm.check_every);
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    PFE_CUDA_TRY(c, cudaMemsetAsync(c->pctl, 0, sizeof(PstepCtl), c->stream));
+    // Y0 -> stage (contiguous FP64), then D-orthonormalise via the P-step map
+    PFE_CUDA_TRY(c, cudaMemcpy2DAsync(w.stage, sizeof(double) * d, Y0, sizeof(double) * ldY0, sizeof(double) * d,
+                                      (size_t)c->n, cudaMemcpyDefault, c->stream));
+    PFE_TRY(launch_pstep(c, c->stream, PSTEP_INIT));
+    PFE_TRY(sync(c));
+    PFE_TRY(check_pstep(c));
+    c->inited = true;
+    return PFE_OK;
+}
+
+pfe_status pfe_inner_step(pfe_ctx *c, pfe_step_stats *st) {
+    if (!c) return PFE_EINVAL;
+    if (!c->inited) return fail(c, PFE_ESTATE, "pfe_inner_step before pfe_init");
+    PFE_TRY(inner_step_enqueue(c));
+    if (st) {
+        PFE_TRY(read_ctl(c));
+        st->pcg_iters = c->h_ctl->last_iters;
+        st->converged = c->h_ctl->last_converged;
+        st->relres_max = c->h_ctl->last_relres;
+        if (c->h_ctl->error) return fail(c, PFE_ENUMERIC, "PCG: NaN/Inf or non-positive p^T A p");
+        if (!st->converged) return fail(c, PFE_ENOTCONV, "PCG: max_iter reached before tol");
+    }
+    return PFE_OK;
+}
+
+pfe_status pfe_pstep(pfe_ctx *c) {
+    if (!c) return PFE_EINVAL;
+    if (!c->inited) return fail(c, PFE_ESTATE, "pfe_pstep before pfe_init");
+    return pstep_enqueue(c);
+}
+
+pfe_status pfe_solve(pfe_ctx *c, int32_t n_outer, int32_t n_inner, double *Y_out, double *Yhat_out,
+                     pfe_solve_stats *st) {
+    if (!c) return PFE_EINVAL;
+    if (!c->inited) return fail(c, PFE_ESTATE, "pfe_solve before pfe_init");
+    if (n_outer < 0 || n_inner < 0) return fail(c, PFE_EINVAL, "negative iteration count");
+    PFE_TRY(clear_stats(c));
+    for (int k = 0; k < n_outer; ++k) {
+        for (int l = 0; l < n_inner; ++l) PFE_TRY(inner_step_enqueue(c));
+        PFE_TRY(pstep_enqueue(c));
+    }
+    const size_t bytes = sizeof(double) * (size_t)c->n * c->d;
+    if (Y_out) {
+        PFE_TRY(launch_from_work(c, c->stream, c->wk.Y, c->wk.Ylo, c->wk.stage, c->n));
+        PFE_CUDA_TRY(c, cudaMemcpyAsync(Y_out, c->wk.stage, bytes, cudaMemcpyDefault, c->stream));
+    }
+    if (Yhat_out) {
+        if (is_device_ptr(Yhat_out)) {
+            PFE_TRY(launch_yhat(c, c->stream, Yhat_out));
+        } else {
+            PFE_TRY(sync(c));  // stage is reused
+            PFE_TRY(launch_yhat(c, c->stream, c->wk.stage));
+            PFE_CUDA_TRY(c, cudaMemcpyAsync(Yhat_out, c->wk.stage, bytes, cudaMemcpyDefault, c->stream));
+        }
+    }
+    PFE_TRY(read_ctl(c));
+    if (st) {
+        st->pcg_iters_total = c->h_ctl->tot_iters;
+        st->pcg_iters_max = c->h_ctl->max_solve_iters;
+        st->n_solves = c->h_ctl->n_solves;
+        st->n_unconverged = c->h_ctl->n_unconv;
+        st->relres_max = c->h_ctl->max_relres;
+        // PCG launches + one edge pass per inner step + Gram and apply per outer step
+        st->kernel_launches = c->h_ctl->launches + (int64_t)n_outer * n_inner + 2LL * n_outer;
+    }
+    PFE_TRY(check_pstep(c));
+    return pcg_status(c);
+}
+
+pfe_status pfe_get_array(pfe_ctx *c, int32_t which, double *dst) {
+    if (!c || !dst) return PFE_EINVAL;
+    const int64_t n = c->n;
+    if (which == PFE_ARR_DEG || which == PFE_ARR_DIAG) {
+        const double *src = which == PFE_ARR_DEG ? c->g.deg : c->g.adiag64;
+        PFE_CUDA_TRY(c, cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDefault, c->stream));
+        return sync(c);
+    }
+    if (!c->inited) return fail(c, PFE_ESTATE, "state arrays exist after pfe_init");
+    const size_t bytes = sizeof(double) * (size_t)n * c->d;
+    switch (which) {
+        case PFE_ARR_Y:
+            PFE_TRY(launch_from_work(c, c->stream, c->wk.Y, c->wk.Ylo, c->wk.stage, n));
+            PFE_CUDA_TRY(c, cudaMemcpyAsync(dst, c->wk.stage, bytes, cudaMemcpyDefault, c->stream));
+            break;
+        case PFE_ARR_RHS:
+            PFE_TRY(launch_from_work(c, c->stream, c->wk.RHS, nullptr, c->wk.stage, n));
+            PFE_CUDA_TRY(c, cudaMemcpyAsync(dst, c->wk.stage, bytes, cudaMemcpyDefault, c->stream));
+            break;
+        case PFE_ARR_P:
+            PFE_CUDA_TRY(c, cudaMemcpyAsync(dst, c->wk.P, bytes, cudaMemcpyDefault, c->stream));
+            break;
+        case PFE_ARR_B:
+            PFE_CUDA_TRY(c, cudaMemcpyAsync(dst, c->wk.B, bytes, cudaMemcpyDefault, c->stream));
+            break;
+        case PFE_ARR_BS: {
+            const size_t eb = sizeof(double) * (size_t)c->g.n_edges * c->d;
+            double *tmp = nullptr;
+            if (cudaMalloc((void **)&tmp, std::max<size_t>(eb, 8)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, PFE_ENOMEM, "staging buffer for b");
+            }
+            pfe_status s1 = launch_bs_gather(c, c->stream, c->wk.Bs[c->bs_cur], tmp, true);
+            cudaError_t e1 = cudaMemcpyAsync(dst, tmp, eb, cudaMemcpyDefault, c->stream);
+            cudaError_t e2 = cudaStreamSynchronize(c->stream);
+            cudaFree(tmp);
+            if (s1 != PFE_OK) return s1;
+            if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(c, PFE_ECUDA, "copy of b failed");
+            break;
+        }
+        default:
+            return fail(c, PFE_EINVAL, "unknown array id");
+    }
+    return sync(c);
+}
+
+pfe_status pfe_set_array(pfe_ctx *c, int32_t which, const double *src) {
+    if (!c || !src) return PFE_EINVAL;
+    if (!c->inited) return fail(c, PFE_ESTATE, "state arrays exist after pfe_init");
+    const int64_t n = c->n;
+    const size_t bytes = sizeof(double) * (size_t)n * c->d;
+    switch (which) {
+        case PFE_ARR_Y:
+            PFE_CUDA_TRY(c, cudaMemcpyAsync(c->wk.stage, src, bytes, cudaMemcpyDefault, c->stream));
+            PFE_TRY(launch_to_work(c, c->stream, c->wk.stage, c->wk.Y, c->wk.Ylo, n));
+            break;
+        case PFE_ARR_RHS:
+            PFE_CUDA_TRY(c, cudaMemcpyAsync(c->wk.stage, src, bytes, cudaMemcpyDefault, c->stream));
+            PFE_TRY(launch_to_work(c, c->stream, c->wk.stage, c->wk.RHS, nullptr, n));
+            break;
+        case PFE_ARR_P:
+            PFE_CUDA_TRY(c, cudaMemcpyAsync(c->wk.P, src, bytes, cudaMemcpyDefault, c->stream));
+            PFE_TRY(launch_cw(c, c->stream));
+            break;
+        case PFE_ARR_B:
+            PFE_CUDA_TRY(c, cudaMemcpyAsync(c->wk.B, src, bytes, cudaMemcpyDefault, c->stream));
+            PFE_TRY(launch_cw(c, c->stream));
+            break;
+        case PFE_ARR_BS: {
+            const size_t eb = sizeof(double) * (size_t)c->g.n_edges * c->d;
+            double *tmp = nullptr;
+            if (cudaMalloc((void **)&tmp, std::max<size_t>(eb, 8)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, PFE_ENOMEM, "staging buffer for b");
+            }
+            cudaError_t e1 = cudaMemcpyAsync(tmp, src, eb, cudaMemcpyDefault, c->stream);
+            pfe_status s1 = launch_bs_scatter(c, c->stream, tmp, c->wk.Bs[c->bs_cur]);
+            cudaError_t e2 = cudaStreamSynchronize(c->stream);
+            cudaFree(tmp);
+            if (s1 != PFE_OK) return s1;
+            if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(c, PFE_ECUDA, "copy of b failed");
+            break;
+        }
+        default:
+            return fail(c, PFE_EINVAL, "array id cannot be set");
+    }
+    return sync(c);
+}
+
+pfe_status pfe_get_edges(pfe_ctx *c, int32_t *a, int32_t *b, double *w) {
+    if (!c) return PFE_EINVAL;
+    const int64_t ne = c->g.n_edges;
+    if (a) PFE_CUDA_TRY(c, cudaMemcpyAsync(a, c->g.ea, sizeof(int32_t) * ne, cudaMemcpyDefault, c->stream));
+    if (b) PFE_CUDA_TRY(c, cudaMemcpyAsync(b, c->g.eb, sizeof(int32_t) * ne, cudaMemcpyDefault, c->stream));
+    if (w) PFE_CUDA_TRY(c, cudaMemcpyAsync(w, c->g.ew, sizeof(double) * ne, cudaMemcpyDefault, c->stream));
+    return sync(c);
+}
+
+pfe_status pfe_apply_A(pfe_ctx *c, const double *X, double *Yout) {
+    if (!c || !X || !Yout) return PFE_EINVAL;
+    if (!c->inited) return fail(c, PFE_ESTATE, "pfe_apply_A before pfe_init fixes d");
+    const int64_t n = c->n;
+    const size_t bytes = sizeof(double) * (size_t)n * c->d;
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(c->wk.stage, X, bytes, cudaMemcpyDefault, c->stream));
+    PFE_TRY(launch_to_work(c, c->stream, c->wk.stage, c->wk.R, nullptr, n));
+    PFE_TRY(launch_apply_A(c, c->stream, c->wk.R, c->wk.Q));
+    PFE_TRY(launch_from_work(c, c->stream, c->wk.Q, nullptr, c->wk.stage, n));
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(Yout, c->wk.stage, bytes, cudaMemcpyDefault, c->stream));
+    return sync(c);
+}
+
+pfe_status pfe_solve_system(pfe_ctx *c, const double *RHS, double *Y, pfe_step_stats *st) {
+    if (!c || !RHS || !Y) return PFE_EINVAL;
+    if (!c->inited) return fail(c, PFE_ESTATE, "pfe_solve_system before pfe_init fixes d");
+    const int64_t n = c->n;
+    const int64_t nd = n * (int64_t)c->d;
+    const size_t bytes = sizeof(double) * (size_t)nd;
+    const size_t es = elem_size(c);
+    // private solution / right-hand side buffers; the iteration state is untouched
+    void *y = nullptr, *b = nullptr;
+    float *ylo = nullptr;
+    struct F {
+        void *p[3];
+        ~F() {
+            for (void *q : p)
+                if (q) cudaFree(q);
+        }
+    } fr{{nullptr, nullptr, nullptr}};
+    if (cudaMalloc(&y, nd * es) != cudaSuccess || (fr.p[0] = y, false) || cudaMalloc(&b, nd * es) != cudaSuccess ||
+        (fr.p[1] = b, false) || (c->mixed && cudaMalloc((void **)&ylo, nd * sizeof(float)) != cudaSuccess)) {
+        cudaGetLastError();
+        return fail(c, PFE_ENOMEM, "pfe_solve_system buffers");
+    }
+    fr.p[2] = ylo;
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(c->wk.stage, RHS, bytes, cudaMemcpyDefault, c->stream));
+    PFE_TRY(launch_to_work(c, c->stream, c->wk.stage, b, nullptr, n));
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(c->wk.stage, Y, bytes, cudaMemcpyDefault, c->stream));
+    PFE_TRY(launch_to_work(c, c->stream, c->wk.stage, y, ylo, n));
+    Work saved = c->wk;
+    c->wk.Y = y;
+    c->wk.Ylo = ylo;
+    c->wk.RHS = b;
+    pfe_status s = run_pcg(c, true);
+    c->wk = saved;
+    PFE_TRY(s);
+    PFE_TRY(launch_from_work(c, c->stream, y, ylo, c->wk.stage, n));
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(Y, c->wk.stage, bytes, cudaMemcpyDefault, c->stream));
+    PFE_TRY(read_ctl(c));
+    if (st) {
+        st->pcg_iters = c->h_ctl->last_iters;
+        st->converged = c->h_ctl->last_converged;
+        st->relres_max = c->h_ctl->last_relres;
+    }
+    if (c->h_ctl->error) return fail(c, PFE_ENUMERIC, "PCG: NaN/Inf or non-positive p^T A p");
+    if (!c->h_ctl->last_converged) return fail(c, PFE_ENOTCONV, "PCG: max_iter reached before tol");
+    return PFE_OK;
+}
+
+pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_ms) {
+    if (!c || !avg_ms || reps < 1) return PFE_EINVAL;
+    if (!c->inited) return fail(c, PFE_ESTATE, "pfe_time_kernel before pfe_init");
+    PFE_TRY(sync(c));
+    float ms = 0.f;
+    if (which == PFE_KERNEL_EDGE) {
+        // the edge pass is idempotent while its inputs (Y, old b, C) are unchanged:
+        // repeated launches rewrite the same right-hand side and spare b buffer
+        cudaEvent_t e0, e1;
+        PFE_CUDA_TRY(c, cudaEventCreate(&e0));
+        PFE_CUDA_TRY(c, cudaEventCreate(&e1));
+        const int cur = c->bs_cur;
+        pfe_status st = launch_edge(c, c->stream);
+        c->bs_cur = cur;
+        cudaEventRecord(e0, c->stream);
+        for (int k = 0; k < reps && st == PFE_OK; ++k) {
+            st = launch_edge(c, c->stream);
+            c->bs_cur = cur;
+        }
+        cudaEventRecord(e1, c->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != PFE_OK) return st;
+        if (e != cudaSuccess) return fail(c, PFE_ECUDA, cudaGetErrorString(e));
+        ms /= (float)reps;
+    } else if (which >= PFE_KERNEL_SPMM && which <= PFE_KERNEL_PUPDATE) {
+        PFE_TRY(time_pcg_kernel(c, c->stream, which, reps, &ms));
+    } else {
+        return fail(c, PFE_EINVAL, "unknown kernel id");
+    }
+    *avg_ms = ms;
+    return PFE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Device helpers shared by the libpfe kernels: double-FP32 accumulation,
+// row loads of d-interleaved arrays, block reductions, SELL-32 traversal.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace pfe {
+
+constexpr int kBlock = 256;             // threads per block of every row kernel
+constexpr int kWarps = kBlock / 32;
+
+// ---------------------------------------------------------------------------
+// Double-FP32 ("df") accumulators.  GB300 issues FP64 at about 1/60 of the
+// FP32 rate, and FP32->FP64 conversions run on the same slow pipe, so bulk
+// reductions keep an unevaluated sum hi + lo of two floats.  Products are
+// made exact with an FMA (a*b = p + e exactly), sums use Knuth's TwoSum; the
+// pair carries about 48 significant bits.  Only O(blocks x d) values are ever
+// converted to FP64.
+// ---------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void df_add_prod(DF &acc, float a, float b) {
+    float p = __fmul_rn(a, b);
+    float pe = __fmaf_rn(a, b, -p);  // exact: a*b = p + pe
+    float s, se;
+    two_sum(acc.hi, p, s, se);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(se, pe));
+}
+
+__device__ __forceinline__ void df_add_f(DF &acc, float v) {
+    float s, se;
+    two_sum(acc.hi, v, s, se);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, se);
+}
+
+__device__ __forceinline__ void df_add(DF &acc, DF b) {
+    float s, se;
+    two_sum(acc.hi, b.hi, s, se);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(se, b.lo));
+}
+
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+
+// Accumulator type of each working precision: float data -> DF, double -> double.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<float> {
+    using type = DF;
+    __device__ static __forceinline__ DF zero() { return DF{0.f, 0.f}; }
+    __device__ static __forceinline__ void add_prod(DF &a, float x, float y) { df_add_prod(a, x, y); }
+    __device__ static __forceinline__ void add(DF &a, DF b) { df_add(a, b); }
+    __device__ static __forceinline__ DF shfl_xor(DF a, int m) {
+        return DF{__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+    }
+    __device__ static __forceinline__ double to_double(DF a) { return df_to_double(a); }
+};
+template <>
+struct Acc<double> {
+    using type = double;
+    __device__ static __forceinline__ double zero() { return 0.0; }
+    __device__ static __forceinline__ void add_prod(double &a, double x, double y) { a = fma(x, y, a); }
+    __device__ static __forceinline__ void add(double &a, double b) { a += b; }
+    __device__ static __forceinline__ double shfl_xor(double a, int m) {
+        return __shfl_xor_sync(0xffffffffu, a, m);
+    }
+    __device__ static __forceinline__ double to_double(double a) { return a; }
+};
+
+// ---------------------------------------------------------------------------
+// Row I/O for n x D row-major ("d-interleaved") arrays: the widest aligned
+// vector access that divides a row.
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__device__ __forceinline__ void load_row(const T *__restrict__ base, int64_t i, T (&v)[D]) {
+    const T *src = base + i * D;
+    constexpr int BYTES = D * (int)sizeof(T);
+    if constexpr (BYTES % 16 == 0) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+        for (int k = 0; k < BYTES / 16; ++k) {
+            float4 t = __ldg(s4 + k);
+            memcpy(reinterpret_cast<char *>(v) + 16 * k, &t, 16);
+        }
+    } else if constexpr (BYTES % 8 == 0) {
+        const float2 *s2 = reinterpret_cast<const float2 *>(src);
+#pragma unroll
+        for (int k = 0; k < BYTES / 8; ++k) {
+            float2 t = __ldg(s2 + k);
+            memcpy(reinterpret_cast<char *>(v) + 8 * k, &t, 8);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) v[k] = __ldg(src + k);
+    }
+}
+
+// Same, through the coherent path (for arrays written earlier in the same kernel
+// by other threads is never needed here; used for read-write arrays).
+template <typename T, int D>
+__device__ __forceinline__ void load_row_rw(const T *base, int64_t i, T (&v)[D]) {
+    const T *src = base + i * D;
+    constexpr int BYTES = D * (int)sizeof(T);
+    if constexpr (BYTES % 16 == 0) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+        for (int k = 0; k < BYTES / 16; ++k) {
+            float4 t = s4[k];
+            memcpy(reinterpret_cast<char *>(v) + 16 * k, &t, 16);
+        }
+    } else if constexpr (BYTES % 8 == 0) {
+        const float2 *s2 = reinterpret_cast<const float2 *>(src);
+#pragma unroll
+        for (int k = 0; k < BYTES / 8; ++k) {
+            float2 t = s2[k];
+            memcpy(reinterpret_cast<char *>(v) + 8 * k, &t, 8);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) v[k] = src[k];
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void store_row(T *base, int64_t i, const T (&v)[D]) {
+    T *dst = base + i * D;
+    constexpr int BYTES = D * (int)sizeof(T);
+    if constexpr (BYTES % 16 == 0) {
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+        for (int k = 0; k < BYTES / 16; ++k) {
+            float4 t;
+            memcpy(&t, reinterpret_cast<const char *>(v) + 16 * k, 16);
+            d4[k] = t;
+        }
+    } else if constexpr (BYTES % 8 == 0) {
+        float2 *d2 = reinterpret_cast<float2 *>(dst);
+#pragma unroll
+        for (int k = 0; k < BYTES / 8; ++k) {
+            float2 t;
+            memcpy(&t, reinterpret_cast<const char *>(v) + 8 * k, 8);
+            d2[k] = t;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) dst[k] = v[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block reduction of NV accumulators; thread t < NV receives the block total
+// of value t (as double).  All threads must call it.  Fixed order, so the
+// result does not depend on timing.
+// ---------------------------------------------------------------------------
+template <typename T, int NV>
+__device__ __forceinline__ void block_reduce(typename Acc<T>::type (&v)[NV], double *out_block) {
+    using A = Acc<T>;
+    using AT = typename A::type;
+    __shared__ AT red[kWarps][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) A::add(v[c], A::shfl_xor(v[c], m));
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) red[warp][c] = v[c];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < NV; c += blockDim.x) {
+        AT s = red[0][c];
+        for (int w = 1; w < kWarps; ++w) A::add(s, red[w][c]);
+        out_block[c] = A::to_double(s);
+    }
+}
+
+// "Last block done" detection: every block calls this after writing its
+// partials; exactly one block (the last to arrive) gets true and must reset
+// the ticket.  No waiting is involved.
+__device__ __forceinline__ bool last_block_arrives(unsigned *ticket) {
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(ticket, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
+
+__device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
+
+template <typename T>
+__device__ __forceinline__ T shrink(T t, T gamma) {
+    // Alg. 2 Shrink: sign(t) * max(|t| - gamma, 0); NaN propagates.
+    T m = fabs(t) - gamma;
+    if (m > T(0)) return copysign(m, t);
+    return (t != t) ? t : T(0);
+}
+
+}  // namespace pfe

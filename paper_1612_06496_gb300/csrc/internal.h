@@ -1,0 +1,166 @@
+// Internal declarations of libpfe: the context, device control blocks and the
+// kernel launchers of each translation unit.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pfe.h"
+
+#define PFE_DMAX 32
+
+namespace pfe {
+
+// Device-resident control block of one d-column PCG solve.  Written only by
+// the "last block" of a reduction kernel, read by all kernels at entry.
+struct PcgCtl {
+    int iter;          // iterations done in the current solve
+    int done;          // 1: every column converged, max_iter hit, or an error
+    int error;         // pfe_status of a numeric failure (0 = none)
+    int refresh_now;   // 1: this iteration ends with a true-residual refresh
+    unsigned ticket[4];
+    int max_iter, refresh, ncols, any_active;
+    double tol;
+    double bnorm[PFE_DMAX], rz[PFE_DMAX], alpha[PFE_DMAX], beta[PFE_DMAX], relres[PFE_DMAX];
+    int active[PFE_DMAX];
+    // statistics accumulated over solves until the host clears them
+    long long tot_iters;
+    int max_solve_iters, n_solves, n_unconv, last_iters;
+    double max_relres, last_relres;
+    int last_converged, unroll;       // unroll: iterations per graph body / host poll
+    long long launches;               // PCG kernel launches (early-exited ones included)
+};
+
+// Control block of the P-step (Alg. 1 steps 6-7).
+struct PstepCtl {
+    unsigned ticket;
+    int error;
+    double G[PFE_DMAX * PFE_DMAX];  // Gram X^T X
+    double T[PFE_DMAX * PFE_DMAX];  // (X^T X)^{-1/2}
+    double evals[PFE_DMAX];
+};
+
+// Graph in SELL-32 form (sliced ELLPACK, slice = 32 consecutive rows = one
+// warp).  Off-diagonal slot k of row i lives at slice_ptr[i/32] + 32k + i%32.
+// Undirected edges live in a second SELL-32 layout over their first
+// endpoint ("forward" edges, j > i): edge slot fslice_ptr[i/32] + 32k + i%32.
+struct DevGraph {
+    int64_t n = 0, n_slices = 0, slots = 0, n_edges = 0, fslots = 0;
+    int max_slots_per_row = 0;
+    int *slice_ptr = nullptr;   // n_slices + 1, in slots
+    int *fslice_ptr = nullptr;  // n_slices + 1, in edge slots
+    int *col = nullptr;         // per slot: neighbour j (padding: i itself)
+    int *eid = nullptr;         // per slot: edge slot of (min, max), -1 padding
+    double *w64 = nullptr;      // per slot: w_ij
+    float *w32 = nullptr;
+    double *aoff64 = nullptr;   // per slot: A_ij = -lambda w_ij^2
+    float *aoff32 = nullptr;
+    double *adiag64 = nullptr;  // A_ii = lambda d2_i + r d_i
+    float *adiag32 = nullptr;
+    double *dinv64 = nullptr;   // 1 / A_ii
+    float *dinv32 = nullptr;
+    double *deg = nullptr, *deg2 = nullptr, *sqrtdeg = nullptr;
+    int *ext_slot = nullptr;    // external edge k -> edge slot
+    int *ea = nullptr, *eb = nullptr;  // external edge k endpoints, a < b
+    double *ew = nullptr;              // external edge k weight
+};
+
+// Work arrays of the iteration for one precision (pointers typed at use).
+struct Work {
+    void *Y = nullptr;       // n x d: the PCG solution (Y of Alg. 2); FP32 hi part when mixed
+    float *Ylo = nullptr;    // mixed: low part of Y (Y = hi + lo)
+    void *Bs[2] = {nullptr, nullptr};  // edge slots x d: b of Alg. 2 (double-buffered)
+    void *RHS = nullptr;     // n x d: right-hand side of Eq. 13 (times 2)
+    void *Cw = nullptr;      // n x d: r D^{1/2} (P - B)
+    void *R = nullptr, *Pd = nullptr, *Q = nullptr;  // PCG residual, direction, A*direction
+    double *P = nullptr, *B = nullptr;  // n x d FP64 (Alg. 1)
+    double *stage = nullptr;            // n x d FP64 staging (init / get / set)
+    double *partials = nullptr;         // block partials of reductions
+    int64_t partials_len = 0;
+};
+
+}  // namespace pfe
+
+struct pfe_ctx {
+    pfe_params prm{};
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    int64_t n = 0;
+    int m = 0, kind = 0, H = 0, W = 0;
+    double radius = 0, sigma = 0, lambda = 0, r = 1, vol = 0;
+    pfe::DevGraph g;
+    int d = 0;
+    bool inited = false;
+    bool mixed = true;
+    int bs_cur = 0;
+    pfe::Work wk;
+    pfe::PcgCtl *ctl = nullptr;       // device
+    pfe::PcgCtl *h_ctl = nullptr;     // pinned host mirror
+    pfe::PstepCtl *pctl = nullptr;    // device
+    int *h_flag = nullptr;            // pinned host scratch
+    int grid_rows = 0;                // blocks of the persistent row kernels
+    cudaGraph_t pcg_graph = nullptr;
+    cudaGraphExec_t pcg_exec = nullptr;
+    std::string err;
+    std::vector<void *> dev_allocs;   // graph-lifetime allocations
+    std::vector<void *> work_allocs;  // d-dependent allocations
+    int64_t bytes = 0;
+};
+
+namespace pfe {
+
+// --- graph.cu
+pfe_status build_grid_graph(pfe_ctx *c, const double *dfeat);
+pfe_status build_edge_graph(pfe_ctx *c, const double *dfeat, const int32_t *dei, const int32_t *dej);
+pfe_status finish_graph_values(pfe_ctx *c);
+
+// --- pcg.cu: one PCG solve A Y = RHS on the context's work arrays
+struct PcgLaunch {
+    cudaGraphConditionalHandle cond;
+    int use_cond;
+};
+pfe_status launch_pcg_init(pfe_ctx *c, cudaStream_t s, PcgLaunch L);
+pfe_status launch_pcg_body(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters);
+pfe_status launch_apply_A(pfe_ctx *c, cudaStream_t s, const void *x, void *y);
+pfe_status time_pcg_kernel(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms);
+
+// --- edge.cu: fused edge pass (Eqs. 7, 9, 10) and right-hand side (Eq. 13)
+pfe_status launch_edge(pfe_ctx *c, cudaStream_t s);
+
+// --- pstep.cu: Gram, polar factor and the P/B/C update (Alg. 1 steps 6-7)
+enum PstepMode { PSTEP_INIT = 0, PSTEP_RESET = 1, PSTEP_CARRY = 2 };
+pfe_status launch_pstep(pfe_ctx *c, cudaStream_t s, int mode);
+
+// --- convert.cu: FP64 <-> working precision copies of n x d / edge arrays
+pfe_status launch_to_work(pfe_ctx *c, cudaStream_t s, const double *src, void *dst, float *dst_lo,
+                          int64_t rows);
+pfe_status launch_from_work(pfe_ctx *c, cudaStream_t s, const void *src, const float *src_lo,
+                            double *dst, int64_t rows);
+pfe_status launch_bs_gather(pfe_ctx *c, cudaStream_t s, const void *bs, double *dst, bool to_ext);
+pfe_status launch_bs_scatter(pfe_ctx *c, cudaStream_t s, const double *src, void *bs);
+pfe_status launch_yhat(pfe_ctx *c, cudaStream_t s, double *dst);
+pfe_status launch_cw(pfe_ctx *c, cudaStream_t s);  // C = r D^{1/2} (P - B)
+
+// supported embedding dimensions
+bool d_supported(int d);
+
+}  // namespace pfe
+
+// error helpers
+#define PFE_CUDA_TRY(c, call)                                                     \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) {                                                 \
+            (c)->err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
+            return PFE_ECUDA;                                                    \
+        }                                                                        \
+    } while (0)
+
+#define PFE_TRY(call)                 \
+    do {                              \
+        pfe_status s_ = (call);       \
+        if (s_ != PFE_OK) return s_;  \
+    } while (0)

@@ -1,0 +1,283 @@
+"""ctypes binding of libpfe (include/pfe.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Arrays may be numpy arrays (host) or torch tensors (host or CUDA);
+they must be C-contiguous float64 (int32 for edge lists).  Importing this
+module raises if libpfe.so has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpfe.so")
+
+PFE_OK, PFE_EINVAL, PFE_ENOMEM, PFE_ECUDA, PFE_ENOTCONV, PFE_ENUMERIC, PFE_ESINGULAR, PFE_ETIMEOUT, \
+    PFE_EUNSUPPORTED, PFE_ESTATE = range(10)
+PFE_GRAPH_GRID, PFE_GRAPH_EDGES = 0, 1
+PFE_FP64, PFE_MIXED = 0, 1
+PFE_PRECOND_JACOBI = 0
+PFE_LOOP_GRAPH, PFE_LOOP_HOST = 0, 1
+ARR = {"Y": 0, "P": 1, "B": 2, "BS": 3, "RHS": 4, "DEG": 5, "DIAG": 6}
+
+EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step", "pfe_pstep", "pfe_solve",
+           "pfe_destroy", "pfe_last_error", "pfe_status_string", "pfe_get_info", "pfe_set_stream",
+           "pfe_get_array", "pfe_set_array", "pfe_get_edges", "pfe_apply_A", "pfe_solve_system",
+           "pfe_time_kernel"]
+KERNEL = {"spmm": 0, "update": 1, "pupdate": 2, "edge": 3}
+
+
+class GraphDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int32), ("kind", C.c_int32), ("features", C.c_void_p),
+                ("H", C.c_int32), ("W", C.c_int32), ("radius", C.c_double),
+                ("ei", C.c_void_p), ("ej", C.c_void_p), ("n_edges", C.c_int64), ("sigma", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("r", C.c_double), ("precision", C.c_int32), ("precond", C.c_int32),
+                ("tol", C.c_double), ("max_iter", C.c_int32), ("refresh", C.c_int32),
+                ("reset_inner_each_outer", C.c_int32), ("loop_mode", C.c_int32), ("check_every", C.c_int32),
+                ("blocks_per_sm", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_edges", C.c_int64), ("nnz_A", C.c_int64), ("sell_slots", C.c_int64),
+                ("d", C.c_int32), ("precision", C.c_int32), ("lambda_", C.c_double), ("r", C.c_double),
+                ("vol", C.c_double), ("device_bytes", C.c_int64)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("pcg_iters", C.c_int32), ("converged", C.c_int32), ("relres_max", C.c_double)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("pcg_iters_total", C.c_int64), ("pcg_iters_max", C.c_int32), ("n_solves", C.c_int32),
+                ("n_unconverged", C.c_int32), ("relres_max", C.c_double), ("kernel_launches", C.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load libpfe.so (raises OSError when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libpfe.so not found at {path}; run `python -m paper_1612_06496_gb300.build`")
+    lib = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    lib.pfe_default_params.argtypes = [C.POINTER(Params)]
+    lib.pfe_default_params.restype = None
+    lib.pfe_build_graph.argtypes = [C.POINTER(vp), C.POINTER(GraphDesc), C.POINTER(Params), vp]
+    lib.pfe_init.argtypes = [vp, i32, vp, i64]
+    lib.pfe_inner_step.argtypes = [vp, C.POINTER(StepStats)]
+    lib.pfe_pstep.argtypes = [vp]
+    lib.pfe_solve.argtypes = [vp, i32, i32, vp, vp, C.POINTER(SolveStats)]
+    lib.pfe_destroy.argtypes = [vp]
+    lib.pfe_last_error.argtypes = [vp]
+    lib.pfe_last_error.restype = C.c_char_p
+    lib.pfe_status_string.argtypes = [C.c_int]
+    lib.pfe_status_string.restype = C.c_char_p
+    lib.pfe_get_info.argtypes = [vp, C.POINTER(Info)]
+    lib.pfe_set_stream.argtypes = [vp, vp]
+    lib.pfe_get_array.argtypes = [vp, i32, vp]
+    lib.pfe_set_array.argtypes = [vp, i32, vp]
+    lib.pfe_get_edges.argtypes = [vp, vp, vp, vp]
+    lib.pfe_apply_A.argtypes = [vp, vp, vp]
+    lib.pfe_solve_system.argtypes = [vp, vp, vp, C.POINTER(StepStats)]
+    lib.pfe_time_kernel.argtypes = [vp, i32, i32, C.POINTER(dbl)]
+    for name in EXPORTS:
+        if name not in ("pfe_default_params", "pfe_last_error", "pfe_status_string"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class PFEError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+def _ptr(a, dtype=np.float64):
+    """(pointer, keep-alive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected C-contiguous {np.dtype(dtype).name} array")
+        return a.ctypes.data, a
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        want = torch.float64 if dtype == np.float64 else torch.int32
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected contiguous {want} tensor")
+        return a.data_ptr(), a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:  # pragma: no cover
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class PFE:
+    """One embedding problem: graph, system matrix and iteration state on the GPU."""
+
+    def __init__(self, features, *, sigma: float, H: int | None = None, W: int | None = None,
+                 radius: float | None = None, edges=None, lam: float = 0.0, r: float = 1.0,
+                 precision: str = "mixed", tol: float = 1e-6, max_iter: int = 5000, refresh: int = 50,
+                 reset_inner: bool = True, loop: str = "graph", check_every: int = 4,
+                 blocks_per_sm: int = 0, stream=None):
+        self.lib = load_library()
+        self.ctx = C.c_void_p()
+        fp, self._feat = _ptr(features)
+        n, m = features.shape
+        gd = GraphDesc()
+        gd.n, gd.m, gd.features, gd.sigma = n, m, fp, float(sigma)
+        if edges is None:
+            gd.kind, gd.H, gd.W, gd.radius = PFE_GRAPH_GRID, int(H), int(W), float(radius)
+        else:
+            ei, ej = edges
+            pi, self._ei = _ptr(ei, np.int32)
+            pj, self._ej = _ptr(ej, np.int32)
+            gd.kind, gd.ei, gd.ej, gd.n_edges = PFE_GRAPH_EDGES, pi, pj, int(ei.shape[0])
+        p = Params()
+        self.lib.pfe_default_params(C.byref(p))
+        p.lambda_, p.r = float(lam), float(r)
+        p.precision = PFE_MIXED if precision == "mixed" else PFE_FP64
+        p.tol, p.max_iter, p.refresh = float(tol), int(max_iter), int(refresh)
+        p.reset_inner_each_outer = 1 if reset_inner else 0
+        p.loop_mode = PFE_LOOP_GRAPH if loop == "graph" else PFE_LOOP_HOST
+        p.check_every, p.blocks_per_sm = int(check_every), int(blocks_per_sm)
+        self.params = p
+        self.n = n
+        self.d = 0
+        st = self.lib.pfe_build_graph(C.byref(self.ctx), C.byref(gd), C.byref(p), _stream_ptr(stream))
+        self._feat = self._ei = self._ej = None
+        if st != PFE_OK:
+            raise PFEError(st, f"pfe_build_graph failed: {self.lib.pfe_status_string(st).decode()}")
+
+    # -- helpers
+    def _check(self, st: int, what: str, ok=(PFE_OK,)):
+        if st not in ok:
+            msg = self.lib.pfe_last_error(self.ctx).decode()
+            raise PFEError(st, f"{what}: {self.lib.pfe_status_string(st).decode()}: {msg}")
+        return st
+
+    def close(self):
+        if getattr(self, "ctx", None) and self.ctx.value:
+            self.lib.pfe_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- API
+    def info(self) -> dict:
+        i = Info()
+        self._check(self.lib.pfe_get_info(self.ctx, C.byref(i)), "pfe_get_info")
+        return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def set_stream(self, stream):
+        self._check(self.lib.pfe_set_stream(self.ctx, _stream_ptr(stream)), "pfe_set_stream")
+
+    def init(self, Y0):
+        d = Y0.shape[1]
+        p, keep = _ptr(Y0)
+        self._check(self.lib.pfe_init(self.ctx, d, p, d), "pfe_init")
+        self.d = d
+
+    def inner_step(self, stats: bool = False, allow_notconv: bool = False):
+        if not stats:
+            self._check(self.lib.pfe_inner_step(self.ctx, None), "pfe_inner_step")
+            return None
+        s = StepStats()
+        ok = (PFE_OK, PFE_ENOTCONV) if allow_notconv else (PFE_OK,)
+        self._check(self.lib.pfe_inner_step(self.ctx, C.byref(s)), "pfe_inner_step", ok)
+        return {"pcg_iters": s.pcg_iters, "converged": bool(s.converged), "relres_max": s.relres_max}
+
+    def pstep(self):
+        self._check(self.lib.pfe_pstep(self.ctx), "pfe_pstep")
+
+    def solve(self, n_outer: int, n_inner: int, Y_out=None, Yhat_out=None, allow_notconv: bool = False):
+        py, ky = _ptr(Y_out)
+        ph, kh = _ptr(Yhat_out)
+        s = SolveStats()
+        ok = (PFE_OK, PFE_ENOTCONV) if allow_notconv else (PFE_OK,)
+        st = self._check(self.lib.pfe_solve(self.ctx, n_outer, n_inner, py, ph, C.byref(s)), "pfe_solve", ok)
+        return {"pcg_iters_total": s.pcg_iters_total, "pcg_iters_max": s.pcg_iters_max, "n_solves": s.n_solves,
+                "n_unconverged": s.n_unconverged, "relres_max": s.relres_max,
+                "kernel_launches": s.kernel_launches, "status": st}
+
+    def get(self, which: str, out=None):
+        if out is None:
+            rows = self.n
+            if which == "BS":
+                rows = self.info()["n_edges"]
+            shape = (rows,) if which in ("DEG", "DIAG") else (rows, self.d)
+            out = np.empty(shape, dtype=np.float64)
+        p, keep = _ptr(out)
+        self._check(self.lib.pfe_get_array(self.ctx, ARR[which], p), f"pfe_get_array({which})")
+        return out
+
+    def set(self, which: str, arr):
+        p, keep = _ptr(arr)
+        self._check(self.lib.pfe_set_array(self.ctx, ARR[which], p), f"pfe_set_array({which})")
+
+    def edges(self):
+        ne = self.info()["n_edges"]
+        a = np.empty(ne, dtype=np.int32)
+        b = np.empty(ne, dtype=np.int32)
+        w = np.empty(ne, dtype=np.float64)
+        self._check(self.lib.pfe_get_edges(self.ctx, a.ctypes.data, b.ctypes.data, w.ctypes.data),
+                    "pfe_get_edges")
+        return a, b, w
+
+    def apply_A(self, X, out=None):
+        out = np.empty_like(X) if out is None else out
+        px, kx = _ptr(X)
+        po, ko = _ptr(out)
+        self._check(self.lib.pfe_apply_A(self.ctx, px, po), "pfe_apply_A")
+        return out
+
+    def solve_system(self, RHS, Y, allow_notconv: bool = False):
+        """Solve A Y = RHS in place (Y holds the initial guess); returns stats."""
+        pr, kr = _ptr(RHS)
+        py, ky = _ptr(Y)
+        s = StepStats()
+        ok = (PFE_OK, PFE_ENOTCONV) if allow_notconv else (PFE_OK,)
+        self._check(self.lib.pfe_solve_system(self.ctx, pr, py, C.byref(s)), "pfe_solve_system", ok)
+        return {"pcg_iters": s.pcg_iters, "converged": bool(s.converged), "relres_max": s.relres_max}
+
+    def time_kernel(self, which: str, reps: int = 20) -> float:
+        """Average milliseconds of one launch of a hot-path kernel (CUDA events)."""
+        ms = C.c_double()
+        self._check(self.lib.pfe_time_kernel(self.ctx, KERNEL[which], int(reps), C.byref(ms)),
+                    f"pfe_time_kernel({which})")
+        return ms.value

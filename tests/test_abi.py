@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry
+point that include/pfe.h declares (no compute calls: no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1612_06496_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "pfe.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"PFE_API\s+[\w\s\*]*?\b(pfe_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("pfe_build_graph", "pfe_init", "pfe_inner_step", "pfe_solve"):
+        assert name in syms
+    assert len(syms) >= 16
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_export():
+    from paper_1612_06496_gb300 import EXPORTS
+    assert sorted(EXPORTS) == declared_symbols()
+
+
+def test_default_params_and_status_strings(lib):
+    from paper_1612_06496_gb300.pfe import Params, load_library
+    L = load_library()
+    p = Params()
+    L.pfe_default_params(ctypes.byref(p))
+    assert p.r == 1.0 and p.tol == 1e-6 and p.max_iter == 5000 and p.refresh == 50
+    assert p.reset_inner_each_outer == 1
+    assert L.pfe_status_string(4) == b"PFE_ENOTCONV"
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    """Argument checks run before any CUDA call."""
+    from paper_1612_06496_gb300.pfe import GraphDesc, Params, load_library
+    L = load_library()
+    ctx = ctypes.c_void_p()
+    p = Params()
+    L.pfe_default_params(ctypes.byref(p))
+    g = GraphDesc()
+    assert L.pfe_build_graph(ctypes.byref(ctx), None, ctypes.byref(p), None) == 1
+    g.n = 1
+    assert L.pfe_build_graph(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(p), None) == 1
+    g.n, g.m, g.sigma, g.kind = 16, 5, 0.1, 0
+    assert L.pfe_build_graph(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(p), None) == 1  # no features
+    assert L.pfe_init(None, 3, None, 3) == 1
+    assert L.pfe_inner_step(None, None) == 1
+    assert L.pfe_solve(None, 1, 1, None, None, None) == 1
+    assert L.pfe_destroy(None) == 0
