@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-window", type=int, default=192)
+    ap.add_argument("--size", type=int, default=0,
+                    help="square image side overriding the workload's size (profiling runs on a smaller case)")
+    ap.add_argument("--n-inner", type=int, default=0, help="override inner iterations per outer step")
+    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
+                    help="PCG loop driver; 'host' launches every kernel from the host (for ncu launch lists)")
     return ap.parse_args()
 
 
@@ -289,6 +294,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     load_library()
     spec = CONFIGS[args.workload]
+    if args.size:
+        spec = replace(spec, H=args.size, W=args.size, name=f"{spec.name}@{args.size}")
+    if args.n_inner:
+        spec = replace(spec, n_inner=args.n_inner)
     if world > 1:
         spec = replace(spec, seed=spec.seed + rank)
     X, Y0 = make_problem(spec)
@@ -312,7 +321,7 @@ def main():
     def run_arm(precision: str, warmup: int, steps: int, clocks: bool):
         t0 = time.perf_counter()
         p = PFE(Xd, sigma=spec.sigma, H=H, W=W, radius=spec.radius, precision=precision, tol=spec.tol,
-                stream=stream)
+                stream=stream, loop=args.loop)
         p.init(Y0d)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
@@ -345,16 +354,16 @@ def main():
     launches = sum(s["kernel_launches"] for s in stats)
     sec_per_outer = ms_max / 1e3 / (args.steps * world)
 
-    # --- roofline of the dominant kernel (SpMM with fused column dots)
+    # --- roofline of the dominant kernel: k_spmm (q = A p with the p.q dots)
     spmm_ms = p.time_kernel("spmm", 20)
     upd_ms = p.time_kernel("update", 20)
     pup_ms = p.time_kernel("pupdate", 20)
     edge_ms = p.time_kernel("edge", 10)
     n, d, nnz = info["n"], info["d"], info["nnz_A"]
-    spmm_bytes = 8 * nnz + 4 * (n + 1) + 2 * 4 * n * d         # FP32 values + int32 indices + p in, q out
+    # FP32 values + int32 indices of A, p in, q out: 8 nnz_A + 4 (n + 1) + 2 * 4 n d
+    spmm_bytes = 8 * nnz + 4 * (n + 1) + 2 * 4 * n * d
     peaks = measured_peaks()
     achieved = spmm_bytes / (spmm_ms * 1e-3) / 1e9
-    pcg_time_est = iters_total * (spmm_ms + upd_ms + pup_ms) * 1e-3
     roofline = {"bound": "hbm", "kernel": "k_spmm<float,%d>" % d, "achieved": round(achieved, 1),
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                 "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
@@ -362,8 +371,11 @@ def main():
                 "algorithmic_bytes_per_launch": spmm_bytes, "avg_launch_ms": round(spmm_ms, 5),
                 "launches_in_timed_region": iters_total,
                 "share_of_timed_region": round(iters_total * spmm_ms / ms, 4),
-                "other_kernels_ms": {"update": round(upd_ms, 5), "pupdate": round(pup_ms, 5),
-                                     "edge": round(edge_ms, 5)}}
+                "other_kernels": {"k_update_ms": round(upd_ms, 5),
+                                  "k_update_GBps": round((3 * 4 * n * d + 4 * n) / (upd_ms * 1e-3) / 1e9, 1),
+                                  "k_pupdate_ms": round(pup_ms, 5),
+                                  "k_pupdate_GBps": round((7 * 4 * n * d + 4 * n) / (pup_ms * 1e-3) / 1e9, 1),
+                                  "k_edge_ms": round(edge_ms, 5)}}
     p.close()
 
     # --- plain FP64 path on the same problem

@@ -68,7 +68,8 @@ enum {
                       accumulation of dot products and of the PCG solution; FP64
                       Gram, polar step, P, B */
 };
-/* Preconditioner of the PCG solve (pfe_params.precond). */
+/* Preconditioner of the PCG solve (pfe_params.precond); the learned FSAI
+ * preconditioner is switched on after construction with pfe_fsai_set(). */
 enum { PFE_PRECOND_JACOBI = 0 };
 /* How the PCG loop is driven (pfe_params.loop_mode). */
 enum {
@@ -261,17 +262,60 @@ PFE_API pfe_status pfe_solve_system(pfe_ctx *c, const double *RHS, double *Y, pf
  * pfe_time_kernel -- average device time of one hot-path kernel, for
  * roofline reporting: `reps` back-to-back launches on the context's current
  * state (after pfe_init), bracketed by CUDA events on the context's stream.
- *   PFE_KERNEL_SPMM     q = A p with the fused p.q column dots (one PCG iteration's SpMM)
- *   PFE_KERNEL_UPDATE   y += alpha p, r -= alpha q with the r.z, r.r dots
- *   PFE_KERNEL_PUPDATE  p = D_A^{-1} r + beta p
+ *   PFE_KERNEL_SPMM     q = A p with the p.q column dots (one per PCG iteration)
+ *   PFE_KERNEL_UPDATE   r -= alpha q with the r.z, r.r column dots
  *   PFE_KERNEL_EDGE     fused M Y / Shrink / b update / M^T scatter (Eqs. 7, 9, 10, 13)
+ *   PFE_KERNEL_PUPDATE  p = D_A^{-1} r + beta p with the delayed y += alpha p
  * The iteration state is not modified (scratch copies and a scratch control
  * block are used; the edge pass rewrites the same right-hand side).  Only
  * the PCG direction p and product q, which every solve re-initialises, are
  * overwritten.  Synchronises; allocates temporary device memory.
  */
-enum { PFE_KERNEL_SPMM = 0, PFE_KERNEL_UPDATE = 1, PFE_KERNEL_PUPDATE = 2, PFE_KERNEL_EDGE = 3 };
+enum { PFE_KERNEL_SPMM = 0, PFE_KERNEL_UPDATE = 1, PFE_KERNEL_EDGE = 2, PFE_KERNEL_PUPDATE = 3 };
 PFE_API pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_ms);
+
+/*
+ * Learned FSAI preconditioner (no counterpart in the paper, which uses an
+ * incomplete-Cholesky preconditioner, Sec. III).  The PCG of the mixed path
+ * can use M^{-1} = G^T G with G lower triangular on the pattern of
+ * tril(A): G_ij = Gh_ij / sqrt(A_jj), Gh_ii = softplus(h_diag),
+ * Gh_ij = h_off, where (h_off, h_diag) is a 4 -> 64 -> 64 -> 2 ReLU network
+ * evaluated per pattern entry.  Edge entry (b, a), a < b, reads
+ * (lam w_ab^2 / sqrt(A_aa A_bb), r d_b / A_bb, r d_a / A_aa, w_ab); diagonal
+ * entry i reads (sum over lower neighbours j of the first feature squared,
+ * r d_i / A_ii, r d_i / A_ii, 1).  The hidden 64 x 64 layer runs on the
+ * tensor cores (BF16 operands, FP32 accumulation).
+ *
+ * params: pfe_fsai_param_count() FP32 values (host or device), laid out as
+ * W1 (4 x 64 row-major), b1 (64), W2 (64 x 64), b2 (64), W3 (64 x 2), b3 (2).
+ * A network with W3 = 0 and b3 = (0, softplus^{-1}(1)) gives G = D_A^{-1/2},
+ * i.e. exactly the Jacobi preconditioner.
+ */
+PFE_API int32_t pfe_fsai_param_count(void);
+
+/* Evaluates the network on every pattern entry (G is built once per graph)
+ * and makes later PCG solves use G^T G.  params == NULL switches back to
+ * Jacobi.  PFE_EUNSUPPORTED on an FP64 context.  Synchronises. */
+PFE_API pfe_status pfe_fsai_set(pfe_ctx *c, const float *params);
+
+/* Training criterion: Kaporin's condition number of G A G^T,
+ *   *loss = log(tr(G A G^T) / n) - (2/n) sum_i log G_ii,
+ * and its gradient with respect to params (written to grad when non-NULL,
+ * host or device).  Does not change which preconditioner the PCG uses, but
+ * G is recomputed from params.  Synchronises. */
+PFE_API pfe_status pfe_fsai_loss_grad(pfe_ctx *c, const float *params, float *grad, double *loss);
+
+/* The current G as FP64: gdiag[i] = G_ii (n values), gedge[k] = G_{b_k a_k}
+ * for edge k of pfe_get_edges (n_edges values); either may be NULL. */
+PFE_API pfe_status pfe_fsai_get(pfe_ctx *c, double *gdiag, double *gedge);
+
+/* One Adam step on device arrays of `count` FP32 values:
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * step >= 1.  Enqueues on `stream` only. */
+PFE_API pfe_status pfe_adam_update(float *params, const float *grad, float *m, float *v, int64_t count,
+                                   int32_t step, double lr, double beta1, double beta2, double eps,
+                                   pfe_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,171 @@
+"""FP64 oracle of the learned factorised-sparse-approximate-inverse (FSAI)
+preconditioner for the PCG solve of Eq. 13.
+
+TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU leg).  The paper
+preconditions its conjugate gradients with incomplete Cholesky (Sec. III);
+this learned preconditioner has no counterpart in the paper.  It is
+M^{-1} = G^T G with G lower triangular on the pattern of tril(A):
+
+* G = Gh diag(A)^{-1/2}: G_ij = Gh_ij / sqrt(A_jj); an untrained network
+  (Gh = I) is exactly the Jacobi preconditioner.
+* Gh_ii = softplus(h_diag), Gh_ij = h_off (j < i), from a 4 -> 64 -> 64 -> 2
+  ReLU MLP evaluated once per pattern entry (n diagonal entries and one per
+  undirected edge).
+* Inputs of entry (b, a), a < b (edge e = (a, b), value G_ba):
+  (rho_ab, theta_b, theta_a, w_ab) with rho_ab = lam w_ab^2 / sqrt(A_aa A_bb)
+  (the Jacobi-scaled coupling), theta_i = r d_i / A_ii (the share of the
+  constraint term in the diagonal) and the heat-kernel weight w_ab (a
+  function of |x_a - x_b|).  Diagonal entry i: (s_i, theta_i, theta_i, 1)
+  with s_i = sum over i's lower neighbours j of rho_ij^2.
+* Training criterion: Kaporin's condition number of G A G^T,
+      L = log(tr(G A G^T) / n) - (2/n) sum_i log G_ii   (+ log det A / n, constant),
+  which classical FSAI minimises over the same pattern.
+
+Parameter vector layout (float64 here, float32 on the GPU):
+  W1 (4 x 64, row-major), b1 (64), W2 (64 x 64), b2 (64), W3 (64 x 2), b3 (2).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+H = 64
+NPARAM = 4 * H + H + H * H + H + H * 2 + 2
+SOFTPLUS_ONE = float(np.log(np.expm1(1.0)))  # softplus^{-1}(1)
+
+
+def unpack(theta: np.ndarray):
+    o = 0
+    W1 = theta[o:o + 4 * H].reshape(4, H); o += 4 * H
+    b1 = theta[o:o + H]; o += H
+    W2 = theta[o:o + H * H].reshape(H, H); o += H * H
+    b2 = theta[o:o + H]; o += H
+    W3 = theta[o:o + 2 * H].reshape(H, 2); o += 2 * H
+    b3 = theta[o:o + 2]; o += 2
+    assert o == NPARAM
+    return W1, b1, W2, b2, W3, b3
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-initialised hidden layers, zero output layer, diagonal bias so that
+    softplus(b3[1]) = 1: the untrained network gives Gh = I (Jacobi)."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((4, H)) * np.sqrt(2.0 / 4)
+    W2 = rng.standard_normal((H, H)) * np.sqrt(2.0 / H)
+    parts = [W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), np.zeros(2 * H), np.array([0.0, SOFTPLUS_ONE])]
+    return np.concatenate(parts)
+
+
+def softplus(x):
+    return np.logaddexp(0.0, x)
+
+
+def sigmoid(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def mlp_forward(theta, F):
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    a1 = F @ W1 + b1
+    h1 = np.maximum(a1, 0.0)
+    a2 = h1 @ W2 + b2
+    h2 = np.maximum(a2, 0.0)
+    out = h2 @ W3 + b3
+    return out, (F, a1, h1, a2, h2)
+
+
+def mlp_backward(theta, cache, dout):
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    F, a1, h1, a2, h2 = cache
+    gW3 = h2.T @ dout
+    gb3 = dout.sum(0)
+    dh2 = dout @ W3.T
+    da2 = dh2 * (a2 > 0)
+    gW2 = h1.T @ da2
+    gb2 = da2.sum(0)
+    dh1 = da2 @ W2.T
+    da1 = dh1 * (a1 > 0)
+    gW1 = F.T @ da1
+    gb1 = da1.sum(0)
+    return np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
+
+
+def entry_features(g):
+    """Features of the n diagonal entries and |E| edge entries of graph g
+    (an oracle Graph: a < b edge lists, w, degrees, lambda, r, A)."""
+    Ad = g.A.diagonal()
+    theta = g.r * g.dvec / Ad
+    rho = g.lam * g.w ** 2 / np.sqrt(Ad[g.a] * Ad[g.b])
+    s = np.zeros(g.n)
+    np.add.at(s, g.b, rho ** 2)                  # lower neighbours of row b are the a's
+    Fd = np.stack([s, theta, theta, np.ones(g.n)], axis=1)
+    Fe = np.stack([rho, theta[g.b], theta[g.a], g.w], axis=1)
+    return Fd, Fe
+
+
+def assemble_G(g, out_d, out_e):
+    """G (sparse lower triangular) from the two heads."""
+    Ad = g.A.diagonal()
+    gd = softplus(out_d[:, 1]) / np.sqrt(Ad)
+    ge = out_e[:, 0] / np.sqrt(Ad[g.a])          # G_ba, column a
+    rows = np.concatenate([np.arange(g.n), g.b])
+    cols = np.concatenate([np.arange(g.n), g.a])
+    return sp.csr_matrix((np.concatenate([gd, ge]), (rows, cols)), shape=(g.n, g.n)), gd, ge
+
+
+def kaporin(g, G):
+    """L = log(tr(G A G^T)/n) - (2/n) sum log G_ii and dL/dG on G's pattern."""
+    n = g.n
+    GA = (G @ g.A).tocsr()
+    T = float(G.multiply(GA).sum())
+    gdiag = G.diagonal()
+    L = np.log(T / n) - 2.0 / n * np.sum(np.log(gdiag))
+    # dT/dG = 2 G A (restricted to the pattern); d(sum log G_ii)/dG_ii = 1/G_ii
+    dG = (2.0 / T) * GA.multiply(G != 0).tocsr()
+    dG = dG + sp.diags(-2.0 / (n * gdiag))
+    return L, dG, T
+
+
+def loss_and_grad(theta, g):
+    """Kaporin loss of the network's G on graph g and its gradient w.r.t. theta."""
+    Fd, Fe = entry_features(g)
+    od, cd = mlp_forward(theta, Fd)
+    oe, ce = mlp_forward(theta, Fe)
+    G, gd, ge = assemble_G(g, od, oe)
+    L, dG, T = kaporin(g, G)
+    Ad = g.A.diagonal()
+    dG = dG.tocsr()
+    dgd = np.asarray(dG[np.arange(g.n), np.arange(g.n)]).ravel()
+    dge = np.asarray(dG[g.b, g.a]).ravel()
+    dout_d = np.zeros_like(od)
+    dout_d[:, 1] = dgd * sigmoid(od[:, 1]) / np.sqrt(Ad)
+    dout_e = np.zeros_like(oe)
+    dout_e[:, 0] = dge / np.sqrt(Ad[g.a])
+    grad = mlp_backward(theta, cd, dout_d) + mlp_backward(theta, ce, dout_e)
+    return L, grad, {"T": T, "gd": gd, "ge": ge, "G": G}
+
+
+def classical_fsai(A) -> sp.csr_matrix:
+    """Classical FSAI on the pattern of tril(A): for row i with pattern S
+    (i last), solve A[S, S] g = e_i and scale by 1/sqrt(g_i).  Minimises the
+    Kaporin number of G A G^T over lower-triangular G with that pattern."""
+    A = A.tocsr()
+    n = A.shape[0]
+    Lp = sp.tril(A).tocsr()
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        S = np.sort(Lp.indices[Lp.indptr[i]:Lp.indptr[i + 1]])
+        As = A[S][:, S].toarray()
+        e = np.zeros(len(S))
+        e[-1] = 1.0
+        gi = np.linalg.solve(As, e)
+        gi = gi / np.sqrt(gi[-1])
+        rows += [i] * len(S)
+        cols += list(S)
+        vals += list(gi)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
+def fsai_apply(G, R):
+    """z = G^T (G r), column by column."""
+    return G.T @ (G @ R)

@@ -57,6 +57,8 @@ void free_work(pfe_ctx *c) {
     for (void *p : c->work_allocs) cudaFree(p);
     c->work_allocs.clear();
     c->wk = Work{};
+    c->fsai.t = nullptr;
+    c->fsai.z = nullptr;
     c->inited = false;
     c->d = 0;
 }
@@ -105,6 +107,13 @@ pfe_status build_pcg_graph(pfe_ctx *c) {
     ce = cudaStreamEndCapture(cs, &b2);
     if (st != PFE_OK) return st;
     PFE_CUDA_TRY(c, ce);
+    // the delayed solution update of the last iteration, after the loop
+    PFE_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(cs, g, &cn, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+    st = launch_pcg_final(c, cs, L);
+    cudaGraph_t g3 = g;
+    ce = cudaStreamEndCapture(cs, &g3);
+    if (st != PFE_OK) return st;
+    PFE_CUDA_TRY(c, ce);
     PFE_CUDA_TRY(c, cudaGraphInstantiate(&c->pcg_exec, g, 0));
     return PFE_OK;
 }
@@ -127,6 +136,7 @@ pfe_status run_pcg(pfe_ctx *c, bool force_host) {
         if (*c->h_flag) break;
         if (it > cap) return fail(c, PFE_ECUDA, "PCG control block never reported completion");
     }
+    PFE_TRY(launch_pcg_final(c, c->stream, L));
     return PFE_OK;
 }
 
@@ -358,11 +368,12 @@ pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
     if (!d_supported(d)) return fail(c, PFE_EUNSUPPORTED, "embedding dimension not built into libpfe");
     free_work(c);
     c->d = d;
+    memset(c->kgrid, 0, sizeof(c->kgrid));  // kernels are sized again for this d
     const int64_t nd = c->n * (int64_t)d;
     const int64_t ed = c->g.fslots * (int64_t)d;
     auto &w = c->wk;
     if (c->mixed) {
-        float *y, *bs0, *bs1, *rhs, *cw, *r, *pd, *q;
+        float *y, *bs0, *bs1, *rhs, *cw, *r, *pd, *pd2, *q;
         PFE_TRY(walloc(c, &y, nd));
         PFE_TRY(walloc(c, &w.Ylo, nd));
         PFE_TRY(walloc(c, &bs0, ed));
@@ -371,10 +382,11 @@ pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
         PFE_TRY(walloc(c, &cw, nd));
         PFE_TRY(walloc(c, &r, nd));
         PFE_TRY(walloc(c, &pd, nd));
+        PFE_TRY(walloc(c, &pd2, nd));
         PFE_TRY(walloc(c, &q, nd));
-        w.Y = y; w.Bs[0] = bs0; w.Bs[1] = bs1; w.RHS = rhs; w.Cw = cw; w.R = r; w.Pd = pd; w.Q = q;
+        w.Y = y; w.Bs[0] = bs0; w.Bs[1] = bs1; w.RHS = rhs; w.Cw = cw; w.R = r; w.Pd = pd; w.Pd2 = pd2; w.Q = q;
     } else {
-        double *y, *bs0, *bs1, *rhs, *cw, *r, *pd, *q;
+        double *y, *bs0, *bs1, *rhs, *cw, *r, *pd, *pd2, *q;
         PFE_TRY(walloc(c, &y, nd));
         PFE_TRY(walloc(c, &bs0, ed));
         PFE_TRY(walloc(c, &bs1, ed));
@@ -382,13 +394,21 @@ pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
         PFE_TRY(walloc(c, &cw, nd));
         PFE_TRY(walloc(c, &r, nd));
         PFE_TRY(walloc(c, &pd, nd));
+        PFE_TRY(walloc(c, &pd2, nd));
         PFE_TRY(walloc(c, &q, nd));
-        w.Y = y; w.Bs[0] = bs0; w.Bs[1] = bs1; w.RHS = rhs; w.Cw = cw; w.R = r; w.Pd = pd; w.Q = q;
+        w.Y = y; w.Bs[0] = bs0; w.Bs[1] = bs1; w.RHS = rhs; w.Cw = cw; w.R = r; w.Pd = pd; w.Pd2 = pd2; w.Q = q;
+    }
+    if (c->fsai.enabled) {
+        float *t, *z;
+        PFE_TRY(walloc(c, &t, nd));
+        PFE_TRY(walloc(c, &z, nd));
+        c->fsai.t = t;
+        c->fsai.z = z;
     }
     PFE_TRY(walloc(c, &w.P, nd));
     PFE_TRY(walloc(c, &w.B, nd));
     PFE_TRY(walloc(c, &w.stage, nd));
-    const int64_t part_pcg = (int64_t)c->grid_rows * 3 * PFE_DMAX;
+    const int64_t part_pcg = (int64_t)c->num_sms * 8 * 3 * PFE_DMAX;  // <= 8 resident blocks of 256 threads
     const int64_t part_gram = (int64_t)c->num_sms * 2 * (PFE_DMAX * (PFE_DMAX + 1) / 2);
     w.partials_len = std::max(part_pcg, part_gram);
     PFE_TRY(walloc(c, &w.partials, w.partials_len));
@@ -396,6 +416,7 @@ pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
     PFE_CUDA_TRY(c, cudaMemsetAsync(w.Bs[0], 0, (size_t)ed * es, c->stream));
     PFE_CUDA_TRY(c, cudaMemsetAsync(w.Bs[1], 0, (size_t)ed * es, c->stream));
     PFE_CUDA_TRY(c, cudaMemsetAsync(w.Pd, 0, (size_t)nd * es, c->stream));
+    PFE_CUDA_TRY(c, cudaMemsetAsync(w.Pd2, 0, (size_t)nd * es, c->stream));
     PFE_CUDA_TRY(c, cudaMemsetAsync(w.Q, 0, (size_t)nd * es, c->stream));
     PFE_CUDA_TRY(c, cudaMemsetAsync(w.R, 0, (size_t)nd * es, c->stream));
     c->bs_cur = 0;
@@ -408,6 +429,8 @@ pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
     h.tol = c->prm.tol;
     h.done = 1;
     h.unroll = std::max(1, c->prm.check_every);
+    h.launch_base = c->fsai.enabled ? 4 : 2;
+    h.launch_per_iter = c->fsai.enabled ? 7 : 5;
     PFE_CUDA_TRY(c, cudaMemcpyAsync(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
     PFE_CUDA_TRY(c, cudaMemsetAsync(c->pctl, 0, sizeof(PstepCtl), c->stream));
     // Y0 -> stage (contiguous FP64), then D-orthonormalise via the P-step map
@@ -664,13 +687,84 @@ pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_
         if (st != PFE_OK) return st;
         if (e != cudaSuccess) return fail(c, PFE_ECUDA, cudaGetErrorString(e));
         ms /= (float)reps;
-    } else if (which >= PFE_KERNEL_SPMM && which <= PFE_KERNEL_PUPDATE) {
-        PFE_TRY(time_pcg_kernel(c, c->stream, which, reps, &ms));
+    } else if (which == PFE_KERNEL_SPMM || which == PFE_KERNEL_UPDATE || which == PFE_KERNEL_PUPDATE) {
+        PFE_TRY(time_pcg_kernel(c, c->stream, which == PFE_KERNEL_PUPDATE ? 2 : which, reps, &ms));
     } else {
         return fail(c, PFE_EINVAL, "unknown kernel id");
     }
     *avg_ms = ms;
     return PFE_OK;
+}
+
+int32_t pfe_fsai_param_count(void) { return kNParam; }
+
+pfe_status pfe_fsai_set(pfe_ctx *c, const float *params) {
+    if (!c) return PFE_EINVAL;
+    PFE_TRY(sync(c));
+    if (!params) {
+        c->fsai.enabled = false;
+    } else {
+        if (!c->mixed) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner runs on the mixed-precision path");
+        PFE_TRY(fsai_alloc(c));
+        PFE_CUDA_TRY(c, cudaMemcpyAsync(c->fsai.params, params, kNParam * sizeof(float), cudaMemcpyDefault,
+                                        c->stream));
+        PFE_TRY(fsai_infer(c));
+        if (c->inited && !c->fsai.t) {
+            const int64_t nd = c->n * (int64_t)c->d;
+            float *t, *z;
+            PFE_TRY(walloc(c, &t, nd));
+            PFE_TRY(walloc(c, &z, nd));
+            c->fsai.t = t;
+            c->fsai.z = z;
+        }
+        c->fsai.enabled = true;
+    }
+    free_pcg_graph(c);  // the loop body differs between preconditioners
+    if (c->inited) {
+        int lc[2] = {c->fsai.enabled ? 4 : 2, c->fsai.enabled ? 7 : 5};
+        PFE_CUDA_TRY(c, cudaMemcpyAsync((char *)c->ctl + offsetof(PcgCtl, launch_base), lc, sizeof(lc),
+                                        cudaMemcpyHostToDevice, c->stream));
+    }
+    return sync(c);
+}
+
+pfe_status pfe_fsai_loss_grad(pfe_ctx *c, const float *params, float *grad, double *loss) {
+    if (!c || !params || !loss) return PFE_EINVAL;
+    PFE_TRY(fsai_alloc(c));
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(c->fsai.params, params, kNParam * sizeof(float), cudaMemcpyDefault, c->stream));
+    PFE_TRY(fsai_loss_grad(c, loss));
+    if (grad)
+        PFE_CUDA_TRY(c, cudaMemcpyAsync(grad, c->fsai.grad, kNParam * sizeof(float), cudaMemcpyDefault, c->stream));
+    return sync(c);
+}
+
+pfe_status pfe_fsai_get(pfe_ctx *c, double *gdiag, double *gedge) {
+    if (!c) return PFE_EINVAL;
+    if (!c->fsai.gdiag) return fail(c, PFE_ESTATE, "no FSAI factor: call pfe_fsai_set or pfe_fsai_loss_grad first");
+    const int64_t n = c->g.n, ne = c->g.n_edges;
+    double *tmp = nullptr;
+    if (cudaMalloc((void **)&tmp, sizeof(double) * std::max<int64_t>(n + ne, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PFE_ENOMEM, "staging buffer for G");
+    }
+    pfe_status st = fsai_export(c, tmp, tmp + n);
+    if (st == PFE_OK && gdiag && cudaMemcpyAsync(gdiag, tmp, sizeof(double) * n, cudaMemcpyDefault, c->stream) != cudaSuccess)
+        st = PFE_ECUDA;
+    if (st == PFE_OK && gedge && ne > 0 &&
+        cudaMemcpyAsync(gedge, tmp + n, sizeof(double) * ne, cudaMemcpyDefault, c->stream) != cudaSuccess)
+        st = PFE_ECUDA;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (st != PFE_OK) return st;
+    if (e != cudaSuccess) return fail(c, PFE_ECUDA, cudaGetErrorString(e));
+    return PFE_OK;
+}
+
+pfe_status pfe_adam_update(float *params, const float *grad, float *m, float *v, int64_t count, int32_t step,
+                           double lr, double beta1, double beta2, double eps, pfe_stream_t stream) {
+    if (!params || !grad || !m || !v || count < 1 || step < 1) return PFE_EINVAL;
+    if (!is_device_ptr(params) || !is_device_ptr(grad) || !is_device_ptr(m) || !is_device_ptr(v)) return PFE_EINVAL;
+    return adam_step(params, grad, m, v, count, step, lr, beta1, beta2, eps, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -2,6 +2,7 @@
 // row loads of d-interleaved arrays, block reductions, SELL-32 traversal.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <cuda_runtime.h>
@@ -207,6 +208,32 @@ __device__ __forceinline__ bool last_block_arrives(unsigned *ticket) {
 }
 
 __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
+
+// Grid of a grid-stride kernel: exactly one wave of the kernel's own
+// occupancy (a second, partial wave would leave most SMs idle while it
+// runs), capped at `need` blocks and rounded down to a multiple of `mult`.
+// Cached per context in c->kgrid[slot].
+enum GridSlot {
+    G_INIT = 0, G_INIT_F, G_PUPD, G_PUPD_F, G_SPMM, G_UPDATE, G_RUPDATE, G_XFLUSH, G_REFRESH, G_REFRESH_F,
+    G_FSAI_T, G_FSAI_Z, G_APPLY, G_EDGE, G_PAPPLY, G_TIME_SPMM, G_TIME_UPDATE, G_NSLOTS
+};
+template <typename K>
+inline int wave_grid(pfe_ctx *c, int slot, K kernel, int64_t need, int mult = 1, size_t smem = 0) {
+    int &g = c->kgrid[slot];
+    if (g == 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBlock, smem) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        int64_t grid = (int64_t)occ * c->num_sms;
+        if (c->prm.blocks_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)c->prm.blocks_per_sm * c->num_sms);
+        grid = std::min<int64_t>(grid, std::max<int64_t>(need, 1));
+        if (mult > 1) grid = std::max<int64_t>(mult, grid / mult * mult);
+        g = (int)grid;
+    }
+    return g;
+}
 
 template <typename T>
 __device__ __forceinline__ T shrink(T t, T gamma) {

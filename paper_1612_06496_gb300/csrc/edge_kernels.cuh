@@ -11,6 +11,7 @@
 // a < b), accumulates (M^T q)_i = sum_e (+-w_e) q_e, and only the first
 // endpoint writes b'.  d is never stored: it is consumed where it is made.
 #pragma once
+#include <cstring>
 #include <type_traits>
 
 #include "common.cuh"
@@ -33,43 +34,110 @@ struct EdgeArgs {
     T lambda, gamma;
 };
 
+template <typename T, int V>
+__device__ __forceinline__ void eldv(const T *__restrict__ p, T (&v)[V]) {
+    if constexpr (V * sizeof(T) == 16) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        memcpy(v, &t, 16);
+    } else if constexpr (V * sizeof(T) == 8) {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        memcpy(v, &t, 8);
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) v[k] = __ldg(p + k);
+    }
+}
+template <typename T, int V>
+__device__ __forceinline__ void estv(T *p, const T (&v)[V]) {
+    if constexpr (V * sizeof(T) == 16) {
+        float4 t;
+        memcpy(&t, v, 16);
+        *reinterpret_cast<float4 *>(p) = t;
+    } else if constexpr (V * sizeof(T) == 8) {
+        float2 t;
+        memcpy(&t, v, 8);
+        *reinterpret_cast<float2 *>(p) = t;
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) p[k] = v[k];
+    }
+}
+
 template <typename T, int D>
 __global__ void __launch_bounds__(kBlock) k_edge(EdgeArgs<T> a) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t s = (int64_t)blockIdx.x * kWarps + warp; s < a.n_slices; s += (int64_t)gridDim.x * kWarps) {
-        const int64_t i = s * 32 + lane;
-        if (i >= a.n) continue;
-        const int64_t base = a.slice_ptr[s];
-        const int len = (a.slice_ptr[s + 1] - (int)base) >> 5;
-        T yi[D], yj[D], bo[D], bn[D], acc[D];
-        load_row<T, D>(a.y, i, yi);
+    // L = D/V lanes per row, V consecutive columns per lane (V = widest of
+    // 16/8/4 bytes dividing a row): row loads of y, b and C are contiguous
+    // warp accesses and the slot work (edge id, column, weight) is shared
+    // by V columns
+    constexpr int V = (sizeof(T) == 4 && D % 4 == 0) ? 4 : (D % 2 == 0 ? 2 : 1);
+    constexpr int L = D / V, RPW = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int rw = lane / L, cg = lane - rw * L, c0 = cg * V;
+    const bool active = lane < RPW * L;
+    const int64_t warp_g = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int64_t warps_total = (int64_t)gridDim.x * kWarps;
+    for (int64_t g = warp_g; g * RPW < a.n; g += warps_total) {
+        const int64_t i = g * RPW + rw;
+        if (!active || i >= a.n) continue;
+        const int64_t s = i >> 5;
+        const int s0 = a.slice_ptr[s];
+        const int len = (a.slice_ptr[s + 1] - s0) >> 5;
+        const int64_t base = (int64_t)s0 + (i & 31) * (int64_t)len;  // row-major within the slice
+        T yi[V], acc[V];
+        eldv<T, V>(a.y + i * D + c0, yi);
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = T(0);
-        for (int k = 0; k < len; ++k) {
-            const int64_t idx = base + (int64_t)k * 32 + lane;
-            const int e = a.eid[idx];
-            if (e < 0) continue;  // padding slot
-            const int j = a.col[idx];
-            const T w = a.w[idx];
-            const bool first = i < j;  // i is the +w endpoint of edge e
-            load_row<T, D>(a.y, j, yj);
-            load_row<T, D>(a.bs_old, e, bo);
+        for (int k = 0; k < V; ++k) acc[k] = T(0);
+        constexpr int CH = 8;  // slots prefetched together: slot loads, then gathers
+        for (int k0 = 0; k0 < len; k0 += CH) {
+            int ee[CH], jj[CH];
+            T ww[CH], yj[CH][V], bo[CH][V];
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const T diff = first ? (yi[c] - yj[c]) : (yj[c] - yi[c]);  // y_a - y_b
-                const T t = w * diff + bo[c];                                // (M Y + b)_e
-                const T z = shrink<T>(t, a.gamma);                           // d_e
-                bn[c] = t - z;                                               // b'_e
-                const T v = w * (z - bn[c]);
-                acc[c] = first ? acc[c] + v : acc[c] - v;
+            for (int g4 = 0; g4 < CH / 4; ++g4) {  // 16-byte loads: len is a multiple of 4
+                const int k = k0 + 4 * g4;
+                if (k < len) {
+                    const int4 e4 = __ldg(reinterpret_cast<const int4 *>(a.eid + base + k));
+                    const int4 c4 = __ldg(reinterpret_cast<const int4 *>(a.col + base + k));
+                    ee[4 * g4] = e4.x; ee[4 * g4 + 1] = e4.y; ee[4 * g4 + 2] = e4.z; ee[4 * g4 + 3] = e4.w;
+                    jj[4 * g4] = c4.x; jj[4 * g4 + 1] = c4.y; jj[4 * g4 + 2] = c4.z; jj[4 * g4 + 3] = c4.w;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) ww[4 * g4 + u] = __ldg(a.w + base + k + u);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        ee[4 * g4 + u] = -1;
+                        jj[4 * g4 + u] = (int)i;
+                        ww[4 * g4 + u] = T(0);
+                    }
+                }
             }
-            if (first) store_row<T, D>(a.bs_new, e, bn);
-        }
-        T ci[D];
-        load_row<T, D>(a.cw, i, ci);
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = a.lambda * acc[c] + ci[c];
-        store_row<T, D>(a.rhs, i, acc);
+            for (int u = 0; u < CH; ++u) {
+                const int e = ee[u] < 0 ? 0 : ee[u];  // padding slots read a valid dummy
+                eldv<T, V>(a.y + (int64_t)jj[u] * D + c0, yj[u]);
+                eldv<T, V>(a.bs_old + (int64_t)e * D + c0, bo[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                if (ee[u] < 0) continue;       // padding slot
+                const bool first = i < jj[u];  // i is the +w endpoint of edge e
+                T bn[V];
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const T diff = first ? (yi[k] - yj[u][k]) : (yj[u][k] - yi[k]);  // y_a - y_b
+                    const T t = ww[u] * diff + bo[u][k];                              // (M Y + b)_e
+                    const T z = shrink<T>(t, a.gamma);                                // d_e
+                    bn[k] = t - z;                                                    // b'_e
+                    const T v = ww[u] * (z - bn[k]);
+                    acc[k] = first ? acc[k] + v : acc[k] - v;
+                }
+                if (first) estv<T, V>(a.bs_new + (int64_t)ee[u] * D + c0, bn);
+            }
+        }
+        T ci[V];
+        eldv<T, V>(a.cw + i * D + c0, ci);
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] = a.lambda * acc[k] + ci[k];
+        estv<T, V>(a.rhs + i * D + c0, acc);
     }
 }
 
@@ -92,7 +160,10 @@ pfe_status edge_T(pfe_ctx *c, cudaStream_t s) {
     a.rhs = (T *)c->wk.RHS;
     a.lambda = (T)c->lambda;
     a.gamma = (T)(1.0 / c->lambda);
-    k_edge<T, D><<<c->grid_rows, kBlock, 0, s>>>(a);
+    constexpr int V = (sizeof(T) == 4 && D % 4 == 0) ? 4 : (D % 2 == 0 ? 2 : 1);
+    constexpr int RPW = 32 / (D / V);
+    const int64_t need = ((c->g.n + RPW - 1) / RPW + kWarps - 1) / kWarps;
+    k_edge<T, D><<<wave_grid(c, G_EDGE, k_edge<T, D>, need), kBlock, 0, s>>>(a);
     PFE_CUDA_TRY(c, cudaGetLastError());
     c->bs_cur = 1 - c->bs_cur;
     return PFE_OK;

@@ -1,0 +1,701 @@
+// Learned factorised sparse approximate inverse (FSAI) preconditioner for the
+// PCG solve of Eq. 13.  (The paper preconditions with incomplete Cholesky,
+// Sec. III; this learned replacement has no counterpart there.)
+//
+//   M^{-1} = G^T G,  G lower triangular on the pattern of tril(A),
+//   G_ij = Gh_ij / sqrt(A_jj),  Gh_ii = softplus(h_diag), Gh_ij = h_off,
+//   (h_off, h_diag) = MLP(features of the entry), 4 -> 64 -> 64 -> 2, ReLU.
+//
+// One network evaluation per pattern entry: n diagonal entries and |E| edge
+// entries (edge (a < b) carries G_ba).  Entry features:
+//   edge:  (rho_ab, theta_b, theta_a, w_ab),  rho = lam w^2 / sqrt(A_aa A_bb),
+//          theta_i = r d_i / A_ii;
+//   diag:  (s_i, theta_i, theta_i, 1),  s_i = sum over lower neighbours j of rho_ij^2.
+// The 64 x 64 hidden layer runs on the tensor cores (mma.sync m16n8k16, BF16
+// operands, FP32 accumulation) in inference and in training; the 4 -> 64 and
+// 64 -> 2 layers are FP32.  Training minimises Kaporin's condition number of
+// G A G^T, L = log(tr(G A G^T)/n) - (2/n) sum log G_ii, whose gradient on the
+// pattern is dL/dG_ij = 2 (A g_i)_j / tr - delta_ij 2/(n G_ii), g_i = row i of G.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace pfe {
+namespace fsai {
+
+constexpr int HW = 64;
+constexpr int OW1 = 0, OB1 = 4 * HW, OW2 = OB1 + HW, OB2 = OW2 + HW * HW, OW3 = OB2 + HW, OB3 = OW3 + 2 * HW;
+static_assert(OB3 + 2 == kNParam, "parameter layout");
+
+constexpr int kMlpWarps = 4;
+constexpr int kMlpThreads = 32 * kMlpWarps;
+
+struct View {
+    int64_t n, n_edges, n_slices;
+    const int *slice_ptr, *col, *eid;
+    const int *ea, *eb, *ext_slot;
+    const double *ew, *deg, *adiag, *w64;
+    double lam, r;
+};
+
+View view(pfe_ctx *c) {
+    View v;
+    v.n = c->g.n;
+    v.n_edges = c->g.n_edges;
+    v.n_slices = c->g.n_slices;
+    v.slice_ptr = c->g.slice_ptr;
+    v.col = c->g.col;
+    v.eid = c->g.eid;
+    v.ea = c->g.ea;
+    v.eb = c->g.eb;
+    v.ext_slot = c->g.ext_slot;
+    v.ew = c->g.ew;
+    v.deg = c->g.deg;
+    v.adiag = c->g.adiag64;
+    v.w64 = c->g.w64;
+    v.lam = c->lambda;
+    v.r = c->r;
+    return v;
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// ---- per-row setup: s_i, the number of lower slots, the edge-slot -> entry map
+
+__global__ void k_rowprep(View g, float *srow, int *kb, int *ent_of_slot) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int64_t s = i >> 5;
+    const int s0 = g.slice_ptr[s];
+    const int len = (g.slice_ptr[s + 1] - s0) >> 5;
+    const int64_t base = s0 + (i & 31) * (int64_t)len;  // row-major within the slice
+    const double aii = g.adiag[i];
+    double acc = 0.0;
+    int nb = 0;
+    for (int k = 0; k < len; ++k) {
+        const int64_t idx = base + k;
+        const int j = g.col[idx];
+        if (j >= i) break;  // slots are sorted by column; padding repeats i
+        const double w = g.w64[idx];
+        const double rho = g.lam * w * w / sqrt(aii * g.adiag[j]);
+        acc = fma(rho, rho, acc);
+        ++nb;
+    }
+    srow[i] = (float)acc;
+    kb[i] = nb;
+}
+
+__global__ void k_entmap(View g, int *ent_of_slot) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n_edges) return;
+    ent_of_slot[g.ext_slot[k]] = (int)k;
+}
+
+// features of entry e (e < n: diagonal i = e; else edge k = e - n)
+__device__ __forceinline__ void features(const View &g, const float *srow, int64_t e, float f[4], int &head,
+                                         float &scale) {
+    if (e < g.n) {
+        const double a = g.adiag[e];
+        const float th = (float)(g.r * g.deg[e] / a);
+        f[0] = srow[e];
+        f[1] = th;
+        f[2] = th;
+        f[3] = 1.f;
+        head = 1;
+        scale = (float)(1.0 / sqrt(a));
+    } else {
+        const int64_t k = e - g.n;
+        const int a = g.ea[k], b = g.eb[k];
+        const double aa = g.adiag[a], ab = g.adiag[b], w = g.ew[k];
+        f[0] = (float)(g.lam * w * w / sqrt(aa * ab));
+        f[1] = (float)(g.r * g.deg[b] / ab);
+        f[2] = (float)(g.r * g.deg[a] / aa);
+        f[3] = (float)w;
+        head = 0;
+        scale = (float)(1.0 / sqrt(aa));
+    }
+}
+
+// ---- tensor-core helpers (mma.sync m16n8k16, BF16 x BF16 -> FP32) ----------
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    return u;
+}
+
+__device__ __forceinline__ uint32_t pair_u32(const __nv_bfloat16 *p) {
+    uint32_t u;
+    memcpy(&u, p, 4);
+    return u;
+}
+
+__device__ __forceinline__ uint32_t pair_strided(const __nv_bfloat16 *p0, const __nv_bfloat16 *p1) {
+    __nv_bfloat162 v;
+    v.x = *p0;
+    v.y = *p1;
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    return u;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Shared-memory weights of one block.
+struct SmemW {
+    float W1[4 * HW], b1[HW], b2[HW], W3[HW * 2], b3[4];
+    __nv_bfloat16 W2t[HW * HW];  // [n = h2 unit][k = h1 unit]: B operand of h1 @ W2
+    __nv_bfloat16 W2r[HW * HW];  // [n = h1 unit][k = h2 unit]: B operand of da2 @ W2^T
+};
+
+__device__ void load_weights(SmemW &s, const float *__restrict__ P) {
+    for (int t = threadIdx.x; t < 4 * HW; t += blockDim.x) s.W1[t] = P[OW1 + t];
+    for (int t = threadIdx.x; t < HW; t += blockDim.x) {
+        s.b1[t] = P[OB1 + t];
+        s.b2[t] = P[OB2 + t];
+    }
+    for (int t = threadIdx.x; t < 2 * HW; t += blockDim.x) s.W3[t] = P[OW3 + t];
+    if (threadIdx.x < 2) s.b3[threadIdx.x] = P[OB3 + threadIdx.x];
+    for (int t = threadIdx.x; t < HW * HW; t += blockDim.x) {
+        const int k = t / HW, n = t % HW;  // W2[k][n], k = h1 unit, n = h2 unit
+        const __nv_bfloat16 v = __float2bfloat16_rn(P[OW2 + t]);
+        s.W2t[n * HW + k] = v;
+        s.W2r[k * HW + n] = v;
+    }
+}
+
+// Per-warp tile scratch.
+struct SmemTile {
+    float f[16][4];
+    int head[16];
+    float scale[16];
+    float hv[16];  // raw head value
+    __nv_bfloat16 h1[16][HW];
+    __nv_bfloat16 da2b[16][HW];
+    float h2[16][HW];
+    float da2[16][HW];
+    float da1[16][HW];
+    float dout[16];
+};
+
+// Forward of one 16-entry tile.  Leaves h1 (bf16) in smem, a2 (pre-ReLU) in
+// the C fragments acc[nt][0..3] (rows gid, gid+8; units 8nt + 2tig + {0,1}).
+__device__ __forceinline__ void tile_forward(const SmemW &W, SmemTile &T, float (&acc)[8][4]) {
+    const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    // layer 1 (FP32): lane handles units lane and lane + 32 of all 16 entries
+    for (int uu = 0; uu < 2; ++uu) {
+        const int u = lane + 32 * uu;
+        for (int e = 0; e < 16; ++e) {
+            float a = W.b1[u];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a = fmaf(T.f[e][k], W.W1[k * HW + u], a);
+            T.h1[e][u] = __float2bfloat16_rn(fmaxf(a, 0.f));
+        }
+    }
+    __syncwarp();
+    // layer 2 on the tensor cores: a2 = h1 @ W2 + b2
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int u0 = 8 * nt + 2 * tig;
+        acc[nt][0] = W.b2[u0];
+        acc[nt][1] = W.b2[u0 + 1];
+        acc[nt][2] = W.b2[u0];
+        acc[nt][3] = W.b2[u0 + 1];
+    }
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+        uint32_t a[4];
+        const int k0 = 16 * ks + 2 * tig;
+        a[0] = pair_u32(&T.h1[gid][k0]);
+        a[1] = pair_u32(&T.h1[gid + 8][k0]);
+        a[2] = pair_u32(&T.h1[gid][k0 + 8]);
+        a[3] = pair_u32(&T.h1[gid + 8][k0 + 8]);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            uint32_t b[2];
+            const int n = 8 * nt + gid;
+            b[0] = pair_u32(&W.W2t[n * HW + k0]);
+            b[1] = pair_u32(&W.W2t[n * HW + k0 + 8]);
+            mma_bf16(acc[nt], a, b);
+        }
+    }
+}
+
+// Output heads of the tile rows gid and gid + 8 (valid on lanes with tig == 0).
+__device__ __forceinline__ void tile_heads(const SmemW &W, SmemTile &T, const float (&acc)[8][4]) {
+    const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    const int h0 = T.head[gid], h1 = T.head[gid + 8];
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int u0 = 8 * nt + 2 * tig;
+        s0 = fmaf(fmaxf(acc[nt][0], 0.f), W.W3[u0 * 2 + h0], s0);
+        s0 = fmaf(fmaxf(acc[nt][1], 0.f), W.W3[(u0 + 1) * 2 + h0], s0);
+        s1 = fmaf(fmaxf(acc[nt][2], 0.f), W.W3[u0 * 2 + h1], s1);
+        s1 = fmaf(fmaxf(acc[nt][3], 0.f), W.W3[(u0 + 1) * 2 + h1], s1);
+    }
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+    if (tig == 0) {
+        T.hv[gid] = s0 + W.b3[h0];
+        T.hv[gid + 8] = s1 + W.b3[h1];
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ float softplusf(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+__device__ __forceinline__ float sigmoidf(float x) { return 1.f / (1.f + expf(-x)); }
+
+// Inference: G entries for every pattern entry.  gdiag[i] = G_ii, gE[edge
+// slot] = G_ba; hraw[e] = the network's head value (training reuses it).
+__global__ void __launch_bounds__(kMlpThreads) k_mlp_fwd(View g, const float *srow, const float *__restrict__ P,
+                                                         float *gdiag, float *gE, float *hraw) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemW &W = *reinterpret_cast<SmemW *>(smem);
+    SmemTile &T = reinterpret_cast<SmemTile *>(smem + sizeof(SmemW))[threadIdx.x >> 5];
+    load_weights(W, P);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t N = g.n + g.n_edges, ntiles = (N + 15) / 16;
+    const int64_t warp_g = (int64_t)blockIdx.x * kMlpWarps + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * kMlpWarps;
+    for (int64_t t = warp_g; t < ntiles; t += nwarps) {
+        if (lane < 16) {
+            const int64_t e = t * 16 + lane;
+            if (e < N) {
+                features(g, srow, e, T.f[lane], T.head[lane], T.scale[lane]);
+            } else {
+                T.f[lane][0] = T.f[lane][1] = T.f[lane][2] = T.f[lane][3] = 0.f;
+                T.head[lane] = 0;
+                T.scale[lane] = 0.f;
+            }
+        }
+        __syncwarp();
+        float acc[8][4];
+        tile_forward(W, T, acc);
+        tile_heads(W, T, acc);
+        if (lane < 16) {
+            const int64_t e = t * 16 + lane;
+            if (e < N) {
+                const float h = T.hv[lane];
+                hraw[e] = h;
+                if (e < g.n)
+                    gdiag[e] = softplusf(h) * T.scale[lane];
+                else
+                    gE[g.ext_slot[e - g.n]] = h * T.scale[lane];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// G values per SELL slot (both orientations of an edge carry G_ba) so that
+// the PCG apply kernels read them coalesced.
+__global__ void k_gslots(View g, const float *gE, float *gslot) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((i >> 5) >= g.n_slices) return;
+    const int64_t s = i >> 5;
+    const int s0 = g.slice_ptr[s];
+    const int len = (g.slice_ptr[s + 1] - s0) >> 5;
+    const int64_t base = s0 + (i & 31) * (int64_t)len;  // row-major within the slice
+    for (int k = 0; k < len; ++k) {
+        const int64_t idx = base + k;
+        const int e = g.eid[idx];
+        gslot[idx] = e >= 0 ? gE[e] : 0.f;
+    }
+}
+
+// Kaporin row terms: q_i = g_i^T A g_i and dq_i/dG_ij = 2 (A g_i)_j for the
+// entries of row i (j = i and the lower neighbours), with
+// (A g_i)_j = lam sum_{k ~ j} w_jk^2 (g_ij - g_ik) + r d_j g_ij,  g_ik = 0 off the row pattern.
+constexpr int kMaxLower = 64;
+__global__ void k_kaporin_rows(View g, const int *kb, const float *gdiag, const float *gslot, const int *ent_of_slot,
+                               float *dq, double *qrow, double *logd) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int64_t s = i >> 5;
+    const int s0 = g.slice_ptr[s];
+    const int len_i = (g.slice_ptr[s + 1] - s0) >> 5;
+    const int64_t base = s0 + (i & 31) * (int64_t)len_i;
+    const int nl = min(kb[i], kMaxLower);
+    int cols[kMaxLower + 1];
+    float vals[kMaxLower + 1];
+    for (int k = 0; k < nl; ++k) {
+        const int64_t idx = base + k;
+        cols[k] = g.col[idx];
+        vals[k] = gslot[idx];
+    }
+    cols[nl] = (int)i;
+    vals[nl] = gdiag[i];
+    double q = 0.0;
+    for (int m = 0; m <= nl; ++m) {
+        const int j = cols[m];
+        const double gij = vals[m];
+        // (A g_i)_j over row j's slots
+        const int64_t sj = (int64_t)j >> 5;
+        const int t0 = g.slice_ptr[sj];
+        const int lj = (g.slice_ptr[sj + 1] - t0) >> 5;
+        const int64_t bj = t0 + (j & 31) * (int64_t)lj;
+        double agj = g.r * g.deg[j] * gij;
+        for (int k = 0; k < lj; ++k) {
+            const int64_t idx = bj + k;
+            if (g.eid[idx] < 0) continue;
+            const int kk = g.col[idx];
+            double gik = 0.0;
+            for (int u = 0; u <= nl; ++u)
+                if (cols[u] == kk) {
+                    gik = vals[u];
+                    break;
+                }
+            const double w = g.w64[idx];
+            agj += g.lam * w * w * (gij - gik);
+        }
+        q = fma(gij, agj, q);
+        const float d = (float)(2.0 * agj);
+        if (m == nl) {
+            dq[i] = d;  // diagonal entry i
+        } else {
+            const int64_t idx = base + m;
+            dq[g.n + ent_of_slot[g.eid[idx]]] = d;  // edge entry (j, i): G_ij
+        }
+    }
+    qrow[i] = q;
+    logd[i] = log((double)gdiag[i]);
+}
+
+// Deterministic sum of two n-vectors: out[0] = sum q, out[1] = sum log G_ii.
+__global__ void k_sum2(int64_t n, const double *a, const double *b, double *part, unsigned *ticket, double *out) {
+    double s[2] = {0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        s[0] += a[i];
+        s[1] += b[i];
+    }
+    block_reduce<double, 2>(s, part + 2 * blockIdx.x);
+    if (last_block_arrives(ticket)) {
+        if (threadIdx.x < 2) {
+            double t = 0.0;
+            for (unsigned k = 0; k < gridDim.x; ++k) t += __ldcg(part + 2 * k + threadIdx.x);
+            out[threadIdx.x] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+}
+
+// dL/dh per entry from dq (in place): L = log(Q/n) - (2/n) sum log G_ii.
+__global__ void k_dloss(View g, const double *sums, const float *gdiag, const float *hraw, float *dq) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t N = g.n + g.n_edges;
+    if (e >= N) return;
+    const double Q = sums[0];
+    double dG = dq[e] / Q;
+    if (e < g.n) {
+        dG -= 2.0 / ((double)g.n * gdiag[e]);
+        const double h = hraw[e];
+        dq[e] = (float)(dG / (1.0 + exp(-h)) / sqrt(g.adiag[e]));  // dG/dh = sigmoid(h)/sqrt(A_ii)
+    } else {
+        dq[e] = (float)(dG / sqrt(g.adiag[g.ea[e - g.n]]));       // dG/dh = 1/sqrt(A_aa)
+    }
+}
+
+// Backward through the network for every entry, given dL/dh per entry.
+// Block partials of the parameter gradient (kNParam floats per block) are
+// reduced by the last block in a fixed order.
+__global__ void __launch_bounds__(kMlpThreads) k_mlp_bwd(View g, const float *srow, const float *__restrict__ P,
+                                                         const float *dh, float *part, unsigned *ticket,
+                                                         float *grad) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemW &W = *reinterpret_cast<SmemW *>(smem);
+    SmemTile *Tall = reinterpret_cast<SmemTile *>(smem + sizeof(SmemW));
+    SmemTile &T = Tall[threadIdx.x >> 5];
+    float *blk = reinterpret_cast<float *>(smem + sizeof(SmemW) + kMlpWarps * sizeof(SmemTile));  // kNParam
+    load_weights(W, P);
+    for (int t = threadIdx.x; t < kNParam; t += blockDim.x) blk[t] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    const int64_t N = g.n + g.n_edges, ntiles = (N + 15) / 16;
+    const int64_t warp_g = (int64_t)blockIdx.x * kMlpWarps + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * kMlpWarps;
+    float gw2[4][8][4];  // tensor-core accumulator of h1^T da2 (rows h1 unit, cols h2 unit)
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) gw2[mt][nt][0] = gw2[mt][nt][1] = gw2[mt][nt][2] = gw2[mt][nt][3] = 0.f;
+    float gw1[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, gb1[2] = {0.f, 0.f};
+    float gw3[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, gb2[2] = {0.f, 0.f}, gb3[2] = {0.f, 0.f};
+    for (int64_t t = warp_g; t < ntiles; t += nwarps) {
+        if (lane < 16) {
+            const int64_t e = t * 16 + lane;
+            if (e < N) {
+                features(g, srow, e, T.f[lane], T.head[lane], T.scale[lane]);
+                T.dout[lane] = dh[e];
+            } else {
+                T.f[lane][0] = T.f[lane][1] = T.f[lane][2] = T.f[lane][3] = 0.f;
+                T.head[lane] = 0;
+                T.scale[lane] = 0.f;
+                T.dout[lane] = 0.f;
+            }
+        }
+        __syncwarp();
+        float acc[8][4];
+        tile_forward(W, T, acc);
+        // da2 = (dout * W3[:, head]) masked by a2 > 0; h2 kept for gW3
+        const int h0 = T.head[gid], h1r = T.head[gid + 8];
+        const float d0 = T.dout[gid], d1 = T.dout[gid + 8];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int u0 = 8 * nt + 2 * tig;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int u = u0 + q;
+                const float a_lo = acc[nt][q], a_hi = acc[nt][2 + q];
+                const float g_lo = a_lo > 0.f ? d0 * W.W3[u * 2 + h0] : 0.f;
+                const float g_hi = a_hi > 0.f ? d1 * W.W3[u * 2 + h1r] : 0.f;
+                T.h2[gid][u] = fmaxf(a_lo, 0.f);
+                T.h2[gid + 8][u] = fmaxf(a_hi, 0.f);
+                T.da2[gid][u] = g_lo;
+                T.da2[gid + 8][u] = g_hi;
+                T.da2b[gid][u] = __float2bfloat16_rn(g_lo);
+                T.da2b[gid + 8][u] = __float2bfloat16_rn(g_hi);
+            }
+        }
+        __syncwarp();
+        // gW2 += h1^T da2 on the tensor cores (K = the 16 entries of the tile)
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+            uint32_t a[4];
+            const int m0 = 16 * mt + gid;
+            const int k0 = 2 * tig;
+            a[0] = pair_strided(&T.h1[k0][m0], &T.h1[k0 + 1][m0]);
+            a[1] = pair_strided(&T.h1[k0][m0 + 8], &T.h1[k0 + 1][m0 + 8]);
+            a[2] = pair_strided(&T.h1[k0 + 8][m0], &T.h1[k0 + 9][m0]);
+            a[3] = pair_strided(&T.h1[k0 + 8][m0 + 8], &T.h1[k0 + 9][m0 + 8]);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                uint32_t b[2];
+                const int n = 8 * nt + gid;
+                b[0] = pair_strided(&T.da2b[k0][n], &T.da2b[k0 + 1][n]);
+                b[1] = pair_strided(&T.da2b[k0 + 8][n], &T.da2b[k0 + 9][n]);
+                mma_bf16(gw2[mt][nt], a, b);
+            }
+        }
+        // dh1 = da2 @ W2^T on the tensor cores
+        float dh1[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) dh1[nt][0] = dh1[nt][1] = dh1[nt][2] = dh1[nt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+            uint32_t a[4];
+            const int k0 = 16 * ks + 2 * tig;
+            a[0] = pair_u32(&T.da2b[gid][k0]);
+            a[1] = pair_u32(&T.da2b[gid + 8][k0]);
+            a[2] = pair_u32(&T.da2b[gid][k0 + 8]);
+            a[3] = pair_u32(&T.da2b[gid + 8][k0 + 8]);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                uint32_t b[2];
+                const int n = 8 * nt + gid;
+                b[0] = pair_u32(&W.W2r[n * HW + k0]);
+                b[1] = pair_u32(&W.W2r[n * HW + k0 + 8]);
+                mma_bf16(dh1[nt], a, b);
+            }
+        }
+        // da1 = dh1 masked by a1 > 0 (a1 recomputed in FP32)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int u = 8 * nt + 2 * tig + q;
+#pragma unroll
+                for (int hr = 0; hr < 2; ++hr) {
+                    const int row = gid + 8 * hr;
+                    float a1 = W.b1[u];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) a1 = fmaf(T.f[row][k], W.W1[k * HW + u], a1);
+                    T.da1[row][u] = a1 > 0.f ? dh1[nt][2 * hr + q] : 0.f;
+                }
+            }
+        }
+        __syncwarp();
+        // FP32 small layers: lane owns units lane and lane + 32
+#pragma unroll
+        for (int uu = 0; uu < 2; ++uu) {
+            const int u = lane + 32 * uu;
+            for (int e = 0; e < 16; ++e) {
+                const float da1 = T.da1[e][u];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) gw1[k][uu] = fmaf(T.f[e][k], da1, gw1[k][uu]);
+                gb1[uu] += da1;
+                gb2[uu] += T.da2[e][u];
+                const float hd = T.h2[e][u] * T.dout[e];
+                gw3[uu][T.head[e]] += hd;
+            }
+        }
+        if (lane < 2) {
+            for (int e = 0; e < 16; ++e)
+                if (T.head[e] == lane) gb3[lane] += T.dout[e];
+        }
+        __syncwarp();
+    }
+    // warp results -> block sums (fixed warp order)
+    for (int w = 0; w < kMlpWarps; ++w) {
+        if ((threadIdx.x >> 5) == w) {
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    const int r0 = 16 * mt + gid, c0 = 8 * nt + 2 * tig;
+                    blk[OW2 + r0 * HW + c0] += gw2[mt][nt][0];
+                    blk[OW2 + r0 * HW + c0 + 1] += gw2[mt][nt][1];
+                    blk[OW2 + (r0 + 8) * HW + c0] += gw2[mt][nt][2];
+                    blk[OW2 + (r0 + 8) * HW + c0 + 1] += gw2[mt][nt][3];
+                }
+#pragma unroll
+            for (int uu = 0; uu < 2; ++uu) {
+                const int u = lane + 32 * uu;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) blk[OW1 + k * HW + u] += gw1[k][uu];
+                blk[OB1 + u] += gb1[uu];
+                blk[OB2 + u] += gb2[uu];
+                blk[OW3 + u * 2] += gw3[uu][0];
+                blk[OW3 + u * 2 + 1] += gw3[uu][1];
+            }
+            if (lane < 2) blk[OB3 + lane] += gb3[lane];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < kNParam; t += blockDim.x) part[(int64_t)blockIdx.x * kNParam + t] = blk[t];
+    if (last_block_arrives(ticket)) {
+        for (int t = threadIdx.x; t < kNParam; t += blockDim.x) {
+            float s = 0.f;
+            for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(part + (int64_t)b * kNParam + t);
+            grad[t] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+}
+
+__global__ void k_adam(int64_t cnt, float *p, const float *gr, float *m, float *v, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    const float gk = gr[k];
+    const float mk = b1 * m[k] + (1.f - b1) * gk;
+    const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    p[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+}
+
+__global__ void k_export(View g, const float *gdiag, const float *gE, double *od, double *oe) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < g.n && od) od[k] = gdiag[k];
+    if (k < g.n_edges && oe) oe[k] = gE[g.ext_slot[k]];
+}
+
+size_t smem_fwd() { return sizeof(SmemW) + kMlpWarps * sizeof(SmemTile); }
+size_t smem_bwd() { return sizeof(SmemW) + kMlpWarps * sizeof(SmemTile) + kNParam * sizeof(float); }
+
+}  // namespace fsai
+
+using namespace fsai;
+
+// Allocate the FSAI buffers of a context once.
+pfe_status fsai_alloc(pfe_ctx *c) {
+    auto &f = c->fsai;
+    if (f.gdiag) return PFE_OK;
+    const int64_t n = c->g.n, ne = c->g.n_edges, N = n + ne;
+    auto al = [&](void **p, size_t bytes) -> bool {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        c->dev_allocs.push_back(*p);
+        c->bytes += (int64_t)bytes;
+        return true;
+    };
+    int nb = std::min<int64_t>((N + 63) / 64, (int64_t)c->num_sms * 2);
+    f.mlp_blocks = std::max(1, nb);
+    if (!al((void **)&f.gdiag, n * sizeof(float)) || !al((void **)&f.gE, std::max<int64_t>(c->g.fslots, 1) * sizeof(float)) ||
+        !al((void **)&f.gslot, c->g.slots * sizeof(float)) || !al((void **)&f.srow, n * sizeof(float)) ||
+        !al((void **)&f.kb, n * sizeof(int)) || !al((void **)&f.ent_of_slot, std::max<int64_t>(c->g.fslots, 1) * sizeof(int)) ||
+        !al((void **)&f.hraw, N * sizeof(float)) || !al((void **)&f.dq, N * sizeof(float)) ||
+        !al((void **)&f.qrow, n * sizeof(double)) || !al((void **)&f.logd, n * sizeof(double)) ||
+        !al((void **)&f.sums, 4 * sizeof(double)) || !al((void **)&f.part, 512 * sizeof(double)) ||
+        !al((void **)&f.gpart, (size_t)f.mlp_blocks * kNParam * sizeof(float)) ||
+        !al((void **)&f.tick, 4 * sizeof(unsigned)) || !al((void **)&f.params, kNParam * sizeof(float)) ||
+        !al((void **)&f.grad, kNParam * sizeof(float))) {
+        c->err = "FSAI buffers: cudaMalloc failed";
+        return PFE_ENOMEM;
+    }
+    cudaStream_t s = c->stream;
+    PFE_CUDA_TRY(c, cudaMemsetAsync(f.tick, 0, 4 * sizeof(unsigned), s));
+    PFE_CUDA_TRY(c, cudaMemsetAsync(f.gE, 0, std::max<int64_t>(c->g.fslots, 1) * sizeof(float), s));
+    View v = view(c);
+    k_rowprep<<<nblk(n, 256), 256, 0, s>>>(v, f.srow, f.kb, f.ent_of_slot);
+    k_entmap<<<nblk(std::max<int64_t>(ne, 1), 256), 256, 0, s>>>(v, f.ent_of_slot);
+    PFE_CUDA_TRY(c, cudaGetLastError());
+    PFE_CUDA_TRY(c, cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fwd()));
+    PFE_CUDA_TRY(c, cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bwd()));
+    return PFE_OK;
+}
+
+// G from the parameters in f.params (device, FP32).
+pfe_status fsai_infer(pfe_ctx *c) {
+    auto &f = c->fsai;
+    cudaStream_t s = c->stream;
+    View v = view(c);
+    k_mlp_fwd<<<f.mlp_blocks, kMlpThreads, smem_fwd(), s>>>(v, f.srow, f.params, f.gdiag, f.gE, f.hraw);
+    k_gslots<<<nblk(c->g.n_slices * 32, 256), 256, 0, s>>>(v, f.gE, f.gslot);
+    PFE_CUDA_TRY(c, cudaGetLastError());
+    return PFE_OK;
+}
+
+// Kaporin loss of the current G and its gradient w.r.t. f.params -> f.grad.
+pfe_status fsai_loss_grad(pfe_ctx *c, double *loss) {
+    auto &f = c->fsai;
+    cudaStream_t s = c->stream;
+    View v = view(c);
+    const int64_t n = c->g.n, N = n + c->g.n_edges;
+    PFE_TRY(fsai_infer(c));
+    k_kaporin_rows<<<nblk(n, 128), 128, 0, s>>>(v, f.kb, f.gdiag, f.gslot, f.ent_of_slot, f.dq, f.qrow, f.logd);
+    k_sum2<<<256, kBlock, 0, s>>>(n, f.qrow, f.logd, f.part, f.tick, f.sums);
+    k_dloss<<<nblk(N, 256), 256, 0, s>>>(v, f.sums, f.gdiag, f.hraw, f.dq);
+    k_mlp_bwd<<<f.mlp_blocks, kMlpThreads, smem_bwd(), s>>>(v, f.srow, f.params, f.dq, f.gpart, f.tick + 1, f.grad);
+    PFE_CUDA_TRY(c, cudaGetLastError());
+    double h[2];
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(h, f.sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PFE_CUDA_TRY(c, cudaStreamSynchronize(s));
+    *loss = std::log(h[0] / (double)n) - 2.0 / (double)n * h[1];
+    return PFE_OK;
+}
+
+// G entries as FP64: od[i] = G_ii (n), oe[k] = G_{b_k a_k} for external edge k.
+pfe_status fsai_export(pfe_ctx *c, double *od, double *oe) {
+    const int64_t m = std::max<int64_t>(c->g.n, c->g.n_edges);
+    k_export<<<nblk(m, 256), 256, 0, c->stream>>>(view(c), c->fsai.gdiag, c->fsai.gE, od, oe);
+    PFE_CUDA_TRY(c, cudaGetLastError());
+    return PFE_OK;
+}
+
+pfe_status adam_step(float *p, const float *gr, float *m, float *v, int64_t cnt, int step, double lr, double b1,
+                     double b2, double eps, cudaStream_t s) {
+    const float c1 = (float)(1.0 - std::pow(b1, step)), c2 = (float)(1.0 - std::pow(b2, step));
+    k_adam<<<nblk(cnt, 256), 256, 0, s>>>(cnt, p, gr, m, v, (float)lr, (float)b1, (float)b2, (float)eps, c1, c2);
+    return cudaGetLastError() == cudaSuccess ? PFE_OK : PFE_ECUDA;
+}
+
+}  // namespace pfe

@@ -1,11 +1,12 @@
 // Graph construction on the device (Sec. II heat kernel and degree matrix,
 // Sec. II edge operator M, Eq. 13 system matrix A = lambda M^T M + r D).
 //
-// Layout: SELL-32.  Rows are taken 32 at a time (one warp); slice s stores
-// its rows' off-diagonal entries slot-major, so that slot k of the 32 rows is
-// one coalesced 128-byte access.  Undirected edges (i < j) are stored in a
-// second SELL-32 layout over their first endpoint; the split-Bregman edge
-// state b (Alg. 2) is indexed by that edge slot.
+// Layout: SELL-32, row-major within a slice.  Rows are taken 32 at a time;
+// slice s stores each row's off-diagonal entries contiguously, padded to the
+// slice's longest row rounded up to 4 slots, so that a row's slots are read
+// with 16-byte vector loads.  Undirected edges (i < j) are stored in a second
+// sliced layout over their first endpoint; the split-Bregman edge state b
+// (Alg. 2) is indexed by that edge slot.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -55,7 +56,7 @@ __global__ void k_grid_count(int64_t n, int64_t n_slices, int H, int W, Offsets 
     int mf = __reduce_max_sync(0xffffffffu, nf);
     if ((threadIdx.x & 31) == 0) {
         int64_t s = i >> 5;
-        slice_len[s] = mb * 32;
+        slice_len[s] = ((mb + 3) & ~3) * 32;  // row length padded to a multiple of 4 slots
         fslice_len[s] = mf * 32;
     }
 }
@@ -68,8 +69,9 @@ __global__ void k_grid_fill(int64_t n, int64_t n_slices, int H, int W, Offsets o
     int64_t s = i >> 5;
     if (s >= n_slices) return;
     int lane = (int)(i & 31);
-    int64_t base = slice_ptr[s];
-    int len = (int)((slice_ptr[s + 1] - base) >> 5);
+    const int len = (int)((slice_ptr[s + 1] - slice_ptr[s]) >> 5);
+    const int64_t base = slice_ptr[s] + (int64_t)lane * len;  // row-major within the slice
+    const int flen = (int)((fslice_ptr[s + 1] - fslice_ptr[s]) >> 5);
     int k = 0;
     if (i < n) {
         int x = (int)(i % W), y = (int)(i / W);
@@ -79,11 +81,11 @@ __global__ void k_grid_fill(int64_t n, int64_t n_slices, int H, int W, Offsets o
             int x2 = x + off.dx[t], y2 = y + off.dy[t];
             if (x2 < 0 || x2 >= W || y2 < 0 || y2 >= H) continue;
             int64_t j = (int64_t)y2 * W + x2;
-            int64_t idx = base + (int64_t)k * 32 + lane;
+            int64_t idx = base + k;
             double w = (j > i) ? heat_weight(X, m, i, j, inv2s2) : heat_weight(X, m, j, i, inv2s2);
             int e;
             if (t >= off.K / 2) {  // forward: i owns the edge
-                e = (int)(fslice_ptr[s] + (int64_t)kf * 32 + lane);
+                e = (int)(fslice_ptr[s] + (int64_t)lane * flen + kf);
                 int64_t ext = fw_off[i] + kf;
                 ext_slot[ext] = e;
                 ea[ext] = (int)i;
@@ -98,7 +100,9 @@ __global__ void k_grid_fill(int64_t n, int64_t n_slices, int H, int W, Offsets o
                     int x3 = xj + off.dx[u], y3 = yj + off.dy[u];
                     if (x3 >= 0 && x3 < W && y3 >= 0 && y3 < H) ++rank;
                 }
-                e = (int)(fslice_ptr[j >> 5] + (int64_t)rank * 32 + (j & 31));
+                const int64_t sj = j >> 5;
+                const int flj = (int)((fslice_ptr[sj + 1] - fslice_ptr[sj]) >> 5);
+                e = (int)(fslice_ptr[sj] + (int64_t)(j & 31) * flj + rank);
             }
             col[idx] = (int)j;
             eid[idx] = e;
@@ -111,7 +115,7 @@ __global__ void k_grid_fill(int64_t n, int64_t n_slices, int H, int W, Offsets o
         deg2[i] = sw2;
     }
     for (; k < len; ++k) {  // padding slots
-        int64_t idx = base + (int64_t)k * 32 + lane;
+        int64_t idx = base + k;
         col[idx] = (i < n) ? (int)i : 0;
         eid[idx] = -1;
         w64[idx] = 0.0;
@@ -143,7 +147,7 @@ __global__ void k_slice_max(int64_t n, int64_t n_slices, const int *nb_row, cons
     int mb = __reduce_max_sync(0xffffffffu, nb);
     int mf = __reduce_max_sync(0xffffffffu, nf);
     if ((threadIdx.x & 31) == 0) {
-        slice_len[i >> 5] = mb * 32;
+        slice_len[i >> 5] = ((mb + 3) & ~3) * 32;  // row length padded to a multiple of 4 slots
         fslice_len[i >> 5] = mf * 32;
     }
 }
@@ -155,11 +159,13 @@ __global__ void k_edges_scatter(int64_t ne, const int32_t *ei, const int32_t *ej
     int64_t u = ei[k], v = ej[k];
     int64_t a = u < v ? u : v, b = u < v ? v : u;
     int pa = atomicAdd(cursor + a, 1);
-    int64_t ia = slice_ptr[a >> 5] + (int64_t)pa * 32 + (a & 31);
+    const int la = (int)((slice_ptr[(a >> 5) + 1] - slice_ptr[a >> 5]) >> 5);
+    int64_t ia = slice_ptr[a >> 5] + (int64_t)(a & 31) * la + pa;
     col[ia] = (int)b;
     tmp_ext[ia] = (int)k;
     int pb = atomicAdd(cursor + b, 1);
-    int64_t ib = slice_ptr[b >> 5] + (int64_t)pb * 32 + (b & 31);
+    const int lb = (int)((slice_ptr[(b >> 5) + 1] - slice_ptr[b >> 5]) >> 5);
+    int64_t ib = slice_ptr[b >> 5] + (int64_t)(b & 31) * lb + pb;
     col[ib] = (int)a;
     tmp_ext[ib] = (int)k;
 }
@@ -172,34 +178,35 @@ __global__ void k_edges_sort(int64_t n, int64_t n_slices, const int64_t *slice_p
     int64_t s = i >> 5;
     if (s >= n_slices) return;
     int lane = (int)(i & 31);
-    int64_t base = slice_ptr[s];
-    int len = (int)((slice_ptr[s + 1] - base) >> 5);
+    const int len = (int)((slice_ptr[s + 1] - slice_ptr[s]) >> 5);
+    const int64_t base = slice_ptr[s] + (int64_t)lane * len;
+    const int flen = (int)((fslice_ptr[s + 1] - fslice_ptr[s]) >> 5);
     int nb = i < n ? nb_row[i] : 0;
     for (int a = 1; a < nb; ++a) {
-        int64_t ia = base + (int64_t)a * 32 + lane;
+        int64_t ia = base + a;
         int ca = col[ia], xa = tmp_ext[ia];
         int b = a - 1;
         while (b >= 0) {
-            int64_t ib = base + (int64_t)b * 32 + lane;
+            int64_t ib = base + b;
             int cb = col[ib];
             if (cb <= ca) break;
-            int64_t ib1 = ib + 32;
+            int64_t ib1 = ib + 1;
             col[ib1] = cb;
             tmp_ext[ib1] = tmp_ext[ib];
             --b;
         }
-        int64_t ib1 = base + (int64_t)(b + 1) * 32 + lane;
+        int64_t ib1 = base + (b + 1);
         col[ib1] = ca;
         tmp_ext[ib1] = xa;
     }
     int kf = 0, prev = -1;
     for (int k = 0; k < nb; ++k) {
-        int64_t idx = base + (int64_t)k * 32 + lane;
+        int64_t idx = base + k;
         int j = col[idx];
         if (j == prev) atomicExch(err, 2);
         prev = j;
         if (j > i) {
-            int e = (int)(fslice_ptr[s] + (int64_t)kf * 32 + lane);
+            int e = (int)(fslice_ptr[s] + (int64_t)lane * flen + kf);
             int ext = tmp_ext[idx];
             ext_slot[ext] = e;
             ea[ext] = (int)i;
@@ -211,7 +218,7 @@ __global__ void k_edges_sort(int64_t n, int64_t n_slices, const int64_t *slice_p
         }
     }
     for (int k = nb; k < len; ++k) {
-        int64_t idx = base + (int64_t)k * 32 + lane;
+        int64_t idx = base + k;
         col[idx] = i < n ? (int)i : 0;
         eid[idx] = -1;
         tmp_ext[idx] = -1;
@@ -225,12 +232,12 @@ __global__ void k_edges_backward(int64_t n, const int64_t *slice_ptr, const int 
     if (i >= n) return;
     int64_t s = i >> 5;
     int lane = (int)(i & 31);
-    int64_t base = slice_ptr[s];
-    int len = (int)((slice_ptr[s + 1] - base) >> 5);
+    const int len = (int)((slice_ptr[s + 1] - slice_ptr[s]) >> 5);
+    const int64_t base = slice_ptr[s] + (int64_t)lane * len;
     int nb = nb_row[i];
     double sw = 0.0, sw2 = 0.0;
     for (int k = 0; k < nb; ++k) {
-        int64_t idx = base + (int64_t)k * 32 + lane;
+        int64_t idx = base + k;
         int j = col[idx];
         if (eid[idx] == -2) eid[idx] = ext_slot[tmp_ext[idx]];
         double w = (j > i) ? heat_weight(X, m, i, j, inv2s2) : heat_weight(X, m, j, i, inv2s2);
@@ -239,7 +246,7 @@ __global__ void k_edges_backward(int64_t n, const int64_t *slice_ptr, const int 
         sw += w;
         sw2 = fma(w, w, sw2);
     }
-    for (int k = nb; k < len; ++k) w64[base + (int64_t)k * 32 + lane] = 0.0;
+    for (int k = nb; k < len; ++k) w64[base + k] = 0.0;
     deg[i] = sw;
     deg2[i] = sw2;
 }

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/pfe.h"
+#include "fsai.h"
 
 #define PFE_DMAX 32
 
@@ -32,6 +33,12 @@ struct PcgCtl {
     double max_relres, last_relres;
     int last_converged, unroll;       // unroll: iterations per graph body / host poll
     long long launches;               // PCG kernel launches (early-exited ones included)
+    int pbuf;                         // which direction buffer holds the current p
+    int p_ready;                      // 1: p was just set by k_pcg_init (no update in k_spmm)
+    int xpending;                     // 1: y += alpha p of the last k_spmm not yet applied
+    int zstart;                       // FSAI: the next k_fsai_z finishes the start of a solve
+    int launch_base, launch_per_iter; // kernel launches outside / per iteration of the loop
+    int pad2;
 };
 
 // Control block of the P-step (Alg. 1 steps 6-7).
@@ -75,7 +82,7 @@ struct Work {
     void *Bs[2] = {nullptr, nullptr};  // edge slots x d: b of Alg. 2 (double-buffered)
     void *RHS = nullptr;     // n x d: right-hand side of Eq. 13 (times 2)
     void *Cw = nullptr;      // n x d: r D^{1/2} (P - B)
-    void *R = nullptr, *Pd = nullptr, *Q = nullptr;  // PCG residual, direction, A*direction
+    void *R = nullptr, *Pd = nullptr, *Pd2 = nullptr, *Q = nullptr;  // PCG residual, direction (x2), A*direction
     double *P = nullptr, *B = nullptr;  // n x d FP64 (Alg. 1)
     double *stage = nullptr;            // n x d FP64 staging (init / get / set)
     double *partials = nullptr;         // block partials of reductions
@@ -101,9 +108,11 @@ struct pfe_ctx {
     pfe::PcgCtl *h_ctl = nullptr;     // pinned host mirror
     pfe::PstepCtl *pctl = nullptr;    // device
     int *h_flag = nullptr;            // pinned host scratch
-    int grid_rows = 0;                // blocks of the persistent row kernels
+    int grid_rows = 0;                // blocks of the persistent row kernels (upper bound)
+    int kgrid[32] = {0};              // per-kernel grid cache (wave_grid), reset by pfe_init
     cudaGraph_t pcg_graph = nullptr;
     cudaGraphExec_t pcg_exec = nullptr;
+    pfe::FsaiState fsai;
     std::string err;
     std::vector<void *> dev_allocs;   // graph-lifetime allocations
     std::vector<void *> work_allocs;  // d-dependent allocations
@@ -124,6 +133,7 @@ struct PcgLaunch {
 };
 pfe_status launch_pcg_init(pfe_ctx *c, cudaStream_t s, PcgLaunch L);
 pfe_status launch_pcg_body(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters);
+pfe_status launch_pcg_final(pfe_ctx *c, cudaStream_t s, PcgLaunch L);
 pfe_status launch_apply_A(pfe_ctx *c, cudaStream_t s, const void *x, void *y);
 pfe_status time_pcg_kernel(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms);
 

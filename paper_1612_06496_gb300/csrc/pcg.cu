@@ -11,6 +11,8 @@ pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L);
 template <typename T, int D>
 pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters);
 template <typename T, int D>
+pfe_status final_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L);
+template <typename T, int D>
 pfe_status apply_T(pfe_ctx *c, cudaStream_t s, const void *x, void *y);
 template <typename T, int D>
 pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms);
@@ -30,6 +32,14 @@ pfe_status launch_pcg_body(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
         PFE_DISPATCH_D(c->d, return body_T<float, D>(c, s, L, iters));
     } else {
         PFE_DISPATCH_D(c->d, return body_T<double, D>(c, s, L, iters));
+    }
+}
+
+pfe_status launch_pcg_final(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
+    if (c->mixed) {
+        PFE_DISPATCH_D(c->d, return final_T<float, D>(c, s, L));
+    } else {
+        PFE_DISPATCH_D(c->d, return final_T<double, D>(c, s, L));
     }
 }
 

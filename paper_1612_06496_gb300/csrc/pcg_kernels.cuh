@@ -1,21 +1,28 @@
-// Kernels of the d-column Jacobi-preconditioned conjugate gradients on A Y = RHS, the
-// normal equations of Eq. 13 (Sec. III, last paragraph: PCG instead of a
-// direct solve).  Each column c runs the textbook recurrences (Barrett et
-// al., Templates, PCG) with its own alpha_c, beta_c; a column whose relative
-// residual |r_c| / |b_c| reaches tol is frozen (alpha_c = 0).
+// Kernels of the d-column Jacobi-preconditioned conjugate gradients on
+// A Y = RHS, the normal equations of Eq. 13 (Sec. III, last paragraph: PCG in
+// place of a direct solve).  Each column c runs the textbook recurrences
+// (Barrett et al., Templates, PCG) with its own alpha_c, beta_c; a column
+// whose relative residual |r_c| / |b_c| reaches tol is frozen (alpha_c = 0).
 //
-// One iteration is four launches, all persistent-grid row kernels over the
-// SELL-32 layout (one thread per row, the d columns of a row interleaved so
-// every nonzero is loaded once for all d columns):
-//   k_spmm     q = A p                 + block partials of p.q  -> alpha
-//   k_update   y += alpha p, r -= alpha q, z = D_A^{-1} r
-//                                       + partials of r.z, r.r  -> beta, convergence
-//   k_refresh  (every `refresh` iterations) r = b - A y in extended precision
-//   k_pupdate  p = z + beta p
-// Scalars live in a device control block; the last block of each reduction
-// (detected with an atomic ticket, no waiting) finishes the scalar work, so
-// the loop needs no host round trip and can run inside a CUDA graph whose
-// WHILE node reads the flag set here.
+// Thread mapping of the gather kernels (SubWarp): L = d/V lanes per row, V
+// consecutive columns per lane, so every load of a d-interleaved row -- own
+// or gathered neighbour -- is one contiguous warp access and a matrix slot
+// (col, value) is fetched once per V columns.  The elementwise kernels use a
+// flat float4/double2 traversal.
+//
+// A Jacobi iteration is three launches (plus two that exit at once except
+// every `refresh` iterations; the FSAI iteration is listed further down):
+//   k_pupdate  p = z + beta p (z = D_A^{-1} r) and y += alpha_prev p_prev (the
+//              solution update of the previous iteration, delayed to share
+//              this pass), in place
+//   k_spmm     q = A p, partials of p.q -> alpha
+//   k_update   r -= alpha q, partials of r.z and r.r -> beta, convergence
+//   k_xflush   (refresh iterations) y += alpha p
+//   k_refresh  (refresh iterations) r = b - A y in extended precision
+// and k_xflush once after the loop.  Scalars live in
+// a device control block; the last block of each reduction (atomic ticket,
+// no waiting) finishes the scalar work, so the loop runs inside a CUDA graph
+// whose WHILE node reads the flag set here.
 #pragma once
 #include <cstring>
 #include <type_traits>
@@ -24,6 +31,8 @@
 
 namespace pfe {
 namespace pcgk {
+
+constexpr int kChunk = 12;  // matrix slots prefetched together by the gather kernels
 
 template <typename T>
 struct SysView {
@@ -40,12 +49,17 @@ struct PcgArgs {
     SysView<T> A;
     T *x;        // solution (hi part when T = float)
     float *xlo;  // low part (float path only)
-    T *r, *p, *q;
+    T *r, *q;
+    T *p[2];     // direction, double-buffered
     const T *b;
     void *part;  // block partials, Acc<T>::type
     PcgCtl *ctl;
     cudaGraphConditionalHandle cond;
     int use_cond;
+    // FSAI preconditioner (float path): z = G^T t, t = G r
+    T *z, *t;
+    const T *gdiag, *gslot;
+    const int *kb;
 };
 
 template <typename T>
@@ -67,7 +81,117 @@ SysView<T> sys_view(pfe_ctx *c) {
     return v;
 }
 
-// ---- device pieces -------------------------------------------------------
+// Sub-warp mapping of a d-interleaved row: V consecutive columns per lane
+// (V = the widest of 16/8/4 bytes that divides a row), L = D/V lanes per row,
+// RPW = floor(32/L) rows per warp.  Gathered rows are contiguous runs of
+// L*V*sizeof(T) bytes and the per-slot scalar work (column index, matrix
+// value) is shared by V columns.
+template <typename T, int D>
+struct SubWarp {
+    static constexpr int V = (sizeof(T) == 4 && D % 4 == 0) ? 4 : (D % 2 == 0 ? 2 : 1);
+    static constexpr int L = D / V;
+    static constexpr int RPW = 32 / L;
+    int r, cg;
+    bool active;
+    __device__ __forceinline__ SubWarp() {
+        const int lane = threadIdx.x & 31;
+        r = lane / L;
+        cg = lane - r * L;
+        active = lane < RPW * L;
+    }
+};
+
+template <typename T, int V>
+__device__ __forceinline__ void ldv(const T *__restrict__ p, T (&v)[V]) {
+    if constexpr (V * sizeof(T) == 16) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        memcpy(v, &t, 16);
+    } else if constexpr (V * sizeof(T) == 8) {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        memcpy(v, &t, 8);
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) v[k] = __ldg(p + k);
+    }
+}
+// coherent load (array written earlier in the same launch by this thread only)
+template <typename T, int V>
+__device__ __forceinline__ void ldv_rw(const T *p, T (&v)[V]) {
+    if constexpr (V * sizeof(T) == 16) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        memcpy(v, &t, 16);
+    } else if constexpr (V * sizeof(T) == 8) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        memcpy(v, &t, 8);
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) v[k] = p[k];
+    }
+}
+template <typename T, int V>
+__device__ __forceinline__ void stv(T *p, const T (&v)[V]) {
+    if constexpr (V * sizeof(T) == 16) {
+        float4 t;
+        memcpy(&t, v, 16);
+        *reinterpret_cast<float4 *>(p) = t;
+    } else if constexpr (V * sizeof(T) == 8) {
+        float2 t;
+        memcpy(&t, v, 8);
+        *reinterpret_cast<float2 *>(p) = t;
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) p[k] = v[k];
+    }
+}
+
+// SELL-32 slot addressing of row i (row-major within the slice): slot k is at
+// base + k; len is a multiple of 4 and base is 16-byte aligned.
+__device__ __forceinline__ void sell_row(const int *__restrict__ slice_ptr, int64_t i, int64_t &base, int &len) {
+    const int64_t s = i >> 5;
+    const int s0 = slice_ptr[s];
+    len = (slice_ptr[s + 1] - s0) >> 5;
+    base = (int64_t)s0 + (i & 31) * (int64_t)len;
+}
+
+// Slots k0 .. k0+CH-1 of a row (CH a multiple of 4): column and value with
+// 16-byte vector loads; slots past len give (own row, 0).
+template <typename T, int CH>
+__device__ __forceinline__ void load_slots(const int *__restrict__ col, const T *__restrict__ val, int64_t base,
+                                           int k0, int len, int self, int (&jj)[CH], T (&av)[CH]) {
+#pragma unroll
+    for (int g4 = 0; g4 < CH / 4; ++g4) {
+        const int k = k0 + 4 * g4;
+        if (k < len) {
+            const int4 cv = __ldg(reinterpret_cast<const int4 *>(col + base + k));
+            jj[4 * g4] = cv.x;
+            jj[4 * g4 + 1] = cv.y;
+            jj[4 * g4 + 2] = cv.z;
+            jj[4 * g4 + 3] = cv.w;
+            if constexpr (sizeof(T) == 4) {
+                const float4 vv = __ldg(reinterpret_cast<const float4 *>(val + base + k));
+                av[4 * g4] = vv.x;
+                av[4 * g4 + 1] = vv.y;
+                av[4 * g4 + 2] = vv.z;
+                av[4 * g4 + 3] = vv.w;
+            } else {
+                const double2 v0 = __ldg(reinterpret_cast<const double2 *>(val + base + k));
+                const double2 v1 = __ldg(reinterpret_cast<const double2 *>(val + base + k + 2));
+                av[4 * g4] = v0.x;
+                av[4 * g4 + 1] = v0.y;
+                av[4 * g4 + 2] = v1.x;
+                av[4 * g4 + 3] = v1.y;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                jj[4 * g4 + u] = self;
+                av[4 * g4 + u] = T(0);
+            }
+        }
+    }
+}
+
+// ---- reductions -------------------------------------------------------------
 
 template <typename A, typename AT>
 __device__ __forceinline__ AT ld_part(const AT *p) {
@@ -79,56 +203,81 @@ __device__ __forceinline__ AT ld_part(const AT *p) {
     }
 }
 
-// Sum the NV values over the block; result in sh[0..NV) (valid after return).
-template <typename T, int NV>
-__device__ __forceinline__ void block_sum(typename Acc<T>::type (&v)[NV], typename Acc<T>::type *sh) {
+// Each lane holds NQ x V accumulators for columns cg*V + v of its row; block
+// totals per (quantity, column) land in sh[q*D + c].  Fixed order.
+template <typename T, int D, int NQ>
+__device__ __forceinline__ void block_sum_cols(typename Acc<T>::type (&v)[NQ][SubWarp<T, D>::V],
+                                               typename Acc<T>::type *sh) {
     using A = Acc<T>;
     using AT = typename A::type;
-    __shared__ AT red[kWarps][NV];
+    using SW = SubWarp<T, D>;
+    __shared__ AT red[NQ][kWarps][32][SW::V];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) {
+    for (int q = 0; q < NQ; ++q)
 #pragma unroll
-        for (int c = 0; c < NV; ++c) A::add(v[c], A::shfl_xor(v[c], m));
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int c = 0; c < NV; ++c) red[warp][c] = v[c];
-    }
+        for (int k = 0; k < SW::V; ++k) red[q][warp][lane][k] = v[q][k];
     __syncthreads();
-    for (int c = threadIdx.x; c < NV; c += blockDim.x) {
-        AT s = red[0][c];
-        for (int w = 1; w < kWarps; ++w) A::add(s, red[w][c]);
-        sh[c] = s;
+    for (int t = threadIdx.x; t < NQ * D; t += blockDim.x) {
+        const int q = t / D, c = t - q * D, cg = c / SW::V, k = c - cg * SW::V;
+        AT s = A::zero();
+        for (int w = 0; w < kWarps; ++w)
+            for (int r = 0; r < SW::RPW; ++r) A::add(s, red[q][w][r * SW::L + cg][k]);
+        sh[t] = s;
     }
     __syncthreads();
 }
 
-// Write this block's NV partials; if this is the last block, reduce all
-// blocks' partials (fixed order) into out[0..NV) (shared, double) and return true.
-template <typename T, int NV>
-__device__ __forceinline__ bool grid_sum(typename Acc<T>::type (&v)[NV], void *part_v, unsigned *ticket,
-                                         double *out) {
+// Write this block's NQ*D partials; the last block to arrive reduces all
+// blocks' partials in a fixed order into out[0..NQ*D) (shared) and returns true.
+template <typename T, int D, int NQ>
+__device__ __forceinline__ bool grid_sum_cols(typename Acc<T>::type (&v)[NQ][SubWarp<T, D>::V], void *part_v,
+                                              unsigned *ticket, double *out) {
     using A = Acc<T>;
     using AT = typename A::type;
+    constexpr int NV = NQ * D;
     __shared__ AT sh[NV];
     AT *part = reinterpret_cast<AT *>(part_v);
-    block_sum<T, NV>(v, sh);
-    for (int c = threadIdx.x; c < NV; c += blockDim.x) part[(int64_t)blockIdx.x * NV + c] = sh[c];
+    block_sum_cols<T, D, NQ>(v, sh);
+    for (int t = threadIdx.x; t < NV; t += blockDim.x) part[(int64_t)blockIdx.x * NV + t] = sh[t];
     if (!last_block_arrives(ticket)) return false;
-    AT acc[NV];
-#pragma unroll
-    for (int c = 0; c < NV; ++c) acc[c] = A::zero();
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-#pragma unroll
-        for (int c = 0; c < NV; ++c) A::add(acc[c], ld_part<A, AT>(part + (int64_t)b * NV + c));
+    // last block: G threads per value, thread (v, h) sums blocks h, h+G, ...;
+    // the G partials of a value are then added in order (fixed order overall)
+    constexpr int G = (kBlock / NV) > 0 ? (kBlock / NV) : 1;
+    __shared__ AT pr[G][NV];
+    if (threadIdx.x < G * NV) {
+        const int v = threadIdx.x % NV, h = threadIdx.x / NV;
+        AT s = A::zero();
+        for (int b = h; b < (int)gridDim.x; b += G) A::add(s, ld_part<A, AT>(part + (int64_t)b * NV + v));
+        pr[h][v] = s;
     }
-    __syncthreads();  // `sh` is reused below
-    block_sum<T, NV>(acc, sh);
-    for (int c = threadIdx.x; c < NV; c += blockDim.x) out[c] = A::to_double(sh[c]);
+    __syncthreads();
+    for (int t = threadIdx.x; t < NV; t += blockDim.x) {
+        AT s = pr[0][t];
+        for (int h = 1; h < G; ++h) A::add(s, pr[h][t]);
+        out[t] = A::to_double(s);
+    }
     if (threadIdx.x == 0) *ticket = 0u;
     __syncthreads();
     return true;
+}
+
+// (hi, lo) += alpha * p for the float path (product and sum errors kept in
+// lo, renormalised); a plain FMA for FP64.
+template <typename T>
+__device__ __forceinline__ void axpy_hilo(T &xh, float &xl, T al, T po) {
+    if constexpr (std::is_same_v<T, float>) {
+        const float dlt = __fmul_rn(al, po);
+        const float de = __fmaf_rn(al, po, -dlt);
+        float sh, se;
+        two_sum(xh, dlt, sh, se);
+        const float lo = __fadd_rn(xl, __fadd_rn(se, de));
+        const float h2 = __fadd_rn(sh, lo);
+        xl = __fsub_rn(lo, __fsub_rn(h2, sh));
+        xh = h2;
+    } else {
+        xh = fma(al, po, xh);
+    }
 }
 
 __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, int value) {
@@ -138,7 +287,7 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, 
 // Finish an iteration (or the start of a solve): residual norms -> relres,
 // beta, freezing, termination.  Runs on thread 0 of the last block.
 static __device__ void finish_scalars(PcgCtl *ctl, const double *rz, const double *rr, int D, bool start,
-                               cudaGraphConditionalHandle cond, int use_cond) {
+                                      cudaGraphConditionalHandle cond, int use_cond) {
     int any = 0;
     for (int c = 0; c < D; ++c) {
         if (start) {
@@ -172,233 +321,600 @@ static __device__ void finish_scalars(PcgCtl *ctl, const double *rz, const doubl
         ctl->last_converged = !any;
         ctl->max_relres = fmax(ctl->max_relres, mr);
         const int u = ctl->unroll > 0 ? ctl->unroll : 1;
-        ctl->launches += 1 + 4LL * u * ((ctl->iter + u - 1) / u);
+        // launches before and after the loop + the loop body's per iteration
+        ctl->launches += ctl->launch_base + (long long)ctl->launch_per_iter * u * ((ctl->iter + u - 1) / u);
     }
     ctl->done = done;
     set_cond(cond, use_cond, !done);
 }
 
-// r_i = b_i - (A y)_i with y = hi + lo accumulated in double-FP32 (float
-// path) or FP64; returns r_i in working precision.
-template <typename T, int D>
-__device__ __forceinline__ void true_residual_row(const PcgArgs<T> &a, int64_t s, int lane, int64_t i,
-                                                  T (&ri)[D]) {
-    const int64_t base = a.A.slice_ptr[s];
-    const int len = (a.A.slice_ptr[s + 1] - (int)base) >> 5;
-    T bi[D];
-    load_row<T, D>(a.b, i, bi);
+// (b - A y) on columns c0 .. c0+V-1 of row i, with y = hi + lo accumulated in
+// double-FP32 (float path) or FP64.
+template <typename T, int D, int V>
+__device__ __forceinline__ void true_residual(const PcgArgs<T> &a, int64_t i, int c0, T (&out)[V]) {
+    int64_t base;
+    int len;
+    sell_row(a.A.slice_ptr, i, base, len);
+    T bi[V];
+    ldv_rw<T, V>(a.b + i * D + c0, bi);
     if constexpr (std::is_same_v<T, float>) {
-        DF acc[D];
-        float xh[D], xl[D];
-        load_row_rw<float, D>(a.x, i, xh);
-        load_row_rw<float, D>(a.xlo, i, xl);
+        DF acc[V];
+        float xh[V], xl[V];
         const float ad = a.A.adiag[i];
+        ldv_rw<float, V>(a.x + i * D + c0, xh);
+        ldv_rw<float, V>(a.xlo + i * D + c0, xl);
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            acc[c] = DF{0.f, 0.f};
-            df_add_prod(acc[c], ad, xh[c]);
-            df_add_f(acc[c], ad * xl[c]);
+        for (int k = 0; k < V; ++k) {
+            acc[k] = DF{0.f, 0.f};
+            df_add_prod(acc[k], ad, xh[k]);
+            df_add_f(acc[k], ad * xl[k]);
         }
-        for (int k = 0; k < len; ++k) {
-            const int64_t idx = base + (int64_t)k * 32 + lane;
+        for (int s = 0; s < len; ++s) {
+            const int64_t idx = base + s;
             const int j = a.A.col[idx];
             const float av = a.A.aoff[idx];
-            load_row_rw<float, D>(a.x, j, xh);
-            load_row_rw<float, D>(a.xlo, j, xl);
+            ldv_rw<float, V>(a.x + (int64_t)j * D + c0, xh);
+            ldv_rw<float, V>(a.xlo + (int64_t)j * D + c0, xl);
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                df_add_prod(acc[c], av, xh[c]);
-                df_add_f(acc[c], av * xl[c]);
+            for (int k = 0; k < V; ++k) {
+                df_add_prod(acc[k], av, xh[k]);
+                df_add_f(acc[k], av * xl[k]);
             }
         }
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
+        for (int k = 0; k < V; ++k) {
             float sh, se;
-            two_sum(bi[c], -acc[c].hi, sh, se);
-            ri[c] = __fadd_rn(sh, __fsub_rn(se, acc[c].lo));
+            two_sum(bi[k], -acc[k].hi, sh, se);
+            out[k] = __fadd_rn(sh, __fsub_rn(se, acc[k].lo));
         }
     } else {
-        double acc[D], xv[D];
-        load_row_rw<double, D>(a.x, i, xv);
+        double acc[V], xv[V];
         const double ad = a.A.adiag[i];
+        ldv_rw<double, V>(a.x + i * D + c0, xv);
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = ad * xv[c];
-        for (int k = 0; k < len; ++k) {
-            const int64_t idx = base + (int64_t)k * 32 + lane;
-            const int j = a.A.col[idx];
+        for (int k = 0; k < V; ++k) acc[k] = ad * xv[k];
+        for (int s = 0; s < len; ++s) {
+            const int64_t idx = base + s;
             const double av = a.A.aoff[idx];
-            load_row_rw<double, D>(a.x, j, xv);
+            ldv_rw<double, V>(a.x + (int64_t)a.A.col[idx] * D + c0, xv);
 #pragma unroll
-            for (int c = 0; c < D; ++c) acc[c] = fma(av, xv[c], acc[c]);
+            for (int k = 0; k < V; ++k) acc[k] = fma(av, xv[k], acc[k]);
         }
 #pragma unroll
-        for (int c = 0; c < D; ++c) ri[c] = bi[c] - acc[c];
+        for (int k = 0; k < V; ++k) out[k] = bi[k] - acc[k];
     }
 }
 
-// ---- kernels -------------------------------------------------------------
+#define PFE_ROW_LOOP(T_, D_)                                                                               \
+    using SW = SubWarp<T_, D_>;                                                                            \
+    constexpr int V = SW::V;                                                                               \
+    const SW lm;                                                                                           \
+    const int64_t warp_g = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);                              \
+    const int64_t warps_total = (int64_t)gridDim.x * kWarps;                                               \
+    for (int64_t g = warp_g; g * SW::RPW < a.A.n; g += warps_total)
 
-// Start of a solve: r = b - A y, p = z = D_A^{-1} r, norms of b, r and r.z.
-template <typename T, int D>
+// ---- kernels ----------------------------------------------------------------
+
+// Start of a solve: r = b - A y, norms of b and r, r.z with z = D_A^{-1} r.
+// With the FSAI preconditioner (PRE = 1) z = G^T G r is made by k_fsai_t /
+// k_fsai_z, which also finish the start of the solve.
+template <typename T, int D, int PRE>
 __global__ void __launch_bounds__(kBlock) k_pcg_init(PcgArgs<T> a) {
     using A = Acc<T>;
     using AT = typename A::type;
-    AT acc[3 * D];  // r.z | r.r | b.b
+    using SWt = SubWarp<T, D>;
+    AT acc[3][SWt::V];  // r.z | r.r | b.b
 #pragma unroll
-    for (int c = 0; c < 3 * D; ++c) acc[c] = A::zero();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t s = (int64_t)blockIdx.x * kWarps + warp; s < a.A.n_slices; s += (int64_t)gridDim.x * kWarps) {
-        const int64_t i = s * 32 + lane;
-        if (i >= a.A.n) continue;
-        T ri[D], bi[D], zi[D];
-        true_residual_row<T, D>(a, s, lane, i, ri);
-        load_row<T, D>(a.b, i, bi);
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int k = 0; k < SWt::V; ++k) acc[q][k] = A::zero();
+    PFE_ROW_LOOP(T, D) {
+        const int64_t i = g * SW::RPW + lm.r;
+        if (!lm.active || i >= a.A.n) continue;
+        const int c0 = lm.cg * V;
+        T ri[V], bi[V];
+        true_residual<T, D, V>(a, i, c0, ri);
+        ldv_rw<T, V>(a.b + i * D + c0, bi);
         const T dv = a.A.dinv[i];
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            zi[c] = dv * ri[c];
-            A::add_prod(acc[c], ri[c], zi[c]);
-            A::add_prod(acc[D + c], ri[c], ri[c]);
-            A::add_prod(acc[2 * D + c], bi[c], bi[c]);
+        for (int k = 0; k < V; ++k) {
+            const T zi = dv * ri[k];
+            A::add_prod(acc[0][k], ri[k], zi);
+            A::add_prod(acc[1][k], ri[k], ri[k]);
+            A::add_prod(acc[2][k], bi[k], bi[k]);
         }
-        store_row<T, D>(a.r, i, ri);
-        store_row<T, D>(a.p, i, zi);
+        stv<T, V>(a.r + i * D + c0, ri);
     }
     __shared__ double tot[3 * D];
-    if (grid_sum<T, 3 * D>(acc, a.part, &a.ctl->ticket[2], tot)) {
+    if (grid_sum_cols<T, D, 3>(acc, a.part, &a.ctl->ticket[2], tot)) {
         if (threadIdx.x == 0) {
             PcgCtl *ctl = a.ctl;
             ctl->iter = 0;
             ctl->error = 0;
             ctl->refresh_now = 0;
+            ctl->p_ready = 1;
+            ctl->xpending = 0;
             for (int c = 0; c < D; ++c) {
                 double bn = sqrt(tot[2 * D + c]);
                 ctl->bnorm[c] = bn > 0.0 ? bn : 1.0;
                 ctl->alpha[c] = 0.0;
             }
-            finish_scalars(ctl, tot, tot + D, D, true, a.cond, a.use_cond);
-        }
-    }
-}
-
-// q = A p and the column dots p.q -> alpha.
-template <typename T, int D>
-__global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
-    if (*(volatile int *)&a.ctl->done) return;
-    using A = Acc<T>;
-    using AT = typename A::type;
-    AT pq[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) pq[c] = A::zero();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t s = (int64_t)blockIdx.x * kWarps + warp; s < a.A.n_slices; s += (int64_t)gridDim.x * kWarps) {
-        const int64_t i = s * 32 + lane;
-        if (i >= a.A.n) continue;
-        const int64_t base = a.A.slice_ptr[s];
-        const int len = (a.A.slice_ptr[s + 1] - (int)base) >> 5;
-        T pi[D], acc[D], pj[D];
-        load_row<T, D>(a.p, i, pi);
-        const T ad = a.A.adiag[i];
-#pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = ad * pi[c];
-        for (int k = 0; k < len; ++k) {
-            const int64_t idx = base + (int64_t)k * 32 + lane;
-            const int j = a.A.col[idx];
-            const T av = a.A.aoff[idx];
-            load_row<T, D>(a.p, j, pj);
-#pragma unroll
-            for (int c = 0; c < D; ++c) acc[c] = fma(av, pj[c], acc[c]);
-        }
-        store_row<T, D>(a.q, i, acc);
-#pragma unroll
-        for (int c = 0; c < D; ++c) A::add_prod(pq[c], pi[c], acc[c]);
-    }
-    __shared__ double tot[D];
-    if (grid_sum<T, D>(pq, a.part, &a.ctl->ticket[0], tot)) {
-        if (threadIdx.x == 0) {
-            PcgCtl *ctl = a.ctl;
-            for (int c = 0; c < D; ++c) {
-                if (!ctl->active[c]) {
-                    ctl->alpha[c] = 0.0;
-                    continue;
-                }
-                double pqc = tot[c];
-                if (!(pqc > 0.0) || !(pqc < INFINITY)) {
-                    ctl->error = PFE_ENUMERIC;
-                    ctl->alpha[c] = 0.0;
-                } else {
-                    ctl->alpha[c] = ctl->rz[c] / pqc;
-                }
+            if (PRE == 0) {
+                finish_scalars(ctl, tot, tot + D, D, true, a.cond, a.use_cond);
+            } else {
+                ctl->zstart = 1;
+                ctl->done = 0;
             }
         }
     }
 }
 
-// y += alpha p, r -= alpha q, and the dots r.z, r.r of the new residual.
+// float4 / double2 views of flat arrays
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+    static constexpr int N = 4;
+    using V = float4;
+    __device__ static __forceinline__ void get(const V &v, float (&o)[4]) {
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    __device__ static __forceinline__ V make(const float (&o)[4]) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+template <>
+struct Vec<double> {
+    static constexpr int N = 2;
+    using V = double2;
+    __device__ static __forceinline__ void get(const V &v, double (&o)[2]) {
+        o[0] = v.x; o[1] = v.y;
+    }
+    __device__ static __forceinline__ V make(const double (&o)[2]) { return make_double2(o[0], o[1]); }
+};
+
+// p = z + beta p (p = z right after k_pcg_init) and the delayed solution
+// update y += alpha_prev p_prev, elementwise and in place (flat float4 /
+// double2 traversal; the grid makes every thread meet fixed columns).
+// z = D_A^{-1} r (Jacobi) or the stored G^T G r (FSAI, PRE = 1).
+template <typename T, int D, int PRE>
+__global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
+    const PcgCtl *ctl = a.ctl;
+    if (*(volatile const int *)&ctl->done) return;
+    const int p_ready = ctl->p_ready, xpending = ctl->xpending;
+    __shared__ T sbeta[D], salpha[D];
+    if (threadIdx.x < D) {
+        sbeta[threadIdx.x] = p_ready ? T(0) : (T)ctl->beta[threadIdx.x];
+        salpha[threadIdx.x] = (T)ctl->alpha[threadIdx.x];
+    }
+    __syncthreads();
+    using VT = Vec<T>;
+    constexpr int VN = VT::N;
+    const int64_t nel = a.A.n * D, nvec = nel / VN;
+    const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
+    T be[VN], al[VN];
+#pragma unroll
+    for (int u = 0; u < VN; ++u) {
+        const int c = (int)((tid * VN + u) % D);
+        be[u] = sbeta[c];
+        al[u] = salpha[c];
+    }
+    using V4 = typename VT::V;
+    V4 *p4 = reinterpret_cast<V4 *>(a.p[0]);
+    const V4 *z4 = reinterpret_cast<const V4 *>(PRE == 0 ? a.r : a.z);
+    V4 *x4 = reinterpret_cast<V4 *>(a.x);
+    float4 *xl4 = reinterpret_cast<float4 *>(a.xlo);  // float path: VN == 4
+    for (int64_t v = tid; v < nvec; v += nthr) {
+        T pv[VN], zv[VN];
+        VT::get(p4[v], pv);
+        VT::get(z4[v], zv);
+        if constexpr (PRE == 0) {
+#pragma unroll
+            for (int u = 0; u < VN; ++u) zv[u] = a.A.dinv[(v * VN + u) / D] * zv[u];
+        }
+        if (xpending) {
+            T xv[VN];
+            float xl[VN];
+            VT::get(x4[v], xv);
+            if constexpr (std::is_same_v<T, float>) {
+                const float4 t = xl4[v];
+                xl[0] = t.x; xl[1] = t.y; xl[2] = t.z; xl[3] = t.w;
+            }
+#pragma unroll
+            for (int u = 0; u < VN; ++u) axpy_hilo<T>(xv[u], xl[u], al[u], pv[u]);
+            x4[v] = VT::make(xv);
+            if constexpr (std::is_same_v<T, float>) xl4[v] = make_float4(xl[0], xl[1], xl[2], xl[3]);
+        }
+#pragma unroll
+        for (int u = 0; u < VN; ++u) pv[u] = p_ready ? zv[u] : zv[u] + be[u] * pv[u];
+        p4[v] = VT::make(pv);
+    }
+    if (tid < nel - nvec * VN) {  // tail elements
+        const int64_t e = nvec * VN + tid;
+        const int c = (int)(e % D);
+        const T z = PRE == 0 ? a.A.dinv[e / D] * a.r[e] : a.z[e];
+        T po = a.p[0][e];
+        if (xpending) {
+            T xh = a.x[e];
+            float xl = 0.f;
+            if constexpr (std::is_same_v<T, float>) xl = a.xlo[e];
+            axpy_hilo<T>(xh, xl, salpha[c], po);
+            a.x[e] = xh;
+            if constexpr (std::is_same_v<T, float>) a.xlo[e] = xl;
+        }
+        a.p[0][e] = p_ready ? z : z + sbeta[c] * po;
+    }
+}
+
+// q = A p and the column dots p.q -> alpha.  Only p is gathered; the matrix
+// slots of a row are fetched kChunk at a time ahead of the gathers.
+template <typename T, int D>
+__global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
+    const PcgCtl *ctl = a.ctl;
+    if (*(volatile const int *)&ctl->done) return;
+    using A = Acc<T>;
+    using AT = typename A::type;
+    using SWt = SubWarp<T, D>;
+    const T *__restrict__ pp = a.p[0];
+    AT pq[1][SWt::V];
+#pragma unroll
+    for (int k = 0; k < SWt::V; ++k) pq[0][k] = A::zero();
+    PFE_ROW_LOOP(T, D) {
+        const int64_t i = g * SW::RPW + lm.r;
+        if (!lm.active || i >= a.A.n) continue;
+        const int c0 = lm.cg * V;
+        const int64_t ic = i * D + c0;
+        int64_t base;
+        int len;
+        sell_row(a.A.slice_ptr, i, base, len);
+        T pi[V], acc[V];
+        ldv<T, V>(pp + ic, pi);
+        const T ad = a.A.adiag[i];
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] = ad * pi[k];
+        for (int k0 = 0; k0 < len; k0 += kChunk) {
+            int jj[kChunk];
+            T av[kChunk], pj[kChunk][V];
+            load_slots<T, kChunk>(a.A.col, a.A.aoff, base, k0, len, (int)i, jj, av);
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) ldv<T, V>(pp + (int64_t)jj[u] * D + c0, pj[u]);
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u)
+#pragma unroll
+                for (int k = 0; k < V; ++k) acc[k] = fma(av[u], pj[u][k], acc[k]);
+        }
+        stv<T, V>(a.q + ic, acc);
+#pragma unroll
+        for (int k = 0; k < V; ++k) A::add_prod(pq[0][k], pi[k], acc[k]);
+    }
+    __shared__ double tot[D];
+    if (grid_sum_cols<T, D, 1>(pq, a.part, &a.ctl->ticket[0], tot)) {
+        if (threadIdx.x == 0) {
+            PcgCtl *w = a.ctl;
+            for (int c = 0; c < D; ++c) {
+                if (!w->active[c]) {
+                    w->alpha[c] = 0.0;
+                    continue;
+                }
+                const double pqc = tot[c];
+                if (!(pqc > 0.0) || !(pqc < INFINITY)) {
+                    w->error = PFE_ENUMERIC;
+                    w->alpha[c] = 0.0;
+                } else {
+                    w->alpha[c] = w->rz[c] / pqc;
+                }
+            }
+            w->p_ready = 0;
+            w->xpending = 1;
+        }
+    }
+}
+
+// Flat vectorised traversal of an n x D array: thread t handles the VEC
+// consecutive elements starting at VEC*t, then strides by VEC * (threads of
+// the grid).  The grid is a multiple of D / gcd(D, VEC*kBlock) blocks, so a
+// thread always meets the same VEC columns and keeps one accumulator per
+// element slot; the tail (n*D mod VEC elements) goes to the first threads.
+// Per-block column sums of flat accumulators: acc[q][u] of thread t belongs to
+// element VEC*(blockIdx*kBlock + t) + u (+ grid strides, same column), and
+// tacc[q] to tail element tcol (or none).  Result per (q, column) in out,
+// the last block reduces all blocks.  Fixed order.
+template <typename T, int D, int NQ>
+__device__ __forceinline__ bool grid_sum_flat(typename Acc<T>::type (&acc)[NQ][Vec<T>::N],
+                                              typename Acc<T>::type (&tacc)[NQ], int tcol, void *part_v,
+                                              unsigned *ticket, double *out) {
+    using A = Acc<T>;
+    using AT = typename A::type;
+    constexpr int VN = Vec<T>::N;
+    constexpr int NV = NQ * D;
+    __shared__ AT red[NQ][kBlock * VN];
+    __shared__ AT tred[NQ][kBlock];
+    __shared__ int tcols[kBlock];
+    __shared__ AT sh[NV];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+        for (int u = 0; u < VN; ++u) red[q][threadIdx.x * VN + u] = acc[q][u];
+        tred[q][threadIdx.x] = tacc[q];
+    }
+    tcols[threadIdx.x] = tcol;
+    __syncthreads();
+    const int64_t e0 = (int64_t)blockIdx.x * kBlock * VN;  // first element of this block
+    for (int t = threadIdx.x; t < NV; t += blockDim.x) {
+        const int q = t / D, c = t - q * D;
+        AT s = A::zero();
+        // positions p with (e0 + p) % D == c
+        int p0 = (int)((c - (e0 % D) + D) % D);
+        for (int p = p0; p < kBlock * VN; p += D) A::add(s, red[q][p]);
+        for (int k = 0; k < kBlock; ++k)
+            if (tcols[k] == c) A::add(s, tred[q][k]);
+        sh[t] = s;
+    }
+    __syncthreads();
+    AT *part = reinterpret_cast<AT *>(part_v);
+    for (int t = threadIdx.x; t < NV; t += blockDim.x) part[(int64_t)blockIdx.x * NV + t] = sh[t];
+    if (!last_block_arrives(ticket)) return false;
+    for (int t = threadIdx.x; t < NV; t += blockDim.x) {
+        AT s = A::zero();
+        for (int b = 0; b < (int)gridDim.x; ++b) A::add(s, ld_part<A, AT>(part + (int64_t)b * NV + t));
+        out[t] = A::to_double(s);
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    __syncthreads();
+    return true;
+}
+
+// r -= alpha q and the dots r.z, r.r of the new residual -> beta, convergence.
+// Sub-warp mapping (cheap per-column block sums), two row groups per step.
 template <typename T, int D>
 __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
     using A = Acc<T>;
     using AT = typename A::type;
-    __shared__ T alpha[D];
-    if (threadIdx.x < D) alpha[threadIdx.x] = (T)a.ctl->alpha[threadIdx.x];
+    using SWt = SubWarp<T, D>;
+    __shared__ T salpha[D];
+    if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.ctl->alpha[threadIdx.x];
     __syncthreads();
-    AT acc[2 * D];
+    AT acc[2][SWt::V];
 #pragma unroll
-    for (int c = 0; c < 2 * D; ++c) acc[c] = A::zero();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t s = (int64_t)blockIdx.x * kWarps + warp; s < a.A.n_slices; s += (int64_t)gridDim.x * kWarps) {
-        const int64_t i = s * 32 + lane;
-        if (i >= a.A.n) continue;
-        T xi[D], pi[D], ri[D], qi[D];
-        load_row_rw<T, D>(a.x, i, xi);
-        load_row_rw<T, D>(a.p, i, pi);
-        load_row_rw<T, D>(a.r, i, ri);
-        load_row_rw<T, D>(a.q, i, qi);
-        const T dv = a.A.dinv[i];
-        if constexpr (std::is_same_v<T, float>) {
-            float xl[D];
-            load_row_rw<float, D>(a.xlo, i, xl);
+    for (int q = 0; q < 2; ++q)
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                // (hi, lo) += alpha * p with the product and sum errors kept in lo
-                float dlt = __fmul_rn(alpha[c], pi[c]);
-                float de = __fmaf_rn(alpha[c], pi[c], -dlt);
-                float sh, se;
-                two_sum(xi[c], dlt, sh, se);
-                float lo = __fadd_rn(xl[c], __fadd_rn(se, de));
-                float h2 = __fadd_rn(sh, lo);  // renormalise
-                xl[c] = __fsub_rn(lo, __fsub_rn(h2, sh));
-                xi[c] = h2;
-                ri[c] = fmaf(-alpha[c], qi[c], ri[c]);
+        for (int k = 0; k < SWt::V; ++k) acc[q][k] = A::zero();
+    {
+        using SW = SWt;
+        constexpr int V = SW::V;
+        const SW lm;
+        const int64_t warp_g = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+        const int64_t warps_total = (int64_t)gridDim.x * kWarps;
+        const int c0 = lm.cg * V;
+        T al[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) al[k] = salpha[c0 + k];
+        for (int64_t g = warp_g; g * SW::RPW < a.A.n; g += 2 * warps_total) {
+            T rv[2][V], qv[2][V], dv[2];
+            bool ok[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t i = (g + h * warps_total) * SW::RPW + lm.r;
+                ok[h] = lm.active && i < a.A.n;
+                const int64_t ic = (ok[h] ? i : 0) * D + c0;
+                ldv<T, V>(a.r + ic, rv[h]);
+                ldv<T, V>(a.q + ic, qv[h]);
+                dv[h] = a.A.dinv[ok[h] ? i : 0];
             }
-            store_row<float, D>(a.xlo, i, xl);
-        } else {
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                xi[c] = fma(alpha[c], pi[c], xi[c]);
-                ri[c] = fma(-alpha[c], qi[c], ri[c]);
+            for (int h = 0; h < 2; ++h) {
+                if (!ok[h]) continue;
+                const int64_t i = (g + h * warps_total) * SW::RPW + lm.r;
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const T ri = fma(-al[k], qv[h][k], rv[h][k]);
+                    A::add_prod(acc[0][k], ri, dv[h] * ri);
+                    A::add_prod(acc[1][k], ri, ri);
+                    rv[h][k] = ri;
+                }
+                stv<T, V>(a.r + i * D + c0, rv[h]);
             }
         }
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            T z = dv * ri[c];
-            A::add_prod(acc[c], ri[c], z);
-            A::add_prod(acc[D + c], ri[c], ri[c]);
-        }
-        store_row<T, D>(a.x, i, xi);
-        store_row<T, D>(a.r, i, ri);
     }
     __shared__ double tot[2 * D];
-    if (grid_sum<T, 2 * D>(acc, a.part, &a.ctl->ticket[1], tot)) {
+    if (grid_sum_cols<T, D, 2>(acc, a.part, &a.ctl->ticket[1], tot)) {
         if (threadIdx.x == 0) {
             PcgCtl *ctl = a.ctl;
             ctl->iter += 1;
             if (!ctl->error && ctl->refresh > 0 && (ctl->iter % ctl->refresh) == 0) {
-                ctl->refresh_now = 1;  // k_refresh finishes this iteration
+                ctl->refresh_now = 1;  // k_xflush + k_refresh finish this iteration
             } else {
                 finish_scalars(ctl, tot, tot + D, D, false, a.cond, a.use_cond);
             }
+        }
+    }
+}
+
+// y += alpha p with the direction of the last k_spmm.  In the loop body it
+// runs only before a refresh; after the loop it applies the final update.
+template <typename T, int D>
+__global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush) {
+    const PcgCtl *ctl = a.ctl;
+    if (!*(volatile const int *)&ctl->xpending) return;
+    if (!final_flush && !*(volatile const int *)&ctl->refresh_now) return;
+    __shared__ T salpha[D];
+    if (threadIdx.x < D) salpha[threadIdx.x] = (T)ctl->alpha[threadIdx.x];
+    __syncthreads();
+    const T *__restrict__ pc = a.p[0];
+    const int64_t nel = a.A.n * D;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < nel; e += (int64_t)gridDim.x * kBlock) {
+        T xh = a.x[e];
+        float xl = 0.f;
+        if constexpr (std::is_same_v<T, float>) xl = a.xlo[e];
+        axpy_hilo<T>(xh, xl, salpha[e % D], pc[e]);
+        a.x[e] = xh;
+        if constexpr (std::is_same_v<T, float>) a.xlo[e] = xl;
+    }
+    // the flag is cleared by whoever reads it next: k_refresh's last block, or
+    // k_pcg_init of the next solve
+    if (final_flush) {
+        if (last_block_arrives(&a.ctl->ticket[3])) {
+            if (threadIdx.x == 0) {
+                a.ctl->xpending = 0;
+                a.ctl->ticket[3] = 0u;
+            }
+        }
+    }
+}
+
+// ---- FSAI preconditioner, z = G^T (G r) --------------------------------------
+// An FSAI iteration is k_pupdate<PRE=1>, k_spmm, k_rupdate (r -= alpha q), k_xflush and
+// k_refresh_f (refresh iterations only), k_fsai_t (t = G r) and k_fsai_z
+// (z = G^T t, the dots r.z and r.r, end of the iteration).
+
+// r -= alpha q, flat and vectorised (no reduction: the dots need z).
+template <typename T, int D>
+__global__ void __launch_bounds__(kBlock) k_rupdate(PcgArgs<T> a) {
+    if (*(volatile int *)&a.ctl->done) return;
+    __shared__ T salpha[D];
+    if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.ctl->alpha[threadIdx.x];
+    __syncthreads();
+    using VT = Vec<T>;
+    constexpr int VN = VT::N;
+    const int64_t nel = a.A.n * D, nvec = nel / VN;
+    const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
+    T al[VN];
+#pragma unroll
+    for (int u = 0; u < VN; ++u) al[u] = salpha[(int)((tid * VN + u) % D)];
+    const typename VT::V *q4 = reinterpret_cast<const typename VT::V *>(a.q);
+    typename VT::V *r4 = reinterpret_cast<typename VT::V *>(a.r);
+    for (int64_t v = tid; v < nvec; v += nthr) {
+        T rv[VN], qv[VN];
+        VT::get(r4[v], rv);
+        VT::get(q4[v], qv);
+#pragma unroll
+        for (int u = 0; u < VN; ++u) rv[u] = fma(-al[u], qv[u], rv[u]);
+        r4[v] = VT::make(rv);
+    }
+    if (tid < nel - nvec * VN) {
+        const int64_t e = nvec * VN + tid;
+        a.r[e] = fma(-salpha[e % D], a.q[e], a.r[e]);
+    }
+}
+
+// Residual replacement without dots (k_fsai_z makes them).
+template <typename T, int D>
+__global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
+    if (!*(volatile int *)&a.ctl->refresh_now) return;
+    PFE_ROW_LOOP(T, D) {
+        const int64_t i = g * SW::RPW + lm.r;
+        if (!lm.active || i >= a.A.n) continue;
+        const int c0 = lm.cg * V;
+        T ri[V];
+        true_residual<T, D, V>(a, i, c0, ri);
+        stv<T, V>(a.r + i * D + c0, ri);
+    }
+    if (last_block_arrives(&a.ctl->ticket[3])) {
+        if (threadIdx.x == 0) {
+            a.ctl->xpending = 0;
+            a.ctl->ticket[3] = 0u;
+        }
+    }
+}
+
+// t = G r: t_i = G_ii r_i + sum over the lower slots (j < i) of G_ij r_j.
+template <typename T, int D>
+__global__ void __launch_bounds__(kBlock) k_fsai_t(PcgArgs<T> a) {
+    if (*(volatile int *)&a.ctl->done) return;
+    PFE_ROW_LOOP(T, D) {
+        const int64_t i = g * SW::RPW + lm.r;
+        if (!lm.active || i >= a.A.n) continue;
+        const int c0 = lm.cg * V;
+        int64_t base;
+        int len;
+        sell_row(a.A.slice_ptr, i, base, len);
+        const int nl = a.kb[i];
+        T acc[V], ri[V];
+        ldv<T, V>(a.r + i * D + c0, ri);
+        const T gd = a.gdiag[i];
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] = gd * ri[k];
+        for (int k0 = 0; k0 < nl; k0 += kChunk) {
+            int jj[kChunk];
+            T gv[kChunk], rj[kChunk][V];
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) {
+                const bool in = k0 + u < nl;
+                const int64_t idx = base + (in ? k0 + u : 0);
+                jj[u] = in ? __ldg(a.A.col + idx) : (int)i;
+                gv[u] = in ? __ldg(a.gslot + idx) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) ldv<T, V>(a.r + (int64_t)jj[u] * D + c0, rj[u]);
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u)
+#pragma unroll
+                for (int k = 0; k < V; ++k) acc[k] = fma(gv[u], rj[u][k], acc[k]);
+        }
+        stv<T, V>(a.t + i * D + c0, acc);
+    }
+}
+
+// z = G^T t: z_i = G_ii t_i + sum over the upper slots (j > i) of G_ji t_j,
+// then the dots r.z, r.r; the last block ends the iteration (or the start of
+// the solve) and decides whether the next iteration refreshes r.
+template <typename T, int D>
+__global__ void __launch_bounds__(kBlock) k_fsai_z(PcgArgs<T> a) {
+    if (*(volatile int *)&a.ctl->done) return;
+    using A = Acc<T>;
+    using AT = typename A::type;
+    using SWt = SubWarp<T, D>;
+    AT acc2[2][SWt::V];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < SWt::V; ++k) acc2[q][k] = A::zero();
+    PFE_ROW_LOOP(T, D) {
+        const int64_t i = g * SW::RPW + lm.r;
+        if (!lm.active || i >= a.A.n) continue;
+        const int c0 = lm.cg * V;
+        int64_t base;
+        int len;
+        sell_row(a.A.slice_ptr, i, base, len);
+        const int nl = a.kb[i];
+        T acc[V], ti[V], ri[V];
+        ldv<T, V>(a.t + i * D + c0, ti);
+        const T gd = a.gdiag[i];
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] = gd * ti[k];
+        for (int k0 = nl; k0 < len; k0 += kChunk) {
+            int jj[kChunk];
+            T gv[kChunk], tj[kChunk][V];
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) {
+                const bool in = k0 + u < len;
+                const int64_t idx = base + (in ? k0 + u : 0);
+                jj[u] = in ? __ldg(a.A.col + idx) : (int)i;
+                gv[u] = in ? __ldg(a.gslot + idx) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) ldv<T, V>(a.t + (int64_t)jj[u] * D + c0, tj[u]);
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u)
+#pragma unroll
+                for (int k = 0; k < V; ++k) acc[k] = fma(gv[u], tj[u][k], acc[k]);
+        }
+        stv<T, V>(a.z + i * D + c0, acc);
+        ldv<T, V>(a.r + i * D + c0, ri);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            A::add_prod(acc2[0][k], ri[k], acc[k]);
+            A::add_prod(acc2[1][k], ri[k], ri[k]);
+        }
+    }
+    __shared__ double tot[2 * D];
+    if (grid_sum_cols<T, D, 2>(acc2, a.part, &a.ctl->ticket[1], tot)) {
+        if (threadIdx.x == 0) {
+            PcgCtl *ctl = a.ctl;
+            const bool start = ctl->zstart != 0;
+            ctl->zstart = 0;
+            if (!start) ctl->iter += 1;
+            finish_scalars(ctl, tot, tot + D, D, start, a.cond, a.use_cond);
+            ctl->refresh_now = (ctl->refresh > 0 && ((ctl->iter + 1) % ctl->refresh) == 0) ? 1 : 0;
         }
     }
 }
@@ -410,81 +926,66 @@ __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
     if (!*(volatile int *)&a.ctl->refresh_now) return;
     using A = Acc<T>;
     using AT = typename A::type;
-    AT acc[2 * D];
+    using SWt = SubWarp<T, D>;
+    AT acc[2][SWt::V];
 #pragma unroll
-    for (int c = 0; c < 2 * D; ++c) acc[c] = A::zero();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t s = (int64_t)blockIdx.x * kWarps + warp; s < a.A.n_slices; s += (int64_t)gridDim.x * kWarps) {
-        const int64_t i = s * 32 + lane;
-        if (i >= a.A.n) continue;
-        T ri[D];
-        true_residual_row<T, D>(a, s, lane, i, ri);
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < SWt::V; ++k) acc[q][k] = A::zero();
+    PFE_ROW_LOOP(T, D) {
+        const int64_t i = g * SW::RPW + lm.r;
+        if (!lm.active || i >= a.A.n) continue;
+        const int c0 = lm.cg * V;
+        T ri[V];
+        true_residual<T, D, V>(a, i, c0, ri);
         const T dv = a.A.dinv[i];
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            T z = dv * ri[c];
-            A::add_prod(acc[c], ri[c], z);
-            A::add_prod(acc[D + c], ri[c], ri[c]);
+        for (int k = 0; k < V; ++k) {
+            A::add_prod(acc[0][k], ri[k], dv * ri[k]);
+            A::add_prod(acc[1][k], ri[k], ri[k]);
         }
-        store_row<T, D>(a.r, i, ri);
+        stv<T, V>(a.r + i * D + c0, ri);
     }
     __shared__ double tot[2 * D];
-    if (grid_sum<T, 2 * D>(acc, a.part, &a.ctl->ticket[3], tot)) {
+    if (grid_sum_cols<T, D, 2>(acc, a.part, &a.ctl->ticket[3], tot)) {
         if (threadIdx.x == 0) {
             a.ctl->refresh_now = 0;
+            a.ctl->xpending = 0;
             finish_scalars(a.ctl, tot, tot + D, D, false, a.cond, a.use_cond);
         }
     }
 }
 
-// p = z + beta p, z = D_A^{-1} r.
+// y = A x without dots (pfe_apply_A).
 template <typename T, int D>
-__global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
-    if (*(volatile int *)&a.ctl->done) return;
-    __shared__ T beta[D];
-    if (threadIdx.x < D) beta[threadIdx.x] = (T)a.ctl->beta[threadIdx.x];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t s = (int64_t)blockIdx.x * kWarps + warp; s < a.A.n_slices; s += (int64_t)gridDim.x * kWarps) {
-        const int64_t i = s * 32 + lane;
-        if (i >= a.A.n) continue;
-        T ri[D], pi[D];
-        load_row_rw<T, D>(a.r, i, ri);
-        load_row_rw<T, D>(a.p, i, pi);
-        const T dv = a.A.dinv[i];
+__global__ void __launch_bounds__(kBlock) k_apply(SysView<T> Av, const T *__restrict__ x, T *__restrict__ y) {
+    struct {
+        SysView<T> A;
+    } a{Av};
+    PFE_ROW_LOOP(T, D) {
+        const int64_t i = g * SW::RPW + lm.r;
+        if (!lm.active || i >= a.A.n) continue;
+        const int c0 = lm.cg * V;
+        int64_t base;
+        int len;
+        sell_row(a.A.slice_ptr, i, base, len);
+        T acc[V], xv[V];
+        ldv<T, V>(x + i * D + c0, xv);
+        const T ad = a.A.adiag[i];
 #pragma unroll
-        for (int c = 0; c < D; ++c) pi[c] = fma(beta[c], pi[c], dv * ri[c]);
-        store_row<T, D>(a.p, i, pi);
-    }
-}
-
-// y = A x without dots (pfe_apply_A and kernel timing).
-template <typename T, int D>
-__global__ void __launch_bounds__(kBlock) k_apply(SysView<T> A, const T *__restrict__ x, T *__restrict__ y) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t s = (int64_t)blockIdx.x * kWarps + warp; s < A.n_slices; s += (int64_t)gridDim.x * kWarps) {
-        const int64_t i = s * 32 + lane;
-        if (i >= A.n) continue;
-        const int64_t base = A.slice_ptr[s];
-        const int len = (A.slice_ptr[s + 1] - (int)base) >> 5;
-        T acc[D], xj[D];
-        load_row<T, D>(x, i, xj);
-        const T ad = A.adiag[i];
+        for (int k = 0; k < V; ++k) acc[k] = ad * xv[k];
+        for (int s = 0; s < len; ++s) {
+            const int64_t idx = base + s;
+            const T av = a.A.aoff[idx];
+            ldv<T, V>(x + (int64_t)a.A.col[idx] * D + c0, xv);
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = ad * xj[c];
-        for (int k = 0; k < len; ++k) {
-            const int64_t idx = base + (int64_t)k * 32 + lane;
-            const int j = A.col[idx];
-            const T av = A.aoff[idx];
-            load_row<T, D>(x, j, xj);
-#pragma unroll
-            for (int c = 0; c < D; ++c) acc[c] = fma(av, xj[c], acc[c]);
+            for (int k = 0; k < V; ++k) acc[k] = fma(av, xv[k], acc[k]);
         }
-        store_row<T, D>(y, i, acc);
+        stv<T, V>(y + i * D + c0, acc);
     }
 }
 
-// ---- host side -----------------------------------------------------------
+// ---- host side -----------------------------------------------------------------
 
 template <typename T>
 PcgArgs<T> pcg_args(pfe_ctx *c, PcgLaunch L) {
@@ -493,19 +994,67 @@ PcgArgs<T> pcg_args(pfe_ctx *c, PcgLaunch L) {
     a.x = (T *)c->wk.Y;
     a.xlo = c->wk.Ylo;
     a.r = (T *)c->wk.R;
-    a.p = (T *)c->wk.Pd;
+    a.p[0] = (T *)c->wk.Pd;
+    a.p[1] = (T *)c->wk.Pd;
     a.q = (T *)c->wk.Q;
     a.b = (const T *)c->wk.RHS;
     a.part = c->wk.partials;
     a.ctl = c->ctl;
     a.cond = L.cond;
     a.use_cond = L.use_cond;
+    a.z = (T *)c->fsai.z;
+    a.t = (T *)c->fsai.t;
+    a.gdiag = nullptr;
+    a.gslot = nullptr;
+    if constexpr (std::is_same_v<T, float>) {
+        a.gdiag = c->fsai.gdiag;
+        a.gslot = c->fsai.gslot;
+    }
+    a.kb = c->fsai.kb;
     return a;
+}
+
+// blocks that cover every row group once / every vector of a flat traversal once
+template <typename T, int D>
+int64_t rows_need(const pfe_ctx *c) {
+    const int64_t groups = (c->g.n + SubWarp<T, D>::RPW - 1) / SubWarp<T, D>::RPW;
+    return (groups + kWarps - 1) / kWarps;
+}
+template <typename T, int D>
+int64_t flat_need(const pfe_ctx *c) {
+    return (c->g.n * D / Vec<T>::N + kBlock - 1) / kBlock;
+}
+// flat kernels that keep per-column state need (grid * kBlock * VEC) % D == 0
+template <typename T, int D>
+constexpr int flat_mult() {
+    int a = D, b = kBlock * Vec<T>::N;
+    while (b) {
+        const int r = a % b;
+        a = b;
+        b = r;
+    }
+    return D / a;
+}
+
+// FSAI runs on the float path only (the FP64 path is the plain Jacobi reference)
+template <typename T>
+bool use_fsai(const pfe_ctx *c) {
+    return std::is_same_v<T, float> && c->fsai.enabled;
 }
 
 template <typename T, int D>
 pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
-    k_pcg_init<T, D><<<c->grid_rows, kBlock, 0, s>>>(pcg_args<T>(c, L));
+    PcgArgs<T> a = pcg_args<T>(c, L);
+    if constexpr (std::is_same_v<T, float>) {
+        if (use_fsai<T>(c)) {
+            k_pcg_init<T, D, 1><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            k_fsai_t<T, D><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            k_fsai_z<T, D><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            PFE_CUDA_TRY(c, cudaGetLastError());
+            return PFE_OK;
+        }
+    }
+    k_pcg_init<T, D, 0><<<wave_grid(c, G_INIT, k_pcg_init<T, D, 0>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
     PFE_CUDA_TRY(c, cudaGetLastError());
     return PFE_OK;
 }
@@ -513,28 +1062,52 @@ pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
 template <typename T, int D>
 pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
     PcgArgs<T> a = pcg_args<T>(c, L);
+    if constexpr (std::is_same_v<T, float>) {
+        if (use_fsai<T>(c)) {
+            for (int u = 0; u < iters; ++u) {
+                k_pupdate<T, D, 1><<<wave_grid(c, G_PUPD_F, k_pupdate<T, D, 1>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0, s>>>(a);
+                k_spmm<T, D><<<wave_grid(c, G_SPMM, k_spmm<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+                k_rupdate<T, D><<<wave_grid(c, G_RUPDATE, k_rupdate<T, D>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0, s>>>(a);
+                k_xflush<T, D><<<wave_grid(c, G_XFLUSH, k_xflush<T, D>, flat_need<T, D>(c)), kBlock, 0, s>>>(a, 0);
+                k_refresh_f<T, D><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+                k_fsai_t<T, D><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+                k_fsai_z<T, D><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            }
+            PFE_CUDA_TRY(c, cudaGetLastError());
+            return PFE_OK;
+        }
+    }
     for (int u = 0; u < iters; ++u) {
-        k_spmm<T, D><<<c->grid_rows, kBlock, 0, s>>>(a);
-        k_update<T, D><<<c->grid_rows, kBlock, 0, s>>>(a);
-        k_refresh<T, D><<<c->grid_rows, kBlock, 0, s>>>(a);
-        k_pupdate<T, D><<<c->grid_rows, kBlock, 0, s>>>(a);
+        k_pupdate<T, D, 0><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0, s>>>(a);
+        k_spmm<T, D><<<wave_grid(c, G_SPMM, k_spmm<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        k_update<T, D><<<wave_grid(c, G_UPDATE, k_update<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        k_xflush<T, D><<<wave_grid(c, G_XFLUSH, k_xflush<T, D>, flat_need<T, D>(c)), kBlock, 0, s>>>(a, 0);
+        k_refresh<T, D><<<wave_grid(c, G_REFRESH, k_refresh<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
     }
     PFE_CUDA_TRY(c, cudaGetLastError());
     return PFE_OK;
 }
 
 template <typename T, int D>
+pfe_status final_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
+    k_xflush<T, D><<<wave_grid(c, G_XFLUSH, k_xflush<T, D>, flat_need<T, D>(c)), kBlock, 0, s>>>(pcg_args<T>(c, L), 1);
+    PFE_CUDA_TRY(c, cudaGetLastError());
+    return PFE_OK;
+}
+
+template <typename T, int D>
 pfe_status apply_T(pfe_ctx *c, cudaStream_t s, const void *x, void *y) {
-    k_apply<T, D><<<c->grid_rows, kBlock, 0, s>>>(sys_view<T>(c), (const T *)x, (T *)y);
+    k_apply<T, D><<<wave_grid(c, G_APPLY, k_apply<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(sys_view<T>(c), (const T *)x, (T *)y);
     PFE_CUDA_TRY(c, cudaGetLastError());
     return PFE_OK;
 }
 
 // Average duration of `reps` back-to-back launches of one PCG kernel on the
 // current vectors, bracketed by CUDA events on stream s.  Uses a scratch
-// control block (every column active) and scratch copies of y and r, so the
-// iteration state is left as it was.  which: 0 = k_spmm, 1 = k_update,
-// 2 = k_pupdate.
+// control block (every column active, a steady-state iteration: direction
+// update and delayed solution update both on) and scratch copies of y, r and
+// the direction buffers, so the iteration state is left as it was.
+// which: 0 = k_spmm, 1 = k_update.
 template <typename T, int D>
 pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     PcgCtl h;
@@ -542,6 +1115,8 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     h.max_iter = 1 << 30;
     h.ncols = D;
     h.tol = 0.0;
+    h.p_ready = 0;
+    h.xpending = 1;
     for (int k = 0; k < D; ++k) {
         h.active[k] = 1;
         h.rz[k] = 1.0;
@@ -551,20 +1126,19 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     }
     const int64_t nd = c->g.n * (int64_t)D;
     PcgCtl *dctl = nullptr;
-    T *xs = nullptr, *rs = nullptr;
+    T *xs = nullptr, *rs = nullptr, *p0 = nullptr, *p1 = nullptr;
     float *xls = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     pfe_status st = PFE_OK;
     auto cleanup = [&]() {
-        if (dctl) cudaFree(dctl);
-        if (xs) cudaFree(xs);
-        if (rs) cudaFree(rs);
-        if (xls) cudaFree(xls);
+        for (void *q : {(void *)dctl, (void *)xs, (void *)rs, (void *)p0, (void *)p1, (void *)xls})
+            if (q) cudaFree(q);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
     if (cudaMalloc((void **)&dctl, sizeof(PcgCtl)) != cudaSuccess || cudaMalloc((void **)&xs, nd * sizeof(T)) != cudaSuccess ||
-        cudaMalloc((void **)&rs, nd * sizeof(T)) != cudaSuccess ||
+        cudaMalloc((void **)&rs, nd * sizeof(T)) != cudaSuccess || cudaMalloc((void **)&p0, nd * sizeof(T)) != cudaSuccess ||
+        cudaMalloc((void **)&p1, nd * sizeof(T)) != cudaSuccess ||
         (std::is_same_v<T, float> && cudaMalloc((void **)&xls, nd * sizeof(float)) != cudaSuccess)) {
         cudaGetLastError();
         cleanup();
@@ -576,19 +1150,24 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     a.x = xs;
     a.r = rs;
     a.xlo = xls;
+    a.p[0] = p0;
+    a.p[1] = p1;
     cudaMemcpyAsync(dctl, &h, sizeof(h), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(xs, c->wk.Y, nd * sizeof(T), cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(rs, c->wk.R, nd * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(p0, c->wk.Pd, nd * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(p1, c->wk.Pd, nd * sizeof(T), cudaMemcpyDeviceToDevice, s);
     if (xls) cudaMemcpyAsync(xls, c->wk.Ylo, nd * sizeof(float), cudaMemcpyDeviceToDevice, s);
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     auto launch = [&]() {
         if (which == 0)
-            k_spmm<T, D><<<c->grid_rows, kBlock, 0, s>>>(a);
+            k_spmm<T, D><<<wave_grid(c, G_SPMM, k_spmm<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
         else if (which == 1)
-            k_update<T, D><<<c->grid_rows, kBlock, 0, s>>>(a);
+            k_update<T, D><<<wave_grid(c, G_UPDATE, k_update<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
         else
-            k_pupdate<T, D><<<c->grid_rows, kBlock, 0, s>>>(a);
+            k_pupdate<T, D, 0><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0>, flat_need<T, D>(c), flat_mult<T, D>()),
+                                 kBlock, 0, s>>>(a);
     };
     launch();  // warm-up
     cudaEventRecord(e0, s);
@@ -611,8 +1190,9 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
 }  // namespace pcgk
 }  // namespace pfe
 
-#define PFE_INSTANTIATE(T, D)                                                                 \
+#define PFE_INSTANTIATE(T, D)                                                                        \
     template pfe_status pfe::pcgk::init_T<T, D>(pfe_ctx *, cudaStream_t, pfe::PcgLaunch);          \
     template pfe_status pfe::pcgk::body_T<T, D>(pfe_ctx *, cudaStream_t, pfe::PcgLaunch, int);     \
+    template pfe_status pfe::pcgk::final_T<T, D>(pfe_ctx *, cudaStream_t, pfe::PcgLaunch);         \
     template pfe_status pfe::pcgk::apply_T<T, D>(pfe_ctx *, cudaStream_t, const void *, void *);     \
     template pfe_status pfe::pcgk::time_T<T, D>(pfe_ctx *, cudaStream_t, int, int, float *);

@@ -270,7 +270,7 @@ pfe_status pstep_T(pfe_ctx *c, cudaStream_t s, int mode) {
     const int64_t ntiles = (a.n + kTile - 1) / kTile;
     const int gblocks = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms * 2);
     k_gram<T, D><<<gblocks, kBlock, 0, s>>>(a);
-    k_papply<T, D><<<c->grid_rows, kBlock, 0, s>>>(a);
+    k_papply<T, D><<<wave_grid(c, G_PAPPLY, k_papply<T, D>, (a.n + kBlock - 1) / kBlock), kBlock, 0, s>>>(a);
     PFE_CUDA_TRY(c, cudaGetLastError());
     return PFE_OK;
 }

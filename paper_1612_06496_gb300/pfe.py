@@ -26,8 +26,9 @@ ARR = {"Y": 0, "P": 1, "B": 2, "BS": 3, "RHS": 4, "DEG": 5, "DIAG": 6}
 EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step", "pfe_pstep", "pfe_solve",
            "pfe_destroy", "pfe_last_error", "pfe_status_string", "pfe_get_info", "pfe_set_stream",
            "pfe_get_array", "pfe_set_array", "pfe_get_edges", "pfe_apply_A", "pfe_solve_system",
-           "pfe_time_kernel"]
-KERNEL = {"spmm": 0, "update": 1, "pupdate": 2, "edge": 3}
+           "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
+           "pfe_adam_update"]
+KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3}
 
 
 class GraphDesc(C.Structure):
@@ -90,6 +91,11 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_apply_A.argtypes = [vp, vp, vp]
     lib.pfe_solve_system.argtypes = [vp, vp, vp, C.POINTER(StepStats)]
     lib.pfe_time_kernel.argtypes = [vp, i32, i32, C.POINTER(dbl)]
+    lib.pfe_fsai_param_count.argtypes = []
+    lib.pfe_fsai_set.argtypes = [vp, vp]
+    lib.pfe_fsai_loss_grad.argtypes = [vp, vp, vp, C.POINTER(dbl)]
+    lib.pfe_fsai_get.argtypes = [vp, vp, vp]
+    lib.pfe_adam_update.argtypes = [vp, vp, vp, vp, i64, i32, dbl, dbl, dbl, dbl, vp]
     for name in EXPORTS:
         if name not in ("pfe_default_params", "pfe_last_error", "pfe_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -281,3 +287,54 @@ class PFE:
         self._check(self.lib.pfe_time_kernel(self.ctx, KERNEL[which], int(reps), C.byref(ms)),
                     f"pfe_time_kernel({which})")
         return ms.value
+
+    # -- learned FSAI preconditioner
+    def fsai_set(self, params):
+        """Build G from the network parameters (None: back to Jacobi)."""
+        if params is None:
+            self._check(self.lib.pfe_fsai_set(self.ctx, None), "pfe_fsai_set")
+            return
+        pp, keep = _ptr_f32(params)
+        self._check(self.lib.pfe_fsai_set(self.ctx, pp), "pfe_fsai_set")
+
+    def fsai_loss_grad(self, params, grad=None):
+        """Kaporin loss of G(params) and its gradient (returns (loss, grad))."""
+        pp, kp = _ptr_f32(params)
+        if grad is None:
+            grad = np.empty(self.lib.pfe_fsai_param_count(), dtype=np.float32)
+        pg, kg = _ptr_f32(grad)
+        loss = C.c_double()
+        self._check(self.lib.pfe_fsai_loss_grad(self.ctx, pp, pg, C.byref(loss)), "pfe_fsai_loss_grad")
+        return loss.value, grad
+
+    def fsai_get(self):
+        info = self.info()
+        gd = np.empty(info["n"], dtype=np.float64)
+        ge = np.empty(info["n_edges"], dtype=np.float64)
+        self._check(self.lib.pfe_fsai_get(self.ctx, gd.ctypes.data, ge.ctypes.data), "pfe_fsai_get")
+        return gd, ge
+
+
+def _ptr_f32(a):
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected C-contiguous float32 array")
+        return a.ctypes.data, a
+    import torch
+    if a.dtype != torch.float32 or not a.is_contiguous():
+        raise TypeError("expected contiguous float32 tensor")
+    return a.data_ptr(), a
+
+
+def fsai_param_count() -> int:
+    return load_library().pfe_fsai_param_count()
+
+
+def adam_update(params, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                eps: float = 1e-8, stream=None):
+    """One Adam step on device float32 tensors (libpfe kernel)."""
+    lib = load_library()
+    st = lib.pfe_adam_update(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), params.numel(),
+                             int(step), float(lr), float(beta1), float(beta2), float(eps), _stream_ptr(stream))
+    if st != PFE_OK:
+        raise PFEError(st, "pfe_adam_update failed")

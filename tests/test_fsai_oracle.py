@@ -1,0 +1,116 @@
+"""Pins of the learned-FSAI oracle: finite differences for every gradient,
+the untrained network equals Jacobi, and the Kaporin gradient vanishes at
+classical FSAI (the known minimiser over the same pattern)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import fsai_oracle as F
+from oracle import pfe_oracle as O
+from synth import ImageSpec, make_problem
+
+
+def _tiny_graph(H=6, W=6, radius=2.0, seed=3):
+    spec = ImageSpec("t", H, W, 3, 0.05, seed=seed, radius=radius, sigma=0.1, d=2)
+    X, _ = make_problem(spec)
+    return O.build_grid_graph(X, H, W, radius, 0.1)
+
+
+def test_untrained_network_is_jacobi():
+    g = _tiny_graph()
+    th = F.init_params(1)
+    Fd, Fe = F.entry_features(g)
+    od, _ = F.mlp_forward(th, Fd)
+    oe, _ = F.mlp_forward(th, Fe)
+    G, gd, ge = F.assemble_G(g, od, oe)
+    Ad = g.A.diagonal()
+    np.testing.assert_allclose(gd, 1.0 / np.sqrt(Ad), rtol=1e-15)
+    assert np.all(ge == 0.0)
+    R = np.random.default_rng(0).standard_normal((g.n, 3))
+    np.testing.assert_allclose(F.fsai_apply(G, R), R / Ad[:, None], rtol=1e-13)
+
+
+def test_features_definition():
+    g = _tiny_graph()
+    Fd, Fe = F.entry_features(g)
+    Ad = g.A.diagonal()
+    k = 7
+    a, b = g.a[k], g.b[k]
+    assert Fe[k, 0] == pytest.approx(g.lam * g.w[k] ** 2 / np.sqrt(Ad[a] * Ad[b]), rel=1e-14)
+    assert Fe[k, 1] == pytest.approx(g.r * g.dvec[b] / Ad[b], rel=1e-14)
+    assert Fe[k, 2] == pytest.approx(g.r * g.dvec[a] / Ad[a], rel=1e-14)
+    i = 20
+    lower = g.b == i
+    assert Fd[i, 0] == pytest.approx(np.sum(Fe[lower, 0] ** 2), rel=1e-13)
+    # rho lies in (0, 1): the Jacobi-scaled coupling of an M-matrix row
+    assert np.all(Fe[:, 0] > 0) and np.all(Fe[:, 0] < 1)
+
+
+def test_kaporin_gradient_matches_finite_differences():
+    g = _tiny_graph(5, 5)
+    G0 = F.classical_fsai(g.A)
+    rng = np.random.default_rng(2)
+    G = G0.copy()
+    G.data = G.data * (1 + 0.1 * rng.standard_normal(G.data.shape))
+    L, dG, _ = F.kaporin(g, G)
+    dG = dG.tocsr()
+    Gc = G.tocoo()
+    for t in rng.choice(Gc.nnz, 15, replace=False):
+        i, j = Gc.row[t], Gc.col[t]
+        # central differences: rounding ~eps*|L|/h plus truncation ~h^2, both
+        # well below 1e-5 relative at this step
+        h = 1e-5 * max(abs(Gc.data[t]), 1e-3)
+        Gp = G.tolil(); Gp[i, j] += h
+        Gm = G.tolil(); Gm[i, j] -= h
+        fd = (F.kaporin(g, Gp.tocsr())[0] - F.kaporin(g, Gm.tocsr())[0]) / (2 * h)
+        assert fd == pytest.approx(dG[i, j], rel=1e-5, abs=1e-9)
+
+
+def test_kaporin_stationary_at_classical_fsai():
+    """Classical FSAI minimises the Kaporin number over the pattern, so the
+    gradient vanishes there and tr(G A G^T) = n."""
+    g = _tiny_graph(7, 6)
+    G = F.classical_fsai(g.A)
+    L, dG, T = F.kaporin(g, G)
+    assert T == pytest.approx(g.n, rel=1e-12)
+    assert np.max(np.abs(dG.toarray())) < 1e-12
+    # and it beats Jacobi and perturbations of itself
+    Lj = F.kaporin(g, sp.diags(1.0 / np.sqrt(g.A.diagonal())).tocsr())[0]
+    assert L < Lj
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        Gp = G.copy()
+        Gp.data = Gp.data * (1 + 0.05 * rng.standard_normal(Gp.data.shape))
+        assert F.kaporin(g, Gp)[0] > L
+
+
+def test_network_gradient_matches_finite_differences():
+    g = _tiny_graph(6, 6)
+    th = F.init_params(5)
+    rng = np.random.default_rng(6)
+    th = th + 0.05 * rng.standard_normal(th.shape)   # away from the all-zero output layer
+    L, grad, _ = F.loss_and_grad(th, g)
+    for k in rng.choice(F.NPARAM, 25, replace=False):
+        h = 1e-6
+        tp = th.copy(); tp[k] += h
+        tm = th.copy(); tm[k] -= h
+        fd = (F.loss_and_grad(tp, g)[0] - F.loss_and_grad(tm, g)[0]) / (2 * h)
+        assert fd == pytest.approx(grad[k], rel=1e-5, abs=1e-9), k
+
+
+def test_classical_fsai_reduces_pcg_iterations():
+    g = _tiny_graph(24, 24)
+    rng = np.random.default_rng(7)
+    Bm = rng.standard_normal((g.n, 2))
+    dinv = 1.0 / g.A.diagonal()
+    G = F.classical_fsai(g.A)
+
+    def pcg(Minv):
+        X = np.zeros_like(Bm); R = Bm.copy(); Z = Minv(R); P = Z.copy(); rz = (R * Z).sum(0)
+        for it in range(1, 2000):
+            Q = g.A @ P; al = rz / (P * Q).sum(0); X += al * P; R -= al * Q
+            if np.max(np.linalg.norm(R, axis=0) / np.linalg.norm(Bm, axis=0)) < 1e-8:
+                return it
+            Z = Minv(R); rzn = (R * Z).sum(0); P = Z + rzn / rz * P; rz = rzn
+        return 2000
+    assert pcg(lambda R: F.fsai_apply(G, R)) < pcg(lambda R: dinv[:, None] * R)

@@ -1,0 +1,78 @@
+"""Learned FSAI preconditioner on the GPU (through the C ABI) against the
+FP64 oracle.  The hidden layer runs with BF16 operands, so network outputs
+carry ~2^-9 relative rounding; tolerances below are set from that."""
+import numpy as np
+import pytest
+
+from oracle import fsai_oracle as F
+from oracle import pfe_oracle as O
+from tests.gpu_common import gpu_problem, oracle_graph, relerr, small_spec
+
+pytestmark = pytest.mark.gpu
+
+
+def _perturbed_params(seed=3, scale=0.05):
+    th = F.init_params(seed)
+    rng = np.random.default_rng(seed + 100)
+    return th + scale * rng.standard_normal(th.shape)
+
+
+def test_untrained_network_is_jacobi():
+    spec = small_spec(H=17, W=19, d=3)
+    p, X, Y0 = gpu_problem(spec, "mixed")
+    g = oracle_graph(spec, X)
+    p.fsai_set(F.init_params(0).astype(np.float32))
+    gd, ge = p.fsai_get()
+    np.testing.assert_allclose(gd, 1.0 / np.sqrt(g.A.diagonal()), rtol=2e-6)
+    assert np.all(ge == 0.0)
+    p.close()
+
+
+def test_fsai_forward_matches_oracle():
+    spec = small_spec(H=21, W=23, d=3, radius=3.0)
+    p, X, Y0 = gpu_problem(spec, "mixed")
+    g = oracle_graph(spec, X)
+    th = _perturbed_params()
+    p.fsai_set(th.astype(np.float32))
+    gd, ge = p.fsai_get()
+    Fd, Fe = F.entry_features(g)
+    od, _ = F.mlp_forward(th, Fd)
+    oe, _ = F.mlp_forward(th, Fe)
+    _, gd_ref, ge_ref = F.assemble_G(g, od, oe)
+    # BF16 hidden layer: ~2^-9 relative per product, accumulated in FP32
+    assert relerr(gd, gd_ref) < 1e-2
+    assert relerr(ge, ge_ref) < 3e-2
+    p.close()
+
+
+def test_fsai_loss_and_gradient_match_oracle():
+    spec = small_spec(H=12, W=13, d=2)
+    p, X, Y0 = gpu_problem(spec, "mixed")
+    g = oracle_graph(spec, X)
+    th = _perturbed_params(5, 0.05)
+    L_ref, grad_ref, _ = F.loss_and_grad(th, g)
+    L, grad = p.fsai_loss_grad(th.astype(np.float32))
+    assert abs(L - L_ref) < 2e-3 * max(1.0, abs(L_ref))
+    cos = float(grad @ grad_ref / (np.linalg.norm(grad) * np.linalg.norm(grad_ref)))
+    assert cos > 0.995, cos
+    assert relerr(grad, grad_ref) < 0.1
+    p.close()
+
+
+def test_pcg_with_fsai_solves_exactly():
+    spec = small_spec(H=26, W=24, d=4)
+    p, X, Y0 = gpu_problem(spec, "mixed", tol=1e-6)
+    g = oracle_graph(spec, X)
+    p.init(Y0)
+    p.fsai_set(_perturbed_params(7, 0.02).astype(np.float32))
+    rng = np.random.default_rng(9)
+    R = rng.standard_normal((g.n, 4))
+    Y = np.zeros_like(R)
+    st = p.solve_system(R, Y)
+    assert st["converged"]
+    assert relerr(Y, O.DirectSolver(g.A)(R)[0]) < 1e-4
+    # and the whole iteration runs with it (graph loop)
+    Yo = np.empty((spec.n, 4))
+    s = p.solve(2, 3, Yo, None)
+    assert s["n_unconverged"] == 0
+    p.close()
