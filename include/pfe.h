@@ -317,6 +317,39 @@ PFE_API pfe_status pfe_adam_update(float *params, const float *grad, float *m, f
                                    int32_t step, double lr, double beta1, double beta2, double eps,
                                    pfe_stream_t stream);
 
+/*
+ * pfe_orthonormalize_noalloc -- the D-orthonormalisation that pfe_init
+ * applies to a starting embedding, Yhat = D^{-1/2} polar(D^{1/2} Y), with no
+ * device memory allocated at all.  (There is no counterpart in the paper:
+ * this entry point exists for callers, not for the method.)
+ *
+ * Who needs it: code that cannot call cudaMalloc -- a routine running while
+ * its stream is being captured into a CUDA graph (allocation is illegal
+ * there), a plug-in inside a host application that owns every device
+ * allocation through its own memory pool, or a service that sizes device
+ * memory once at start-up and must not grow it later.  Every other libpfe
+ * entry point allocates its buffers itself.
+ *
+ * Y (n x d) and deg (n, every d_i > 0) are FP64 device arrays the caller
+ * owns; Yhat (n x d, FP64 device, may not alias Y) receives the result,
+ * which satisfies Yhat^T D Yhat = I.  The scratch (the Gram matrix's block
+ * partials and a small control block, about 0.6 MB) is a fixed array
+ * compiled into the library: every GPU that loads libpfe holds it until the
+ * process exits.  Limits: 1 <= d <= 16 and d <= n; larger d, host
+ * pointers or NULL give PFE_EINVAL before any work is queued.
+ *
+ * All calls on a device share that array and it keeps the last call's
+ * contents (the call resets what must start at zero), so calls that
+ * overlap on the GPU -- two streams at once, or two threads -- race and
+ * must be serialised by the caller.  The first call on each device looks
+ * up the array's device address once (with that device current); make that
+ * first call before any stream capture.  The call queues its work on
+ * `stream` and synchronises it to report PFE_ESINGULAR when D^{1/2} Y is
+ * numerically rank deficient.  It calls no allocating routine.
+ */
+PFE_API pfe_status pfe_orthonormalize_noalloc(const double *Y, const double *deg, int64_t n, int32_t d,
+                                              double *Yhat, pfe_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif
