@@ -242,6 +242,29 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def replica_spec(spec, rank: int, world: int):
+    """Each rank solves its own image: the workload with seed + rank."""
+    from dataclasses import replace
+    return replace(spec, seed=spec.seed + rank) if world > 1 else spec
+
+
+def max_over_ranks_dist(v: float, world: int, device: str) -> float:
+    """The slowest rank's value (the job's time), over torch.distributed."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_seconds_per_outer(ms_max: float, steps: int, world: int) -> float:
+    """Whole-job seconds per outer iteration: world replicas each ran `steps`
+    outer iterations inside the slowest rank's ms_max."""
+    return ms_max / 1e3 / (steps * world)
+
+
 def full_graph_size_and_lambda(spec):
     """nnz_A and lambda = sqrt(vol) of the full image, from the oracle's graph
     definition (pure NumPy; no GPU)."""
@@ -298,8 +321,7 @@ def main():
         spec = replace(spec, H=args.size, W=args.size, name=f"{spec.name}@{args.size}")
     if args.n_inner:
         spec = replace(spec, n_inner=args.n_inner)
-    if world > 1:
-        spec = replace(spec, seed=spec.seed + rank)
+    spec = replica_spec(spec, rank, world)
     X, Y0 = make_problem(spec)
     H, W = spec.shape
     stream = torch.cuda.current_stream()
@@ -309,11 +331,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_dist(v, world, "cuda")
 
     Xd = torch.from_numpy(X).cuda()
     Y0d = torch.from_numpy(Y0).cuda()
@@ -352,7 +370,7 @@ def main():
     iters_total = sum(s["pcg_iters_total"] for s in stats)
     n_solves = sum(s["n_solves"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
-    sec_per_outer = ms_max / 1e3 / (args.steps * world)
+    sec_per_outer = job_seconds_per_outer(ms_max, args.steps, world)
 
     # --- roofline of the dominant kernel: k_spmm (q = A p with the p.q dots)
     spmm_ms = p.time_kernel("spmm", 20)

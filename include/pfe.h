@@ -298,6 +298,14 @@ PFE_API int32_t pfe_fsai_param_count(void);
  * Jacobi.  PFE_EUNSUPPORTED on an FP64 context.  Synchronises. */
 PFE_API pfe_status pfe_fsai_set(pfe_ctx *c, const float *params);
 
+/* The classical FSAI factor on the same pattern (no network): for each row
+ * i with pattern S (i and its lower neighbours), A[S,S] g = e_i solved in
+ * FP64 and scaled by 1/sqrt(g_i).  It minimises the Kaporin number over the
+ * pattern and bounds what the learned factor can reach.  Switches the PCG to
+ * G^T G like pfe_fsai_set.  PFE_EUNSUPPORTED on an FP64 context or when a
+ * row has more than 23 lower neighbours.  Synchronises. */
+PFE_API pfe_status pfe_fsai_classical(pfe_ctx *c);
+
 /* Training criterion: Kaporin's condition number of G A G^T,
  *   *loss = log(tr(G A G^T) / n) - (2/n) sum_i log G_ii,
  * and its gradient with respect to params (written to grad when non-NULL,

@@ -59,6 +59,7 @@ void free_work(pfe_ctx *c) {
     c->wk = Work{};
     c->fsai.t = nullptr;
     c->fsai.z = nullptr;
+    c->fsai.r1 = nullptr;
     c->inited = false;
     c->d = 0;
 }
@@ -66,6 +67,39 @@ void free_work(pfe_ctx *c) {
 pfe_status sync(pfe_ctx *c) {
     PFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return PFE_OK;
+}
+
+// Work vectors of the FSAI iteration: t = G r, z = G^T t and the second
+// residual buffer (n x d each, work precision float).
+pfe_status fsai_vectors(pfe_ctx *c, int64_t nd) {
+    float *t, *z, *r1;
+    PFE_TRY(walloc(c, &t, nd));
+    PFE_TRY(walloc(c, &z, nd));
+    PFE_TRY(walloc(c, &r1, nd));
+    c->fsai.t = t;
+    c->fsai.z = z;
+    c->fsai.r1 = r1;
+    return PFE_OK;
+}
+
+// Launches per solve: the init kernels plus the final flush, and per
+// iteration (the counts the device reports in pfe_solve_stats).
+void launch_counts(const pfe_ctx *c, int lc[2]) {
+    lc[0] = c->fsai.enabled ? 4 : 2;
+    lc[1] = c->fsai.enabled ? 7 : 5;
+}
+
+// After the preconditioner changed: drop the captured loop (its body differs
+// between preconditioners) and update the launch counts.
+pfe_status fsai_switched(pfe_ctx *c) {
+    free_pcg_graph(c);
+    if (c->inited) {
+        int lc[2];
+        launch_counts(c, lc);
+        PFE_CUDA_TRY(c, cudaMemcpyAsync((char *)c->ctl + offsetof(PcgCtl, launch_base), lc, sizeof(lc),
+                                        cudaMemcpyHostToDevice, c->stream));
+    }
+    return sync(c);
 }
 
 // Build the CUDA graph {init kernel -> WHILE(body of check_every iterations)}.
@@ -398,13 +432,7 @@ pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
         PFE_TRY(walloc(c, &q, nd));
         w.Y = y; w.Bs[0] = bs0; w.Bs[1] = bs1; w.RHS = rhs; w.Cw = cw; w.R = r; w.Pd = pd; w.Pd2 = pd2; w.Q = q;
     }
-    if (c->fsai.enabled) {
-        float *t, *z;
-        PFE_TRY(walloc(c, &t, nd));
-        PFE_TRY(walloc(c, &z, nd));
-        c->fsai.t = t;
-        c->fsai.z = z;
-    }
+    if (c->fsai.enabled) PFE_TRY(fsai_vectors(c, nd));
     PFE_TRY(walloc(c, &w.P, nd));
     PFE_TRY(walloc(c, &w.B, nd));
     PFE_TRY(walloc(c, &w.stage, nd));
@@ -429,8 +457,10 @@ pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
     h.tol = c->prm.tol;
     h.done = 1;
     h.unroll = std::max(1, c->prm.check_every);
-    h.launch_base = c->fsai.enabled ? 4 : 2;
-    h.launch_per_iter = c->fsai.enabled ? 7 : 5;
+    int lc[2];
+    launch_counts(c, lc);
+    h.launch_base = lc[0];
+    h.launch_per_iter = lc[1];
     PFE_CUDA_TRY(c, cudaMemcpyAsync(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
     PFE_CUDA_TRY(c, cudaMemsetAsync(c->pctl, 0, sizeof(PstepCtl), c->stream));
     // Y0 -> stage (contiguous FP64), then D-orthonormalise via the P-step map
@@ -709,23 +739,21 @@ pfe_status pfe_fsai_set(pfe_ctx *c, const float *params) {
         PFE_CUDA_TRY(c, cudaMemcpyAsync(c->fsai.params, params, kNParam * sizeof(float), cudaMemcpyDefault,
                                         c->stream));
         PFE_TRY(fsai_infer(c));
-        if (c->inited && !c->fsai.t) {
-            const int64_t nd = c->n * (int64_t)c->d;
-            float *t, *z;
-            PFE_TRY(walloc(c, &t, nd));
-            PFE_TRY(walloc(c, &z, nd));
-            c->fsai.t = t;
-            c->fsai.z = z;
-        }
+        if (c->inited && !c->fsai.t) PFE_TRY(fsai_vectors(c, c->n * (int64_t)c->d));
         c->fsai.enabled = true;
     }
-    free_pcg_graph(c);  // the loop body differs between preconditioners
-    if (c->inited) {
-        int lc[2] = {c->fsai.enabled ? 4 : 2, c->fsai.enabled ? 7 : 5};
-        PFE_CUDA_TRY(c, cudaMemcpyAsync((char *)c->ctl + offsetof(PcgCtl, launch_base), lc, sizeof(lc),
-                                        cudaMemcpyHostToDevice, c->stream));
-    }
-    return sync(c);
+    return fsai_switched(c);
+}
+
+pfe_status pfe_fsai_classical(pfe_ctx *c) {
+    if (!c) return PFE_EINVAL;
+    if (!c->mixed) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner runs on the mixed-precision path");
+    PFE_TRY(sync(c));
+    PFE_TRY(fsai_alloc(c));
+    PFE_TRY(fsai_classical(c));
+    if (c->inited && !c->fsai.t) PFE_TRY(fsai_vectors(c, c->n * (int64_t)c->d));
+    c->fsai.enabled = true;
+    return fsai_switched(c);
 }
 
 pfe_status pfe_fsai_loss_grad(pfe_ctx *c, const float *params, float *grad, double *loss) {

@@ -214,8 +214,8 @@ __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
 // runs), capped at `need` blocks and rounded down to a multiple of `mult`.
 // Cached per context in c->kgrid[slot].
 enum GridSlot {
-    G_INIT = 0, G_INIT_F, G_PUPD, G_PUPD_F, G_SPMM, G_UPDATE, G_RUPDATE, G_XFLUSH, G_REFRESH, G_REFRESH_F,
-    G_FSAI_T, G_FSAI_Z, G_APPLY, G_EDGE, G_PAPPLY, G_TIME_SPMM, G_TIME_UPDATE, G_NSLOTS
+    G_INIT = 0, G_INIT_F, G_PUPD, G_PUPD_F, G_SPMM, G_UPDATE, G_FSAI_TR, G_XFLUSH, G_REFRESH, G_REFRESH_F,
+    G_FSAI_T, G_FSAI_T1, G_FSAI_Z, G_APPLY, G_EDGE, G_PAPPLY, G_TIME_SPMM, G_TIME_UPDATE, G_NSLOTS
 };
 template <typename K>
 inline int wave_grid(pfe_ctx *c, int slot, K kernel, int64_t need, int mult = 1, size_t smem = 0) {

@@ -600,6 +600,86 @@ __global__ void k_adam(int64_t cnt, float *p, const float *gr, float *m, float *
     p[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
 }
 
+// Classical FSAI (the comparator of the learned factor): for row i with
+// pattern S = {lower neighbours of i} + {i} (i last), solve A[S,S] g = e_i by
+// an FP64 Cholesky factorisation and scale g by 1/sqrt(g_i).  This G is the
+// minimiser of the Kaporin number of G A G^T over the same pattern.
+constexpr int kMaxS = 24;
+__global__ void k_fsai_classical(View g, const int *kb, float *gdiag, float *gE, int *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int64_t s = i >> 5;
+    const int s0 = g.slice_ptr[s];
+    const int len_i = (g.slice_ptr[s + 1] - s0) >> 5;
+    const int64_t base = s0 + (i & 31) * (int64_t)len_i;
+    const int nl = kb[i];
+    if (nl + 1 > kMaxS) {
+        atomicExch(err, 1);
+        return;
+    }
+    const int m = nl + 1;
+    int S[kMaxS];
+    for (int k = 0; k < nl; ++k) S[k] = g.col[base + k];
+    S[nl] = (int)i;
+    double Ls[kMaxS * kMaxS];
+    // A[S,S]: diagonal from A_jj, off-diagonal by searching row S[p]'s slots
+    for (int p = 0; p < m; ++p) {
+        const int j = S[p];
+        const int64_t sj = (int64_t)j >> 5;
+        const int t0 = g.slice_ptr[sj];
+        const int lj = (g.slice_ptr[sj + 1] - t0) >> 5;
+        const int64_t bj = t0 + (j & 31) * (int64_t)lj;
+        for (int q = 0; q < m; ++q) {
+            double v = 0.0;
+            if (q == p) {
+                v = g.adiag[j];
+            } else {
+                const int k = S[q];
+                for (int t = 0; t < lj; ++t) {
+                    const int64_t idx = bj + t;
+                    if (g.eid[idx] >= 0 && g.col[idx] == k) {
+                        const double w = g.w64[idx];
+                        v = -g.lam * w * w;
+                        break;
+                    }
+                }
+            }
+            Ls[p * kMaxS + q] = v;
+        }
+    }
+    // Cholesky A = L L^T (lower part of Ls)
+    for (int p = 0; p < m; ++p) {
+        double d = Ls[p * kMaxS + p];
+        for (int k = 0; k < p; ++k) d -= Ls[p * kMaxS + k] * Ls[p * kMaxS + k];
+        if (!(d > 0.0)) {
+            atomicExch(err, 2);
+            return;
+        }
+        d = sqrt(d);
+        Ls[p * kMaxS + p] = d;
+        for (int q = p + 1; q < m; ++q) {
+            double v = Ls[q * kMaxS + p];
+            for (int k = 0; k < p; ++k) v -= Ls[q * kMaxS + k] * Ls[p * kMaxS + k];
+            Ls[q * kMaxS + p] = v / d;
+        }
+    }
+    // solve L y = e_last, L^T x = y
+    double x[kMaxS];
+    for (int p = 0; p < m; ++p) {
+        double v = (p == m - 1) ? 1.0 : 0.0;
+        for (int k = 0; k < p; ++k) v -= Ls[p * kMaxS + k] * x[k];
+        x[p] = v / Ls[p * kMaxS + p];
+    }
+    for (int p = m - 1; p >= 0; --p) {
+        double v = x[p];
+        for (int k = p + 1; k < m; ++k) v -= Ls[k * kMaxS + p] * x[k];
+        x[p] = v / Ls[p * kMaxS + p];
+    }
+    const double sc = 1.0 / sqrt(x[m - 1]);
+    gdiag[i] = (float)(x[m - 1] * sc);
+    for (int k = 0; k < nl; ++k) gE[g.eid[base + k]] = (float)(x[k] * sc);
+}
+
 __global__ void k_export(View g, const float *gdiag, const float *gE, double *od, double *oe) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < g.n && od) od[k] = gdiag[k];
@@ -680,6 +760,30 @@ pfe_status fsai_loss_grad(pfe_ctx *c, double *loss) {
     PFE_CUDA_TRY(c, cudaMemcpyAsync(h, f.sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     PFE_CUDA_TRY(c, cudaStreamSynchronize(s));
     *loss = std::log(h[0] / (double)n) - 2.0 / (double)n * h[1];
+    return PFE_OK;
+}
+
+// Classical FSAI factor into the FSAI buffers.
+pfe_status fsai_classical(pfe_ctx *c) {
+    auto &f = c->fsai;
+    cudaStream_t s = c->stream;
+    View v = view(c);
+    int *derr = reinterpret_cast<int *>(f.tick + 2);
+    PFE_CUDA_TRY(c, cudaMemsetAsync(derr, 0, sizeof(int), s));
+    k_fsai_classical<<<nblk(c->g.n, 64), 64, 0, s>>>(v, f.kb, f.gdiag, f.gE, derr);
+    k_gslots<<<nblk(c->g.n_slices * 32, 256), 256, 0, s>>>(v, f.gE, f.gslot);
+    PFE_CUDA_TRY(c, cudaGetLastError());
+    int h = 0;
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(&h, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PFE_CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (h == 1) {
+        c->err = "classical FSAI: a row has more than 23 lower neighbours";
+        return PFE_EUNSUPPORTED;
+    }
+    if (h == 2) {
+        c->err = "classical FSAI: a local matrix is not positive definite";
+        return PFE_ENUMERIC;
+    }
     return PFE_OK;
 }
 

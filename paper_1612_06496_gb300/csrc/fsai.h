@@ -31,12 +31,14 @@ struct FsaiState {
     float *params = nullptr;   // network parameters in use (device copy)
     float *grad = nullptr;     // last gradient
     void *t = nullptr, *z = nullptr;  // PCG work vectors t = G r, z = G^T t (n x d)
+    void *r1 = nullptr;               // second residual buffer (n x d)
 };
 
 pfe_status fsai_alloc(pfe_ctx *c);
 pfe_status fsai_infer(pfe_ctx *c);
 pfe_status fsai_loss_grad(pfe_ctx *c, double *loss);
 pfe_status fsai_export(pfe_ctx *c, double *od, double *oe);
+pfe_status fsai_classical(pfe_ctx *c);
 pfe_status adam_step(float *p, const float *gr, float *m, float *v, int64_t cnt, int step, double lr, double b1,
                      double b2, double eps, cudaStream_t s);
 

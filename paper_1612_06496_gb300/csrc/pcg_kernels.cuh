@@ -56,8 +56,10 @@ struct PcgArgs {
     PcgCtl *ctl;
     cudaGraphConditionalHandle cond;
     int use_cond;
-    // FSAI preconditioner (float path): z = G^T t, t = G r
+    // FSAI preconditioner (float path): z = G^T t, t = G r; the residual
+    // alternates between r2[0] (= r) and r2[1]
     T *z, *t;
+    T *r2[2];
     const T *gdiag, *gslot;
     const int *kb;
 };
@@ -247,8 +249,20 @@ __device__ __forceinline__ bool grid_sum_cols(typename Acc<T>::type (&v)[NQ][Sub
     __shared__ AT pr[G][NV];
     if (threadIdx.x < G * NV) {
         const int v = threadIdx.x % NV, h = threadIdx.x / NV;
+        const int nb = (int)gridDim.x;
         AT s = A::zero();
-        for (int b = h; b < (int)gridDim.x; b += G) A::add(s, ld_part<A, AT>(part + (int64_t)b * NV + v));
+        // eight independent loads in flight, then the additions in block order
+        for (int b0 = h; b0 < nb; b0 += 8 * G) {
+            AT vals[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int b = b0 + u * G;
+                vals[u] = b < nb ? ld_part<A, AT>(part + (int64_t)b * NV + v) : A::zero();
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (b0 + u * G < nb) A::add(s, vals[u]);
+        }
         pr[h][v] = s;
     }
     __syncthreads();
@@ -613,55 +627,6 @@ __global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
 // the grid).  The grid is a multiple of D / gcd(D, VEC*kBlock) blocks, so a
 // thread always meets the same VEC columns and keeps one accumulator per
 // element slot; the tail (n*D mod VEC elements) goes to the first threads.
-// Per-block column sums of flat accumulators: acc[q][u] of thread t belongs to
-// element VEC*(blockIdx*kBlock + t) + u (+ grid strides, same column), and
-// tacc[q] to tail element tcol (or none).  Result per (q, column) in out,
-// the last block reduces all blocks.  Fixed order.
-template <typename T, int D, int NQ>
-__device__ __forceinline__ bool grid_sum_flat(typename Acc<T>::type (&acc)[NQ][Vec<T>::N],
-                                              typename Acc<T>::type (&tacc)[NQ], int tcol, void *part_v,
-                                              unsigned *ticket, double *out) {
-    using A = Acc<T>;
-    using AT = typename A::type;
-    constexpr int VN = Vec<T>::N;
-    constexpr int NV = NQ * D;
-    __shared__ AT red[NQ][kBlock * VN];
-    __shared__ AT tred[NQ][kBlock];
-    __shared__ int tcols[kBlock];
-    __shared__ AT sh[NV];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-#pragma unroll
-        for (int u = 0; u < VN; ++u) red[q][threadIdx.x * VN + u] = acc[q][u];
-        tred[q][threadIdx.x] = tacc[q];
-    }
-    tcols[threadIdx.x] = tcol;
-    __syncthreads();
-    const int64_t e0 = (int64_t)blockIdx.x * kBlock * VN;  // first element of this block
-    for (int t = threadIdx.x; t < NV; t += blockDim.x) {
-        const int q = t / D, c = t - q * D;
-        AT s = A::zero();
-        // positions p with (e0 + p) % D == c
-        int p0 = (int)((c - (e0 % D) + D) % D);
-        for (int p = p0; p < kBlock * VN; p += D) A::add(s, red[q][p]);
-        for (int k = 0; k < kBlock; ++k)
-            if (tcols[k] == c) A::add(s, tred[q][k]);
-        sh[t] = s;
-    }
-    __syncthreads();
-    AT *part = reinterpret_cast<AT *>(part_v);
-    for (int t = threadIdx.x; t < NV; t += blockDim.x) part[(int64_t)blockIdx.x * NV + t] = sh[t];
-    if (!last_block_arrives(ticket)) return false;
-    for (int t = threadIdx.x; t < NV; t += blockDim.x) {
-        AT s = A::zero();
-        for (int b = 0; b < (int)gridDim.x; ++b) A::add(s, ld_part<A, AT>(part + (int64_t)b * NV + t));
-        out[t] = A::to_double(s);
-    }
-    if (threadIdx.x == 0) *ticket = 0u;
-    __syncthreads();
-    return true;
-}
-
 // r -= alpha q and the dots r.z, r.r of the new residual -> beta, convergence.
 // Sub-warp mapping (cheap per-column block sums), two row groups per step.
 template <typename T, int D>
@@ -762,51 +727,24 @@ __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush
 }
 
 // ---- FSAI preconditioner, z = G^T (G r) --------------------------------------
-// An FSAI iteration is k_pupdate<PRE=1>, k_spmm, k_rupdate (r -= alpha q), k_xflush and
-// k_refresh_f (refresh iterations only), k_fsai_t (t = G r) and k_fsai_z
-// (z = G^T t, the dots r.z and r.r, end of the iteration).
+// An FSAI iteration is k_pupdate<PRE=1>, k_spmm, k_fsai_tr (r -= alpha q and
+// t = G r in one pass), then on refresh iterations only k_xflush, k_refresh_f
+// and k_fsai_t<1> (t from the true residual), and k_fsai_z (z = G^T t, the dots
+// r.z and r.r, end of the iteration).
 
-// r -= alpha q, flat and vectorised (no reduction: the dots need z).
-template <typename T, int D>
-__global__ void __launch_bounds__(kBlock) k_rupdate(PcgArgs<T> a) {
-    if (*(volatile int *)&a.ctl->done) return;
-    __shared__ T salpha[D];
-    if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.ctl->alpha[threadIdx.x];
-    __syncthreads();
-    using VT = Vec<T>;
-    constexpr int VN = VT::N;
-    const int64_t nel = a.A.n * D, nvec = nel / VN;
-    const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
-    T al[VN];
-#pragma unroll
-    for (int u = 0; u < VN; ++u) al[u] = salpha[(int)((tid * VN + u) % D)];
-    const typename VT::V *q4 = reinterpret_cast<const typename VT::V *>(a.q);
-    typename VT::V *r4 = reinterpret_cast<typename VT::V *>(a.r);
-    for (int64_t v = tid; v < nvec; v += nthr) {
-        T rv[VN], qv[VN];
-        VT::get(r4[v], rv);
-        VT::get(q4[v], qv);
-#pragma unroll
-        for (int u = 0; u < VN; ++u) rv[u] = fma(-al[u], qv[u], rv[u]);
-        r4[v] = VT::make(rv);
-    }
-    if (tid < nel - nvec * VN) {
-        const int64_t e = nvec * VN + tid;
-        a.r[e] = fma(-salpha[e % D], a.q[e], a.r[e]);
-    }
-}
-
-// Residual replacement without dots (k_fsai_z makes them).
+// Residual replacement without dots (k_fsai_z makes them); it overwrites the
+// residual that k_fsai_tr has just written.
 template <typename T, int D>
 __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
     if (!*(volatile int *)&a.ctl->refresh_now) return;
+    T *__restrict__ rdst = a.r2[(a.ctl->iter + 1) & 1];
     PFE_ROW_LOOP(T, D) {
         const int64_t i = g * SW::RPW + lm.r;
         if (!lm.active || i >= a.A.n) continue;
         const int c0 = lm.cg * V;
         T ri[V];
         true_residual<T, D, V>(a, i, c0, ri);
-        stv<T, V>(a.r + i * D + c0, ri);
+        stv<T, V>(rdst + i * D + c0, ri);
     }
     if (last_block_arrives(&a.ctl->ticket[3])) {
         if (threadIdx.x == 0) {
@@ -816,10 +754,75 @@ __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
     }
 }
 
-// t = G r: t_i = G_ii r_i + sum over the lower slots (j < i) of G_ij r_j.
+// In FSAI mode the residual is double-buffered: during iteration k (k =
+// ctl->iter) the current residual is r2[k & 1] and the new one is written to
+// r2[(k + 1) & 1]; k_fsai_z ends the iteration by incrementing k.
+
+// r' = r - alpha q and t = G r' in one pass: r' is recomputed at each
+// gathered lower neighbour from the old r and q (the same FMA its owner
+// uses), the owner writes its r' to the other buffer.
 template <typename T, int D>
+__global__ void __launch_bounds__(kBlock) k_fsai_tr(PcgArgs<T> a) {
+    const PcgCtl *ctl = a.ctl;
+    if (*(volatile const int *)&ctl->done) return;
+    __shared__ T salpha[D];
+    if (threadIdx.x < D) salpha[threadIdx.x] = (T)ctl->alpha[threadIdx.x];
+    __syncthreads();
+    const int par = ctl->iter & 1;
+    const T *__restrict__ rold = a.r2[par];
+    T *__restrict__ rnew = a.r2[1 - par];
+    PFE_ROW_LOOP(T, D) {
+        const int64_t i = g * SW::RPW + lm.r;
+        if (!lm.active || i >= a.A.n) continue;
+        const int c0 = lm.cg * V;
+        T al[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) al[k] = salpha[c0 + k];
+        int64_t base;
+        int len;
+        sell_row(a.A.slice_ptr, i, base, len);
+        const int nl = a.kb[i];
+        T acc[V], ri[V], qi[V];
+        ldv<T, V>(rold + i * D + c0, ri);
+        ldv<T, V>(a.q + i * D + c0, qi);
+#pragma unroll
+        for (int k = 0; k < V; ++k) ri[k] = fma(-al[k], qi[k], ri[k]);
+        stv<T, V>(rnew + i * D + c0, ri);
+        const T gd = a.gdiag[i];
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] = gd * ri[k];
+        for (int k0 = 0; k0 < nl; k0 += kChunk) {
+            int jj[kChunk];
+            T gv[kChunk], rj[kChunk][V], qj[kChunk][V];
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) {
+                const bool in = k0 + u < nl;
+                const int64_t idx = base + (in ? k0 + u : 0);
+                jj[u] = in ? __ldg(a.A.col + idx) : (int)i;
+                gv[u] = in ? __ldg(a.gslot + idx) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) {
+                ldv<T, V>(rold + (int64_t)jj[u] * D + c0, rj[u]);
+                ldv<T, V>(a.q + (int64_t)jj[u] * D + c0, qj[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u)
+#pragma unroll
+                for (int k = 0; k < V; ++k) acc[k] = fma(gv[u], fma(-al[k], qj[u][k], rj[u][k]), acc[k]);
+        }
+        stv<T, V>(a.t + i * D + c0, acc);
+    }
+}
+
+// t = G r: t_i = G_ii r_i + sum over the lower slots (j < i) of G_ij r_j.
+// MODE 0: at the start of a solve (residual in r2[0]); MODE 1: only after a
+// residual refresh (residual in the new buffer).
+template <typename T, int D, int MODE>
 __global__ void __launch_bounds__(kBlock) k_fsai_t(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
+    if (MODE == 1 && !*(volatile int *)&a.ctl->refresh_now) return;
+    const T *__restrict__ rsrc = MODE == 0 ? a.r2[0] : a.r2[(a.ctl->iter + 1) & 1];
     PFE_ROW_LOOP(T, D) {
         const int64_t i = g * SW::RPW + lm.r;
         if (!lm.active || i >= a.A.n) continue;
@@ -829,7 +832,7 @@ __global__ void __launch_bounds__(kBlock) k_fsai_t(PcgArgs<T> a) {
         sell_row(a.A.slice_ptr, i, base, len);
         const int nl = a.kb[i];
         T acc[V], ri[V];
-        ldv<T, V>(a.r + i * D + c0, ri);
+        ldv<T, V>(rsrc + i * D + c0, ri);
         const T gd = a.gdiag[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = gd * ri[k];
@@ -844,7 +847,7 @@ __global__ void __launch_bounds__(kBlock) k_fsai_t(PcgArgs<T> a) {
                 gv[u] = in ? __ldg(a.gslot + idx) : T(0);
             }
 #pragma unroll
-            for (int u = 0; u < kChunk; ++u) ldv<T, V>(a.r + (int64_t)jj[u] * D + c0, rj[u]);
+            for (int u = 0; u < kChunk; ++u) ldv<T, V>(rsrc + (int64_t)jj[u] * D + c0, rj[u]);
 #pragma unroll
             for (int u = 0; u < kChunk; ++u)
 #pragma unroll
@@ -860,6 +863,9 @@ __global__ void __launch_bounds__(kBlock) k_fsai_t(PcgArgs<T> a) {
 template <typename T, int D>
 __global__ void __launch_bounds__(kBlock) k_fsai_z(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
+    // the residual of this iteration: r2[0] at the start of a solve, else the
+    // buffer k_fsai_tr (or k_refresh_f) wrote
+    const T *__restrict__ rcur = a.ctl->zstart ? a.r2[0] : a.r2[(a.ctl->iter + 1) & 1];
     using A = Acc<T>;
     using AT = typename A::type;
     using SWt = SubWarp<T, D>;
@@ -899,7 +905,7 @@ __global__ void __launch_bounds__(kBlock) k_fsai_z(PcgArgs<T> a) {
                 for (int k = 0; k < V; ++k) acc[k] = fma(gv[u], tj[u][k], acc[k]);
         }
         stv<T, V>(a.z + i * D + c0, acc);
-        ldv<T, V>(a.r + i * D + c0, ri);
+        ldv<T, V>(rcur + i * D + c0, ri);
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             A::add_prod(acc2[0][k], ri[k], acc[k]);
@@ -1004,6 +1010,8 @@ PcgArgs<T> pcg_args(pfe_ctx *c, PcgLaunch L) {
     a.use_cond = L.use_cond;
     a.z = (T *)c->fsai.z;
     a.t = (T *)c->fsai.t;
+    a.r2[0] = a.r;
+    a.r2[1] = (T *)c->fsai.r1;
     a.gdiag = nullptr;
     a.gslot = nullptr;
     if constexpr (std::is_same_v<T, float>) {
@@ -1048,7 +1056,7 @@ pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
     if constexpr (std::is_same_v<T, float>) {
         if (use_fsai<T>(c)) {
             k_pcg_init<T, D, 1><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-            k_fsai_t<T, D><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            k_fsai_t<T, D, 0><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D, 0>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
             k_fsai_z<T, D><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
             PFE_CUDA_TRY(c, cudaGetLastError());
             return PFE_OK;
@@ -1067,10 +1075,10 @@ pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
             for (int u = 0; u < iters; ++u) {
                 k_pupdate<T, D, 1><<<wave_grid(c, G_PUPD_F, k_pupdate<T, D, 1>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0, s>>>(a);
                 k_spmm<T, D><<<wave_grid(c, G_SPMM, k_spmm<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-                k_rupdate<T, D><<<wave_grid(c, G_RUPDATE, k_rupdate<T, D>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0, s>>>(a);
+                k_fsai_tr<T, D><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
                 k_xflush<T, D><<<wave_grid(c, G_XFLUSH, k_xflush<T, D>, flat_need<T, D>(c)), kBlock, 0, s>>>(a, 0);
                 k_refresh_f<T, D><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-                k_fsai_t<T, D><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+                k_fsai_t<T, D, 1><<<wave_grid(c, G_FSAI_T1, k_fsai_t<T, D, 1>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
                 k_fsai_z<T, D><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
             }
             PFE_CUDA_TRY(c, cudaGetLastError());

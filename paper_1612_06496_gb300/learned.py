@@ -111,7 +111,8 @@ def train(images: int, epochs: int, batch: int, lr: float, out: str, seed: int =
 def evaluate(params: np.ndarray | None, specs, tol: float = 1e-6, n_inner: int = 10) -> list[dict]:
     """PCG iterations and solve time over the second outer iteration of each
     image (the first one runs untimed), for Jacobi (FP32), the learned FSAI
-    (FP32), the untrained network (FP32; equals Jacobi) and plain FP64 Jacobi."""
+    (FP32), the untrained network (FP32; equals Jacobi), the classical FSAI
+    on the same pattern (FP32) and plain FP64 Jacobi."""
     import torch
 
     from paper_1612_06496_gb300 import PFE
@@ -124,12 +125,15 @@ def evaluate(params: np.ndarray | None, specs, tol: float = 1e-6, n_inner: int =
         Xd, Y0d = torch.from_numpy(X).to(dev), torch.from_numpy(Y0).to(dev)
         res = {"image": s.name, "n": s.n, "radius": s.radius, "d": s.d}
         arms = [("jacobi_fp32", "mixed", None), ("learned_fp32", "mixed", params),
-                ("untrained_fp32", "mixed", init_params(0)), ("jacobi_fp64", "fp64", None)]
+                ("untrained_fp32", "mixed", init_params(0)), ("classical_fp32", "mixed", "classical"),
+                ("jacobi_fp64", "fp64", None)]
         for name, prec, th in arms:
             if th is None and name == "learned_fp32":
                 continue
             p = PFE(Xd, sigma=s.sigma, H=s.H, W=s.W, radius=s.radius, precision=prec, tol=tol)
-            if th is not None:
+            if isinstance(th, str):
+                p.fsai_classical()
+            elif th is not None:
                 p.fsai_set(th)
             p.init(Y0d)
             p.solve(1, n_inner)  # first outer iteration (also builds the CUDA graph)

@@ -27,7 +27,7 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_destroy", "pfe_last_error", "pfe_status_string", "pfe_get_info", "pfe_set_stream",
            "pfe_get_array", "pfe_set_array", "pfe_get_edges", "pfe_apply_A", "pfe_solve_system",
            "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
-           "pfe_adam_update", "pfe_orthonormalize_noalloc"]
+           "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical"]
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3}
 
 
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_time_kernel.argtypes = [vp, i32, i32, C.POINTER(dbl)]
     lib.pfe_fsai_param_count.argtypes = []
     lib.pfe_fsai_set.argtypes = [vp, vp]
+    lib.pfe_fsai_classical.argtypes = [vp]
     lib.pfe_fsai_loss_grad.argtypes = [vp, vp, vp, C.POINTER(dbl)]
     lib.pfe_fsai_get.argtypes = [vp, vp, vp]
     lib.pfe_adam_update.argtypes = [vp, vp, vp, vp, i64, i32, dbl, dbl, dbl, dbl, vp]
@@ -296,6 +297,10 @@ class PFE:
             return
         pp, keep = _ptr_f32(params)
         self._check(self.lib.pfe_fsai_set(self.ctx, pp), "pfe_fsai_set")
+
+    def fsai_classical(self):
+        """Use the classical FSAI factor (per-row dense solves) as preconditioner."""
+        self._check(self.lib.pfe_fsai_classical(self.ctx), "pfe_fsai_classical")
 
     def fsai_loss_grad(self, params, grad=None):
         """Kaporin loss of G(params) and its gradient (returns (loss, grad))."""

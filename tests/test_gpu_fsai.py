@@ -76,3 +76,24 @@ def test_pcg_with_fsai_solves_exactly():
     s = p.solve(2, 3, Yo, None)
     assert s["n_unconverged"] == 0
     p.close()
+
+
+def test_classical_fsai_matches_oracle_and_cuts_iterations():
+    spec = small_spec(H=30, W=28, d=3, radius=3.0)
+    p, X, Y0 = gpu_problem(spec, "mixed", tol=1e-6)
+    g = oracle_graph(spec, X)
+    p.init(Y0)
+    rng = np.random.default_rng(11)
+    R = rng.standard_normal((g.n, 3))
+    Y = np.zeros_like(R)
+    it_jacobi = p.solve_system(R, Y)["pcg_iters"]
+    p.fsai_classical()
+    gd, ge = p.fsai_get()
+    G = F.classical_fsai(g.A).tocsr()
+    np.testing.assert_allclose(gd, G.diagonal(), rtol=1e-6)
+    np.testing.assert_allclose(ge, np.asarray(G[g.b, g.a]).ravel(), rtol=1e-5, atol=1e-7 * np.abs(ge).max())
+    Y = np.zeros_like(R)
+    st = p.solve_system(R, Y)
+    assert st["converged"] and st["pcg_iters"] < it_jacobi
+    assert relerr(Y, O.DirectSolver(g.A)(R)[0]) < 1e-4
+    p.close()
