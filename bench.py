@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--precond", default="learned", choices=["learned", "jacobi"],
+                    help="preconditioner of the timed FP32 arm (learned FSAI or Jacobi)")
+    ap.add_argument("--no-alt", action="store_true", help="skip the FP32 arm with the other preconditioner")
+    ap.add_argument("--alt-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-window", type=int, default=192)
     ap.add_argument("--size", type=int, default=0,
@@ -309,6 +313,7 @@ def main():
     import torch.distributed as dist
 
     from paper_1612_06496_gb300 import PFE, load_library
+    from paper_1612_06496_gb300.learned import load_weights
     from synth import CONFIGS, make_problem
     from dataclasses import replace
 
@@ -336,10 +341,12 @@ def main():
     Xd = torch.from_numpy(X).cuda()
     Y0d = torch.from_numpy(Y0).cuda()
 
-    def run_arm(precision: str, warmup: int, steps: int, clocks: bool):
+    def run_arm(precision: str, warmup: int, steps: int, clocks: bool, precond: str = "jacobi"):
         t0 = time.perf_counter()
         p = PFE(Xd, sigma=spec.sigma, H=H, W=W, radius=spec.radius, precision=precision, tol=spec.tol,
                 stream=stream, loop=args.loop)
+        if precond == "learned":
+            p.fsai_set(fsai_params)  # network inference of G runs inside the timed setup
         p.init(Y0d)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
@@ -363,8 +370,10 @@ def main():
         clk = sampler.stop() if sampler else None
         return p, ms, stats, setup_s, clk
 
+    fsai_params = load_weights() if (args.precond == "learned" or not args.no_alt) else None
+
     # --- FP32 path (the timed arm)
-    p, ms, stats, setup_s, clk = run_arm("mixed", args.warmup, args.steps, True)
+    p, ms, stats, setup_s, clk = run_arm("mixed", args.warmup, args.steps, True, args.precond)
     ms_max = max_over_ranks(ms)
     info = p.info()
     iters_total = sum(s["pcg_iters_total"] for s in stats)
@@ -378,6 +387,15 @@ def main():
     pup_ms = p.time_kernel("pupdate", 20)
     edge_ms = p.time_kernel("edge", 10)
     n, d, nnz = info["n"], info["d"], info["nnz_A"]
+    fsai_k = {}
+    if args.precond == "learned":
+        # lower (upper) slots: FP32 G value + int32 column each, kb and G_ii per row;
+        # t = G r': r, q in, r', t out; z = G^T t: t, r in, z out
+        tr_ms, z_ms = p.time_kernel("fsai_tr", 20), p.time_kernel("fsai_z", 20)
+        tr_b = 4 * nnz + 8 * n + 16 * n * d
+        z_b = 4 * nnz + 8 * n + 12 * n * d
+        fsai_k = {"k_fsai_tr_ms": round(tr_ms, 5), "k_fsai_tr_GBps": round(tr_b / (tr_ms * 1e-3) / 1e9, 1),
+                  "k_fsai_z_ms": round(z_ms, 5), "k_fsai_z_GBps": round(z_b / (z_ms * 1e-3) / 1e9, 1)}
     # FP32 values + int32 indices of A, p in, q out: 8 nnz_A + 4 (n + 1) + 2 * 4 n d
     spmm_bytes = 8 * nnz + 4 * (n + 1) + 2 * 4 * n * d
     peaks = measured_peaks()
@@ -393,8 +411,21 @@ def main():
                                   "k_update_GBps": round((3 * 4 * n * d + 4 * n) / (upd_ms * 1e-3) / 1e9, 1),
                                   "k_pupdate_ms": round(pup_ms, 5),
                                   "k_pupdate_GBps": round((7 * 4 * n * d + 4 * n) / (pup_ms * 1e-3) / 1e9, 1),
-                                  "k_edge_ms": round(edge_ms, 5)}}
+                                  "k_edge_ms": round(edge_ms, 5), **fsai_k}}
     p.close()
+
+    # --- the FP32 path with the other preconditioner
+    alt = None
+    if not args.no_alt:
+        other = "jacobi" if args.precond == "learned" else "learned"
+        qa, msa, sta, _, _ = run_arm("mixed", 1, args.alt_steps, False, other)
+        msa = max_over_ranks(msa)
+        ita = sum(s["pcg_iters_total"] for s in sta)
+        nsa = sum(s["n_solves"] for s in sta)
+        alt = {"precond": other, "sec_per_outer_iter": msa / 1e3 / (args.alt_steps * world),
+               "pcg_iters_mean": ita / max(nsa, 1), "pcg_iters_max": max(s["pcg_iters_max"] for s in sta),
+               "steps": args.alt_steps}
+        qa.close()
 
     # --- plain FP64 path on the same problem
     fp64 = None
@@ -427,6 +458,8 @@ def main():
         for _ in range(e2e_steps):
             r = PFE(Xh, sigma=spec.sigma, H=H, W=W, radius=spec.radius, precision="mixed", tol=spec.tol,
                     stream=stream)
+            if args.precond == "learned":
+                r.fsai_set(fsai_params)  # host copy of the network weights
             r.init(Y0h)
             r.solve(1, spec.n_inner, Yo, Yho)
             r.close()
@@ -436,9 +469,10 @@ def main():
         barrier()
         ms_e2e = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3))
         e2e = {"value": ms_e2e / 1e3 / (e2e_steps * world), "unit": UNIT,
-               "h2d_bytes_per_step": int(X.nbytes + Y0.nbytes), "d2h_bytes_per_step": int(2 * Yo.numel() * 8),
+               "h2d_bytes_per_step": int(X.nbytes + Y0.nbytes + (fsai_params.nbytes if args.precond == "learned" else 0)),
+               "d2h_bytes_per_step": int(2 * Yo.numel() * 8),
                "steps": e2e_steps,
-               "what": "per step: pfe_build_graph from host features, pfe_init from host Y0, one outer "
+               "what": "per step: pfe_build_graph from host features, the preconditioner set up, pfe_init from host Y0, one outer "
                        "iteration (pfe_solve 1 x n_inner), Y and Yhat copied back to pinned host memory"}
 
     # --- CPU oracle baseline (rank 0, N = 1 only)
@@ -461,12 +495,16 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(spec, world),
             "precision_path": "FP32 edge/SpMM/vectors, double-FP32 dots and PCG solution, FP64 P-step; "
-                              "Jacobi preconditioner",
+                              + ("learned FSAI preconditioner (BF16 tensor-core MLP, weights "
+                                 "paper_1612_06496_gb300/fsai_weights.npz)" if args.precond == "learned"
+                                 else "Jacobi preconditioner"),
+            "precond": args.precond,
             "pcg_iters_mean": iters_total / max(n_solves, 1),
             "pcg_iters_max": max(s["pcg_iters_max"] for s in stats),
             "pcg_relres_max": max(s["relres_max"] for s in stats),
             "gnnz_rhs_per_s": nnz * d * iters_total / (ms / 1e3) / 1e9,
             "setup_s": setup_s, "lambda": info["lambda_"],
+            "fp32_other_precond": alt,
             "fp64": fp64,
             "speedup_vs_fp64": (fp64["sec_per_outer_iter"] / sec_per_outer) if fp64 else None,
             "roofline": roofline,

@@ -717,8 +717,10 @@ pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_
         if (st != PFE_OK) return st;
         if (e != cudaSuccess) return fail(c, PFE_ECUDA, cudaGetErrorString(e));
         ms /= (float)reps;
-    } else if (which == PFE_KERNEL_SPMM || which == PFE_KERNEL_UPDATE || which == PFE_KERNEL_PUPDATE) {
-        PFE_TRY(time_pcg_kernel(c, c->stream, which == PFE_KERNEL_PUPDATE ? 2 : which, reps, &ms));
+    } else if (which == PFE_KERNEL_SPMM || which == PFE_KERNEL_UPDATE || which == PFE_KERNEL_PUPDATE ||
+               which == PFE_KERNEL_FSAI_TR || which == PFE_KERNEL_FSAI_Z) {
+        const int k = which == PFE_KERNEL_PUPDATE ? 2 : which == PFE_KERNEL_FSAI_TR ? 3 : which == PFE_KERNEL_FSAI_Z ? 4 : which;
+        PFE_TRY(time_pcg_kernel(c, c->stream, k, reps, &ms));
     } else {
         return fail(c, PFE_EINVAL, "unknown kernel id");
     }

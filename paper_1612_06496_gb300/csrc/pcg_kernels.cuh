@@ -758,11 +758,68 @@ __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
 // ctl->iter) the current residual is r2[k & 1] and the new one is written to
 // r2[(k + 1) & 1]; k_fsai_z ends the iteration by incrementing k.
 
+// acc += sum of g_k * v(j_k) over the slots k in [lo, hi) among the CH slots
+// from k0 on (k0 a multiple of 4; 16-byte slot loads, slots outside the range
+// gather the own row with weight 0).  v = src, or src - alpha q with QS.
+template <typename T, int D, int V, int CH, bool QS>
+__device__ __forceinline__ void gslot_chunk(const int *__restrict__ col, const T *__restrict__ gs, int64_t base,
+                                            int k0, int len, int lo, int hi, int self, int c0,
+                                            const T *__restrict__ src, const T *__restrict__ qsrc, const T (&al)[V],
+                                            T (&acc)[V]) {
+    int jj[CH];
+    T gv[CH];
+    load_slots<T, CH>(col, gs, base, k0, len, self, jj, gv);
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+        const int k = k0 + u;
+        if (k < lo || k >= hi) {
+            jj[u] = self;
+            gv[u] = T(0);
+        }
+    }
+    T vj[CH][V];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) ldv<T, V>(src + (int64_t)jj[u] * D + c0, vj[u]);
+    if constexpr (QS) {
+        T qj[CH][V];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) ldv<T, V>(qsrc + (int64_t)jj[u] * D + c0, qj[u]);
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+#pragma unroll
+            for (int k = 0; k < V; ++k) vj[u][k] = fma(-al[k], qj[u][k], vj[u][k]);
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] = fma(gv[u], vj[u][k], acc[k]);
+}
+
+// The FSAI gather kernels are latency-bound: 5 resident blocks of kBlock per SM
+// (48 registers a thread) with up to 2 columns a lane, 4 with 4 (16 bytes).
+template <typename T, int D>
+constexpr int gather_min_blocks() {
+    return SubWarp<T, D>::V * (int)sizeof(T) >= 16 ? 4 : 5;
+}
+
+// All slots in [lo, hi): chunks of kGChunk = 8 slots (the 6 lower or upper
+// slots of a radius-2 row in one chunk), then one chunk of 4 if needed.
+constexpr int kGChunk = 8;
+template <typename T, int D, int V, bool QS>
+__device__ __forceinline__ void gslot_range(const int *__restrict__ col, const T *__restrict__ gs, int64_t base,
+                                            int len, int lo, int hi, int self, int c0, const T *__restrict__ src,
+                                            const T *__restrict__ qsrc, const T (&al)[V], T (&acc)[V]) {
+    int k0 = lo & ~3;
+    for (; k0 + 4 < hi; k0 += kGChunk)
+        gslot_chunk<T, D, V, kGChunk, QS>(col, gs, base, k0, len, lo, hi, self, c0, src, qsrc, al, acc);
+    if (k0 < hi) gslot_chunk<T, D, V, 4, QS>(col, gs, base, k0, len, lo, hi, self, c0, src, qsrc, al, acc);
+}
+
 // r' = r - alpha q and t = G r' in one pass: r' is recomputed at each
 // gathered lower neighbour from the old r and q (the same FMA its owner
 // uses), the owner writes its r' to the other buffer.
 template <typename T, int D>
-__global__ void __launch_bounds__(kBlock) k_fsai_tr(PcgArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
     __shared__ T salpha[D];
@@ -781,7 +838,6 @@ __global__ void __launch_bounds__(kBlock) k_fsai_tr(PcgArgs<T> a) {
         int64_t base;
         int len;
         sell_row(a.A.slice_ptr, i, base, len);
-        const int nl = a.kb[i];
         T acc[V], ri[V], qi[V];
         ldv<T, V>(rold + i * D + c0, ri);
         ldv<T, V>(a.q + i * D + c0, qi);
@@ -791,26 +847,7 @@ __global__ void __launch_bounds__(kBlock) k_fsai_tr(PcgArgs<T> a) {
         const T gd = a.gdiag[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = gd * ri[k];
-        for (int k0 = 0; k0 < nl; k0 += kChunk) {
-            int jj[kChunk];
-            T gv[kChunk], rj[kChunk][V], qj[kChunk][V];
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) {
-                const bool in = k0 + u < nl;
-                const int64_t idx = base + (in ? k0 + u : 0);
-                jj[u] = in ? __ldg(a.A.col + idx) : (int)i;
-                gv[u] = in ? __ldg(a.gslot + idx) : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) {
-                ldv<T, V>(rold + (int64_t)jj[u] * D + c0, rj[u]);
-                ldv<T, V>(a.q + (int64_t)jj[u] * D + c0, qj[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u)
-#pragma unroll
-                for (int k = 0; k < V; ++k) acc[k] = fma(gv[u], fma(-al[k], qj[u][k], rj[u][k]), acc[k]);
-        }
+        gslot_range<T, D, V, true>(a.A.col, a.gslot, base, len, 0, a.kb[i], (int)i, c0, rold, a.q, al, acc);
         stv<T, V>(a.t + i * D + c0, acc);
     }
 }
@@ -819,7 +856,7 @@ __global__ void __launch_bounds__(kBlock) k_fsai_tr(PcgArgs<T> a) {
 // MODE 0: at the start of a solve (residual in r2[0]); MODE 1: only after a
 // residual refresh (residual in the new buffer).
 template <typename T, int D, int MODE>
-__global__ void __launch_bounds__(kBlock) k_fsai_t(PcgArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
     if (MODE == 1 && !*(volatile int *)&a.ctl->refresh_now) return;
     const T *__restrict__ rsrc = MODE == 0 ? a.r2[0] : a.r2[(a.ctl->iter + 1) & 1];
@@ -830,29 +867,13 @@ __global__ void __launch_bounds__(kBlock) k_fsai_t(PcgArgs<T> a) {
         int64_t base;
         int len;
         sell_row(a.A.slice_ptr, i, base, len);
-        const int nl = a.kb[i];
         T acc[V], ri[V];
+        const T nal[V] = {};
         ldv<T, V>(rsrc + i * D + c0, ri);
         const T gd = a.gdiag[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = gd * ri[k];
-        for (int k0 = 0; k0 < nl; k0 += kChunk) {
-            int jj[kChunk];
-            T gv[kChunk], rj[kChunk][V];
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) {
-                const bool in = k0 + u < nl;
-                const int64_t idx = base + (in ? k0 + u : 0);
-                jj[u] = in ? __ldg(a.A.col + idx) : (int)i;
-                gv[u] = in ? __ldg(a.gslot + idx) : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) ldv<T, V>(rsrc + (int64_t)jj[u] * D + c0, rj[u]);
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u)
-#pragma unroll
-                for (int k = 0; k < V; ++k) acc[k] = fma(gv[u], rj[u][k], acc[k]);
-        }
+        gslot_range<T, D, V, false>(a.A.col, a.gslot, base, len, 0, a.kb[i], (int)i, c0, rsrc, nullptr, nal, acc);
         stv<T, V>(a.t + i * D + c0, acc);
     }
 }
@@ -861,7 +882,7 @@ __global__ void __launch_bounds__(kBlock) k_fsai_t(PcgArgs<T> a) {
 // then the dots r.z, r.r; the last block ends the iteration (or the start of
 // the solve) and decides whether the next iteration refreshes r.
 template <typename T, int D>
-__global__ void __launch_bounds__(kBlock) k_fsai_z(PcgArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_z(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
     // the residual of this iteration: r2[0] at the start of a solve, else the
     // buffer k_fsai_tr (or k_refresh_f) wrote
@@ -881,29 +902,13 @@ __global__ void __launch_bounds__(kBlock) k_fsai_z(PcgArgs<T> a) {
         int64_t base;
         int len;
         sell_row(a.A.slice_ptr, i, base, len);
-        const int nl = a.kb[i];
         T acc[V], ti[V], ri[V];
+        const T nal[V] = {};
         ldv<T, V>(a.t + i * D + c0, ti);
         const T gd = a.gdiag[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = gd * ti[k];
-        for (int k0 = nl; k0 < len; k0 += kChunk) {
-            int jj[kChunk];
-            T gv[kChunk], tj[kChunk][V];
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) {
-                const bool in = k0 + u < len;
-                const int64_t idx = base + (in ? k0 + u : 0);
-                jj[u] = in ? __ldg(a.A.col + idx) : (int)i;
-                gv[u] = in ? __ldg(a.gslot + idx) : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) ldv<T, V>(a.t + (int64_t)jj[u] * D + c0, tj[u]);
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u)
-#pragma unroll
-                for (int k = 0; k < V; ++k) acc[k] = fma(gv[u], tj[u][k], acc[k]);
-        }
+        gslot_range<T, D, V, false>(a.A.col, a.gslot, base, len, a.kb[i], len, (int)i, c0, a.t, nullptr, nal, acc);
         stv<T, V>(a.z + i * D + c0, acc);
         ldv<T, V>(rcur + i * D + c0, ri);
 #pragma unroll
@@ -1115,7 +1120,7 @@ pfe_status apply_T(pfe_ctx *c, cudaStream_t s, const void *x, void *y) {
 // control block (every column active, a steady-state iteration: direction
 // update and delayed solution update both on) and scratch copies of y, r and
 // the direction buffers, so the iteration state is left as it was.
-// which: 0 = k_spmm, 1 = k_update.
+// which: 0 = k_spmm, 1 = k_update, 2 = k_pupdate, 3 = k_fsai_tr, 4 = k_fsai_z.
 template <typename T, int D>
 pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     PcgCtl h;
@@ -1133,13 +1138,19 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
         h.beta[k] = 0.5;
     }
     const int64_t nd = c->g.n * (int64_t)D;
+    const bool fsai = which >= 3;
+    if (fsai && !use_fsai<T>(c)) {
+        c->err = "pfe_time_kernel: the FSAI kernels need the FSAI preconditioner on the mixed path";
+        return PFE_EUNSUPPORTED;
+    }
     PcgCtl *dctl = nullptr;
-    T *xs = nullptr, *rs = nullptr, *p0 = nullptr, *p1 = nullptr;
+    T *xs = nullptr, *rs = nullptr, *p0 = nullptr, *p1 = nullptr, *r1s = nullptr, *ts = nullptr, *zs = nullptr;
     float *xls = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     pfe_status st = PFE_OK;
     auto cleanup = [&]() {
-        for (void *q : {(void *)dctl, (void *)xs, (void *)rs, (void *)p0, (void *)p1, (void *)xls})
+        for (void *q : {(void *)dctl, (void *)xs, (void *)rs, (void *)p0, (void *)p1, (void *)xls, (void *)r1s,
+                        (void *)ts, (void *)zs})
             if (q) cudaFree(q);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
@@ -1147,7 +1158,10 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     if (cudaMalloc((void **)&dctl, sizeof(PcgCtl)) != cudaSuccess || cudaMalloc((void **)&xs, nd * sizeof(T)) != cudaSuccess ||
         cudaMalloc((void **)&rs, nd * sizeof(T)) != cudaSuccess || cudaMalloc((void **)&p0, nd * sizeof(T)) != cudaSuccess ||
         cudaMalloc((void **)&p1, nd * sizeof(T)) != cudaSuccess ||
-        (std::is_same_v<T, float> && cudaMalloc((void **)&xls, nd * sizeof(float)) != cudaSuccess)) {
+        (std::is_same_v<T, float> && cudaMalloc((void **)&xls, nd * sizeof(float)) != cudaSuccess) ||
+        (fsai && (cudaMalloc((void **)&r1s, nd * sizeof(T)) != cudaSuccess ||
+                  cudaMalloc((void **)&ts, nd * sizeof(T)) != cudaSuccess ||
+                  cudaMalloc((void **)&zs, nd * sizeof(T)) != cudaSuccess))) {
         cudaGetLastError();
         cleanup();
         c->err = "pfe_time_kernel: scratch allocation failed";
@@ -1160,7 +1174,15 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     a.xlo = xls;
     a.p[0] = p0;
     a.p[1] = p1;
+    a.r2[0] = rs;
+    a.r2[1] = r1s;
+    a.t = ts;
+    a.z = zs;
     cudaMemcpyAsync(dctl, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    if (fsai) {
+        cudaMemcpyAsync(r1s, c->wk.R, nd * sizeof(T), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(ts, c->wk.R, nd * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    }
     cudaMemcpyAsync(xs, c->wk.Y, nd * sizeof(T), cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(rs, c->wk.R, nd * sizeof(T), cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(p0, c->wk.Pd, nd * sizeof(T), cudaMemcpyDeviceToDevice, s);
@@ -1173,9 +1195,15 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
             k_spmm<T, D><<<wave_grid(c, G_SPMM, k_spmm<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
         else if (which == 1)
             k_update<T, D><<<wave_grid(c, G_UPDATE, k_update<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-        else
+        else if (which == 2)
             k_pupdate<T, D, 0><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0>, flat_need<T, D>(c), flat_mult<T, D>()),
                                  kBlock, 0, s>>>(a);
+        else if constexpr (std::is_same_v<T, float>) {
+            if (which == 3)
+                k_fsai_tr<T, D><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            else
+                k_fsai_z<T, D><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        }
     };
     launch();  // warm-up
     cudaEventRecord(e0, s);
