@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="C5", choices=["C1", "C2", "C5"])
+    ap.add_argument("--workload", default="C5", choices=["C1", "C2", "C3", "C5"],
+                    help="C3 is the batch of 64 uneven images (one problem per image, iterated together)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -77,13 +78,20 @@ def cpu_sample_worker(arg: str):
     from synth import CONFIGS, make_problem
     from dataclasses import replace
     cfg = json.loads(arg)
-    spec = CONFIGS[cfg["workload"]]
-    win = cfg["window"]
-    x0 = (spec.W - win) // 2
-    y0 = (spec.H - win) // 2
-    wspec = replace(spec, crop=(x0, y0, win, win))
-    X, Y0 = make_problem(wspec)
-    g = O.build_grid_graph(X, win, win, spec.radius, spec.sigma, lam=cfg["lambda"])
+    if cfg["workload"] == "C3":
+        from synth import batch_specs
+        specs = batch_specs()
+        spec = min(specs, key=lambda s: s.n)  # the smallest image, with its own lambda
+        X, Y0 = make_problem(spec)
+        g = O.build_grid_graph(X, spec.H, spec.W, spec.radius, spec.sigma)
+    else:
+        spec = CONFIGS[cfg["workload"]]
+        win = cfg["window"]
+        x0 = (spec.W - win) // 2
+        y0 = (spec.H - win) // 2
+        wspec = replace(spec, crop=(x0, y0, win, win))
+        X, Y0 = make_problem(wspec)
+        g = O.build_grid_graph(X, win, win, spec.radius, spec.sigma, lam=cfg["lambda"])
     st = O.init_state(g, Y0)
     solve = O.PCGSolver(g.A, spec.tol, 5000, 50)
     times, iters = [], []
@@ -238,12 +246,37 @@ def run_reference(args, rank: int, world: int):
         "config": workload_config(spec, args.gpus),
         "pcg_iters_mean": sum(out["iters"][args.warmup:]) / len(timed),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration per step on "
-                                   f"the central {args.cpu_window}x{args.cpu_window} window of the same image "
-                                   f"with the full image's lambda, scaled by nnz_A ratio {out['scale']:.1f}"},
+                         "sample": cpu_sample_text(spec, args.cpu_window, out)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_sample_text(spec, window: int, out: dict) -> str:
+    if spec.name == "C3":
+        return (f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration per step on the smallest image "
+                f"of the batch ({out['n']} pixels, its own lambda, {out['iters'][0]:.0f} PCG iterations per solve), "
+                f"scaled to the whole batch by the nnz_A ratio {out['scale']:.1f}")
+    return (f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration per step on the central "
+            f"{window}x{window} window of the same image with the full image's lambda "
+            f"({out['iters'][0]:.0f} PCG iterations per solve), scaled by nnz_A ratio {out['scale']:.1f}")
+
+
+def problem_inputs(spec, rank: int, world: int):
+    """(features, Y0, geometry kwargs of PFE, spec of the first problem) of the
+    workload; the batch stacks its images' rows (replicas: other seeds)."""
+    import numpy as np
+    from synth import batch_specs, make_problem
+    if spec.name == "C3":
+        specs = batch_specs(seed0=3000 + 64 * rank) if world > 1 else batch_specs()
+        probs = [make_problem(s) for s in specs]
+        X = np.ascontiguousarray(np.vstack([p[0] for p in probs]))
+        Y0 = np.ascontiguousarray(np.vstack([p[1] for p in probs]))
+        return X, Y0, {"shapes": [s.shape for s in specs]}, specs[0]
+    spec = replica_spec(spec, rank, world)
+    X, Y0 = make_problem(spec)
+    H, W = spec.shape
+    return X, Y0, {"H": H, "W": W}, spec
 
 
 def replica_spec(spec, rank: int, world: int):
@@ -270,11 +303,18 @@ def job_seconds_per_outer(ms_max: float, steps: int, world: int) -> float:
 
 
 def full_graph_size_and_lambda(spec):
-    """nnz_A and lambda = sqrt(vol) of the full image, from the oracle's graph
-    definition (pure NumPy; no GPU)."""
+    """nnz_A and lambda = sqrt(vol) of the full image (the batch: total nnz_A,
+    lambda unused), from the oracle's graph definition (pure NumPy; no GPU)."""
     import numpy as np
     from oracle import pfe_oracle as O
     from synth import make_problem
+    if spec.name == "C3":
+        from synth import batch_specs
+        tot = 0
+        for s in batch_specs():
+            a, _ = O.grid_edges(s.H, s.W, s.radius)
+            tot += s.n + 2 * a.shape[0]
+        return tot, 0.0
     X, _ = make_problem(spec)
     a, b = O.grid_edges(spec.H, spec.W, spec.radius)
     w = O.heat_kernel_weights(X, a, b, spec.sigma)
@@ -283,6 +323,15 @@ def full_graph_size_and_lambda(spec):
 
 
 def workload_config(spec, gpus: int) -> dict:
+    if spec.name == "C3":
+        from synth import batch_specs
+        specs = batch_specs()
+        return {"workload": f"C3: batch of {len(specs)} synthetic Voronoi images, 96..481 x 96..321 pixels, "
+                            f"3-12 regions, radius-2 graphs, sigma=0.1, d=5, 10 inner iterations per outer step "
+                            f"(every image), PCG rel-res 1e-06, one launch per kernel for the whole batch",
+                "n": sum(s.n for s in specs), "images": len(specs), "d": 5, "n_inner": 10, "tol": 1e-6,
+                "l2": "working set per step >> L2 (inputs larger than L2, no flush)",
+                "parallelism": f"replicas x{gpus}" if gpus > 1 else "single GPU"}
     return {"workload": f"{spec.name}: {spec.W}x{spec.H} synthetic Voronoi image, radius-{spec.radius:g} graph, "
                         f"sigma={spec.sigma:g}, d={spec.d}, {spec.n_inner} inner iterations per outer step, "
                         f"PCG rel-res {spec.tol:g}",
@@ -321,14 +370,17 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     load_library()
+    batch = args.workload == "C3"
     spec = CONFIGS[args.workload]
-    if args.size:
+    if args.size and not batch:
         spec = replace(spec, H=args.size, W=args.size, name=f"{spec.name}@{args.size}")
+    X, Y0, geom, spec0 = problem_inputs(spec, rank, world)
+    if not batch:
+        spec = spec0
     if args.n_inner:
         spec = replace(spec, n_inner=args.n_inner)
-    spec = replica_spec(spec, rank, world)
-    X, Y0 = make_problem(spec)
-    H, W = spec.shape
+    if batch and args.precond == "learned":
+        args.precond, args.no_alt = "jacobi", True  # the FSAI preconditioner is built for one problem
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -343,8 +395,8 @@ def main():
 
     def run_arm(precision: str, warmup: int, steps: int, clocks: bool, precond: str = "jacobi"):
         t0 = time.perf_counter()
-        p = PFE(Xd, sigma=spec.sigma, H=H, W=W, radius=spec.radius, precision=precision, tol=spec.tol,
-                stream=stream, loop=args.loop)
+        p = PFE(Xd, sigma=spec.sigma, radius=spec.radius, precision=precision, tol=spec.tol,
+                stream=stream, loop=args.loop, **geom)
         if precond == "learned":
             p.fsai_set(fsai_params)  # network inference of G runs inside the timed setup
         p.init(Y0d)
@@ -363,6 +415,8 @@ def main():
         stats = []
         for _ in range(steps):
             stats.append(p.solve(1, spec.n_inner))
+            if batch:  # each image's iterations of this step (64 integers)
+                stats[-1]["seg_iters"] = p.segment_stats(totals=True)[2]
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -377,7 +431,18 @@ def main():
     ms_max = max_over_ranks(ms)
     info = p.info()
     iters_total = sum(s["pcg_iters_total"] for s in stats)
+    rounds = sum(s["pcg_rounds"] for s in stats)  # k_spmm launches (a batch: its longest image's iterations)
     n_solves = sum(s["n_solves"] for s in stats)
+    if batch:
+        # nonzeros x iterations of each image: A_s has n_s + 2|E_s| nonzeros
+        import numpy as np
+        off, _ = p.segments()
+        ea, _, _ = p.edges()
+        es = np.bincount(np.searchsorted(off, ea, side="right") - 1, minlength=len(off) - 1)
+        nnz_seg = np.diff(off) + 2 * es
+        nnz_iters = float(sum(np.dot(nnz_seg, s["seg_iters"]) for s in stats))
+    else:
+        nnz_iters = float(info["nnz_A"]) * iters_total
     launches = sum(s["kernel_launches"] for s in stats)
     sec_per_outer = job_seconds_per_outer(ms_max, args.steps, world)
 
@@ -405,8 +470,8 @@ def main():
                 "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic": ncu_traffic(args.workload, "spmm", nnz),
                 "algorithmic_bytes_per_launch": spmm_bytes, "avg_launch_ms": round(spmm_ms, 5),
-                "launches_in_timed_region": iters_total,
-                "share_of_timed_region": round(iters_total * spmm_ms / ms, 4),
+                "launches_in_timed_region": rounds,
+                "share_of_timed_region": round(rounds * spmm_ms / ms, 4),
                 "other_kernels": {"k_update_ms": round(upd_ms, 5),
                                   "k_update_GBps": round((3 * 4 * n * d + 4 * n) / (upd_ms * 1e-3) / 1e9, 1),
                                   "k_pupdate_ms": round(pup_ms, 5),
@@ -446,7 +511,7 @@ def main():
     if not args.no_e2e:
         Xh = torch.from_numpy(X).pin_memory()
         Y0h = torch.from_numpy(Y0).pin_memory()
-        Yo = torch.empty((spec.n, spec.d), dtype=torch.float64).pin_memory()
+        Yo = torch.empty(tuple(Y0.shape), dtype=torch.float64).pin_memory()
         Yho = torch.empty_like(Yo).pin_memory()
         e2e_steps = max(1, min(args.steps, 3))
         torch.cuda.synchronize()
@@ -456,8 +521,8 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(e2e_steps):
-            r = PFE(Xh, sigma=spec.sigma, H=H, W=W, radius=spec.radius, precision="mixed", tol=spec.tol,
-                    stream=stream)
+            r = PFE(Xh, sigma=spec.sigma, radius=spec.radius, precision="mixed", tol=spec.tol,
+                    stream=stream, **geom)
             if args.precond == "learned":
                 r.fsai_set(fsai_params)  # host copy of the network weights
             r.init(Y0h)
@@ -481,10 +546,7 @@ def main():
         try:
             out = run_cpu_sample(args.workload, info["lambda_"], 1, args.cpu_window, nnz)
             cpu = {"value": out["per_step_scaled"][0], "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration on the central "
-                             f"{args.cpu_window}x{args.cpu_window} window of the same image with the full "
-                             f"image's lambda ({out['iters'][0]:.0f} PCG iterations per solve), "
-                             f"{out['times'][0]:.1f} s scaled by nnz_A ratio {out['scale']:.1f}"}
+                   "sample": cpu_sample_text(spec, args.cpu_window, out) + f" ({out['times'][0]:.1f} s measured)"}
         except Exception as ex:  # report, do not hide
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
 
@@ -502,7 +564,7 @@ def main():
             "pcg_iters_mean": iters_total / max(n_solves, 1),
             "pcg_iters_max": max(s["pcg_iters_max"] for s in stats),
             "pcg_relres_max": max(s["relres_max"] for s in stats),
-            "gnnz_rhs_per_s": nnz * d * iters_total / (ms / 1e3) / 1e9,
+            "gnnz_rhs_per_s": nnz_iters * d / (ms / 1e3) / 1e9,
             "setup_s": setup_s, "lambda": info["lambda_"],
             "fp32_other_precond": alt,
             "fp64": fp64,

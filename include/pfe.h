@@ -97,7 +97,23 @@ typedef struct pfe_graph_desc {
     const int32_t *ei, *ej;
     int64_t n_edges;
     double sigma;            /* heat-kernel width, > 0 */
+    /* Batch: nseg >= 2 independent problems (images) in one block-diagonal
+     * graph, iterated together (one launch per kernel for all of them), each
+     * with its own lambda (sqrt of its own volume by default), PCG scalars,
+     * convergence and P-step (Alg. 1 and Alg. 2 applied per problem).  nseg =
+     * 0 or 1: one problem, the fields below are not read.  Host arrays:
+     *   PFE_GRAPH_GRID:  seg_hw[2s], seg_hw[2s+1] = H_s, W_s of image s; the
+     *     pixels of image s follow those of image s-1 and n = sum_s H_s W_s
+     *     (H, W are not read);
+     *   PFE_GRAPH_EDGES: seg_off[0..nseg], seg_off[0] = 0, seg_off[nseg] = n:
+     *     segment s is vertices seg_off[s] .. seg_off[s+1]-1; no edge may join
+     *     two segments (PFE_EINVAL).
+     * Every segment has >= 2 vertices; nseg <= PFE_MAX_SEGMENTS. */
+    int32_t nseg;
+    const int32_t *seg_hw;
+    const int64_t *seg_off;
 } pfe_graph_desc;
+#define PFE_MAX_SEGMENTS 4096
 
 typedef struct pfe_params {
     double lambda;        /* split-Bregman penalty (Alg. 2); <= 0 selects sqrt(sum_i d_i) */
@@ -128,6 +144,7 @@ typedef struct pfe_info {
     double lambda, r;     /* values in use */
     double vol;           /* sum_i d_i */
     int64_t device_bytes; /* bytes of device memory the context holds */
+    int32_t nseg;         /* problems in the batch (1 for one problem) */
 } pfe_info;
 
 typedef struct pfe_step_stats {
@@ -139,10 +156,13 @@ typedef struct pfe_step_stats {
 typedef struct pfe_solve_stats {
     int64_t pcg_iters_total;  /* sum over solves of the per-solve iteration count */
     int32_t pcg_iters_max;    /* largest per-solve iteration count */
-    int32_t n_solves;         /* inner steps run by this call */
+    int32_t n_solves;         /* inner steps run by this call (times the batch's problems) */
     int32_t n_unconverged;    /* solves that stopped at max_iter */
     double relres_max;        /* largest final relative residual of any solve */
     int64_t kernel_launches;  /* libpfe kernels launched by this call's iterations */
+    int64_t pcg_rounds;       /* PCG iterations the kernels ran, summed over inner steps: for a
+                                 batch the longest problem's count per step (= pcg_iters_total
+                                 for one problem) */
 } pfe_solve_stats;
 
 /*
@@ -215,6 +235,18 @@ PFE_API pfe_status pfe_get_info(const pfe_ctx *c, pfe_info *info);
 
 /* Changes the stream later calls enqueue on. */
 PFE_API pfe_status pfe_set_stream(pfe_ctx *c, pfe_stream_t stream);
+
+/* Segments of a batch (host arrays, either may be NULL): off[0..nseg] first
+ * vertex of each problem (off[nseg] = n), lambda[0..nseg-1] the penalty in
+ * use for each.  Never synchronises. */
+PFE_API pfe_status pfe_get_segments(const pfe_ctx *c, int64_t *off, double *lambda);
+
+/* Per-problem outcome of the PCG solves (after pfe_init; host arrays, any
+ * may be NULL): iters[s] iterations problem s ran in the last solve before
+ * all its columns reached tol (or the cap), relres[s*d + c] the final
+ * relative residual of its column c, iters_total[s] its iterations summed
+ * over the solves of the last pfe_solve call.  Synchronises. */
+PFE_API pfe_status pfe_get_segment_stats(pfe_ctx *c, int32_t *iters, double *relres, int64_t *iters_total);
 
 /*
  * State arrays, for checkpoint/resume and for tests (all FP64, row-major,

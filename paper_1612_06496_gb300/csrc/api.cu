@@ -60,6 +60,9 @@ void free_work(pfe_ctx *c) {
     c->fsai.t = nullptr;
     c->fsai.z = nullptr;
     c->fsai.r1 = nullptr;
+    c->sc = SegScal{};
+    c->seg_T = nullptr;
+    c->seg_pticket = nullptr;
     c->inited = false;
     c->d = 0;
 }
@@ -185,6 +188,8 @@ pfe_status clear_stats(pfe_ctx *c) {
     const size_t off = offsetof(PcgCtl, tot_iters), end = offsetof(PcgCtl, unroll);
     PFE_CUDA_TRY(c, cudaMemsetAsync((char *)c->ctl + off, 0, end - off, c->stream));
     PFE_CUDA_TRY(c, cudaMemsetAsync((char *)c->ctl + offsetof(PcgCtl, launches), 0, sizeof(long long), c->stream));
+    if (c->sc.seg_iters_tot)
+        PFE_CUDA_TRY(c, cudaMemsetAsync(c->sc.seg_iters_tot, 0, sizeof(long long) * c->nseg, c->stream));
     return PFE_OK;
 }
 
@@ -279,10 +284,36 @@ pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_pa
     if (!gd || !p) return PFE_EINVAL;
     if (gd->n < 2 || gd->m < 1 || !gd->features || !(gd->sigma > 0.0)) return PFE_EINVAL;
     if (gd->n > (int64_t)INT32_MAX - 64) return PFE_EINVAL;
+    const int nseg = gd->nseg > 1 ? gd->nseg : 1;
+    if (gd->nseg < 0 || nseg > PFE_MAX_SEGMENTS) return PFE_EINVAL;
+    std::vector<int64_t> soff(nseg + 1, 0);
+    std::vector<int> sh(nseg, 0), sw(nseg, 0);
     if (gd->kind == PFE_GRAPH_GRID) {
-        if (gd->H < 1 || gd->W < 1 || (int64_t)gd->H * gd->W != gd->n) return PFE_EINVAL;
         if (!(gd->radius >= 1.0) || gd->radius > 8.0) return PFE_EINVAL;
+        if (nseg == 1) {
+            if (gd->H < 1 || gd->W < 1 || (int64_t)gd->H * gd->W != gd->n) return PFE_EINVAL;
+            sh[0] = gd->H;
+            sw[0] = gd->W;
+        } else {
+            if (!gd->seg_hw) return PFE_EINVAL;
+            for (int q = 0; q < nseg; ++q) {
+                sh[q] = gd->seg_hw[2 * q];
+                sw[q] = gd->seg_hw[2 * q + 1];
+                if (sh[q] < 1 || sw[q] < 1 || (int64_t)sh[q] * sw[q] < 2) return PFE_EINVAL;
+                soff[q + 1] = soff[q] + (int64_t)sh[q] * sw[q];
+            }
+            if (soff[nseg] != gd->n) return PFE_EINVAL;
+        }
+        soff[nseg] = gd->n;
     } else if (gd->kind == PFE_GRAPH_EDGES) {
+        if (nseg > 1) {
+            if (!gd->seg_off || gd->seg_off[0] != 0 || gd->seg_off[nseg] != gd->n) return PFE_EINVAL;
+            for (int q = 0; q < nseg; ++q) {
+                if (gd->seg_off[q + 1] - gd->seg_off[q] < 2) return PFE_EINVAL;
+                soff[q + 1] = gd->seg_off[q + 1];
+            }
+        }
+        soff[nseg] = gd->n;
         if (gd->n_edges < 1 || !gd->ei || !gd->ej || gd->n_edges > (int64_t)INT32_MAX / 2) return PFE_EINVAL;
     } else {
         return PFE_EINVAL;
@@ -305,6 +336,11 @@ pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_pa
     c->sigma = gd->sigma;
     c->mixed = p->precision == PFE_MIXED;
     c->g.n_edges = gd->kind == PFE_GRAPH_EDGES ? gd->n_edges : 0;
+    c->g.n = gd->n;
+    c->nseg = nseg;
+    c->h_seg_off = soff;
+    c->h_seg_h = sh;
+    c->h_seg_w = sw;
     auto bail = [&](pfe_status s) {
         std::string msg = c->err;
         pfe_destroy(c);
@@ -340,7 +376,8 @@ pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_pa
             return bail(PFE_ECUDA);
         dfeat = feat_tmp;
     }
-    pfe_status st;
+    pfe_status st = setup_segments(c);
+    if (st != PFE_OK) return bail(st);
     if (gd->kind == PFE_GRAPH_GRID) {
         st = build_grid_graph(c, dfeat);
     } else {
@@ -361,6 +398,7 @@ pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_pa
             dej = ej_tmp;
         }
         st = build_edge_graph(c, dfeat, dei, dej);
+        if (st == PFE_OK && nseg > 1) st = check_edges_in_segments(c);
     }
     if (st != PFE_OK) return bail(st);
     st = finish_graph_values(c);
@@ -391,6 +429,30 @@ pfe_status pfe_get_info(const pfe_ctx *c, pfe_info *info) {
     info->r = c->r;
     info->vol = c->vol;
     info->device_bytes = c->bytes;
+    info->nseg = c->nseg;
+    return PFE_OK;
+}
+
+pfe_status pfe_get_segments(const pfe_ctx *c, int64_t *off, double *lambda) {
+    if (!c) return PFE_EINVAL;
+    if (off)
+        for (int q = 0; q <= c->nseg; ++q) off[q] = c->h_seg_off[q];
+    if (lambda)
+        for (int q = 0; q < c->nseg; ++q) lambda[q] = c->h_seg_lam[q];
+    return PFE_OK;
+}
+
+pfe_status pfe_get_segment_stats(pfe_ctx *c, int32_t *iters, double *relres, int64_t *iters_total) {
+    if (!c) return PFE_EINVAL;
+    if (!c->inited) return fail(c, PFE_ESTATE, "pfe_get_segment_stats before pfe_init");
+    PFE_TRY(sync(c));
+    if (iters)
+        PFE_CUDA_TRY(c, cudaMemcpy(iters, c->sc.seg_iters, sizeof(int) * c->nseg, cudaMemcpyDeviceToHost));
+    if (relres)
+        PFE_CUDA_TRY(c, cudaMemcpy(relres, c->sc.relres, sizeof(double) * c->nseg * c->d, cudaMemcpyDeviceToHost));
+    if (iters_total)
+        PFE_CUDA_TRY(c, cudaMemcpy(iters_total, c->sc.seg_iters_tot, sizeof(long long) * c->nseg,
+                                   cudaMemcpyDeviceToHost));
     return PFE_OK;
 }
 
@@ -436,10 +498,20 @@ pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
     PFE_TRY(walloc(c, &w.P, nd));
     PFE_TRY(walloc(c, &w.B, nd));
     PFE_TRY(walloc(c, &w.stage, nd));
-    const int64_t part_pcg = (int64_t)c->num_sms * 8 * 3 * PFE_DMAX;  // <= 8 resident blocks of 256 threads
-    const int64_t part_gram = (int64_t)c->num_sms * 2 * (PFE_DMAX * (PFE_DMAX + 1) / 2);
+    // <= 8 resident blocks of 256 threads, and at least one block per segment
+    const int64_t part_pcg = std::max<int64_t>((int64_t)c->num_sms * 8, c->nseg) * 3 * PFE_DMAX;
+    const int64_t part_gram = std::max<int64_t>((int64_t)c->num_sms * 2, c->nseg) * (PFE_DMAX * (PFE_DMAX + 1) / 2);
     w.partials_len = std::max(part_pcg, part_gram);
     PFE_TRY(walloc(c, &w.partials, w.partials_len));
+    {
+        unsigned char *scb;
+        PFE_TRY(walloc(c, &scb, (int64_t)segscal_bytes(c->nseg, d)));
+        c->sc = segscal_carve(scb, c->nseg, d);
+        PFE_CUDA_TRY(c, cudaMemsetAsync(scb, 0, segscal_bytes(c->nseg, d), c->stream));
+        PFE_TRY(walloc(c, &c->seg_T, (int64_t)c->nseg * d * d));
+        PFE_TRY(walloc(c, &c->seg_pticket, c->nseg));
+        PFE_CUDA_TRY(c, cudaMemsetAsync(c->seg_pticket, 0, sizeof(unsigned) * c->nseg, c->stream));
+    }
     const size_t es = elem_size(c);
     PFE_CUDA_TRY(c, cudaMemsetAsync(w.Bs[0], 0, (size_t)ed * es, c->stream));
     PFE_CUDA_TRY(c, cudaMemsetAsync(w.Bs[1], 0, (size_t)ed * es, c->stream));
@@ -521,6 +593,7 @@ pfe_status pfe_solve(pfe_ctx *c, int32_t n_outer, int32_t n_inner, double *Y_out
     PFE_TRY(read_ctl(c));
     if (st) {
         st->pcg_iters_total = c->h_ctl->tot_iters;
+        st->pcg_rounds = c->h_ctl->tot_rounds;
         st->pcg_iters_max = c->h_ctl->max_solve_iters;
         st->n_solves = c->h_ctl->n_solves;
         st->n_unconverged = c->h_ctl->n_unconv;
@@ -732,6 +805,7 @@ int32_t pfe_fsai_param_count(void) { return kNParam; }
 
 pfe_status pfe_fsai_set(pfe_ctx *c, const float *params) {
     if (!c) return PFE_EINVAL;
+    if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner is built for one problem, not a batch");
     PFE_TRY(sync(c));
     if (!params) {
         c->fsai.enabled = false;
@@ -749,6 +823,7 @@ pfe_status pfe_fsai_set(pfe_ctx *c, const float *params) {
 
 pfe_status pfe_fsai_classical(pfe_ctx *c) {
     if (!c) return PFE_EINVAL;
+    if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner is built for one problem, not a batch");
     if (!c->mixed) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner runs on the mixed-precision path");
     PFE_TRY(sync(c));
     PFE_TRY(fsai_alloc(c));
@@ -760,6 +835,7 @@ pfe_status pfe_fsai_classical(pfe_ctx *c) {
 
 pfe_status pfe_fsai_loss_grad(pfe_ctx *c, const float *params, float *grad, double *loss) {
     if (!c || !params || !loss) return PFE_EINVAL;
+    if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner is built for one problem, not a batch");
     PFE_TRY(fsai_alloc(c));
     PFE_CUDA_TRY(c, cudaMemcpyAsync(c->fsai.params, params, kNParam * sizeof(float), cudaMemcpyDefault, c->stream));
     PFE_TRY(fsai_loss_grad(c, loss));

@@ -194,18 +194,60 @@ __device__ __forceinline__ void block_reduce(typename Acc<T>::type (&v)[NV], dou
 // "Last block done" detection: every block calls this after writing its
 // partials; exactly one block (the last to arrive) gets true and must reset
 // the ticket.  No waiting is involved.
-__device__ __forceinline__ bool last_block_arrives(unsigned *ticket) {
+__device__ __forceinline__ bool last_block_arrives(unsigned *ticket, unsigned count) {
     __shared__ bool am_last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned t = atomicAdd(ticket, 1u);
-        am_last = (t == gridDim.x - 1);
+        am_last = (t == count - 1);
     }
     __syncthreads();
     if (am_last) __threadfence();
     return am_last;
 }
+__device__ __forceinline__ bool last_block_arrives(unsigned *ticket) { return last_block_arrives(ticket, gridDim.x); }
+
+// ---- segments ----------------------------------------------------------------
+// The blocks of a grid of G >= nseg blocks are split among the segments in
+// proportion to their rows, at least one each: segment s owns blocks
+// [seg_first_block(s), seg_first_block(s + 1)).
+__device__ __forceinline__ int seg_first_block(const Segs &sg, int s, int G) {
+    return s + (int)(((int64_t)(G - sg.nseg) * sg.off[s]) / sg.n);
+}
+struct BlockSeg {
+    int seg, b0, nb;  // segment of this block, its first block and block count
+    int64_t r0, r1;   // its rows
+};
+// MS = false: a single problem known at compile time (no segment lookups).
+template <bool MS = true>
+__device__ __forceinline__ BlockSeg block_seg(const Segs &sg) {
+    BlockSeg o;
+    const int G = (int)gridDim.x, b = (int)blockIdx.x;
+    if (!MS || sg.nseg == 1) {
+        o.seg = 0;
+        o.b0 = 0;
+        o.nb = G;
+        o.r0 = 0;
+        o.r1 = sg.n;
+        return o;
+    }
+    int lo = 0, hi = sg.nseg - 1;  // the last segment whose first block is <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_first_block(sg, mid, G) <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    o.seg = lo;
+    o.b0 = seg_first_block(sg, lo, G);
+    o.nb = seg_first_block(sg, lo + 1, G) - o.b0;
+    o.r0 = sg.off[lo];
+    o.r1 = sg.off[lo + 1];
+    return o;
+}
+__device__ __forceinline__ int row_seg(const Segs &sg, int64_t i) { return sg.nseg == 1 ? 0 : __ldg(sg.rseg + i); }
 
 __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
 
@@ -217,6 +259,32 @@ enum GridSlot {
     G_INIT = 0, G_INIT_F, G_PUPD, G_PUPD_F, G_SPMM, G_UPDATE, G_FSAI_TR, G_XFLUSH, G_REFRESH, G_REFRESH_F,
     G_FSAI_T, G_FSAI_T1, G_FSAI_Z, G_APPLY, G_EDGE, G_PAPPLY, G_TIME_SPMM, G_TIME_UPDATE, G_NSLOTS
 };
+inline Segs seg_view(const pfe_ctx *c) { return Segs{c->nseg, c->g.n, c->seg_off, c->rseg}; }
+
+// One allocation holds every array of a SegScal: bytes needed, and the
+// arrays carved from a base pointer (doubles first, then ints).
+inline size_t segscal_bytes(int nseg, int d) {
+    return sizeof(double) * 5 * (size_t)nseg * d + sizeof(long long) * (size_t)nseg +
+           sizeof(int) * ((size_t)nseg * d + 2 * (size_t)nseg) + sizeof(unsigned) * 4 * (size_t)nseg;
+}
+inline SegScal segscal_carve(void *base, int nseg, int d) {
+    SegScal sc;
+    double *dp = reinterpret_cast<double *>(base);
+    const size_t nd = (size_t)nseg * d;
+    sc.bnorm = dp;
+    sc.rz = dp + nd;
+    sc.alpha = dp + 2 * nd;
+    sc.beta = dp + 3 * nd;
+    sc.relres = dp + 4 * nd;
+    sc.seg_iters_tot = reinterpret_cast<long long *>(dp + 5 * nd);
+    int *ip = reinterpret_cast<int *>(sc.seg_iters_tot + nseg);
+    sc.active = ip;
+    sc.seg_active = ip + nd;
+    sc.seg_iters = ip + nd + nseg;
+    sc.ticket = reinterpret_cast<unsigned *>(ip + nd + 2 * nseg);
+    return sc;
+}
+
 template <typename K>
 inline int wave_grid(pfe_ctx *c, int slot, K kernel, int64_t need, int mult = 1, size_t smem = 0) {
     int &g = c->kgrid[slot];
@@ -230,6 +298,8 @@ inline int wave_grid(pfe_ctx *c, int slot, K kernel, int64_t need, int mult = 1,
         if (c->prm.blocks_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)c->prm.blocks_per_sm * c->num_sms);
         grid = std::min<int64_t>(grid, std::max<int64_t>(need, 1));
         if (mult > 1) grid = std::max<int64_t>(mult, grid / mult * mult);
+        // every segment owns at least one block of a row kernel
+        if (grid < c->nseg) grid = (c->nseg + std::max(mult, 1) - 1) / std::max(mult, 1) * std::max(mult, 1);
         g = (int)grid;
     }
     return g;

@@ -32,6 +32,8 @@ struct EdgeArgs {
     const T *__restrict__ cw;
     T *__restrict__ rhs;
     T lambda, gamma;
+    Segs sg;                // batch: lambda of each row's segment
+    const double *seg_lam;  // nseg
 };
 
 template <typename T, int V>
@@ -63,7 +65,7 @@ __device__ __forceinline__ void estv(T *p, const T (&v)[V]) {
     }
 }
 
-template <typename T, int D>
+template <typename T, int D, bool MS>
 __global__ void __launch_bounds__(kBlock) k_edge(EdgeArgs<T> a) {
     // L = D/V lanes per row, V consecutive columns per lane (V = widest of
     // 16/8/4 bytes dividing a row): row loads of y, b and C are contiguous
@@ -83,6 +85,12 @@ __global__ void __launch_bounds__(kBlock) k_edge(EdgeArgs<T> a) {
         const int s0 = a.slice_ptr[s];
         const int len = (a.slice_ptr[s + 1] - s0) >> 5;
         const int64_t base = (int64_t)s0 + (i & 31) * (int64_t)len;  // row-major within the slice
+        T lam = a.lambda, gam = a.gamma;
+        if constexpr (MS) {  // batch: lambda of the row's segment
+            const double ls = a.seg_lam[__ldg(a.sg.rseg + i)];
+            lam = (T)ls;
+            gam = (T)(1.0 / ls);
+        }
         T yi[V], acc[V];
         eldv<T, V>(a.y + i * D + c0, yi);
 #pragma unroll
@@ -125,7 +133,7 @@ __global__ void __launch_bounds__(kBlock) k_edge(EdgeArgs<T> a) {
                 for (int k = 0; k < V; ++k) {
                     const T diff = first ? (yi[k] - yj[u][k]) : (yj[u][k] - yi[k]);  // y_a - y_b
                     const T t = ww[u] * diff + bo[u][k];                              // (M Y + b)_e
-                    const T z = shrink<T>(t, a.gamma);                                // d_e
+                    const T z = shrink<T>(t, gam);                                    // d_e
                     bn[k] = t - z;                                                    // b'_e
                     const T v = ww[u] * (z - bn[k]);
                     acc[k] = first ? acc[k] + v : acc[k] - v;
@@ -136,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) k_edge(EdgeArgs<T> a) {
         T ci[V];
         eldv<T, V>(a.cw + i * D + c0, ci);
 #pragma unroll
-        for (int k = 0; k < V; ++k) acc[k] = a.lambda * acc[k] + ci[k];
+        for (int k = 0; k < V; ++k) acc[k] = lam * acc[k] + ci[k];
         estv<T, V>(a.rhs + i * D + c0, acc);
     }
 }
@@ -160,10 +168,15 @@ pfe_status edge_T(pfe_ctx *c, cudaStream_t s) {
     a.rhs = (T *)c->wk.RHS;
     a.lambda = (T)c->lambda;
     a.gamma = (T)(1.0 / c->lambda);
+    a.sg = seg_view(c);
+    a.seg_lam = c->seg_lam;
     constexpr int V = (sizeof(T) == 4 && D % 4 == 0) ? 4 : (D % 2 == 0 ? 2 : 1);
     constexpr int RPW = 32 / (D / V);
     const int64_t need = ((c->g.n + RPW - 1) / RPW + kWarps - 1) / kWarps;
-    k_edge<T, D><<<wave_grid(c, G_EDGE, k_edge<T, D>, need), kBlock, 0, s>>>(a);
+    if (c->nseg > 1)
+        k_edge<T, D, true><<<wave_grid(c, G_EDGE, k_edge<T, D, true>, need), kBlock, 0, s>>>(a);
+    else
+        k_edge<T, D, false><<<wave_grid(c, G_EDGE, k_edge<T, D, false>, need), kBlock, 0, s>>>(a);
     PFE_CUDA_TRY(c, cudaGetLastError());
     c->bs_cur = 1 - c->bs_cur;
     return PFE_OK;

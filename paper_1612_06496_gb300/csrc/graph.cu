@@ -36,13 +36,33 @@ __device__ __forceinline__ double heat_weight(const double *__restrict__ X, int 
 
 // ---- grid graphs --------------------------------------------------------
 
-__global__ void k_grid_count(int64_t n, int64_t n_slices, int H, int W, Offsets off, int *nf_row,
+// Images of a grid graph: image s has H = h[s], W = w[s] and its pixels are
+// vertices off[s] .. off[s+1]-1 (one image: nseg = 1, off = {0, n}).
+struct GridSegs {
+    int nseg;
+    const int64_t *off;
+    const int *h, *w;
+    const int *rseg;
+};
+__device__ __forceinline__ void grid_pos(const GridSegs &gs, int64_t i, int64_t &vo, int &H, int &W, int &x, int &y) {
+    const int s = gs.nseg == 1 ? 0 : gs.rseg[i];
+    vo = gs.off[s];
+    H = gs.h[s];
+    W = gs.w[s];
+    const int64_t li = i - vo;
+    x = (int)(li % W);
+    y = (int)(li / W);
+}
+
+__global__ void k_grid_count(int64_t n, int64_t n_slices, GridSegs gs, Offsets off, int *nf_row,
                              int *slice_len, int *fslice_len) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if ((i >> 5) >= n_slices) return;  // whole warps only
     int nb = 0, nf = 0;
     if (i < n) {
-        int x = (int)(i % W), y = (int)(i / W);
+        int64_t vo;
+        int H, W, x, y;
+        grid_pos(gs, i, vo, H, W, x, y);
         for (int t = 0; t < off.K; ++t) {
             int x2 = x + off.dx[t], y2 = y + off.dy[t];
             if (x2 >= 0 && x2 < W && y2 >= 0 && y2 < H) {
@@ -61,7 +81,7 @@ __global__ void k_grid_count(int64_t n, int64_t n_slices, int H, int W, Offsets 
     }
 }
 
-__global__ void k_grid_fill(int64_t n, int64_t n_slices, int H, int W, Offsets off, const int64_t *slice_ptr,
+__global__ void k_grid_fill(int64_t n, int64_t n_slices, GridSegs gs, Offsets off, const int64_t *slice_ptr,
                             const int64_t *fslice_ptr, const int64_t *fw_off, const double *__restrict__ X,
                             int m, double inv2s2, int *col, int *eid, double *w64, int *ext_slot, int *ea,
                             int *eb, double *ew, double *deg, double *deg2) {
@@ -74,13 +94,15 @@ __global__ void k_grid_fill(int64_t n, int64_t n_slices, int H, int W, Offsets o
     const int flen = (int)((fslice_ptr[s + 1] - fslice_ptr[s]) >> 5);
     int k = 0;
     if (i < n) {
-        int x = (int)(i % W), y = (int)(i / W);
+        int64_t vo;
+        int H, W, x, y;
+        grid_pos(gs, i, vo, H, W, x, y);
         int kf = 0;
         double sw = 0.0, sw2 = 0.0;
         for (int t = 0; t < off.K; ++t) {
             int x2 = x + off.dx[t], y2 = y + off.dy[t];
             if (x2 < 0 || x2 >= W || y2 < 0 || y2 >= H) continue;
-            int64_t j = (int64_t)y2 * W + x2;
+            int64_t j = vo + (int64_t)y2 * W + x2;
             int64_t idx = base + k;
             double w = (j > i) ? heat_weight(X, m, i, j, inv2s2) : heat_weight(X, m, j, i, inv2s2);
             int e;
@@ -328,6 +350,61 @@ __global__ void k_values_rows(int64_t n, double lam, double r, const double *deg
     dinv32[i] = (float)(1.0 / a);
 }
 
+// Segment of each row (binary search over the offsets).
+__global__ void k_fill_rseg(int64_t n, int nseg, const int64_t *off, int *rseg) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    rseg[i] = lo;
+}
+
+// vol_s = sum of d_i over segment s: one block per segment, fixed order.
+__global__ void k_seg_sum(const int64_t *off, const double *v, double *out) {
+    const int s = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t i = off[s] + threadIdx.x; i < off[s + 1]; i += blockDim.x) acc += v[i];
+    double tmp[1] = {acc};
+    __shared__ double res[1];
+    block_reduce<double, 1>(tmp, res);
+    if (threadIdx.x == 0) out[s] = res[0];
+}
+
+// Slot and row values of A with the lambda of each row's segment (batch).
+__global__ void k_values_seg(int64_t n, int64_t n_slices, const int *slice_ptr, const int *rseg,
+                             const double *seg_lam, double r, const double *w64, float *w32, double *aoff64,
+                             float *aoff32, const double *deg, const double *deg2, double *sqrtdeg, double *adiag64,
+                             float *adiag32, double *dinv64, float *dinv32, int *err) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t s = i >> 5;
+    if (s >= n_slices) return;
+    const double lam = i < n ? seg_lam[rseg[i]] : 0.0;
+    const int len = (slice_ptr[s + 1] - slice_ptr[s]) >> 5;
+    const int64_t base = (int64_t)slice_ptr[s] + (i & 31) * (int64_t)len;
+    for (int k = 0; k < len; ++k) {
+        const double w = w64[base + k];
+        const double av = -lam * (w * w);
+        w32[base + k] = (float)w;
+        aoff64[base + k] = av;
+        aoff32[base + k] = (float)av;
+    }
+    if (i >= n) return;
+    const double d = deg[i];
+    if (!(d > 0.0)) atomicExch(err, 3);
+    const double a = lam * deg2[i] + r * d;
+    sqrtdeg[i] = sqrt(d);
+    adiag64[i] = a;
+    adiag32[i] = (float)a;
+    dinv64[i] = 1.0 / a;
+    dinv32[i] = (float)(1.0 / a);
+}
+
 template <typename P>
 pfe_status dalloc(pfe_ctx *c, P **p, int64_t count) {
     size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(P);
@@ -482,7 +559,8 @@ pfe_status build_grid_graph(pfe_ctx *c, const double *dfeat) {
     PFE_TRY(talloc(c, t_sp, &slice_ptr64, g.n_slices + 1));
     PFE_TRY(talloc(c, t_fsp, &fslice_ptr64, g.n_slices + 1));
     PFE_TRY(talloc(c, t_fw, &fw_off, g.n + 1));
-    k_grid_count<<<nblk(nthreads, 256), 256, 0, s>>>(g.n, g.n_slices, c->H, c->W, off, nf_row, slice_len, fslice_len);
+    const GridSegs gs{c->nseg, c->seg_off, c->seg_h, c->seg_w, c->rseg};
+    k_grid_count<<<nblk(nthreads, 256), 256, 0, s>>>(g.n, g.n_slices, gs, off, nf_row, slice_len, fslice_len);
     PFE_CUDA_TRY(c, cudaGetLastError());
     PFE_TRY(scan_exclusive(c, s, slice_len, nullptr, g.n_slices, slice_ptr64));
     PFE_TRY(scan_exclusive(c, s, fslice_len, nullptr, g.n_slices, fslice_ptr64));
@@ -493,7 +571,7 @@ pfe_status build_grid_graph(pfe_ctx *c, const double *dfeat) {
     PFE_TRY(max_row_slots(c, s, slice_len));
     PFE_TRY(alloc_slots(c, s, slice_ptr64, fslice_ptr64));
     const double inv2s2 = 1.0 / (2.0 * c->sigma * c->sigma);
-    k_grid_fill<<<nblk(nthreads, 128), 128, 0, s>>>(g.n, g.n_slices, c->H, c->W, off, slice_ptr64, fslice_ptr64, fw_off,
+    k_grid_fill<<<nblk(nthreads, 128), 128, 0, s>>>(g.n, g.n_slices, gs, off, slice_ptr64, fslice_ptr64, fw_off,
                                                      dfeat, c->m, inv2s2, g.col, g.eid, g.w64, g.ext_slot, g.ea,
                                                      g.eb, g.ew, g.deg, g.deg2);
     PFE_CUDA_TRY(c, cudaGetLastError());
@@ -555,6 +633,47 @@ pfe_status build_edge_graph(pfe_ctx *c, const double *dfeat, const int32_t *dei,
     return PFE_OK;
 }
 
+__global__ void k_check_edge_segs(int64_t ne, const int *ea, const int *eb, const int *rseg, int *err) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < ne && rseg[ea[k]] != rseg[eb[k]]) atomicExch(err, 1);
+}
+
+// A batch's edge list must stay inside the segments.
+pfe_status check_edges_in_segments(pfe_ctx *c) {
+    cudaStream_t s = c->stream;
+    Tmp t_err;
+    int *derr, herr = 0;
+    PFE_TRY(talloc(c, t_err, &derr, 1));
+    PFE_CUDA_TRY(c, cudaMemsetAsync(derr, 0, sizeof(int), s));
+    k_check_edge_segs<<<nblk(c->g.n_edges, 256), 256, 0, s>>>(c->g.n_edges, c->g.ea, c->g.eb, c->rseg, derr);
+    PFE_CUDA_TRY(c, cudaGetLastError());
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PFE_CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (herr) {
+        c->err = "an edge joins two segments of the batch";
+        return PFE_EINVAL;
+    }
+    return PFE_OK;
+}
+
+pfe_status setup_segments(pfe_ctx *c) {
+    cudaStream_t s = c->stream;
+    const int ns = c->nseg;
+    PFE_TRY(dalloc(c, &c->seg_off, ns + 1));
+    PFE_TRY(dalloc(c, &c->seg_h, ns));
+    PFE_TRY(dalloc(c, &c->seg_w, ns));
+    PFE_TRY(dalloc(c, &c->seg_lam, ns));
+    PFE_TRY(dalloc(c, &c->rseg, c->n));
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(c->seg_off, c->h_seg_off.data(), sizeof(int64_t) * (ns + 1),
+                                    cudaMemcpyHostToDevice, s));
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(c->seg_h, c->h_seg_h.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(c->seg_w, c->h_seg_w.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+    k_fill_rseg<<<nblk(c->n, 256), 256, 0, s>>>(c->n, ns, c->seg_off, c->rseg);
+    PFE_CUDA_TRY(c, cudaGetLastError());
+    PFE_CUDA_TRY(c, cudaStreamSynchronize(s));  // the host tables may go out of scope
+    return PFE_OK;
+}
+
 pfe_status finish_graph_values(pfe_ctx *c) {
     cudaStream_t s = c->stream;
     auto &g = c->g;
@@ -570,17 +689,45 @@ pfe_status finish_graph_values(pfe_ctx *c) {
     PFE_TRY(talloc(c, t_err, &derr, 1));
     PFE_CUDA_TRY(c, cudaMemsetAsync(tick, 0, sizeof(unsigned), s));
     PFE_CUDA_TRY(c, cudaMemsetAsync(derr, 0, sizeof(int), s));
-    k_sum_f64<<<nb, kBlock, 0, s>>>(g.n, g.deg, part, tick, res);
-    PFE_CUDA_TRY(c, cudaGetLastError());
-    double vol = 0;
-    PFE_CUDA_TRY(c, cudaMemcpyAsync(&vol, res, sizeof(double), cudaMemcpyDeviceToHost, s));
-    PFE_CUDA_TRY(c, cudaStreamSynchronize(s));
-    c->vol = vol;
-    c->lambda = c->prm.lambda > 0 ? c->prm.lambda : std::sqrt(vol);
     c->r = c->prm.r;
-    k_values_slots<<<nblk(g.slots, 256), 256, 0, s>>>(g.slots, c->lambda, g.w64, g.w32, g.aoff64, g.aoff32);
-    k_values_rows<<<nblk(g.n, 256), 256, 0, s>>>(g.n, c->lambda, c->r, g.deg, g.deg2, g.sqrtdeg, g.adiag64,
-                                                 g.adiag32, g.dinv64, g.dinv32, derr);
+    if (c->nseg == 1) {
+        k_sum_f64<<<nb, kBlock, 0, s>>>(g.n, g.deg, part, tick, res);
+        PFE_CUDA_TRY(c, cudaGetLastError());
+        double vol = 0;
+        PFE_CUDA_TRY(c, cudaMemcpyAsync(&vol, res, sizeof(double), cudaMemcpyDeviceToHost, s));
+        PFE_CUDA_TRY(c, cudaStreamSynchronize(s));
+        c->vol = vol;
+        c->lambda = c->prm.lambda > 0 ? c->prm.lambda : std::sqrt(vol);
+        c->h_seg_vol.assign(1, vol);
+        c->h_seg_lam.assign(1, c->lambda);
+        PFE_CUDA_TRY(c, cudaMemcpyAsync(c->seg_lam, &c->lambda, sizeof(double), cudaMemcpyHostToDevice, s));
+        k_values_slots<<<nblk(g.slots, 256), 256, 0, s>>>(g.slots, c->lambda, g.w64, g.w32, g.aoff64, g.aoff32);
+        k_values_rows<<<nblk(g.n, 256), 256, 0, s>>>(g.n, c->lambda, c->r, g.deg, g.deg2, g.sqrtdeg, g.adiag64,
+                                                     g.adiag32, g.dinv64, g.dinv32, derr);
+    } else {
+        // one volume and one lambda per segment (image)
+        const int ns = c->nseg;
+        Tmp t_vol;
+        double *dvol;
+        PFE_TRY(talloc(c, t_vol, &dvol, ns));
+        k_seg_sum<<<ns, kBlock, 0, s>>>(c->seg_off, g.deg, dvol);
+        PFE_CUDA_TRY(c, cudaGetLastError());
+        c->h_seg_vol.assign(ns, 0.0);
+        PFE_CUDA_TRY(c, cudaMemcpyAsync(c->h_seg_vol.data(), dvol, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+        PFE_CUDA_TRY(c, cudaStreamSynchronize(s));
+        c->h_seg_lam.assign(ns, 0.0);
+        c->vol = 0.0;
+        for (int q = 0; q < ns; ++q) {
+            c->vol += c->h_seg_vol[q];
+            c->h_seg_lam[q] = c->prm.lambda > 0 ? c->prm.lambda : std::sqrt(c->h_seg_vol[q]);
+        }
+        c->lambda = c->h_seg_lam[0];
+        PFE_CUDA_TRY(c, cudaMemcpyAsync(c->seg_lam, c->h_seg_lam.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+        k_values_seg<<<nblk(g.n_slices * 32, 256), 256, 0, s>>>(g.n, g.n_slices, g.slice_ptr, c->rseg, c->seg_lam, c->r,
+                                                                 g.w64, g.w32, g.aoff64, g.aoff32, g.deg, g.deg2,
+                                                                 g.sqrtdeg, g.adiag64, g.adiag32, g.dinv64, g.dinv32,
+                                                                 derr);
+    }
     PFE_CUDA_TRY(c, cudaGetLastError());
     int herr = 0;
     PFE_CUDA_TRY(c, cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));

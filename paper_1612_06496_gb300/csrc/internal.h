@@ -15,8 +15,30 @@
 
 namespace pfe {
 
-// Device-resident control block of one d-column PCG solve.  Written only by
-// the "last block" of a reduction kernel, read by all kernels at entry.
+// Segments: a batch of independent problems (images) stored as one
+// block-diagonal graph; rows [off[s], off[s+1]) belong to segment s.  A single
+// problem is one segment.
+struct Segs {
+    int nseg;
+    int64_t n;               // rows in all segments
+    const int64_t *off;      // nseg + 1 row offsets (device)
+    const int *rseg;         // segment of each row (device)
+};
+
+// Per-segment PCG scalars, index [seg * d + c] (device).  Written only by the
+// last block of a segment in a reduction kernel.
+struct SegScal {
+    double *bnorm, *rz, *alpha, *beta, *relres;  // nseg * d
+    int *active;                                  // nseg * d: column still iterating
+    int *seg_active;                              // nseg: any column of the segment iterating
+    int *seg_iters;                               // nseg: iterations of the segment in this solve
+    long long *seg_iters_tot;                     // nseg: summed over solves until the host clears it
+    unsigned *ticket;                             // nseg * 4: per-segment reduction tickets
+};
+
+// Device-resident control block of one d-column PCG solve (all segments).
+// The per-segment finishers of a reduction kernel count themselves on
+// `ticket`; the last one finishes the iteration (global flags, statistics).
 struct PcgCtl {
     int iter;          // iterations done in the current solve
     int done;          // 1: every column converged, max_iter hit, or an error
@@ -25,10 +47,8 @@ struct PcgCtl {
     unsigned ticket[4];
     int max_iter, refresh, ncols, any_active;
     double tol;
-    double bnorm[PFE_DMAX], rz[PFE_DMAX], alpha[PFE_DMAX], beta[PFE_DMAX], relres[PFE_DMAX];
-    int active[PFE_DMAX];
     // statistics accumulated over solves until the host clears them
-    long long tot_iters;
+    long long tot_iters, tot_rounds;
     int max_solve_iters, n_solves, n_unconv, last_iters;
     double max_relres, last_relres;
     int last_converged, unroll;       // unroll: iterations per graph body / host poll
@@ -41,7 +61,9 @@ struct PcgCtl {
     int pad2;
 };
 
-// Control block of the P-step (Alg. 1 steps 6-7).
+// Control block of the P-step (Alg. 1 steps 6-7).  G, T and evals are
+// those of segment 0 (the only one of a single problem); a batch keeps every
+// segment's T in pfe_ctx::seg_T.
 struct PstepCtl {
     unsigned ticket;
     int error;
@@ -98,6 +120,18 @@ struct pfe_ctx {
     int64_t n = 0;
     int m = 0, kind = 0, H = 0, W = 0;
     double radius = 0, sigma = 0, lambda = 0, r = 1, vol = 0;
+    // segments (a batch of problems; 1 for a single problem)
+    int nseg = 1;
+    std::vector<int64_t> h_seg_off;   // nseg + 1 row offsets
+    std::vector<int> h_seg_h, h_seg_w;
+    std::vector<double> h_seg_lam, h_seg_vol;
+    int64_t *seg_off = nullptr;       // device copies
+    int *seg_h = nullptr, *seg_w = nullptr;
+    int *rseg = nullptr;              // segment of each row
+    double *seg_lam = nullptr;        // lambda of each segment
+    pfe::SegScal sc{};                // per-segment PCG scalars (allocated by pfe_init)
+    double *seg_T = nullptr;          // nseg x d x d P-step transforms
+    unsigned *seg_pticket = nullptr;  // nseg P-step tickets
     pfe::DevGraph g;
     int d = 0;
     bool inited = false;
@@ -124,6 +158,8 @@ namespace pfe {
 // --- graph.cu
 pfe_status build_grid_graph(pfe_ctx *c, const double *dfeat);
 pfe_status build_edge_graph(pfe_ctx *c, const double *dfeat, const int32_t *dei, const int32_t *dej);
+pfe_status setup_segments(pfe_ctx *c);
+pfe_status check_edges_in_segments(pfe_ctx *c);
 pfe_status finish_graph_values(pfe_ctx *c);
 
 // --- pcg.cu: one PCG solve A Y = RHS on the context's work arrays

@@ -26,6 +26,7 @@
 #pragma once
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 
@@ -54,6 +55,8 @@ struct PcgArgs {
     const T *b;
     void *part;  // block partials, Acc<T>::type
     PcgCtl *ctl;
+    Segs sg;     // segments (a batch of problems; nseg = 1 for one)
+    SegScal sc;  // per-segment scalars [seg * D + c]
     cudaGraphConditionalHandle cond;
     int use_cond;
     // FSAI preconditioner (float path): z = G^T t, t = G r; the residual
@@ -230,11 +233,12 @@ __device__ __forceinline__ void block_sum_cols(typename Acc<T>::type (&v)[NQ][Su
     __syncthreads();
 }
 
-// Write this block's NQ*D partials; the last block to arrive reduces all
-// blocks' partials in a fixed order into out[0..NQ*D) (shared) and returns true.
+// Write this block's NQ*D partials; the last block of the segment to arrive
+// reduces the partials of the segment's blocks in a fixed order into
+// out[0..NQ*D) (shared) and returns true.
 template <typename T, int D, int NQ>
 __device__ __forceinline__ bool grid_sum_cols(typename Acc<T>::type (&v)[NQ][SubWarp<T, D>::V], void *part_v,
-                                              unsigned *ticket, double *out) {
+                                              const BlockSeg &bsg, unsigned *ticket, double *out) {
     using A = Acc<T>;
     using AT = typename A::type;
     constexpr int NV = NQ * D;
@@ -242,14 +246,15 @@ __device__ __forceinline__ bool grid_sum_cols(typename Acc<T>::type (&v)[NQ][Sub
     AT *part = reinterpret_cast<AT *>(part_v);
     block_sum_cols<T, D, NQ>(v, sh);
     for (int t = threadIdx.x; t < NV; t += blockDim.x) part[(int64_t)blockIdx.x * NV + t] = sh[t];
-    if (!last_block_arrives(ticket)) return false;
+    if (!last_block_arrives(ticket, (unsigned)bsg.nb)) return false;
+    part += (int64_t)bsg.b0 * NV;
     // last block: G threads per value, thread (v, h) sums blocks h, h+G, ...;
     // the G partials of a value are then added in order (fixed order overall)
     constexpr int G = (kBlock / NV) > 0 ? (kBlock / NV) : 1;
     __shared__ AT pr[G][NV];
     if (threadIdx.x < G * NV) {
         const int v = threadIdx.x % NV, h = threadIdx.x / NV;
-        const int nb = (int)gridDim.x;
+        const int nb = bsg.nb;
         AT s = A::zero();
         // eight independent loads in flight, then the additions in block order
         for (int b0 = h; b0 < nb; b0 += 8 * G) {
@@ -298,39 +303,74 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, 
     if (use) cudaGraphSetConditional(h, value ? 1u : 0u);
 }
 
-// Finish an iteration (or the start of a solve): residual norms -> relres,
-// beta, freezing, termination.  Runs on thread 0 of the last block.
-static __device__ void finish_scalars(PcgCtl *ctl, const double *rz, const double *rr, int D, bool start,
-                                      cudaGraphConditionalHandle cond, int use_cond) {
+// Per-segment part of finishing an iteration `it` (or the start of a solve):
+// residual norms -> relres, beta, freezing.  Thread 0 of the segment's last
+// block.
+static __device__ void finish_seg(PcgCtl *ctl, const SegScal &sc, int seg, const double *rz, const double *rr, int D,
+                                  bool start, int it) {
     int any = 0;
     for (int c = 0; c < D; ++c) {
+        const int k = seg * D + c;
         if (start) {
-            ctl->rz[c] = rz[c];
-            ctl->beta[c] = 0.0;
-            double rel = sqrt(rr[c]) / ctl->bnorm[c];
-            ctl->relres[c] = rel;
-            if (!(rel == rel) || !(rz[c] == rz[c])) ctl->error = PFE_ENUMERIC;
-            ctl->active[c] = rel > ctl->tol;
-        } else if (ctl->active[c]) {
-            double rel = sqrt(rr[c]) / ctl->bnorm[c];
-            ctl->beta[c] = rz[c] / ctl->rz[c];
-            ctl->rz[c] = rz[c];
-            ctl->relres[c] = rel;
-            if (!(rel == rel) || !(rz[c] == rz[c])) ctl->error = PFE_ENUMERIC;
-            if (rel <= ctl->tol) ctl->active[c] = 0;
+            sc.rz[k] = rz[c];
+            sc.beta[k] = 0.0;
+            const double rel = sqrt(rr[c]) / sc.bnorm[k];
+            sc.relres[k] = rel;
+            if (!(rel == rel) || !(rz[c] == rz[c])) atomicMax(&ctl->error, (int)PFE_ENUMERIC);
+            sc.active[k] = rel > ctl->tol;
+        } else if (sc.active[k]) {
+            const double rel = sqrt(rr[c]) / sc.bnorm[k];
+            sc.beta[k] = rz[c] / sc.rz[k];
+            sc.rz[k] = rz[c];
+            sc.relres[k] = rel;
+            if (!(rel == rel) || !(rz[c] == rz[c])) atomicMax(&ctl->error, (int)PFE_ENUMERIC);
+            if (rel <= ctl->tol) sc.active[k] = 0;
         }
-        any |= ctl->active[c];
+        any |= sc.active[k];
     }
+    if (start)
+        sc.seg_iters[seg] = 0;
+    else if (sc.seg_active[seg])
+        sc.seg_iters[seg] = it;
+    sc.seg_active[seg] = any;
+}
+
+// Thread 0 of a segment's last block, after its segment's work: true for the
+// last segment to get here (the one that finishes the iteration).
+__device__ __forceinline__ bool last_segment_arrives(PcgCtl *ctl, int k, int nseg) {
+    __threadfence();
+    const unsigned t = atomicAdd(&ctl->ticket[k], 1u);
+    if (t != (unsigned)nseg - 1) return false;
+    __threadfence();
+    ctl->ticket[k] = 0u;
+    return true;
+}
+
+// Global part: termination (every segment converged, an error, or max_iter)
+// and the statistics of a finished solve.
+static __device__ void finish_all(PcgCtl *ctl, const SegScal &sc, int nseg, int D, cudaGraphConditionalHandle cond,
+                                  int use_cond) {
+    int any = 0;
+    for (int s = 0; s < nseg; ++s) any |= sc.seg_active[s];
     ctl->any_active = any;
-    int done = (!any) || ctl->error || ctl->iter >= ctl->max_iter;
+    const int done = (!any) || ctl->error || ctl->iter >= ctl->max_iter;
     if (done) {
         double mr = 0.0;
-        for (int c = 0; c < D; ++c) mr = fmax(mr, ctl->relres[c]);
-        ctl->tot_iters += ctl->iter;
-        ctl->max_solve_iters = max(ctl->max_solve_iters, ctl->iter);
-        ctl->n_solves += 1;
-        ctl->n_unconv += any ? 1 : 0;
-        ctl->last_iters = ctl->iter;
+        long long tot = 0;
+        int mx = 0, nun = 0;
+        for (int s = 0; s < nseg; ++s) {
+            tot += sc.seg_iters[s];
+            sc.seg_iters_tot[s] += sc.seg_iters[s];
+            mx = max(mx, sc.seg_iters[s]);
+            nun += sc.seg_active[s] ? 1 : 0;
+            for (int c = 0; c < D; ++c) mr = fmax(mr, sc.relres[s * D + c]);
+        }
+        ctl->tot_iters += tot;
+        ctl->tot_rounds += ctl->iter;
+        ctl->max_solve_iters = max(ctl->max_solve_iters, mx);
+        ctl->n_solves += nseg;
+        ctl->n_unconv += nun;
+        ctl->last_iters = mx;
         ctl->last_relres = mr;
         ctl->last_converged = !any;
         ctl->max_relres = fmax(ctl->max_relres, mr);
@@ -399,20 +439,34 @@ __device__ __forceinline__ void true_residual(const PcgArgs<T> &a, int64_t i, in
     }
 }
 
-#define PFE_ROW_LOOP(T_, D_)                                                                               \
+// Row loop of a row kernel: the block's segment (block_seg), its warps
+// stride over the segment's row groups.  LIVE skips segments whose columns
+// have all converged.  Inside, PFE_ROW_I defines row i (skips lanes past the
+// segment).
+#define PFE_ROW_LOOP_(T_, D_, LIVE_, MS_)                                                                  \
     using SW = SubWarp<T_, D_>;                                                                            \
     constexpr int V = SW::V;                                                                               \
     const SW lm;                                                                                           \
-    const int64_t warp_g = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);                              \
-    const int64_t warps_total = (int64_t)gridDim.x * kWarps;                                               \
-    for (int64_t g = warp_g; g * SW::RPW < a.A.n; g += warps_total)
+    const BlockSeg bsg = block_seg<MS_>(a.sg);                                                             \
+    const int64_t warp_g = (int64_t)(blockIdx.x - bsg.b0) * kWarps + (threadIdx.x >> 5);                   \
+    const int64_t warps_total = (int64_t)bsg.nb * kWarps;                                                  \
+    const int64_t seg_rows = ((MS_) && (LIVE_) && !a.sc.seg_active[bsg.seg]) ? 0 : bsg.r1 - bsg.r0;      \
+    for (int64_t g = warp_g; g * SW::RPW < seg_rows; g += warps_total)
+// one problem (FSAI kernels, y = A x)
+#define PFE_ROW_LOOP(T_, D_) PFE_ROW_LOOP_(T_, D_, false, false)
+// MS: batch (segments) or one problem; LIVE skips converged segments
+#define PFE_ROW_LOOP_MS(T_, D_, MS_) PFE_ROW_LOOP_(T_, D_, false, MS_)
+#define PFE_ROW_LOOP_LIVE(T_, D_, MS_) PFE_ROW_LOOP_(T_, D_, true, MS_)
+#define PFE_ROW_I                                 \
+    const int64_t i = bsg.r0 + g * SW::RPW + lm.r; \
+    if (!lm.active || i >= bsg.r1) continue
 
 // ---- kernels ----------------------------------------------------------------
 
 // Start of a solve: r = b - A y, norms of b and r, r.z with z = D_A^{-1} r.
 // With the FSAI preconditioner (PRE = 1) z = G^T G r is made by k_fsai_t /
 // k_fsai_z, which also finish the start of the solve.
-template <typename T, int D, int PRE>
+template <typename T, int D, int PRE, bool MS>
 __global__ void __launch_bounds__(kBlock) k_pcg_init(PcgArgs<T> a) {
     using A = Acc<T>;
     using AT = typename A::type;
@@ -422,9 +476,8 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(PcgArgs<T> a) {
     for (int q = 0; q < 3; ++q)
 #pragma unroll
         for (int k = 0; k < SWt::V; ++k) acc[q][k] = A::zero();
-    PFE_ROW_LOOP(T, D) {
-        const int64_t i = g * SW::RPW + lm.r;
-        if (!lm.active || i >= a.A.n) continue;
+    PFE_ROW_LOOP_MS(T, D, MS) {
+        PFE_ROW_I;
         const int c0 = lm.cg * V;
         T ri[V], bi[V];
         true_residual<T, D, V>(a, i, c0, ri);
@@ -439,25 +492,29 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(PcgArgs<T> a) {
         }
         stv<T, V>(a.r + i * D + c0, ri);
     }
+    // ctl->error was cleared before this launch (segment finishers may set it)
     __shared__ double tot[3 * D];
-    if (grid_sum_cols<T, D, 3>(acc, a.part, &a.ctl->ticket[2], tot)) {
+    if (grid_sum_cols<T, D, 3>(acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 2], tot)) {
         if (threadIdx.x == 0) {
             PcgCtl *ctl = a.ctl;
-            ctl->iter = 0;
-            ctl->error = 0;
-            ctl->refresh_now = 0;
-            ctl->p_ready = 1;
-            ctl->xpending = 0;
+            const int seg = bsg.seg;
             for (int c = 0; c < D; ++c) {
                 double bn = sqrt(tot[2 * D + c]);
-                ctl->bnorm[c] = bn > 0.0 ? bn : 1.0;
-                ctl->alpha[c] = 0.0;
+                a.sc.bnorm[seg * D + c] = bn > 0.0 ? bn : 1.0;
+                a.sc.alpha[seg * D + c] = 0.0;
             }
-            if (PRE == 0) {
-                finish_scalars(ctl, tot, tot + D, D, true, a.cond, a.use_cond);
-            } else {
-                ctl->zstart = 1;
-                ctl->done = 0;
+            if (PRE == 0) finish_seg(ctl, a.sc, seg, tot, tot + D, D, true, 0);
+            if (!MS || last_segment_arrives(ctl, 2, a.sg.nseg)) {
+                ctl->iter = 0;
+                ctl->refresh_now = 0;
+                ctl->p_ready = 1;
+                ctl->xpending = 0;
+                if (PRE == 0) {
+                    finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
+                } else {
+                    ctl->zstart = 1;
+                    ctl->done = 0;
+                }
             }
         }
     }
@@ -489,15 +546,16 @@ struct Vec<double> {
 // update y += alpha_prev p_prev, elementwise and in place (flat float4 /
 // double2 traversal; the grid makes every thread meet fixed columns).
 // z = D_A^{-1} r (Jacobi) or the stored G^T G r (FSAI, PRE = 1).
-template <typename T, int D, int PRE>
+template <typename T, int D, int PRE, bool MS>
 __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
     const int p_ready = ctl->p_ready, xpending = ctl->xpending;
+    constexpr bool multi = MS;  // batch: beta, alpha of each row's segment
     __shared__ T sbeta[D], salpha[D];
     if (threadIdx.x < D) {
-        sbeta[threadIdx.x] = p_ready ? T(0) : (T)ctl->beta[threadIdx.x];
-        salpha[threadIdx.x] = (T)ctl->alpha[threadIdx.x];
+        sbeta[threadIdx.x] = p_ready ? T(0) : (T)a.sc.beta[threadIdx.x];
+        salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
     }
     __syncthreads();
     using VT = Vec<T>;
@@ -505,9 +563,11 @@ __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
     const int64_t nel = a.A.n * D, nvec = nel / VN;
     const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
     T be[VN], al[VN];
+    int cu[VN];
 #pragma unroll
     for (int u = 0; u < VN; ++u) {
         const int c = (int)((tid * VN + u) % D);
+        cu[u] = c;
         be[u] = sbeta[c];
         al[u] = salpha[c];
     }
@@ -518,6 +578,16 @@ __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
     float4 *xl4 = reinterpret_cast<float4 *>(a.xlo);  // float path: VN == 4
     for (int64_t v = tid; v < nvec; v += nthr) {
         T pv[VN], zv[VN];
+        if constexpr (multi) {
+            // element u of this vector is column cu[u] of row v*VN/D + (cu[0] + u)/D
+            const int64_t row0 = v * VN / D;
+#pragma unroll
+            for (int u = 0; u < VN; ++u) {
+                const int sgm = __ldg(a.sg.rseg + row0 + (cu[0] + u) / D);
+                be[u] = p_ready ? T(0) : (T)a.sc.beta[sgm * D + cu[u]];
+                al[u] = (T)a.sc.alpha[sgm * D + cu[u]];
+            }
+        }
         VT::get(p4[v], pv);
         VT::get(z4[v], zv);
         if constexpr (PRE == 0) {
@@ -544,23 +614,26 @@ __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
     if (tid < nel - nvec * VN) {  // tail elements
         const int64_t e = nvec * VN + tid;
         const int c = (int)(e % D);
+        const int sgm = multi ? row_seg(a.sg, e / D) : 0;
+        const T bt = p_ready ? T(0) : (multi ? (T)a.sc.beta[sgm * D + c] : sbeta[c]);
+        const T at = multi ? (T)a.sc.alpha[sgm * D + c] : salpha[c];
         const T z = PRE == 0 ? a.A.dinv[e / D] * a.r[e] : a.z[e];
         T po = a.p[0][e];
         if (xpending) {
             T xh = a.x[e];
             float xl = 0.f;
             if constexpr (std::is_same_v<T, float>) xl = a.xlo[e];
-            axpy_hilo<T>(xh, xl, salpha[c], po);
+            axpy_hilo<T>(xh, xl, at, po);
             a.x[e] = xh;
             if constexpr (std::is_same_v<T, float>) a.xlo[e] = xl;
         }
-        a.p[0][e] = p_ready ? z : z + sbeta[c] * po;
+        a.p[0][e] = p_ready ? z : z + bt * po;
     }
 }
 
 // q = A p and the column dots p.q -> alpha.  Only p is gathered; the matrix
 // slots of a row are fetched kChunk at a time ahead of the gathers.
-template <typename T, int D>
+template <typename T, int D, bool MS>
 __global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
@@ -571,9 +644,8 @@ __global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
     AT pq[1][SWt::V];
 #pragma unroll
     for (int k = 0; k < SWt::V; ++k) pq[0][k] = A::zero();
-    PFE_ROW_LOOP(T, D) {
-        const int64_t i = g * SW::RPW + lm.r;
-        if (!lm.active || i >= a.A.n) continue;
+    PFE_ROW_LOOP_LIVE(T, D, MS) {
+        PFE_ROW_I;
         const int c0 = lm.cg * V;
         const int64_t ic = i * D + c0;
         int64_t base;
@@ -600,24 +672,28 @@ __global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
         for (int k = 0; k < V; ++k) A::add_prod(pq[0][k], pi[k], acc[k]);
     }
     __shared__ double tot[D];
-    if (grid_sum_cols<T, D, 1>(pq, a.part, &a.ctl->ticket[0], tot)) {
+    if (grid_sum_cols<T, D, 1>(pq, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 0], tot)) {
         if (threadIdx.x == 0) {
             PcgCtl *w = a.ctl;
+            const SegScal &sc = a.sc;
             for (int c = 0; c < D; ++c) {
-                if (!w->active[c]) {
-                    w->alpha[c] = 0.0;
+                const int k = bsg.seg * D + c;
+                if (!sc.active[k]) {
+                    sc.alpha[k] = 0.0;
                     continue;
                 }
                 const double pqc = tot[c];
                 if (!(pqc > 0.0) || !(pqc < INFINITY)) {
-                    w->error = PFE_ENUMERIC;
-                    w->alpha[c] = 0.0;
+                    atomicMax(&w->error, (int)PFE_ENUMERIC);
+                    sc.alpha[k] = 0.0;
                 } else {
-                    w->alpha[c] = w->rz[c] / pqc;
+                    sc.alpha[k] = sc.rz[k] / pqc;
                 }
             }
-            w->p_ready = 0;
-            w->xpending = 1;
+            if (!MS || last_segment_arrives(w, 0, a.sg.nseg)) {
+                w->p_ready = 0;
+                w->xpending = 1;
+            }
         }
     }
 }
@@ -629,14 +705,15 @@ __global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
 // element slot; the tail (n*D mod VEC elements) goes to the first threads.
 // r -= alpha q and the dots r.z, r.r of the new residual -> beta, convergence.
 // Sub-warp mapping (cheap per-column block sums), two row groups per step.
-template <typename T, int D>
+template <typename T, int D, bool MS>
 __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
     using A = Acc<T>;
     using AT = typename A::type;
     using SWt = SubWarp<T, D>;
+    const BlockSeg bsg = block_seg<MS>(a.sg);
     __shared__ T salpha[D];
-    if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.ctl->alpha[threadIdx.x];
+    if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.sc.alpha[bsg.seg * D + threadIdx.x];
     __syncthreads();
     AT acc[2][SWt::V];
 #pragma unroll
@@ -647,19 +724,20 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
         using SW = SWt;
         constexpr int V = SW::V;
         const SW lm;
-        const int64_t warp_g = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-        const int64_t warps_total = (int64_t)gridDim.x * kWarps;
+        const int64_t warp_g = (int64_t)(blockIdx.x - bsg.b0) * kWarps + (threadIdx.x >> 5);
+        const int64_t warps_total = (int64_t)bsg.nb * kWarps;
+        const int64_t seg_rows = (!MS || a.sc.seg_active[bsg.seg]) ? bsg.r1 - bsg.r0 : 0;
         const int c0 = lm.cg * V;
         T al[V];
 #pragma unroll
         for (int k = 0; k < V; ++k) al[k] = salpha[c0 + k];
-        for (int64_t g = warp_g; g * SW::RPW < a.A.n; g += 2 * warps_total) {
+        for (int64_t g = warp_g; g * SW::RPW < seg_rows; g += 2 * warps_total) {
             T rv[2][V], qv[2][V], dv[2];
             bool ok[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int64_t i = (g + h * warps_total) * SW::RPW + lm.r;
-                ok[h] = lm.active && i < a.A.n;
+                const int64_t i = bsg.r0 + (g + h * warps_total) * SW::RPW + lm.r;
+                ok[h] = lm.active && i < bsg.r1;
                 const int64_t ic = (ok[h] ? i : 0) * D + c0;
                 ldv<T, V>(a.r + ic, rv[h]);
                 ldv<T, V>(a.q + ic, qv[h]);
@@ -668,7 +746,7 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!ok[h]) continue;
-                const int64_t i = (g + h * warps_total) * SW::RPW + lm.r;
+                const int64_t i = bsg.r0 + (g + h * warps_total) * SW::RPW + lm.r;
 #pragma unroll
                 for (int k = 0; k < V; ++k) {
                     const T ri = fma(-al[k], qv[h][k], rv[h][k]);
@@ -681,14 +759,19 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
         }
     }
     __shared__ double tot[2 * D];
-    if (grid_sum_cols<T, D, 2>(acc, a.part, &a.ctl->ticket[1], tot)) {
+    if (grid_sum_cols<T, D, 2>(acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot)) {
         if (threadIdx.x == 0) {
             PcgCtl *ctl = a.ctl;
-            ctl->iter += 1;
-            if (!ctl->error && ctl->refresh > 0 && (ctl->iter % ctl->refresh) == 0) {
-                ctl->refresh_now = 1;  // k_xflush + k_refresh finish this iteration
-            } else {
-                finish_scalars(ctl, tot, tot + D, D, false, a.cond, a.use_cond);
+            const int it = ctl->iter + 1;
+            // an error here can only come from an earlier kernel while a refresh is due
+            const bool refresh_due = !ctl->error && ctl->refresh > 0 && (it % ctl->refresh) == 0;
+            if (!refresh_due) finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, false, it);
+            if (!MS || last_segment_arrives(ctl, 1, a.sg.nseg)) {
+                ctl->iter = it;
+                if (refresh_due)
+                    ctl->refresh_now = 1;  // k_xflush + k_refresh finish this iteration
+                else
+                    finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
             }
         }
     }
@@ -696,13 +779,14 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
 
 // y += alpha p with the direction of the last k_spmm.  In the loop body it
 // runs only before a refresh; after the loop it applies the final update.
-template <typename T, int D>
+template <typename T, int D, bool MS>
 __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush) {
     const PcgCtl *ctl = a.ctl;
     if (!*(volatile const int *)&ctl->xpending) return;
     if (!final_flush && !*(volatile const int *)&ctl->refresh_now) return;
+    constexpr bool multi = MS;
     __shared__ T salpha[D];
-    if (threadIdx.x < D) salpha[threadIdx.x] = (T)ctl->alpha[threadIdx.x];
+    if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
     __syncthreads();
     const T *__restrict__ pc = a.p[0];
     const int64_t nel = a.A.n * D;
@@ -710,7 +794,9 @@ __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush
         T xh = a.x[e];
         float xl = 0.f;
         if constexpr (std::is_same_v<T, float>) xl = a.xlo[e];
-        axpy_hilo<T>(xh, xl, salpha[e % D], pc[e]);
+        const int c = (int)(e % D);
+        const T al = multi ? (T)a.sc.alpha[__ldg(a.sg.rseg + e / D) * D + c] : salpha[c];
+        axpy_hilo<T>(xh, xl, al, pc[e]);
         a.x[e] = xh;
         if constexpr (std::is_same_v<T, float>) a.xlo[e] = xl;
     }
@@ -739,8 +825,7 @@ __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
     if (!*(volatile int *)&a.ctl->refresh_now) return;
     T *__restrict__ rdst = a.r2[(a.ctl->iter + 1) & 1];
     PFE_ROW_LOOP(T, D) {
-        const int64_t i = g * SW::RPW + lm.r;
-        if (!lm.active || i >= a.A.n) continue;
+        PFE_ROW_I;
         const int c0 = lm.cg * V;
         T ri[V];
         true_residual<T, D, V>(a, i, c0, ri);
@@ -822,15 +907,14 @@ template <typename T, int D>
 __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
-    __shared__ T salpha[D];
-    if (threadIdx.x < D) salpha[threadIdx.x] = (T)ctl->alpha[threadIdx.x];
+    __shared__ T salpha[D];  // FSAI runs on one segment
+    if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
     __syncthreads();
     const int par = ctl->iter & 1;
     const T *__restrict__ rold = a.r2[par];
     T *__restrict__ rnew = a.r2[1 - par];
     PFE_ROW_LOOP(T, D) {
-        const int64_t i = g * SW::RPW + lm.r;
-        if (!lm.active || i >= a.A.n) continue;
+        PFE_ROW_I;
         const int c0 = lm.cg * V;
         T al[V];
 #pragma unroll
@@ -861,8 +945,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(
     if (MODE == 1 && !*(volatile int *)&a.ctl->refresh_now) return;
     const T *__restrict__ rsrc = MODE == 0 ? a.r2[0] : a.r2[(a.ctl->iter + 1) & 1];
     PFE_ROW_LOOP(T, D) {
-        const int64_t i = g * SW::RPW + lm.r;
-        if (!lm.active || i >= a.A.n) continue;
+        PFE_ROW_I;
         const int c0 = lm.cg * V;
         int64_t base;
         int len;
@@ -896,8 +979,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_z(
 #pragma unroll
         for (int k = 0; k < SWt::V; ++k) acc2[q][k] = A::zero();
     PFE_ROW_LOOP(T, D) {
-        const int64_t i = g * SW::RPW + lm.r;
-        if (!lm.active || i >= a.A.n) continue;
+        PFE_ROW_I;
         const int c0 = lm.cg * V;
         int64_t base;
         int len;
@@ -918,13 +1000,14 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_z(
         }
     }
     __shared__ double tot[2 * D];
-    if (grid_sum_cols<T, D, 2>(acc2, a.part, &a.ctl->ticket[1], tot)) {
+    if (grid_sum_cols<T, D, 2>(acc2, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot)) {
         if (threadIdx.x == 0) {
             PcgCtl *ctl = a.ctl;
             const bool start = ctl->zstart != 0;
-            ctl->zstart = 0;
+            finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, start, ctl->iter + 1);
+            ctl->zstart = 0;  // FSAI: one problem (its last block finishes the iteration)
             if (!start) ctl->iter += 1;
-            finish_scalars(ctl, tot, tot + D, D, start, a.cond, a.use_cond);
+            finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
             ctl->refresh_now = (ctl->refresh > 0 && ((ctl->iter + 1) % ctl->refresh) == 0) ? 1 : 0;
         }
     }
@@ -932,7 +1015,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_z(
 
 // Residual replacement: r = b - A y (extended precision), then finish the
 // iteration with the true residual.
-template <typename T, int D>
+template <typename T, int D, bool MS>
 __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
     if (!*(volatile int *)&a.ctl->refresh_now) return;
     using A = Acc<T>;
@@ -943,9 +1026,8 @@ __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
     for (int q = 0; q < 2; ++q)
 #pragma unroll
         for (int k = 0; k < SWt::V; ++k) acc[q][k] = A::zero();
-    PFE_ROW_LOOP(T, D) {
-        const int64_t i = g * SW::RPW + lm.r;
-        if (!lm.active || i >= a.A.n) continue;
+    PFE_ROW_LOOP_LIVE(T, D, MS) {
+        PFE_ROW_I;
         const int c0 = lm.cg * V;
         T ri[V];
         true_residual<T, D, V>(a, i, c0, ri);
@@ -958,11 +1040,15 @@ __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
         stv<T, V>(a.r + i * D + c0, ri);
     }
     __shared__ double tot[2 * D];
-    if (grid_sum_cols<T, D, 2>(acc, a.part, &a.ctl->ticket[3], tot)) {
+    if (grid_sum_cols<T, D, 2>(acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 3], tot)) {
         if (threadIdx.x == 0) {
-            a.ctl->refresh_now = 0;
-            a.ctl->xpending = 0;
-            finish_scalars(a.ctl, tot, tot + D, D, false, a.cond, a.use_cond);
+            PcgCtl *ctl = a.ctl;
+            finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, false, ctl->iter);
+            if (!MS || last_segment_arrives(ctl, 3, a.sg.nseg)) {
+                ctl->refresh_now = 0;
+                ctl->xpending = 0;
+                finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
+            }
         }
     }
 }
@@ -972,10 +1058,11 @@ template <typename T, int D>
 __global__ void __launch_bounds__(kBlock) k_apply(SysView<T> Av, const T *__restrict__ x, T *__restrict__ y) {
     struct {
         SysView<T> A;
-    } a{Av};
+        Segs sg;
+        SegScal sc;
+    } a{Av, Segs{1, Av.n, nullptr, nullptr}, SegScal{}};
     PFE_ROW_LOOP(T, D) {
-        const int64_t i = g * SW::RPW + lm.r;
-        if (!lm.active || i >= a.A.n) continue;
+        PFE_ROW_I;
         const int c0 = lm.cg * V;
         int64_t base;
         int len;
@@ -1011,6 +1098,8 @@ PcgArgs<T> pcg_args(pfe_ctx *c, PcgLaunch L) {
     a.b = (const T *)c->wk.RHS;
     a.part = c->wk.partials;
     a.ctl = c->ctl;
+    a.sg = seg_view(c);
+    a.sc = c->sc;
     a.cond = L.cond;
     a.use_cond = L.use_cond;
     a.z = (T *)c->fsai.z;
@@ -1055,19 +1144,43 @@ bool use_fsai(const pfe_ctx *c) {
     return std::is_same_v<T, float> && c->fsai.enabled;
 }
 
+// Launchers.  MS selects the batch (segment) variants of the Jacobi kernels;
+// a single problem uses the MS = false ones, which carry no segment lookups.
+template <typename T, int D, bool MS>
+void init_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a) {
+    k_pcg_init<T, D, 0, MS><<<wave_grid(c, G_INIT, k_pcg_init<T, D, 0, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+}
+template <typename T, int D, bool MS>
+void body_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int iters) {
+    for (int u = 0; u < iters; ++u) {
+        k_pupdate<T, D, 0, MS><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0, MS>, flat_need<T, D>(c), flat_mult<T, D>()),
+                                 kBlock, 0, s>>>(a);
+        k_spmm<T, D, MS><<<wave_grid(c, G_SPMM, k_spmm<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        k_update<T, D, MS><<<wave_grid(c, G_UPDATE, k_update<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        k_xflush<T, D, MS><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, MS>, flat_need<T, D>(c)), kBlock, 0, s>>>(a, 0);
+        k_refresh<T, D, MS><<<wave_grid(c, G_REFRESH, k_refresh<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+    }
+}
+
 template <typename T, int D>
 pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
     PcgArgs<T> a = pcg_args<T>(c, L);
+    // the error flag of the solve starts clear (the segments' finishers only raise it)
+    PFE_CUDA_TRY(c, cudaMemsetAsync(&c->ctl->error, 0, sizeof(int), s));
     if constexpr (std::is_same_v<T, float>) {
         if (use_fsai<T>(c)) {
-            k_pcg_init<T, D, 1><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            k_pcg_init<T, D, 1, false><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1, false>, rows_need<T, D>(c)), kBlock,
+                                         0, s>>>(a);
             k_fsai_t<T, D, 0><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D, 0>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
             k_fsai_z<T, D><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
             PFE_CUDA_TRY(c, cudaGetLastError());
             return PFE_OK;
         }
     }
-    k_pcg_init<T, D, 0><<<wave_grid(c, G_INIT, k_pcg_init<T, D, 0>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+    if (c->nseg > 1)
+        init_ms<T, D, true>(c, s, a);
+    else
+        init_ms<T, D, false>(c, s, a);
     PFE_CUDA_TRY(c, cudaGetLastError());
     return PFE_OK;
 }
@@ -1078,10 +1191,13 @@ pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
     if constexpr (std::is_same_v<T, float>) {
         if (use_fsai<T>(c)) {
             for (int u = 0; u < iters; ++u) {
-                k_pupdate<T, D, 1><<<wave_grid(c, G_PUPD_F, k_pupdate<T, D, 1>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0, s>>>(a);
-                k_spmm<T, D><<<wave_grid(c, G_SPMM, k_spmm<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+                k_pupdate<T, D, 1, false><<<wave_grid(c, G_PUPD_F, k_pupdate<T, D, 1, false>, flat_need<T, D>(c),
+                                                      flat_mult<T, D>()),
+                                            kBlock, 0, s>>>(a);
+                k_spmm<T, D, false><<<wave_grid(c, G_SPMM, k_spmm<T, D, false>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
                 k_fsai_tr<T, D><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-                k_xflush<T, D><<<wave_grid(c, G_XFLUSH, k_xflush<T, D>, flat_need<T, D>(c)), kBlock, 0, s>>>(a, 0);
+                k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c)), kBlock, 0,
+                                        s>>>(a, 0);
                 k_refresh_f<T, D><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
                 k_fsai_t<T, D, 1><<<wave_grid(c, G_FSAI_T1, k_fsai_t<T, D, 1>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
                 k_fsai_z<T, D><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
@@ -1090,20 +1206,22 @@ pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
             return PFE_OK;
         }
     }
-    for (int u = 0; u < iters; ++u) {
-        k_pupdate<T, D, 0><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0, s>>>(a);
-        k_spmm<T, D><<<wave_grid(c, G_SPMM, k_spmm<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-        k_update<T, D><<<wave_grid(c, G_UPDATE, k_update<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-        k_xflush<T, D><<<wave_grid(c, G_XFLUSH, k_xflush<T, D>, flat_need<T, D>(c)), kBlock, 0, s>>>(a, 0);
-        k_refresh<T, D><<<wave_grid(c, G_REFRESH, k_refresh<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-    }
+    if (c->nseg > 1)
+        body_ms<T, D, true>(c, s, a, iters);
+    else
+        body_ms<T, D, false>(c, s, a, iters);
     PFE_CUDA_TRY(c, cudaGetLastError());
     return PFE_OK;
 }
 
 template <typename T, int D>
 pfe_status final_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
-    k_xflush<T, D><<<wave_grid(c, G_XFLUSH, k_xflush<T, D>, flat_need<T, D>(c)), kBlock, 0, s>>>(pcg_args<T>(c, L), 1);
+    if (c->nseg > 1)
+        k_xflush<T, D, true><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, true>, flat_need<T, D>(c)), kBlock, 0, s>>>(
+            pcg_args<T>(c, L), 1);
+    else
+        k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c)), kBlock, 0, s>>>(
+            pcg_args<T>(c, L), 1);
     PFE_CUDA_TRY(c, cudaGetLastError());
     return PFE_OK;
 }
@@ -1130,13 +1248,22 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     h.tol = 0.0;
     h.p_ready = 0;
     h.xpending = 1;
-    for (int k = 0; k < D; ++k) {
-        h.active[k] = 1;
-        h.rz[k] = 1.0;
-        h.bnorm[k] = 1.0;
-        h.alpha[k] = 1e-30;
-        h.beta[k] = 0.5;
+    // scratch per-segment scalars: every column active
+    const int nseg = c->nseg;
+    const size_t sc_bytes = segscal_bytes(nseg, D);
+    std::vector<unsigned char> hsc(sc_bytes, 0);
+    {
+        SegScal hs = segscal_carve(hsc.data(), nseg, D);
+        for (int k = 0; k < nseg * D; ++k) {
+            hs.active[k] = 1;
+            hs.rz[k] = 1.0;
+            hs.bnorm[k] = 1.0;
+            hs.alpha[k] = 1e-30;
+            hs.beta[k] = 0.5;
+        }
+        for (int q = 0; q < nseg; ++q) hs.seg_active[q] = 1;
     }
+    void *dsc = nullptr;
     const int64_t nd = c->g.n * (int64_t)D;
     const bool fsai = which >= 3;
     if (fsai && !use_fsai<T>(c)) {
@@ -1150,12 +1277,13 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     pfe_status st = PFE_OK;
     auto cleanup = [&]() {
         for (void *q : {(void *)dctl, (void *)xs, (void *)rs, (void *)p0, (void *)p1, (void *)xls, (void *)r1s,
-                        (void *)ts, (void *)zs})
+                        (void *)ts, (void *)zs, dsc})
             if (q) cudaFree(q);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
-    if (cudaMalloc((void **)&dctl, sizeof(PcgCtl)) != cudaSuccess || cudaMalloc((void **)&xs, nd * sizeof(T)) != cudaSuccess ||
+    if (cudaMalloc((void **)&dctl, sizeof(PcgCtl)) != cudaSuccess || cudaMalloc(&dsc, sc_bytes) != cudaSuccess ||
+        cudaMalloc((void **)&xs, nd * sizeof(T)) != cudaSuccess ||
         cudaMalloc((void **)&rs, nd * sizeof(T)) != cudaSuccess || cudaMalloc((void **)&p0, nd * sizeof(T)) != cudaSuccess ||
         cudaMalloc((void **)&p1, nd * sizeof(T)) != cudaSuccess ||
         (std::is_same_v<T, float> && cudaMalloc((void **)&xls, nd * sizeof(float)) != cudaSuccess) ||
@@ -1169,6 +1297,7 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     }
     PcgArgs<T> a = pcg_args<T>(c, PcgLaunch{0, 0});
     a.ctl = dctl;
+    a.sc = segscal_carve(dsc, nseg, D);
     a.x = xs;
     a.r = rs;
     a.xlo = xls;
@@ -1179,6 +1308,7 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     a.t = ts;
     a.z = zs;
     cudaMemcpyAsync(dctl, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dsc, hsc.data(), sc_bytes, cudaMemcpyHostToDevice, s);
     if (fsai) {
         cudaMemcpyAsync(r1s, c->wk.R, nd * sizeof(T), cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(ts, c->wk.R, nd * sizeof(T), cudaMemcpyDeviceToDevice, s);
@@ -1190,14 +1320,24 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     if (xls) cudaMemcpyAsync(xls, c->wk.Ylo, nd * sizeof(float), cudaMemcpyDeviceToDevice, s);
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    const bool multi = c->nseg > 1;
     auto launch = [&]() {
-        if (which == 0)
-            k_spmm<T, D><<<wave_grid(c, G_SPMM, k_spmm<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        if (which == 0 && multi)
+            k_spmm<T, D, true><<<wave_grid(c, G_SPMM, k_spmm<T, D, true>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        else if (which == 0)
+            k_spmm<T, D, false><<<wave_grid(c, G_SPMM, k_spmm<T, D, false>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        else if (which == 1 && multi)
+            k_update<T, D, true><<<wave_grid(c, G_UPDATE, k_update<T, D, true>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
         else if (which == 1)
-            k_update<T, D><<<wave_grid(c, G_UPDATE, k_update<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            k_update<T, D, false><<<wave_grid(c, G_UPDATE, k_update<T, D, false>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        else if (which == 2 && multi)
+            k_pupdate<T, D, 0, true><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0, true>, flat_need<T, D>(c),
+                                                 flat_mult<T, D>()),
+                                       kBlock, 0, s>>>(a);
         else if (which == 2)
-            k_pupdate<T, D, 0><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0>, flat_need<T, D>(c), flat_mult<T, D>()),
-                                 kBlock, 0, s>>>(a);
+            k_pupdate<T, D, 0, false><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0, false>, flat_need<T, D>(c),
+                                                  flat_mult<T, D>()),
+                                        kBlock, 0, s>>>(a);
         else if constexpr (std::is_same_v<T, float>) {
             if (which == 3)
                 k_fsai_tr<T, D><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);

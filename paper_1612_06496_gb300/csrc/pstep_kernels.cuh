@@ -33,6 +33,9 @@ struct PArgs {
     double *part;           // block partials of the Gram (D*(D+1)/2 per block)
     PstepCtl *ctl;
     int mode;
+    Segs sg;                // segments: one Gram and transform each
+    double *Tseg;           // nseg x D x D transforms (segment 0: ctl->T for one segment)
+    unsigned *tickets;      // nseg Gram tickets
 };
 
 template <typename T, int D>
@@ -117,13 +120,15 @@ __global__ void __launch_bounds__(kBlock) k_gram(PArgs<T> a) {
 #pragma unroll
     for (int k = 0; k < PER; ++k) g[k] = 0.0;
     __syncthreads();
-    const int64_t ntiles = (a.n + kTile - 1) / kTile;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t r0 = t * kTile;
+    // this block's segment; its blocks stride over the segment's row tiles
+    const BlockSeg bsg = block_seg(a.sg);
+    const int64_t ntiles = (bsg.r1 - bsg.r0 + kTile - 1) / kTile;
+    for (int64_t t = blockIdx.x - bsg.b0; t < ntiles; t += bsg.nb) {
+        const int64_t r0 = bsg.r0 + t * kTile;
         for (int rr = threadIdx.x; rr < kTile; rr += blockDim.x) {
             const int64_t i = r0 + rr;
             double x[D];
-            if (i < a.n) {
+            if (i < bsg.r1) {
                 x_row<T, D>(a, i, x);
             } else {
 #pragma unroll
@@ -150,38 +155,42 @@ __global__ void __launch_bounds__(kBlock) k_gram(PArgs<T> a) {
         const int e = threadIdx.x + k * kBlock;
         if (e < NE) a.part[(int64_t)blockIdx.x * NE + e] = g[k];
     }
-    if (!last_block_arrives(&a.ctl->ticket)) return;
+    unsigned *ticket = a.sg.nseg == 1 ? &a.ctl->ticket : a.tickets + bsg.seg;
+    if (!last_block_arrives(ticket, (unsigned)bsg.nb)) return;
     __shared__ double G[D * D], V[D * D];
     for (int e = threadIdx.x; e < NE; e += blockDim.x) {
         double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(a.part + (int64_t)b * NE + e);
+        for (int b = 0; b < bsg.nb; ++b) s += __ldcg(a.part + (int64_t)(bsg.b0 + b) * NE + e);
         const int p = ep[e], q = eq[e];
         G[p * D + q] = s;
         G[q * D + p] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        // ctl->error was cleared before the launch; any segment may set it
         PstepCtl *ctl = a.ctl;
-        for (int k = 0; k < D * D; ++k) ctl->G[k] = G[k];
+        const bool first = bsg.seg == 0;
+        if (first)
+            for (int k = 0; k < D * D; ++k) ctl->G[k] = G[k];
         jacobi_eig(G, V, D);
         double lmax = 0.0, lmin = INFINITY;
         for (int k = 0; k < D; ++k) {
-            ctl->evals[k] = G[k * D + k];
+            if (first) ctl->evals[k] = G[k * D + k];
             lmax = fmax(lmax, G[k * D + k]);
             lmin = fmin(lmin, G[k * D + k]);
         }
         if (!(lmin > 1e-13 * lmax) || !(lmax < INFINITY)) {
-            ctl->error = PFE_ESINGULAR;
+            atomicMax(&ctl->error, (int)PFE_ESINGULAR);
         } else {
-            ctl->error = 0;
+            double *Tout = a.sg.nseg == 1 ? ctl->T : a.Tseg + (int64_t)bsg.seg * D * D;
             for (int p = 0; p < D; ++p)
                 for (int q = 0; q < D; ++q) {
                     double s = 0.0;
                     for (int k = 0; k < D; ++k) s += V[p * D + k] * V[q * D + k] / sqrt(G[k * D + k]);
-                    ctl->T[p * D + q] = s;
+                    Tout[p * D + q] = s;
                 }
         }
-        ctl->ticket = 0u;
+        *ticket = 0u;
     }
 }
 
@@ -189,9 +198,12 @@ template <typename T, int D>
 __global__ void __launch_bounds__(kBlock) k_papply(PArgs<T> a) {
     __shared__ double Tm[D * D];
     if (a.ctl->error) return;
-    for (int k = threadIdx.x; k < D * D; k += blockDim.x) Tm[k] = a.ctl->T[k];
+    const BlockSeg bsg = block_seg(a.sg);
+    const double *Tsrc = a.sg.nseg == 1 ? a.ctl->T : a.Tseg + (int64_t)bsg.seg * D * D;
+    for (int k = threadIdx.x; k < D * D; k += blockDim.x) Tm[k] = Tsrc[k];
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = bsg.r0 + (int64_t)(blockIdx.x - bsg.b0) * blockDim.x + threadIdx.x; i < bsg.r1;
+         i += (int64_t)bsg.nb * blockDim.x) {
         double x[D], p[D], b[D];
         x_row<T, D>(a, i, x);
 #pragma unroll
@@ -267,8 +279,12 @@ pfe_status pstep_T(pfe_ctx *c, cudaStream_t s, int mode) {
     a.part = c->wk.partials;
     a.ctl = c->pctl;
     a.mode = mode;
+    a.sg = seg_view(c);
+    a.Tseg = c->seg_T;
+    a.tickets = c->seg_pticket;
     const int64_t ntiles = (a.n + kTile - 1) / kTile;
-    const int gblocks = (int)std::min<int64_t>(ntiles, (int64_t)c->num_sms * 2);
+    const int gblocks = (int)std::max<int64_t>(std::min<int64_t>(ntiles, (int64_t)c->num_sms * 2), c->nseg);
+    PFE_CUDA_TRY(c, cudaMemsetAsync(&c->pctl->error, 0, sizeof(int), s));
     k_gram<T, D><<<gblocks, kBlock, 0, s>>>(a);
     k_papply<T, D><<<wave_grid(c, G_PAPPLY, k_papply<T, D>, (a.n + kBlock - 1) / kBlock), kBlock, 0, s>>>(a);
     PFE_CUDA_TRY(c, cudaGetLastError());

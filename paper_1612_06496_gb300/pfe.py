@@ -27,14 +27,16 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_destroy", "pfe_last_error", "pfe_status_string", "pfe_get_info", "pfe_set_stream",
            "pfe_get_array", "pfe_set_array", "pfe_get_edges", "pfe_apply_A", "pfe_solve_system",
            "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
-           "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical"]
+           "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_get_segments",
+           "pfe_get_segment_stats"]
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3, "fsai_tr": 4, "fsai_z": 5}
 
 
 class GraphDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int32), ("kind", C.c_int32), ("features", C.c_void_p),
                 ("H", C.c_int32), ("W", C.c_int32), ("radius", C.c_double),
-                ("ei", C.c_void_p), ("ej", C.c_void_p), ("n_edges", C.c_int64), ("sigma", C.c_double)]
+                ("ei", C.c_void_p), ("ej", C.c_void_p), ("n_edges", C.c_int64), ("sigma", C.c_double),
+                ("nseg", C.c_int32), ("seg_hw", C.c_void_p), ("seg_off", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -47,7 +49,7 @@ class Params(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_edges", C.c_int64), ("nnz_A", C.c_int64), ("sell_slots", C.c_int64),
                 ("d", C.c_int32), ("precision", C.c_int32), ("lambda_", C.c_double), ("r", C.c_double),
-                ("vol", C.c_double), ("device_bytes", C.c_int64)]
+                ("vol", C.c_double), ("device_bytes", C.c_int64), ("nseg", C.c_int32)]
 
 
 class StepStats(C.Structure):
@@ -56,7 +58,8 @@ class StepStats(C.Structure):
 
 class SolveStats(C.Structure):
     _fields_ = [("pcg_iters_total", C.c_int64), ("pcg_iters_max", C.c_int32), ("n_solves", C.c_int32),
-                ("n_unconverged", C.c_int32), ("relres_max", C.c_double), ("kernel_launches", C.c_int64)]
+                ("n_unconverged", C.c_int32), ("relres_max", C.c_double), ("kernel_launches", C.c_int64),
+                ("pcg_rounds", C.c_int64)]
 
 
 _lib = None
@@ -97,6 +100,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_fsai_loss_grad.argtypes = [vp, vp, vp, C.POINTER(dbl)]
     lib.pfe_fsai_get.argtypes = [vp, vp, vp]
     lib.pfe_adam_update.argtypes = [vp, vp, vp, vp, i64, i32, dbl, dbl, dbl, dbl, vp]
+    lib.pfe_get_segments.argtypes = [vp, vp, vp]
+    lib.pfe_get_segment_stats.argtypes = [vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("pfe_default_params", "pfe_last_error", "pfe_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -145,26 +150,39 @@ def _stream_ptr(stream):
 
 
 class PFE:
-    """One embedding problem: graph, system matrix and iteration state on the GPU."""
+    """One embedding problem -- or a batch of independent problems (``shapes``
+    for images, ``seg_off`` for edge lists) -- with graph, system matrix and
+    iteration state on the GPU."""
 
     def __init__(self, features, *, sigma: float, H: int | None = None, W: int | None = None,
                  radius: float | None = None, edges=None, lam: float = 0.0, r: float = 1.0,
                  precision: str = "mixed", tol: float = 1e-6, max_iter: int = 5000, refresh: int = 50,
                  reset_inner: bool = True, loop: str = "graph", check_every: int = 4,
-                 blocks_per_sm: int = 0, stream=None):
+                 blocks_per_sm: int = 0, stream=None, shapes=None, seg_off=None):
         self.lib = load_library()
         self.ctx = C.c_void_p()
         fp, self._feat = _ptr(features)
         n, m = features.shape
         gd = GraphDesc()
         gd.n, gd.m, gd.features, gd.sigma = n, m, fp, float(sigma)
+        keep = []
         if edges is None:
-            gd.kind, gd.H, gd.W, gd.radius = PFE_GRAPH_GRID, int(H), int(W), float(radius)
+            gd.kind, gd.radius = PFE_GRAPH_GRID, float(radius)
+            if shapes is not None:  # batch of images: (H_s, W_s) each
+                hw = np.ascontiguousarray(np.asarray(shapes, dtype=np.int32).reshape(-1))
+                keep.append(hw)
+                gd.nseg, gd.seg_hw = len(shapes), hw.ctypes.data
+            else:
+                gd.H, gd.W = int(H), int(W)
         else:
             ei, ej = edges
             pi, self._ei = _ptr(ei, np.int32)
             pj, self._ej = _ptr(ej, np.int32)
             gd.kind, gd.ei, gd.ej, gd.n_edges = PFE_GRAPH_EDGES, pi, pj, int(ei.shape[0])
+            if seg_off is not None:
+                so = np.ascontiguousarray(np.asarray(seg_off, dtype=np.int64))
+                keep.append(so)
+                gd.nseg, gd.seg_off = len(so) - 1, so.ctypes.data
         p = Params()
         self.lib.pfe_default_params(C.byref(p))
         p.lambda_, p.r = float(lam), float(r)
@@ -214,6 +232,26 @@ class PFE:
     def set_stream(self, stream):
         self._check(self.lib.pfe_set_stream(self.ctx, _stream_ptr(stream)), "pfe_set_stream")
 
+    def segments(self):
+        """(row offsets [nseg + 1], lambda per segment) of a batch."""
+        ns = self.info()["nseg"]
+        off = np.empty(ns + 1, dtype=np.int64)
+        lam = np.empty(ns, dtype=np.float64)
+        self._check(self.lib.pfe_get_segments(self.ctx, off.ctypes.data, lam.ctypes.data), "pfe_get_segments")
+        return off, lam
+
+    def segment_stats(self, totals: bool = False):
+        """(iterations [nseg], relative residuals [nseg, d]) of the last PCG
+        solve; with totals, also each segment's iterations summed over the
+        solves of the last solve() call."""
+        ns = self.info()["nseg"]
+        it = np.empty(ns, dtype=np.int32)
+        rr = np.empty((ns, self.d), dtype=np.float64)
+        tot = np.empty(ns, dtype=np.int64)
+        self._check(self.lib.pfe_get_segment_stats(self.ctx, it.ctypes.data, rr.ctypes.data, tot.ctypes.data),
+                    "pfe_get_segment_stats")
+        return (it, rr, tot) if totals else (it, rr)
+
     def init(self, Y0):
         d = Y0.shape[1]
         p, keep = _ptr(Y0)
@@ -240,7 +278,7 @@ class PFE:
         st = self._check(self.lib.pfe_solve(self.ctx, n_outer, n_inner, py, ph, C.byref(s)), "pfe_solve", ok)
         return {"pcg_iters_total": s.pcg_iters_total, "pcg_iters_max": s.pcg_iters_max, "n_solves": s.n_solves,
                 "n_unconverged": s.n_unconverged, "relres_max": s.relres_max,
-                "kernel_launches": s.kernel_launches, "status": st}
+                "kernel_launches": s.kernel_launches, "pcg_rounds": s.pcg_rounds, "status": st}
 
     def get(self, which: str, out=None):
         if out is None:

@@ -63,6 +63,10 @@ CONFIGS: dict[str, ImageSpec] = {
                     n_outer=10, n_inner=10, tol=1e-8),
     "C2": ImageSpec("C2", 321, 481, 8, 0.03, seed=2, gradient=True, radius=3.0,
                     sigma=0.08, d=8, n_outer=20, n_inner=10, tol=1e-6),
+    # C3 stands for the whole batch (batch_specs()): the per-problem settings
+    # shared by its 64 images; H, W, regions and seed here are those of image 0
+    "C3": ImageSpec("C3", 96, 96, 3, 0.03, seed=3000, radius=2.0, sigma=0.1, d=5,
+                    n_outer=10, n_inner=10, tol=1e-6),
     "C4": ImageSpec("C4", 321, 481, 8, 0.03, seed=49000, gradient=True, radius=3.0,
                     sigma=0.08, d=8, n_outer=1, n_inner=10, tol=1e-6),
     "C5": ImageSpec("C5", 2048, 2048, 40, 0.03, seed=5, texture=True, radius=2.0,
