@@ -36,6 +36,10 @@ notes of the repository):
 * lam defaults to sqrt(vol) = sqrt(sum_i d_i), r to 1 (values are not printed).
 * The starting embedding is D-orthonormalised by the same polar step:
   Y0 <- D^{-1/2} polar(D^{1/2} Y0).
+* The Laplacian-eigenmap start (Sec. I) is the d smallest generalised
+  eigenvectors of (D - W) v = mu D v on the D-orthogonal complement of the
+  constant vector, D-normalised, each with its largest-magnitude entry made
+  positive (ties: the smallest index).
 """
 from __future__ import annotations
 
@@ -189,6 +193,55 @@ def d_orthonormalize(Y0: np.ndarray, dvec: np.ndarray) -> np.ndarray:
     """Y = D^{-1/2} polar(D^{1/2} Y0), so that Y^T D Y = I (Eq. 1 constraint)."""
     sq = np.sqrt(dvec)[:, None]
     return polar_factor(sq * Y0) / sq
+
+
+def sign_fix(V: np.ndarray) -> np.ndarray:
+    """Deterministic sign of each column: the entry of largest magnitude is
+    made positive (ties: the smallest row index)."""
+    V = np.array(V, dtype=np.float64, copy=True)
+    for c in range(V.shape[1]):
+        i = int(np.argmax(np.abs(V[:, c])))  # argmax returns the first maximum
+        if V[i, c] < 0:
+            V[:, c] = -V[:, c]
+    return V
+
+
+def laplacian_eigenmap(g: Graph, d: int) -> np.ndarray:
+    """Laplacian-eigenmap start (Sec. I; Belkin & Niyogi): the generalised
+    eigenvectors of (D - W) v = mu D v for the d smallest mu on the
+    D-orthogonal complement of the constant vector (the trivial solution,
+    mu = 0), in ascending mu, each with v^T D v = 1 and its sign fixed by
+    ``sign_fix``.  On a connected graph this drops the first eigenvector; on
+    a graph of k components it keeps the k - 1 piecewise-constant directions
+    orthogonal to the constant one.
+
+    The d + 1 smallest eigenvectors come from dense ``scipy.linalg.eigh``
+    (n <= 3000) or shift-invert Lanczos (``scipy.sparse.linalg.eigsh``);
+    the constant direction is then removed inside their span and the rest
+    rotated back to eigenvectors (Rayleigh-Ritz)."""
+    Wm = adjacency(g.n, g.a, g.b, g.w)
+    Dm = sp.diags(g.dvec)
+    L = (Dm - Wm).tocsc()
+    if g.n <= 3000:
+        import scipy.linalg as sla
+        mu, V = sla.eigh(L.toarray(), np.diag(g.dvec), subset_by_index=[0, d])
+    else:
+        shift = -1e-6 * float(np.max(g.dvec))
+        mu, V = spla.eigsh(L, k=d + 1, M=Dm.tocsc(), sigma=shift, which="LM")
+        order = np.argsort(mu)
+        mu, V = mu[order], V[:, order]
+    V = V / np.sqrt(np.einsum("ic,i,ic->c", V, g.dvec, V))[None, :]
+    # coordinates of the D-unit constant vector in the (D-orthonormal) basis V,
+    # and an orthonormal basis of their complement in R^{d+1}
+    vol = float(np.sum(g.dvec))
+    cvec = V.T @ g.dvec / np.sqrt(vol)
+    _, _, Vt = np.linalg.svd(cvec[None, :])
+    Vp = V @ Vt[1:].T                        # D-orthonormal, D-orthogonal to the constant
+    H = Vp.T @ (L @ Vp)
+    theta, C = np.linalg.eigh(0.5 * (H + H.T))
+    Vp = Vp @ C                               # ascending Rayleigh quotients
+    Vp = Vp / np.sqrt(np.einsum("ic,i,ic->c", Vp, g.dvec, Vp))[None, :]
+    return sign_fix(Vp)
 
 
 def objective(g: Graph, Y: np.ndarray) -> float:
