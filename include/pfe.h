@@ -145,6 +145,8 @@ typedef struct pfe_info {
     double vol;           /* sum_i d_i */
     int64_t device_bytes; /* bytes of device memory the context holds */
     int32_t nseg;         /* problems in the batch (1 for one problem) */
+    int32_t le_iters;     /* iterations of the last Laplacian-eigenmap start (pfe_init, Y0 NULL) */
+    double le_residual;   /* its largest residual |P v - theta v|_D */
 } pfe_info;
 
 typedef struct pfe_step_stats {
@@ -186,11 +188,30 @@ PFE_API pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *g, const
  * library D-orthonormalises it, Y = D^{-1/2} polar(D^{1/2} Y0) (the P-step
  * map of Alg. 1 step 6 applied to D^{1/2} Y0), then sets P = D^{1/2} Y,
  * B = 0 and the split-Bregman variables b = d = 0 (Alg. 2 step 3).
- * Y0 == NULL is PFE_EINVAL (no built-in initialiser).  d must be one of the
- * dimensions built into the library (1..16, 20, 24, 25, 32), else
- * PFE_EUNSUPPORTED.  PFE_ESINGULAR if D^{1/2} Y0 is rank deficient.
+ * Y0 == NULL starts from the Laplacian eigenmap (pfe_laplacian_eigenmap with
+ * its default cap and tolerance; a start short of the tolerance is still
+ * used, see pfe_info.le_residual); not for a batch (PFE_EUNSUPPORTED).  d must
+ * be one of the dimensions built into the library (1..16, 20, 24, 25, 32),
+ * else PFE_EUNSUPPORTED.  PFE_ESINGULAR if D^{1/2} Y0 is rank deficient.
  */
 PFE_API pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0);
+
+/*
+ * pfe_laplacian_eigenmap -- the Laplacian-eigenmap embedding of the graph
+ * (Sec. I, the l2 analogue of Eq. 1; Belkin & Niyogi): the d generalised
+ * eigenvectors of (D - W) v = mu D v with the smallest mu on the
+ * D-orthogonal complement of the constant vector (the trivial solution), in
+ * ascending mu, with v^T D v = 1, each signed so that its entry of largest
+ * magnitude is positive (ties: the smallest index).  V is n x d row-major FP64
+ * (host or device).  Chebyshev-filtered subspace iteration on D^{-1} W in
+ * FP64 until every wanted residual |D^{-1} W v - (1 - mu) v|_D <= tol or
+ * max_iter rounds (PFE_ENOTCONV, results written); *iters and *residual
+ * (either may be NULL) receive the rounds and the largest residual.  Needs
+ * n > d + 2 + d/4 and d <= 30; not for a batch.  Synchronises; allocates
+ * temporary device memory.
+ */
+PFE_API pfe_status pfe_laplacian_eigenmap(pfe_ctx *c, int32_t d, double *V, int32_t max_iter, double tol,
+                                          int32_t *iters, double *residual);
 
 /*
  * pfe_inner_step -- one split-Bregman iteration (Alg. 2 steps 5-7 in the

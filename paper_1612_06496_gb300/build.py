@@ -22,7 +22,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpfe.so")
 
-SOURCES = ["api.cu", "graph.cu", "pcg.cu", "edge.cu", "pstep.cu", "convert.cu", "fsai.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "graph.cu", "pcg.cu", "edge.cu", "pstep.cu", "convert.cu", "fsai.cu", "noalloc.cu", "le.cu"]
 # Template instantiations (precision x groups of d), one generated
 # translation unit each, so that nvcc runs them in parallel.  The d values
 # must match PFE_DISPATCH_D in csrc/dispatch.cuh.
@@ -30,7 +30,10 @@ D_GROUPS = {
     "pcg": [[1, 2, 3, 4], [5, 6, 7, 8], [9, 10, 11, 12], [13, 14, 15, 16], [20], [24], [25], [32]],
     "pstep": [[1, 2, 3, 4, 5, 6, 7, 8], [9, 10, 11, 12, 13, 14, 15, 16], [20, 24], [25, 32]],
     "edge": [[1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 20, 24, 25, 32]],
+    # Laplacian-eigenmap block widths (FP64 only)
+    "le": [[1, 2, 3, 4, 5, 6, 7, 8, 9, 10], [11, 12, 13, 14, 15, 16], [20, 24, 25, 32]],
 }
+TYPES = {"le": ("double",)}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -46,7 +49,7 @@ def _generated_sources() -> list[str]:
     os.makedirs(gen, exist_ok=True)
     out = []
     for comp, groups in D_GROUPS.items():
-        for t in ("float", "double"):
+        for t in TYPES.get(comp, ("float", "double")):
             for gi, ds in enumerate(groups):
                 path = os.path.join(gen, f"{comp}_{t}_{gi}.cu")
                 text = f'#include "{comp}_kernels.cuh"\n' + "".join(

@@ -72,6 +72,12 @@ pfe_status sync(pfe_ctx *c) {
     return PFE_OK;
 }
 
+// Laplacian-eigenmap start of pfe_init: iteration cap, residual tolerance
+// (|P v - theta v|_D of each wanted vector) and Chebyshev filter degree.
+constexpr int kLeMaxIter = 400;
+constexpr double kLeTol = 1e-9;
+constexpr int kLeDegree = 10;
+
 // Work vectors of the FSAI iteration: t = G r, z = G^T t and the second
 // residual buffer (n x d each, work precision float).
 pfe_status fsai_vectors(pfe_ctx *c, int64_t nd) {
@@ -430,7 +436,38 @@ pfe_status pfe_get_info(const pfe_ctx *c, pfe_info *info) {
     info->vol = c->vol;
     info->device_bytes = c->bytes;
     info->nseg = c->nseg;
+    info->le_iters = c->le_iters;
+    info->le_residual = c->le_residual;
     return PFE_OK;
+}
+
+pfe_status pfe_laplacian_eigenmap(pfe_ctx *c, int32_t d, double *V, int32_t max_iter, double tol, int32_t *iters,
+                                  double *residual) {
+    if (!c || !V || d < 1 || max_iter < 0 || !(tol >= 0.0)) return PFE_EINVAL;
+    if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "no batched eigenmap: one problem per context");
+    if (le_block(d) == 0) return fail(c, PFE_EUNSUPPORTED, "d too large for the eigenmap");
+    if (c->n <= le_block(d)) return fail(c, PFE_EINVAL, "too few vertices for the eigenmap");
+    PFE_TRY(sync(c));
+    double *dv = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)c->n * d;
+    const bool dev = is_device_ptr(V);
+    if (!dev && cudaMalloc((void **)&dv, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PFE_ENOMEM, "pfe_laplacian_eigenmap: device allocation failed");
+    }
+    int its = 0;
+    double res = 0.0;
+    pfe_status st = launch_le(c, d, dev ? V : dv, max_iter, tol, kLeDegree, &its, &res);
+    if (!dev) {
+        if (st == PFE_OK || st == PFE_ENOTCONV) {
+            cudaError_t e = cudaMemcpy(V, dv, bytes, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) st = fail(c, PFE_ECUDA, cudaGetErrorString(e));
+        }
+        cudaFree(dv);
+    }
+    if (iters) *iters = its;
+    if (residual) *residual = res;
+    return st;
 }
 
 pfe_status pfe_get_segments(const pfe_ctx *c, int64_t *off, double *lambda) {
@@ -458,10 +495,15 @@ pfe_status pfe_get_segment_stats(pfe_ctx *c, int32_t *iters, double *relres, int
 
 pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
     if (!c) return PFE_EINVAL;
-    if (!Y0) return fail(c, PFE_EINVAL, "Y0 is NULL: the library has no built-in initialiser");
     if (d < 1 || d > c->n) return fail(c, PFE_EINVAL, "d must be in [1, n]");
-    if (ldY0 < d) return fail(c, PFE_EINVAL, "ldY0 < d");
+    if (Y0 && ldY0 < d) return fail(c, PFE_EINVAL, "ldY0 < d");
     if (!d_supported(d)) return fail(c, PFE_EUNSUPPORTED, "embedding dimension not built into libpfe");
+    const bool le_start = Y0 == nullptr;  // Laplacian-eigenmap start
+    if (le_start) {
+        if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "a batch takes its start in Y0 (no batched eigenmap)");
+        if (le_block(d) == 0) return fail(c, PFE_EUNSUPPORTED, "d too large for the eigenmap start");
+        if (c->n <= le_block(d)) return fail(c, PFE_EINVAL, "too few vertices for the eigenmap start");
+    }
     free_work(c);
     c->d = d;
     memset(c->kgrid, 0, sizeof(c->kgrid));  // kernels are sized again for this d
@@ -535,9 +577,20 @@ pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
     h.launch_per_iter = lc[1];
     PFE_CUDA_TRY(c, cudaMemcpyAsync(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
     PFE_CUDA_TRY(c, cudaMemsetAsync(c->pctl, 0, sizeof(PstepCtl), c->stream));
-    // Y0 -> stage (contiguous FP64), then D-orthonormalise via the P-step map
-    PFE_CUDA_TRY(c, cudaMemcpy2DAsync(w.stage, sizeof(double) * d, Y0, sizeof(double) * ldY0, sizeof(double) * d,
-                                      (size_t)c->n, cudaMemcpyDefault, c->stream));
+    // Y0 (or the eigenmap) -> stage (contiguous FP64), then D-orthonormalise
+    // via the P-step map
+    if (le_start) {
+        int its = 0;
+        double res = 0.0;
+        const pfe_status ls = launch_le(c, d, w.stage, kLeMaxIter, kLeTol, kLeDegree, &its, &res);
+        c->le_iters = its;
+        c->le_residual = res;
+        // an eigenmap short of the tolerance is still a valid start
+        if (ls != PFE_OK && ls != PFE_ENOTCONV) return ls;
+    } else {
+        PFE_CUDA_TRY(c, cudaMemcpy2DAsync(w.stage, sizeof(double) * d, Y0, sizeof(double) * ldY0,
+                                          sizeof(double) * d, (size_t)c->n, cudaMemcpyDefault, c->stream));
+    }
     PFE_TRY(launch_pstep(c, c->stream, PSTEP_INIT));
     PFE_TRY(sync(c));
     PFE_TRY(check_pstep(c));

@@ -208,6 +208,45 @@ __device__ __forceinline__ bool last_block_arrives(unsigned *ticket, unsigned co
 }
 __device__ __forceinline__ bool last_block_arrives(unsigned *ticket) { return last_block_arrives(ticket, gridDim.x); }
 
+// Cyclic Jacobi eigendecomposition of the symmetric G (in place -> diagonal),
+// V receives the eigenvectors as columns.  Golub & Van Loan, Alg. 8.5.3.
+static __device__ __noinline__ void jacobi_eig(double *G, double *V, int D) {
+    for (int p = 0; p < D; ++p)
+        for (int q = 0; q < D; ++q) V[p * D + q] = (p == q) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int p = 0; p < D; ++p) {
+            dia += G[p * D + p] * G[p * D + p];
+            for (int q = p + 1; q < D; ++q) off += G[p * D + q] * G[p * D + q];
+        }
+        if (off <= 1e-32 * dia) break;
+        for (int p = 0; p < D - 1; ++p) {
+            for (int q = p + 1; q < D; ++q) {
+                const double apq = G[p * D + q];
+                if (apq == 0.0) continue;
+                const double tau = (G[q * D + q] - G[p * D + p]) / (2.0 * apq);
+                const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+                for (int k = 0; k < D; ++k) {  // columns p, q of G J
+                    const double gp = G[k * D + p], gq = G[k * D + q];
+                    G[k * D + p] = cs * gp - sn * gq;
+                    G[k * D + q] = sn * gp + cs * gq;
+                }
+                for (int k = 0; k < D; ++k) {  // rows p, q of J^T (G J)
+                    const double gp = G[p * D + k], gq = G[q * D + k];
+                    G[p * D + k] = cs * gp - sn * gq;
+                    G[q * D + k] = sn * gp + cs * gq;
+                }
+                for (int k = 0; k < D; ++k) {  // V J
+                    const double vp = V[k * D + p], vq = V[k * D + q];
+                    V[k * D + p] = cs * vp - sn * vq;
+                    V[k * D + q] = sn * vp + cs * vq;
+                }
+            }
+        }
+    }
+}
+
 // ---- segments ----------------------------------------------------------------
 // The blocks of a grid of G >= nseg blocks are split among the segments in
 // proportion to their rows, at least one each: segment s owns blocks

@@ -151,6 +151,8 @@ struct pfe_ctx {
     std::vector<void *> dev_allocs;   // graph-lifetime allocations
     std::vector<void *> work_allocs;  // d-dependent allocations
     int64_t bytes = 0;
+    int le_iters = 0;                 // last Laplacian-eigenmap computation
+    double le_residual = 0.0;
 };
 
 namespace pfe {
@@ -159,6 +161,10 @@ namespace pfe {
 pfe_status build_grid_graph(pfe_ctx *c, const double *dfeat);
 pfe_status build_edge_graph(pfe_ctx *c, const double *dfeat, const int32_t *dei, const int32_t *dej);
 pfe_status setup_segments(pfe_ctx *c);
+// --- le.cu: Laplacian-eigenmap start (n x d FP64, row-major, device)
+int le_block(int d);
+pfe_status launch_le(pfe_ctx *c, int d, double *yout, int max_iter, double tol, int degree, int *iters,
+                     double *res);
 pfe_status check_edges_in_segments(pfe_ctx *c);
 pfe_status finish_graph_values(pfe_ctx *c);
 

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kBlock) k_gram_na(const double *__restrict__ Y
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        pstepk::jacobi_eig(G, V, D);
+        jacobi_eig(G, V, D);
         double lmax = 0.0, lmin = INFINITY;
         for (int k = 0; k < D; ++k) {
             lmax = fmax(lmax, G[k * D + k]);

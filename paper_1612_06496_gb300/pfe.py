@@ -28,7 +28,7 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_get_array", "pfe_set_array", "pfe_get_edges", "pfe_apply_A", "pfe_solve_system",
            "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
            "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_get_segments",
-           "pfe_get_segment_stats"]
+           "pfe_get_segment_stats", "pfe_laplacian_eigenmap"]
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3, "fsai_tr": 4, "fsai_z": 5}
 
 
@@ -49,7 +49,8 @@ class Params(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_edges", C.c_int64), ("nnz_A", C.c_int64), ("sell_slots", C.c_int64),
                 ("d", C.c_int32), ("precision", C.c_int32), ("lambda_", C.c_double), ("r", C.c_double),
-                ("vol", C.c_double), ("device_bytes", C.c_int64), ("nseg", C.c_int32)]
+                ("vol", C.c_double), ("device_bytes", C.c_int64), ("nseg", C.c_int32), ("le_iters", C.c_int32),
+                ("le_residual", C.c_double)]
 
 
 class StepStats(C.Structure):
@@ -102,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_adam_update.argtypes = [vp, vp, vp, vp, i64, i32, dbl, dbl, dbl, dbl, vp]
     lib.pfe_get_segments.argtypes = [vp, vp, vp]
     lib.pfe_get_segment_stats.argtypes = [vp, vp, vp, vp]
+    lib.pfe_laplacian_eigenmap.argtypes = [vp, i32, vp, i32, dbl, C.POINTER(i32), C.POINTER(dbl)]
     for name in EXPORTS:
         if name not in ("pfe_default_params", "pfe_last_error", "pfe_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -252,11 +254,27 @@ class PFE:
                     "pfe_get_segment_stats")
         return (it, rr, tot) if totals else (it, rr)
 
-    def init(self, Y0):
+    def init(self, Y0=None, d: int | None = None):
+        """Start from Y0 (n x d), or from the Laplacian eigenmap when Y0 is None."""
+        if Y0 is None:
+            self._check(self.lib.pfe_init(self.ctx, int(d), None, int(d)), "pfe_init")
+            self.d = int(d)
+            return
         d = Y0.shape[1]
         p, keep = _ptr(Y0)
         self._check(self.lib.pfe_init(self.ctx, d, p, d), "pfe_init")
         self.d = d
+
+    def laplacian_eigenmap(self, d: int, max_iter: int = 400, tol: float = 1e-9, out=None,
+                           allow_notconv: bool = False):
+        """(V [n x d], rounds, residual): the Laplacian-eigenmap embedding."""
+        V = np.empty((self.n, d)) if out is None else out
+        pv, kv = _ptr(V)
+        it, res = C.c_int32(), C.c_double()
+        ok = (PFE_OK, PFE_ENOTCONV) if allow_notconv else (PFE_OK,)
+        self._check(self.lib.pfe_laplacian_eigenmap(self.ctx, int(d), pv, int(max_iter), float(tol), C.byref(it),
+                                                    C.byref(res)), "pfe_laplacian_eigenmap", ok)
+        return V, it.value, res.value
 
     def inner_step(self, stats: bool = False, allow_notconv: bool = False):
         if not stats:

@@ -134,8 +134,8 @@ def test_dimension_and_call_order_errors():
         p.init(np.zeros((spec.n, 17)))
     assert ei.value.status == 8                          # d = 17 not built in
     lib = load_library()
-    assert lib.pfe_init(p.ctx, 3, None, 3) == 1          # NULL start
     assert lib.pfe_init(p.ctx, 3, Y0.ctypes.data, 2) == 1  # ldY0 < d
+    assert lib.pfe_init(p.ctx, 40, None, 40) == 8          # d = 40: not built in
     p.close()
 
 
