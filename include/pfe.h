@@ -197,6 +197,19 @@ PFE_API pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *g, const
 PFE_API pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0);
 
 /*
+ * pfe_objective -- diagnostics of the current embedding (FP64 reductions in a
+ * fixed order): *l1 = |M Y|_1 = sum over undirected edges a < b of
+ * w_ab |y_a - y_b|_1 (Eq. 1 sums every ordered pair, i.e. twice this), and
+ * *ortho_err = |Y^T D Y - I|_F, the distance from the constraint of Eq. 1
+ * (for a batch: the largest over its problems; l1 sums them).  which:
+ * PFE_OBJ_Y the iterate Y of Alg. 2 (not constrained), PFE_OBJ_YHAT the
+ * embedding D^{-1/2} P (constrained after every P-step).  Either output may
+ * be NULL.  Synchronises; uses the staging buffer.
+ */
+enum { PFE_OBJ_Y = 0, PFE_OBJ_YHAT = 1 };
+PFE_API pfe_status pfe_objective(pfe_ctx *c, int32_t which, double *l1, double *ortho_err);
+
+/*
  * pfe_laplacian_eigenmap -- the Laplacian-eigenmap embedding of the graph
  * (Sec. I, the l2 analogue of Eq. 1; Belkin & Niyogi): the d generalised
  * eigenvectors of (D - W) v = mu D v with the smallest mu on the

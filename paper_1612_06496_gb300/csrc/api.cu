@@ -441,6 +441,13 @@ pfe_status pfe_get_info(const pfe_ctx *c, pfe_info *info) {
     return PFE_OK;
 }
 
+pfe_status pfe_objective(pfe_ctx *c, int32_t which, double *l1, double *ortho_err) {
+    if (!c || (which != PFE_OBJ_Y && which != PFE_OBJ_YHAT)) return PFE_EINVAL;
+    if (!c->inited) return fail(c, PFE_ESTATE, "pfe_objective before pfe_init");
+    PFE_TRY(sync(c));
+    return diag_objective(c, which, l1, ortho_err);
+}
+
 pfe_status pfe_laplacian_eigenmap(pfe_ctx *c, int32_t d, double *V, int32_t max_iter, double tol, int32_t *iters,
                                   double *residual) {
     if (!c || !V || d < 1 || max_iter < 0 || !(tol >= 0.0)) return PFE_EINVAL;

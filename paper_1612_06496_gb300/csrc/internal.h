@@ -161,6 +161,8 @@ namespace pfe {
 pfe_status build_grid_graph(pfe_ctx *c, const double *dfeat);
 pfe_status build_edge_graph(pfe_ctx *c, const double *dfeat, const int32_t *dei, const int32_t *dej);
 pfe_status setup_segments(pfe_ctx *c);
+// --- diag.cu: |M Y|_1 and |Y^T D Y - I|_F (which: 0 = Y, 1 = Yhat)
+pfe_status diag_objective(pfe_ctx *c, int which, double *l1, double *ortho);
 // --- le.cu: Laplacian-eigenmap start (n x d FP64, row-major, device)
 int le_block(int d);
 pfe_status launch_le(pfe_ctx *c, int d, double *yout, int max_iter, double tol, int degree, int *iters,

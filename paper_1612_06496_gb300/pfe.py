@@ -28,7 +28,7 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_get_array", "pfe_set_array", "pfe_get_edges", "pfe_apply_A", "pfe_solve_system",
            "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
            "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_get_segments",
-           "pfe_get_segment_stats", "pfe_laplacian_eigenmap"]
+           "pfe_get_segment_stats", "pfe_laplacian_eigenmap", "pfe_objective"]
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3, "fsai_tr": 4, "fsai_z": 5}
 
 
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_get_segments.argtypes = [vp, vp, vp]
     lib.pfe_get_segment_stats.argtypes = [vp, vp, vp, vp]
     lib.pfe_laplacian_eigenmap.argtypes = [vp, i32, vp, i32, dbl, C.POINTER(i32), C.POINTER(dbl)]
+    lib.pfe_objective.argtypes = [vp, i32, C.POINTER(dbl), C.POINTER(dbl)]
     for name in EXPORTS:
         if name not in ("pfe_default_params", "pfe_last_error", "pfe_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -264,6 +265,13 @@ class PFE:
         p, keep = _ptr(Y0)
         self._check(self.lib.pfe_init(self.ctx, d, p, d), "pfe_init")
         self.d = d
+
+    def objective(self, which: str = "yhat"):
+        """(|M Y|_1, |Y^T D Y - I|_F) of the iterate ("y") or the embedding ("yhat")."""
+        l1, oe = C.c_double(), C.c_double()
+        self._check(self.lib.pfe_objective(self.ctx, 0 if which == "y" else 1, C.byref(l1), C.byref(oe)),
+                    "pfe_objective")
+        return l1.value, oe.value
 
     def laplacian_eigenmap(self, d: int, max_iter: int = 400, tol: float = 1e-9, out=None,
                            allow_notconv: bool = False):
