@@ -22,6 +22,7 @@ namespace edgek {
 template <typename T>
 struct EdgeArgs {
     int64_t n, n_slices;
+    int row_len;  // > 0: uniform row length
     const int *__restrict__ slice_ptr;
     const int *__restrict__ col;
     const int *__restrict__ eid;
@@ -81,10 +82,17 @@ __global__ void __launch_bounds__(kBlock) k_edge(EdgeArgs<T> a) {
     for (int64_t g = warp_g; g * RPW < a.n; g += warps_total) {
         const int64_t i = g * RPW + rw;
         if (!active || i >= a.n) continue;
-        const int64_t s = i >> 5;
-        const int s0 = a.slice_ptr[s];
-        const int len = (a.slice_ptr[s + 1] - s0) >> 5;
-        const int64_t base = (int64_t)s0 + (i & 31) * (int64_t)len;  // row-major within the slice
+        int len;
+        int64_t base;
+        if (a.row_len > 0) {  // uniform rows (grid graphs): no slice lookup
+            len = a.row_len;
+            base = i * a.row_len;
+        } else {
+            const int64_t s = i >> 5;
+            const int s0 = a.slice_ptr[s];
+            len = (a.slice_ptr[s + 1] - s0) >> 5;
+            base = (int64_t)s0 + (i & 31) * (int64_t)len;  // row-major within the slice
+        }
         T lam = a.lambda, gam = a.gamma;
         if constexpr (MS) {  // batch: lambda of the row's segment
             const double ls = a.seg_lam[__ldg(a.sg.rseg + i)];
@@ -154,6 +162,7 @@ pfe_status edge_T(pfe_ctx *c, cudaStream_t s) {
     EdgeArgs<T> a;
     a.n = c->g.n;
     a.n_slices = c->g.n_slices;
+    a.row_len = c->g.row_len;
     a.slice_ptr = c->g.slice_ptr;
     a.col = c->g.col;
     a.eid = c->g.eid;

@@ -74,15 +74,21 @@ __global__ void k_rowprep(View g, float *srow, int *kb, int *ent_of_slot) {
     const int64_t base = s0 + (i & 31) * (int64_t)len;  // row-major within the slice
     const double aii = g.adiag[i];
     double acc = 0.0;
-    int nb = 0;
+    // kb = position of the first strictly upper slot (valid slots are sorted by
+    // column; padding slots repeat i and may sit anywhere in a fixed-position
+    // row): the lower entries are the valid slots before it
+    int nb = len;
     for (int k = 0; k < len; ++k) {
         const int64_t idx = base + k;
         const int j = g.col[idx];
-        if (j >= i) break;  // slots are sorted by column; padding repeats i
+        if (j > i) {
+            nb = k;
+            break;
+        }
+        if (j == i || g.eid[idx] < 0) continue;  // padding
         const double w = g.w64[idx];
         const double rho = g.lam * w * w / sqrt(aii * g.adiag[j]);
         acc = fma(rho, rho, acc);
-        ++nb;
     }
     srow[i] = (float)acc;
     kb[i] = nb;
@@ -329,13 +335,17 @@ __global__ void k_kaporin_rows(View g, const int *kb, const float *gdiag, const 
     const int s0 = g.slice_ptr[s];
     const int len_i = (g.slice_ptr[s + 1] - s0) >> 5;
     const int64_t base = s0 + (i & 31) * (int64_t)len_i;
-    const int nl = min(kb[i], kMaxLower);
-    int cols[kMaxLower + 1];
+    // the valid lower entries (padding slots skipped), at most kMaxLower
+    int cols[kMaxLower + 1], slot_of[kMaxLower];
     float vals[kMaxLower + 1];
-    for (int k = 0; k < nl; ++k) {
+    int nl = 0;
+    for (int k = 0; k < kb[i] && nl < kMaxLower; ++k) {
         const int64_t idx = base + k;
-        cols[k] = g.col[idx];
-        vals[k] = gslot[idx];
+        if (g.eid[idx] < 0 || g.col[idx] >= i) continue;
+        cols[nl] = g.col[idx];
+        vals[nl] = gslot[idx];
+        slot_of[nl] = k;
+        ++nl;
     }
     cols[nl] = (int)i;
     vals[nl] = gdiag[i];
@@ -367,7 +377,7 @@ __global__ void k_kaporin_rows(View g, const int *kb, const float *gdiag, const 
         if (m == nl) {
             dq[i] = d;  // diagonal entry i
         } else {
-            const int64_t idx = base + m;
+            const int64_t idx = base + slot_of[m];
             dq[g.n + ent_of_slot[g.eid[idx]]] = d;  // edge entry (j, i): G_ij
         }
     }
@@ -612,14 +622,20 @@ __global__ void k_fsai_classical(View g, const int *kb, float *gdiag, float *gE,
     const int s0 = g.slice_ptr[s];
     const int len_i = (g.slice_ptr[s + 1] - s0) >> 5;
     const int64_t base = s0 + (i & 31) * (int64_t)len_i;
-    const int nl = kb[i];
-    if (nl + 1 > kMaxS) {
-        atomicExch(err, 1);
-        return;
+    int S[kMaxS], slot_of[kMaxS];
+    int nl = 0;  // the valid lower entries (padding slots skipped)
+    for (int k = 0; k < kb[i]; ++k) {
+        const int64_t idx = base + k;
+        if (g.eid[idx] < 0 || g.col[idx] >= i) continue;
+        if (nl + 1 >= kMaxS) {
+            atomicExch(err, 1);
+            return;
+        }
+        S[nl] = g.col[idx];
+        slot_of[nl] = k;
+        ++nl;
     }
     const int m = nl + 1;
-    int S[kMaxS];
-    for (int k = 0; k < nl; ++k) S[k] = g.col[base + k];
     S[nl] = (int)i;
     double Ls[kMaxS * kMaxS];
     // A[S,S]: diagonal from A_jj, off-diagonal by searching row S[p]'s slots
@@ -677,7 +693,7 @@ __global__ void k_fsai_classical(View g, const int *kb, float *gdiag, float *gE,
     }
     const double sc = 1.0 / sqrt(x[m - 1]);
     gdiag[i] = (float)(x[m - 1] * sc);
-    for (int k = 0; k < nl; ++k) gE[g.eid[base + k]] = (float)(x[k] * sc);
+    for (int k = 0; k < nl; ++k) gE[g.eid[base + slot_of[k]]] = (float)(x[k] * sc);
 }
 
 __global__ void k_export(View g, const float *gdiag, const float *gE, double *od, double *oe) {

@@ -4,7 +4,10 @@
 // Layout: SELL-32, row-major within a slice.  Rows are taken 32 at a time;
 // slice s stores each row's off-diagonal entries contiguously, padded to the
 // slice's longest row rounded up to 4 slots, so that a row's slots are read
-// with 16-byte vector loads.  Undirected edges (i < j) are stored in a second
+// with 16-byte vector loads.  Grid graphs use fixed positions: slot t of
+// every row is stencil offset t (a padding slot -- column i, weight 0, edge
+// id -1 -- where the offset leaves the image), so every row has the same
+// length and a kernel finds row i's slots at i * K without a slice lookup.  Undirected edges (i < j) are stored in a second
 // sliced layout over their first endpoint; the split-Bregman edge state b
 // (Alg. 2) is indexed by that edge slot.
 #include <algorithm>
@@ -72,11 +75,13 @@ __global__ void k_grid_count(int64_t n, int64_t n_slices, GridSegs gs, Offsets o
         }
         nf_row[i] = nf;
     }
-    int mb = __reduce_max_sync(0xffffffffu, nb);
+    (void)nb;
     int mf = __reduce_max_sync(0xffffffffu, nf);
     if ((threadIdx.x & 31) == 0) {
         int64_t s = i >> 5;
-        slice_len[s] = ((mb + 3) & ~3) * 32;  // row length padded to a multiple of 4 slots
+        // fixed positions: slot t of every row is stencil offset t (K is a
+        // multiple of 4: the offsets come in orbits of the 90-degree rotation)
+        slice_len[s] = off.K * 32;
         fslice_len[s] = mf * 32;
     }
 }
@@ -101,9 +106,14 @@ __global__ void k_grid_fill(int64_t n, int64_t n_slices, GridSegs gs, Offsets of
         double sw = 0.0, sw2 = 0.0;
         for (int t = 0; t < off.K; ++t) {
             int x2 = x + off.dx[t], y2 = y + off.dy[t];
-            if (x2 < 0 || x2 >= W || y2 < 0 || y2 >= H) continue;
+            int64_t idx = base + t;
+            if (x2 < 0 || x2 >= W || y2 < 0 || y2 >= H) {  // off the image: padding slot
+                col[idx] = (int)i;
+                eid[idx] = -1;
+                w64[idx] = 0.0;
+                continue;
+            }
             int64_t j = vo + (int64_t)y2 * W + x2;
-            int64_t idx = base + k;
             double w = (j > i) ? heat_weight(X, m, i, j, inv2s2) : heat_weight(X, m, j, i, inv2s2);
             int e;
             if (t >= off.K / 2) {  // forward: i owns the edge
@@ -131,12 +141,12 @@ __global__ void k_grid_fill(int64_t n, int64_t n_slices, GridSegs gs, Offsets of
             w64[idx] = w;
             sw += w;
             sw2 = fma(w, w, sw2);
-            ++k;
         }
         deg[i] = sw;
         deg2[i] = sw2;
+        k = off.K;
     }
-    for (; k < len; ++k) {  // padding slots
+    for (; k < len; ++k) {  // rows past n in the last slice
         int64_t idx = base + k;
         col[idx] = (i < n) ? (int)i : 0;
         eid[idx] = -1;
@@ -570,6 +580,7 @@ pfe_status build_grid_graph(pfe_ctx *c, const double *dfeat) {
     g.n_edges = ne;
     PFE_TRY(max_row_slots(c, s, slice_len));
     PFE_TRY(alloc_slots(c, s, slice_ptr64, fslice_ptr64));
+    g.row_len = off.K;  // every row: K slots, slot t = offset t
     const double inv2s2 = 1.0 / (2.0 * c->sigma * c->sigma);
     k_grid_fill<<<nblk(nthreads, 128), 128, 0, s>>>(g.n, g.n_slices, gs, off, slice_ptr64, fslice_ptr64, fw_off,
                                                      dfeat, c->m, inv2s2, g.col, g.eid, g.w64, g.ext_slot, g.ea,

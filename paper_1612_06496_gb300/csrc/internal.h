@@ -79,6 +79,7 @@ struct PstepCtl {
 struct DevGraph {
     int64_t n = 0, n_slices = 0, slots = 0, n_edges = 0, fslots = 0;
     int max_slots_per_row = 0;
+    int row_len = 0;            // > 0: every row has exactly row_len slots (grid graphs), row i at i * row_len
     int *slice_ptr = nullptr;   // n_slices + 1, in slots
     int *fslice_ptr = nullptr;  // n_slices + 1, in edge slots
     int *col = nullptr;         // per slot: neighbour j (padding: i itself)

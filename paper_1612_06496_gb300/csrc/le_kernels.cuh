@@ -36,6 +36,7 @@ constexpr int kTileLe = 32;  // rows staged per Gram step
 
 struct LeGraph {
     int64_t n;
+    int row_len;
     const int *__restrict__ slice_ptr;
     const int *__restrict__ col;
     const double *__restrict__ w;    // per slot w_ij (0 on padding)
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(kBlock) k_le_cheb(LeGraph g, const double *__r
         const int c0 = lm.cg * V;
         int64_t base;
         int len;
-        sell_row(g.slice_ptr, i, base, len);
+        sell_row(g.slice_ptr, g.row_len, i, base, len);
         double acc[V], yi[V], yp[V];
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = 0.0;
@@ -407,7 +408,7 @@ pfe_status le_T(pfe_ctx *c, int d, double *yout, int max_iter, double tol, int d
                 double *res_out) {
     cudaStream_t s = c->stream;
     const int64_t n = c->g.n;
-    const LeGraph g{n, c->g.slice_ptr, c->g.col, c->g.w64, c->g.deg};
+    const LeGraph g{n, c->g.row_len, c->g.slice_ptr, c->g.col, c->g.w64, c->g.deg};
     constexpr int NV = 3 * (K * (K + 1) / 2) + K;
     const int64_t ntiles = (n + kTileLe - 1) / kTileLe;
     const int ggrid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)c->num_sms * 2));

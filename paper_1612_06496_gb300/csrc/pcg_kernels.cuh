@@ -38,6 +38,7 @@ constexpr int kChunk = 12;  // matrix slots prefetched together by the gather ke
 template <typename T>
 struct SysView {
     int64_t n, n_slices;
+    int row_len;  // > 0: uniform row length (row i's slots at i * row_len)
     const int *__restrict__ slice_ptr;
     const int *__restrict__ col;
     const T *__restrict__ aoff;
@@ -72,6 +73,7 @@ SysView<T> sys_view(pfe_ctx *c) {
     SysView<T> v;
     v.n = c->g.n;
     v.n_slices = c->g.n_slices;
+    v.row_len = c->g.row_len;
     v.slice_ptr = c->g.slice_ptr;
     v.col = c->g.col;
     if constexpr (std::is_same_v<T, float>) {
@@ -150,8 +152,16 @@ __device__ __forceinline__ void stv(T *p, const T (&v)[V]) {
 }
 
 // SELL-32 slot addressing of row i (row-major within the slice): slot k is at
-// base + k; len is a multiple of 4 and base is 16-byte aligned.
-__device__ __forceinline__ void sell_row(const int *__restrict__ slice_ptr, int64_t i, int64_t &base, int &len) {
+// base + k; len is a multiple of 4 and base is 16-byte aligned.  With a
+// uniform row length (grid graphs) the address is computed, saving the
+// dependent slice lookup ahead of the slot loads.
+__device__ __forceinline__ void sell_row(const int *__restrict__ slice_ptr, int row_len, int64_t i, int64_t &base,
+                                         int &len) {
+    if (row_len > 0) {
+        len = row_len;
+        base = i * row_len;
+        return;
+    }
     const int64_t s = i >> 5;
     const int s0 = slice_ptr[s];
     len = (slice_ptr[s + 1] - s0) >> 5;
@@ -388,7 +398,7 @@ template <typename T, int D, int V>
 __device__ __forceinline__ void true_residual(const PcgArgs<T> &a, int64_t i, int c0, T (&out)[V]) {
     int64_t base;
     int len;
-    sell_row(a.A.slice_ptr, i, base, len);
+    sell_row(a.A.slice_ptr, a.A.row_len, i, base, len);
     T bi[V];
     ldv_rw<T, V>(a.b + i * D + c0, bi);
     if constexpr (std::is_same_v<T, float>) {
@@ -650,7 +660,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
         const int64_t ic = i * D + c0;
         int64_t base;
         int len;
-        sell_row(a.A.slice_ptr, i, base, len);
+        sell_row(a.A.slice_ptr, a.A.row_len, i, base, len);
         T pi[V], acc[V];
         ldv<T, V>(pp + ic, pi);
         const T ad = a.A.adiag[i];
@@ -921,7 +931,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr
         for (int k = 0; k < V; ++k) al[k] = salpha[c0 + k];
         int64_t base;
         int len;
-        sell_row(a.A.slice_ptr, i, base, len);
+        sell_row(a.A.slice_ptr, a.A.row_len, i, base, len);
         T acc[V], ri[V], qi[V];
         ldv<T, V>(rold + i * D + c0, ri);
         ldv<T, V>(a.q + i * D + c0, qi);
@@ -949,7 +959,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(
         const int c0 = lm.cg * V;
         int64_t base;
         int len;
-        sell_row(a.A.slice_ptr, i, base, len);
+        sell_row(a.A.slice_ptr, a.A.row_len, i, base, len);
         T acc[V], ri[V];
         const T nal[V] = {};
         ldv<T, V>(rsrc + i * D + c0, ri);
@@ -983,7 +993,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_z(
         const int c0 = lm.cg * V;
         int64_t base;
         int len;
-        sell_row(a.A.slice_ptr, i, base, len);
+        sell_row(a.A.slice_ptr, a.A.row_len, i, base, len);
         T acc[V], ti[V], ri[V];
         const T nal[V] = {};
         ldv<T, V>(a.t + i * D + c0, ti);
@@ -1066,7 +1076,7 @@ __global__ void __launch_bounds__(kBlock) k_apply(SysView<T> Av, const T *__rest
         const int c0 = lm.cg * V;
         int64_t base;
         int len;
-        sell_row(a.A.slice_ptr, i, base, len);
+        sell_row(a.A.slice_ptr, a.A.row_len, i, base, len);
         T acc[V], xv[V];
         ldv<T, V>(x + i * D + c0, xv);
         const T ad = a.A.adiag[i];
