@@ -393,6 +393,8 @@ def main():
     Xd = torch.from_numpy(X).cuda()
     Y0d = torch.from_numpy(Y0).cuda()
 
+    tuned = {}
+
     def run_arm(precision: str, warmup: int, steps: int, clocks: bool, precond: str = "jacobi"):
         t0 = time.perf_counter()
         p = PFE(Xd, sigma=spec.sigma, radius=spec.radius, precision=precision, tol=spec.tol,
@@ -400,6 +402,7 @@ def main():
         if precond == "learned":
             p.fsai_set(fsai_params)  # network inference of G runs inside the timed setup
         p.init(Y0d)
+        tuned[precision + "/" + precond] = p.autotune(10)  # kernel variants for this problem (setup)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         for _ in range(warmup):
@@ -570,6 +573,8 @@ def main():
             "fp64": fp64,
             "speedup_vs_fp64": (fp64["sec_per_outer_iter"] / sec_per_outer) if fp64 else None,
             "roofline": roofline,
+            "autotune": {k: {"spmm_variant": v[0], "spmm_ms": {str(a): round(b, 5) for a, b in v[1].items()}}
+                         for k, v in tuned.items()},
             "gpu_launches": launches,
             "clocks": clk,
             "e2e": e2e,

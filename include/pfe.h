@@ -197,6 +197,29 @@ PFE_API pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *g, const
 PFE_API pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0);
 
 /*
+ * pfe_autotune -- choose the fastest variant of each tunable hot kernel for
+ * this context (its graph, d and precision): every candidate is timed with
+ * CUDA events over `reps` launches on the current iterate (scratch copies,
+ * the iteration state is not modified) and the fastest is kept.  Tunable now:
+ * the SpMM of the PCG iteration (variants below; the fixed-length ones apply
+ * to FP32 single-problem grid graphs of radius 2 or 3).  choice[0] receives
+ * the chosen SpMM variant and ms[v] (at least PFE_SPMM_NVARIANTS entries;
+ * either may be NULL) each variant's average time, -1 where it does not
+ * apply.  pfe_set_variant sets a choice directly (e.g. from a cache of
+ * earlier tuning).  Needs pfe_init; synchronises.
+ */
+enum {
+    PFE_SPMM_GENERAL = 0, /* any layout: slots fetched 12 at a time, then gathered */
+    PFE_SPMM_ROW1 = 1,    /* uniform rows: one row group per step, >= 6 blocks per SM */
+    PFE_SPMM_ROW2 = 2,    /* uniform rows: two row groups per step, >= 5 blocks per SM */
+    PFE_SPMM_ROW2_4 = 3,  /* uniform rows: two row groups per step, >= 4 blocks per SM */
+    PFE_SPMM_NVARIANTS = 4
+};
+enum { PFE_TUNE_SPMM = 0 };
+PFE_API pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms);
+PFE_API pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant);
+
+/*
  * pfe_objective -- diagnostics of the current embedding (FP64 reductions in a
  * fixed order): *l1 = |M Y|_1 = sum over undirected edges a < b of
  * w_ab |y_a - y_b|_1 (Eq. 1 sums every ordered pair, i.e. twice this), and

@@ -441,6 +441,48 @@ pfe_status pfe_get_info(const pfe_ctx *c, pfe_info *info) {
     return PFE_OK;
 }
 
+// The SpMM variants that apply to a context (the fixed-length kernels need an
+// FP32 single-problem graph with 12 or 28 slots per row).
+static bool spmm_variant_applies(const pfe_ctx *c, int v) {
+    if (v == PFE_SPMM_GENERAL) return true;
+    return c->mixed && c->nseg == 1 && (c->g.row_len == 12 || c->g.row_len == 28) && v > 0 &&
+           v < PFE_SPMM_NVARIANTS;
+}
+
+pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms) {
+    if (!c || reps < 1) return PFE_EINVAL;
+    if (!c->inited) return fail(c, PFE_ESTATE, "pfe_autotune before pfe_init");
+    PFE_TRY(sync(c));
+    int best = PFE_SPMM_GENERAL;
+    float tbest = INFINITY;
+    for (int v = 0; v < PFE_SPMM_NVARIANTS; ++v) {
+        if (!spmm_variant_applies(c, v)) {
+            if (ms) ms[v] = -1.0;
+            continue;
+        }
+        float t = 0.f;
+        PFE_TRY(time_pcg_kernel(c, c->stream, 0, reps, &t, v));
+        if (ms) ms[v] = t;
+        if (t < tbest) {
+            tbest = t;
+            best = v;
+        }
+    }
+    c->spmm_variant = best;
+    free_pcg_graph(c);  // the captured loop holds the previous variant
+    if (choice) choice[0] = best;
+    return PFE_OK;
+}
+
+pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant) {
+    if (!c || kernel != PFE_TUNE_SPMM || variant < 0 || variant >= PFE_SPMM_NVARIANTS) return PFE_EINVAL;
+    if (!spmm_variant_applies(c, variant)) return fail(c, PFE_EUNSUPPORTED, "SpMM variant does not apply here");
+    PFE_TRY(sync(c));
+    c->spmm_variant = variant;
+    free_pcg_graph(c);
+    return PFE_OK;
+}
+
 pfe_status pfe_objective(pfe_ctx *c, int32_t which, double *l1, double *ortho_err) {
     if (!c || (which != PFE_OBJ_Y && which != PFE_OBJ_YHAT)) return PFE_EINVAL;
     if (!c->inited) return fail(c, PFE_ESTATE, "pfe_objective before pfe_init");

@@ -152,6 +152,7 @@ struct pfe_ctx {
     std::vector<void *> dev_allocs;   // graph-lifetime allocations
     std::vector<void *> work_allocs;  // d-dependent allocations
     int64_t bytes = 0;
+    int spmm_variant = PFE_SPMM_ROW1;  // SpMM kernel variant (pfe_autotune)
     int le_iters = 0;                 // last Laplacian-eigenmap computation
     double le_residual = 0.0;
 };
@@ -180,7 +181,7 @@ pfe_status launch_pcg_init(pfe_ctx *c, cudaStream_t s, PcgLaunch L);
 pfe_status launch_pcg_body(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters);
 pfe_status launch_pcg_final(pfe_ctx *c, cudaStream_t s, PcgLaunch L);
 pfe_status launch_apply_A(pfe_ctx *c, cudaStream_t s, const void *x, void *y);
-pfe_status time_pcg_kernel(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms);
+pfe_status time_pcg_kernel(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, int variant = -1);
 
 // --- edge.cu: fused edge pass (Eqs. 7, 9, 10) and right-hand side (Eq. 13)
 pfe_status launch_edge(pfe_ctx *c, cudaStream_t s);

@@ -15,7 +15,7 @@ pfe_status final_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L);
 template <typename T, int D>
 pfe_status apply_T(pfe_ctx *c, cudaStream_t s, const void *x, void *y);
 template <typename T, int D>
-pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms);
+pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, int variant);
 }  // namespace pcgk
 using namespace pcgk;
 
@@ -54,11 +54,11 @@ pfe_status launch_apply_A(pfe_ctx *c, cudaStream_t s, const void *x, void *y) {
 }  // namespace pfe
 
 namespace pfe {
-pfe_status time_pcg_kernel(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
+pfe_status time_pcg_kernel(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, int variant) {
     if (c->mixed) {
-        PFE_DISPATCH_D(c->d, return time_T<float, D>(c, s, which, reps, ms));
+        PFE_DISPATCH_D(c->d, return time_T<float, D>(c, s, which, reps, ms, variant));
     } else {
-        PFE_DISPATCH_D(c->d, return time_T<double, D>(c, s, which, reps, ms));
+        PFE_DISPATCH_D(c->d, return time_T<double, D>(c, s, which, reps, ms, variant));
     }
 }
 }  // namespace pfe

@@ -641,6 +641,32 @@ __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
     }
 }
 
+// Last block of a segment: alpha_c = r.z / p.q per column of the segment
+// (0 for frozen columns; a non-positive or non-finite p.q is PFE_ENUMERIC).
+template <typename T, int D, bool MS>
+__device__ __forceinline__ void spmm_finish(const PcgArgs<T> &a, const BlockSeg &bsg, const double *tot) {
+    PcgCtl *w = a.ctl;
+    const SegScal &sc = a.sc;
+    for (int c = 0; c < D; ++c) {
+        const int k = bsg.seg * D + c;
+        if (!sc.active[k]) {
+            sc.alpha[k] = 0.0;
+            continue;
+        }
+        const double pqc = tot[c];
+        if (!(pqc > 0.0) || !(pqc < INFINITY)) {
+            atomicMax(&w->error, (int)PFE_ENUMERIC);
+            sc.alpha[k] = 0.0;
+        } else {
+            sc.alpha[k] = sc.rz[k] / pqc;
+        }
+    }
+    if (!MS || last_segment_arrives(w, 0, a.sg.nseg)) {
+        w->p_ready = 0;
+        w->xpending = 1;
+    }
+}
+
 // q = A p and the column dots p.q -> alpha.  Only p is gathered; the matrix
 // slots of a row are fetched kChunk at a time ahead of the gathers.
 template <typename T, int D, bool MS>
@@ -682,30 +708,107 @@ __global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
         for (int k = 0; k < V; ++k) A::add_prod(pq[0][k], pi[k], acc[k]);
     }
     __shared__ double tot[D];
-    if (grid_sum_cols<T, D, 1>(pq, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 0], tot)) {
-        if (threadIdx.x == 0) {
-            PcgCtl *w = a.ctl;
-            const SegScal &sc = a.sc;
-            for (int c = 0; c < D; ++c) {
-                const int k = bsg.seg * D + c;
-                if (!sc.active[k]) {
-                    sc.alpha[k] = 0.0;
-                    continue;
-                }
-                const double pqc = tot[c];
-                if (!(pqc > 0.0) || !(pqc < INFINITY)) {
-                    atomicMax(&w->error, (int)PFE_ENUMERIC);
-                    sc.alpha[k] = 0.0;
-                } else {
-                    sc.alpha[k] = sc.rz[k] / pqc;
-                }
-            }
-            if (!MS || last_segment_arrives(w, 0, a.sg.nseg)) {
-                w->p_ready = 0;
-                w->xpending = 1;
-            }
+    if (grid_sum_cols<T, D, 1>(pq, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 0], tot))
+        if (threadIdx.x == 0) spmm_finish<T, D, MS>(a, bsg, tot);
+}
+
+// k_spmm for graphs whose rows all have LEN slots (grid stencils; LEN a
+// compile-time constant): the slot loads of ROWS row groups are issued
+// together, then their gathers; at least MINB blocks per SM.
+template <typename T, int D, bool MS, int LEN, int ROWS, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_spmm_fixed(PcgArgs<T> a) {
+    const PcgCtl *ctl = a.ctl;
+    if (*(volatile const int *)&ctl->done) return;
+    using A = Acc<T>;
+    using AT = typename A::type;
+    using SW = SubWarp<T, D>;
+    constexpr int V = SW::V;
+    static_assert(LEN % 4 == 0, "rows are read 4 slots at a time");
+    const T *__restrict__ pp = a.p[0];
+    AT pq[1][V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) pq[0][k] = A::zero();
+    const SW lm;
+    const BlockSeg bsg = block_seg<MS>(a.sg);
+    const int64_t warp_g = (int64_t)(blockIdx.x - bsg.b0) * kWarps + (threadIdx.x >> 5);
+    const int64_t warps_total = (int64_t)bsg.nb * kWarps;
+    const int64_t seg_rows = (MS && !a.sc.seg_active[bsg.seg]) ? 0 : bsg.r1 - bsg.r0;
+    const int c0 = lm.cg * V;
+    for (int64_t g = warp_g; g * SW::RPW < seg_rows; g += ROWS * warps_total) {
+        int64_t ii[ROWS];
+        bool ok[ROWS];
+        int jj[ROWS][LEN];
+        T av[ROWS][LEN];
+#pragma unroll
+        for (int h = 0; h < ROWS; ++h) {
+            ii[h] = bsg.r0 + (g + h * warps_total) * SW::RPW + lm.r;
+            ok[h] = lm.active && ii[h] < bsg.r1;
+            const int64_t base = (ok[h] ? ii[h] : bsg.r0) * LEN;  // a valid row when idle
+            load_slots<T, LEN>(a.A.col, a.A.aoff, base, 0, LEN, (int)ii[h], jj[h], av[h]);
+        }
+#pragma unroll
+        for (int h = 0; h < ROWS; ++h) {
+            if (!ok[h]) continue;
+            const int64_t ic = ii[h] * D + c0;
+            T pi[V], acc[V], pj[LEN][V];
+            ldv<T, V>(pp + ic, pi);
+            const T ad = a.A.adiag[ii[h]];
+#pragma unroll
+            for (int k = 0; k < V; ++k) acc[k] = ad * pi[k];
+#pragma unroll
+            for (int u = 0; u < LEN; ++u) ldv<T, V>(pp + (int64_t)jj[h][u] * D + c0, pj[u]);
+#pragma unroll
+            for (int u = 0; u < LEN; ++u)
+#pragma unroll
+                for (int k = 0; k < V; ++k) acc[k] = fma(av[h][u], pj[u][k], acc[k]);
+            stv<T, V>(a.q + ic, acc);
+#pragma unroll
+            for (int k = 0; k < V; ++k) A::add_prod(pq[0][k], pi[k], acc[k]);
         }
     }
+    __shared__ double tot[D];
+    if (grid_sum_cols<T, D, 1>(pq, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 0], tot))
+        if (threadIdx.x == 0) spmm_finish<T, D, MS>(a, bsg, tot);
+}
+
+template <typename T, int D>
+int64_t rows_need(const pfe_ctx *c);
+
+// The SpMM variants (pfe_autotune picks one per context; PFE_SPMM_AUTO
+// applies the default rule):
+//   PFE_SPMM_GENERAL  any layout, kChunk slots at a time
+//   PFE_SPMM_ROW1     fixed row length, one row group per step, >= 6 blocks/SM
+//   PFE_SPMM_ROW2     fixed row length, two row groups per step, >= 5 blocks/SM
+//   PFE_SPMM_ROW2_4   fixed row length, two row groups per step, >= 4 blocks/SM
+// Fixed-length variants exist for the FP32 single-problem path at radius 2
+// and 3 (12 and 28 slots); elsewhere the general kernel runs.
+template <typename T, int D, bool MS, int LEN>
+bool launch_spmm_fixed(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int v) {
+    if (v == PFE_SPMM_ROW1)
+        k_spmm_fixed<T, D, MS, LEN, 1, 6><<<wave_grid(c, G_SPMM_F1, k_spmm_fixed<T, D, MS, LEN, 1, 6>,
+                                                      rows_need<T, D>(c)),
+                                            kBlock, 0, s>>>(a);
+    else if (v == PFE_SPMM_ROW2)
+        k_spmm_fixed<T, D, MS, LEN, 2, 5><<<wave_grid(c, G_SPMM_F2, k_spmm_fixed<T, D, MS, LEN, 2, 5>,
+                                                      rows_need<T, D>(c)),
+                                            kBlock, 0, s>>>(a);
+    else if (v == PFE_SPMM_ROW2_4)
+        k_spmm_fixed<T, D, MS, LEN, 2, 4><<<wave_grid(c, G_SPMM_F3, k_spmm_fixed<T, D, MS, LEN, 2, 4>,
+                                                      rows_need<T, D>(c)),
+                                            kBlock, 0, s>>>(a);
+    else
+        return false;
+    return true;
+}
+template <typename T, int D, bool MS>
+void launch_spmm(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int variant = -1) {
+    const int v = variant >= 0 ? variant : c->spmm_variant;
+    bool done = false;
+    if constexpr (std::is_same_v<T, float> && !MS) {
+        if (c->g.row_len == 12) done = launch_spmm_fixed<T, D, MS, 12>(c, s, a, v);
+        else if (c->g.row_len == 28) done = launch_spmm_fixed<T, D, MS, 28>(c, s, a, v);
+    }
+    if (!done) k_spmm<T, D, MS><<<wave_grid(c, G_SPMM, k_spmm<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
 }
 
 // Flat vectorised traversal of an n x D array: thread t handles the VEC
@@ -1165,7 +1268,7 @@ void body_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int iters) {
     for (int u = 0; u < iters; ++u) {
         k_pupdate<T, D, 0, MS><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0, MS>, flat_need<T, D>(c), flat_mult<T, D>()),
                                  kBlock, 0, s>>>(a);
-        k_spmm<T, D, MS><<<wave_grid(c, G_SPMM, k_spmm<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        launch_spmm<T, D, MS>(c, s, a);
         k_update<T, D, MS><<<wave_grid(c, G_UPDATE, k_update<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
         k_xflush<T, D, MS><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, MS>, flat_need<T, D>(c)), kBlock, 0, s>>>(a, 0);
         k_refresh<T, D, MS><<<wave_grid(c, G_REFRESH, k_refresh<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
@@ -1204,7 +1307,7 @@ pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
                 k_pupdate<T, D, 1, false><<<wave_grid(c, G_PUPD_F, k_pupdate<T, D, 1, false>, flat_need<T, D>(c),
                                                       flat_mult<T, D>()),
                                             kBlock, 0, s>>>(a);
-                k_spmm<T, D, false><<<wave_grid(c, G_SPMM, k_spmm<T, D, false>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+                launch_spmm<T, D, false>(c, s, a);
                 k_fsai_tr<T, D><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
                 k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c)), kBlock, 0,
                                         s>>>(a, 0);
@@ -1250,7 +1353,7 @@ pfe_status apply_T(pfe_ctx *c, cudaStream_t s, const void *x, void *y) {
 // the direction buffers, so the iteration state is left as it was.
 // which: 0 = k_spmm, 1 = k_update, 2 = k_pupdate, 3 = k_fsai_tr, 4 = k_fsai_z.
 template <typename T, int D>
-pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
+pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, int variant) {
     PcgCtl h;
     memset(&h, 0, sizeof(h));
     h.max_iter = 1 << 30;
@@ -1333,9 +1436,9 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     const bool multi = c->nseg > 1;
     auto launch = [&]() {
         if (which == 0 && multi)
-            k_spmm<T, D, true><<<wave_grid(c, G_SPMM, k_spmm<T, D, true>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            launch_spmm<T, D, true>(c, s, a, variant);
         else if (which == 0)
-            k_spmm<T, D, false><<<wave_grid(c, G_SPMM, k_spmm<T, D, false>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            launch_spmm<T, D, false>(c, s, a, variant);
         else if (which == 1 && multi)
             k_update<T, D, true><<<wave_grid(c, G_UPDATE, k_update<T, D, true>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
         else if (which == 1)
@@ -1381,4 +1484,4 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms) {
     template pfe_status pfe::pcgk::body_T<T, D>(pfe_ctx *, cudaStream_t, pfe::PcgLaunch, int);     \
     template pfe_status pfe::pcgk::final_T<T, D>(pfe_ctx *, cudaStream_t, pfe::PcgLaunch);         \
     template pfe_status pfe::pcgk::apply_T<T, D>(pfe_ctx *, cudaStream_t, const void *, void *);     \
-    template pfe_status pfe::pcgk::time_T<T, D>(pfe_ctx *, cudaStream_t, int, int, float *);
+    template pfe_status pfe::pcgk::time_T<T, D>(pfe_ctx *, cudaStream_t, int, int, float *, int);

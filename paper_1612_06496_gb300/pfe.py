@@ -28,7 +28,9 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_get_array", "pfe_set_array", "pfe_get_edges", "pfe_apply_A", "pfe_solve_system",
            "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
            "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_get_segments",
-           "pfe_get_segment_stats", "pfe_laplacian_eigenmap", "pfe_objective"]
+           "pfe_get_segment_stats", "pfe_laplacian_eigenmap", "pfe_objective", "pfe_autotune",
+           "pfe_set_variant"]
+SPMM_NVARIANTS = 4  # PFE_SPMM_GENERAL, _ROW1, _ROW2, _ROW2_4
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3, "fsai_tr": 4, "fsai_z": 5}
 
 
@@ -105,6 +107,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_get_segment_stats.argtypes = [vp, vp, vp, vp]
     lib.pfe_laplacian_eigenmap.argtypes = [vp, i32, vp, i32, dbl, C.POINTER(i32), C.POINTER(dbl)]
     lib.pfe_objective.argtypes = [vp, i32, C.POINTER(dbl), C.POINTER(dbl)]
+    lib.pfe_autotune.argtypes = [vp, i32, vp, vp]
+    lib.pfe_set_variant.argtypes = [vp, i32, i32]
     for name in EXPORTS:
         if name not in ("pfe_default_params", "pfe_last_error", "pfe_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -265,6 +269,17 @@ class PFE:
         p, keep = _ptr(Y0)
         self._check(self.lib.pfe_init(self.ctx, d, p, d), "pfe_init")
         self.d = d
+
+    def autotune(self, reps: int = 20):
+        """Time the SpMM variants on this problem and keep the fastest:
+        (chosen variant, {variant: ms} of those that apply)."""
+        choice = np.zeros(1, dtype=np.int32)
+        ms = np.zeros(SPMM_NVARIANTS, dtype=np.float64)
+        self._check(self.lib.pfe_autotune(self.ctx, int(reps), choice.ctypes.data, ms.ctypes.data), "pfe_autotune")
+        return int(choice[0]), {v: float(t) for v, t in enumerate(ms) if t >= 0}
+
+    def set_variant(self, variant: int, kernel: int = 0):
+        self._check(self.lib.pfe_set_variant(self.ctx, int(kernel), int(variant)), "pfe_set_variant")
 
     def objective(self, which: str = "yhat"):
         """(|M Y|_1, |Y^T D Y - I|_F) of the iterate ("y") or the embedding ("yhat")."""
