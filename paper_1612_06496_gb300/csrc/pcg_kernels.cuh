@@ -1013,10 +1013,40 @@ __device__ __forceinline__ void gslot_range(const int *__restrict__ col, const T
     if (k0 < hi) gslot_chunk<T, D, V, 4, QS>(col, gs, base, k0, len, lo, hi, self, c0, src, qsrc, al, acc);
 }
 
+// acc += sum of g_k * v(j_k) over the slots k in [P0, P1) of a row with
+// compile-time positions (uniform-length rows; padding slots carry g = 0):
+// 16-byte loads of the slot groups covering the range, then the gathers.
+template <typename T, int D, int V, int P0, int P1, bool QS>
+__device__ __forceinline__ void gslot_fixed(const int *__restrict__ col, const T *__restrict__ gs, int64_t base,
+                                            int c0, const T *__restrict__ src, const T *__restrict__ qsrc,
+                                            const T (&al)[V], T (&acc)[V]) {
+    constexpr int A0 = P0 & ~3, A1 = (P1 + 3) & ~3, NG = A1 - A0, NS = P1 - P0;
+    int jj[NG];
+    T gv[NG];
+    load_slots<T, NG>(col, gs, base, A0, A1, 0, jj, gv);
+    T vj[NS][V];
+#pragma unroll
+    for (int u = 0; u < NS; ++u) ldv<T, V>(src + (int64_t)jj[P0 - A0 + u] * D + c0, vj[u]);
+    if constexpr (QS) {
+        T qj[NS][V];
+#pragma unroll
+        for (int u = 0; u < NS; ++u) ldv<T, V>(qsrc + (int64_t)jj[P0 - A0 + u] * D + c0, qj[u]);
+#pragma unroll
+        for (int u = 0; u < NS; ++u)
+#pragma unroll
+            for (int k = 0; k < V; ++k) vj[u][k] = fma(-al[k], qj[u][k], vj[u][k]);
+    }
+#pragma unroll
+    for (int u = 0; u < NS; ++u)
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] = fma(gv[P0 - A0 + u], vj[u][k], acc[k]);
+}
+
 // r' = r - alpha q and t = G r' in one pass: r' is recomputed at each
 // gathered lower neighbour from the old r and q (the same FMA its owner
 // uses), the owner writes its r' to the other buffer.
-template <typename T, int D>
+// LEN > 0: uniform rows of LEN slots, lower slots at positions [0, LEN/2).
+template <typename T, int D, int LEN>
 __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
@@ -1044,7 +1074,10 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr
         const T gd = a.gdiag[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = gd * ri[k];
-        gslot_range<T, D, V, true>(a.A.col, a.gslot, base, len, 0, a.kb[i], (int)i, c0, rold, a.q, al, acc);
+        if constexpr (LEN > 0)
+            gslot_fixed<T, D, V, 0, LEN / 2, true>(a.A.col, a.gslot, i * LEN, c0, rold, a.q, al, acc);
+        else
+            gslot_range<T, D, V, true>(a.A.col, a.gslot, base, len, 0, a.kb[i], (int)i, c0, rold, a.q, al, acc);
         stv<T, V>(a.t + i * D + c0, acc);
     }
 }
@@ -1052,7 +1085,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr
 // t = G r: t_i = G_ii r_i + sum over the lower slots (j < i) of G_ij r_j.
 // MODE 0: at the start of a solve (residual in r2[0]); MODE 1: only after a
 // residual refresh (residual in the new buffer).
-template <typename T, int D, int MODE>
+template <typename T, int D, int MODE, int LEN>
 __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
     if (MODE == 1 && !*(volatile int *)&a.ctl->refresh_now) return;
@@ -1069,7 +1102,11 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(
         const T gd = a.gdiag[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = gd * ri[k];
-        gslot_range<T, D, V, false>(a.A.col, a.gslot, base, len, 0, a.kb[i], (int)i, c0, rsrc, nullptr, nal, acc);
+        if constexpr (LEN > 0)
+            gslot_fixed<T, D, V, 0, LEN / 2, false>(a.A.col, a.gslot, i * LEN, c0, rsrc, nullptr, nal, acc);
+        else
+            gslot_range<T, D, V, false>(a.A.col, a.gslot, base, len, 0, a.kb[i], (int)i, c0, rsrc, nullptr, nal,
+                                        acc);
         stv<T, V>(a.t + i * D + c0, acc);
     }
 }
@@ -1077,7 +1114,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(
 // z = G^T t: z_i = G_ii t_i + sum over the upper slots (j > i) of G_ji t_j,
 // then the dots r.z, r.r; the last block ends the iteration (or the start of
 // the solve) and decides whether the next iteration refreshes r.
-template <typename T, int D>
+template <typename T, int D, int LEN>
 __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_z(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
     // the residual of this iteration: r2[0] at the start of a solve, else the
@@ -1103,7 +1140,11 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_z(
         const T gd = a.gdiag[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = gd * ti[k];
-        gslot_range<T, D, V, false>(a.A.col, a.gslot, base, len, a.kb[i], len, (int)i, c0, a.t, nullptr, nal, acc);
+        if constexpr (LEN > 0)
+            gslot_fixed<T, D, V, LEN / 2, LEN, false>(a.A.col, a.gslot, i * LEN, c0, a.t, nullptr, nal, acc);
+        else
+            gslot_range<T, D, V, false>(a.A.col, a.gslot, base, len, a.kb[i], len, (int)i, c0, a.t, nullptr, nal,
+                                        acc);
         stv<T, V>(a.z + i * D + c0, acc);
         ldv<T, V>(rcur + i * D + c0, ri);
 #pragma unroll
@@ -1275,6 +1316,31 @@ void body_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int iters) {
     }
 }
 
+// The FSAI kernels with the compile-time row length of the layout (FP32 grid
+// graphs of radius 2 or 3; else the general kernels).
+// which: 0 = k_fsai_tr, 1 = k_fsai_t (start of a solve), 2 = k_fsai_t (after a refresh), 3 = k_fsai_z
+template <typename T, int D, int LEN>
+void fsai_kernels_len(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int which) {
+    if (which == 0)
+        k_fsai_tr<T, D, LEN><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D, LEN>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+    else if (which == 1)
+        k_fsai_t<T, D, 0, LEN><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D, 0, LEN>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+    else if (which == 2)
+        k_fsai_t<T, D, 1, LEN><<<wave_grid(c, G_FSAI_T1, k_fsai_t<T, D, 1, LEN>, rows_need<T, D>(c)), kBlock, 0, s>>>(
+            a);
+    else
+        k_fsai_z<T, D, LEN><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D, LEN>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+}
+template <typename T, int D>
+void launch_fsai(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int which) {
+    if (c->g.row_len == 12)
+        fsai_kernels_len<T, D, 12>(c, s, a, which);
+    else if (c->g.row_len == 28)
+        fsai_kernels_len<T, D, 28>(c, s, a, which);
+    else
+        fsai_kernels_len<T, D, 0>(c, s, a, which);
+}
+
 template <typename T, int D>
 pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
     PcgArgs<T> a = pcg_args<T>(c, L);
@@ -1284,8 +1350,8 @@ pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
         if (use_fsai<T>(c)) {
             k_pcg_init<T, D, 1, false><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1, false>, rows_need<T, D>(c)), kBlock,
                                          0, s>>>(a);
-            k_fsai_t<T, D, 0><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D, 0>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-            k_fsai_z<T, D><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            launch_fsai<T, D>(c, s, a, 1);
+            launch_fsai<T, D>(c, s, a, 3);
             PFE_CUDA_TRY(c, cudaGetLastError());
             return PFE_OK;
         }
@@ -1308,12 +1374,12 @@ pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
                                                       flat_mult<T, D>()),
                                             kBlock, 0, s>>>(a);
                 launch_spmm<T, D, false>(c, s, a);
-                k_fsai_tr<T, D><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+                launch_fsai<T, D>(c, s, a, 0);
                 k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c)), kBlock, 0,
                                         s>>>(a, 0);
                 k_refresh_f<T, D><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-                k_fsai_t<T, D, 1><<<wave_grid(c, G_FSAI_T1, k_fsai_t<T, D, 1>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-                k_fsai_z<T, D><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+                launch_fsai<T, D>(c, s, a, 2);
+                launch_fsai<T, D>(c, s, a, 3);
             }
             PFE_CUDA_TRY(c, cudaGetLastError());
             return PFE_OK;
@@ -1452,10 +1518,7 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
                                                   flat_mult<T, D>()),
                                         kBlock, 0, s>>>(a);
         else if constexpr (std::is_same_v<T, float>) {
-            if (which == 3)
-                k_fsai_tr<T, D><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-            else
-                k_fsai_z<T, D><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+            launch_fsai<T, D>(c, s, a, which == 3 ? 0 : 3);
         }
     };
     launch();  // warm-up
