@@ -278,6 +278,18 @@ PFE_API pfe_status pfe_pstep(pfe_ctx *c);
 PFE_API pfe_status pfe_solve(pfe_ctx *c, int32_t n_outer, int32_t n_inner, double *Y_out,
                      double *Yhat_out, pfe_solve_stats *st);
 
+/*
+ * pfe_solve_two_stage -- the two-stage schedule of Sec. IV: Stage I is
+ * pfe_solve(n_outer, n_inner) (SOC iterations with P-steps); Stage II relaxes
+ * the orthogonality constraint -- P and B keep their Stage I values and only
+ * penalise it through the r-term -- and runs n_stage2 further split-Bregman
+ * iterations (one more call of Alg. 2: b = d = 0 at its start).  The paper's
+ * counts: at most 10 x 5 in Stage I, 100 in Stage II.  Y_out receives Stage
+ * II's Y, Yhat_out D^{-1/2} P of Stage I; statistics and status as pfe_solve.
+ */
+PFE_API pfe_status pfe_solve_two_stage(pfe_ctx *c, int32_t n_outer, int32_t n_inner, int32_t n_stage2,
+                                       double *Y_out, double *Yhat_out, pfe_solve_stats *st);
+
 /* Frees every library allocation of the context (NULL is allowed). */
 PFE_API pfe_status pfe_destroy(pfe_ctx *c);
 

@@ -402,6 +402,22 @@ def soc_pfe(g: Graph, Y0: np.ndarray, n_outer: int, n_inner: int, solver: str = 
     return st
 
 
+def two_stage(g: Graph, Y0: np.ndarray, n_outer: int, n_inner: int, n_stage2: int, solver: str = "direct",
+              tol: float = 1e-8, max_iter: int = 5000, refresh: int = 50) -> State:
+    """Sec. IV two-stage schedule.  Stage I: Alg. 1 (n_outer SOC iterations
+    of n_inner split-Bregman iterations each).  Stage II: the orthogonality
+    constraint is relaxed -- P and B keep their Stage I values, so it is only
+    penalised by the r-term -- and one more call of Alg. 2 (b = d = 0 at its
+    start) runs n_stage2 split-Bregman iterations.  ``state.Y`` is Stage
+    II's Y; P, B (and ``embedding``) are Stage I's."""
+    st = soc_pfe(g, Y0, n_outer, n_inner, solver, tol, max_iter, refresh)
+    solve = DirectSolver(g.A) if solver == "direct" else PCGSolver(g.A, tol, max_iter, refresh)
+    reset_inner(st)
+    for _ in range(n_stage2):
+        split_bregman_step(g, st, solve)
+    return st
+
+
 def embedding(g: Graph, st: State) -> np.ndarray:
     """Yhat = D^{-1/2} P, the D-orthonormal embedding."""
     return st.P / np.sqrt(g.dvec)[:, None]

@@ -668,16 +668,24 @@ pfe_status pfe_pstep(pfe_ctx *c) {
     return pstep_enqueue(c);
 }
 
-pfe_status pfe_solve(pfe_ctx *c, int32_t n_outer, int32_t n_inner, double *Y_out, double *Yhat_out,
-                     pfe_solve_stats *st) {
-    if (!c) return PFE_EINVAL;
+// Stage I (n_outer SOC iterations of n_inner split-Bregman iterations), then
+// Stage II (n_stage2 split-Bregman iterations with P and B held).
+static pfe_status solve_stages(pfe_ctx *c, int32_t n_outer, int32_t n_inner, int32_t n_stage2, double *Y_out,
+                               double *Yhat_out, pfe_solve_stats *st) {
     if (!c->inited) return fail(c, PFE_ESTATE, "pfe_solve before pfe_init");
-    if (n_outer < 0 || n_inner < 0) return fail(c, PFE_EINVAL, "negative iteration count");
+    if (n_outer < 0 || n_inner < 0 || n_stage2 < 0) return fail(c, PFE_EINVAL, "negative iteration count");
     PFE_TRY(clear_stats(c));
     for (int k = 0; k < n_outer; ++k) {
         for (int l = 0; l < n_inner; ++l) PFE_TRY(inner_step_enqueue(c));
         PFE_TRY(pstep_enqueue(c));
     }
+    // Stage II is one more call of Alg. 2: b starts at zero (a P-step with
+    // reset_inner_each_outer already cleared it)
+    if (n_stage2 > 0 && n_outer == 0 && c->prm.reset_inner_each_outer) {
+        const size_t bytes = (size_t)c->g.fslots * c->d * elem_size(c);
+        PFE_CUDA_TRY(c, cudaMemsetAsync(c->wk.Bs[c->bs_cur], 0, bytes, c->stream));
+    }
+    for (int l = 0; l < n_stage2; ++l) PFE_TRY(inner_step_enqueue(c));
     const size_t bytes = sizeof(double) * (size_t)c->n * c->d;
     if (Y_out) {
         PFE_TRY(launch_from_work(c, c->stream, c->wk.Y, c->wk.Ylo, c->wk.stage, c->n));
@@ -701,10 +709,22 @@ pfe_status pfe_solve(pfe_ctx *c, int32_t n_outer, int32_t n_inner, double *Y_out
         st->n_unconverged = c->h_ctl->n_unconv;
         st->relres_max = c->h_ctl->max_relres;
         // PCG launches + one edge pass per inner step + Gram and apply per outer step
-        st->kernel_launches = c->h_ctl->launches + (int64_t)n_outer * n_inner + 2LL * n_outer;
+        st->kernel_launches = c->h_ctl->launches + (int64_t)n_outer * n_inner + n_stage2 + 2LL * n_outer;
     }
     PFE_TRY(check_pstep(c));
     return pcg_status(c);
+}
+
+pfe_status pfe_solve(pfe_ctx *c, int32_t n_outer, int32_t n_inner, double *Y_out, double *Yhat_out,
+                     pfe_solve_stats *st) {
+    if (!c) return PFE_EINVAL;
+    return solve_stages(c, n_outer, n_inner, 0, Y_out, Yhat_out, st);
+}
+
+pfe_status pfe_solve_two_stage(pfe_ctx *c, int32_t n_outer, int32_t n_inner, int32_t n_stage2, double *Y_out,
+                               double *Yhat_out, pfe_solve_stats *st) {
+    if (!c) return PFE_EINVAL;
+    return solve_stages(c, n_outer, n_inner, n_stage2, Y_out, Yhat_out, st);
 }
 
 pfe_status pfe_get_array(pfe_ctx *c, int32_t which, double *dst) {

@@ -29,7 +29,7 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
            "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_get_segments",
            "pfe_get_segment_stats", "pfe_laplacian_eigenmap", "pfe_objective", "pfe_autotune",
-           "pfe_set_variant"]
+           "pfe_set_variant", "pfe_solve_two_stage"]
 SPMM_NVARIANTS = 4  # PFE_SPMM_GENERAL, _ROW1, _ROW2, _ROW2_4
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3, "fsai_tr": 4, "fsai_z": 5}
 
@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_objective.argtypes = [vp, i32, C.POINTER(dbl), C.POINTER(dbl)]
     lib.pfe_autotune.argtypes = [vp, i32, vp, vp]
     lib.pfe_set_variant.argtypes = [vp, i32, i32]
+    lib.pfe_solve_two_stage.argtypes = [vp, i32, i32, i32, vp, vp, C.POINTER(SolveStats)]
     for name in EXPORTS:
         if name not in ("pfe_default_params", "pfe_last_error", "pfe_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -317,6 +318,20 @@ class PFE:
         s = SolveStats()
         ok = (PFE_OK, PFE_ENOTCONV) if allow_notconv else (PFE_OK,)
         st = self._check(self.lib.pfe_solve(self.ctx, n_outer, n_inner, py, ph, C.byref(s)), "pfe_solve", ok)
+        return {"pcg_iters_total": s.pcg_iters_total, "pcg_iters_max": s.pcg_iters_max, "n_solves": s.n_solves,
+                "n_unconverged": s.n_unconverged, "relres_max": s.relres_max,
+                "kernel_launches": s.kernel_launches, "pcg_rounds": s.pcg_rounds, "status": st}
+
+    def solve_two_stage(self, n_outer: int, n_inner: int, n_stage2: int, Y_out=None, Yhat_out=None,
+                        allow_notconv: bool = False):
+        """Stage I (n_outer x n_inner with P-steps), then n_stage2 split-Bregman
+        iterations with P, B held (Sec. IV)."""
+        py, ky = _ptr(Y_out)
+        ph, kh = _ptr(Yhat_out)
+        s = SolveStats()
+        ok = (PFE_OK, PFE_ENOTCONV) if allow_notconv else (PFE_OK,)
+        st = self._check(self.lib.pfe_solve_two_stage(self.ctx, n_outer, n_inner, n_stage2, py, ph, C.byref(s)),
+                         "pfe_solve_two_stage", ok)
         return {"pcg_iters_total": s.pcg_iters_total, "pcg_iters_max": s.pcg_iters_max, "n_solves": s.n_solves,
                 "n_unconverged": s.n_unconverged, "relres_max": s.relres_max,
                 "kernel_launches": s.kernel_launches, "pcg_rounds": s.pcg_rounds, "status": st}

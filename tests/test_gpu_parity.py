@@ -263,3 +263,20 @@ def test_device_pointers_and_torch_stream():
     ost = O.soc_pfe(g, Y0, 2, 3, solver="direct")
     assert relerr(Yd.cpu().numpy(), ost.Y) <= FP64_TOL
     p.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 2e-4)])
+def test_two_stage_schedule(precision, tol):
+    """Sec. IV: Stage I (SOC) then Stage II (split Bregman with P, B held)."""
+    spec = CONFIGS["C1"]
+    p, X, Y0 = gpu_problem(spec, precision, tol=1e-12 if precision == "fp64" else 1e-6)
+    g = oracle_graph(spec, X)
+    p.init(Y0)
+    Y = np.empty_like(Y0)
+    Yh = np.empty_like(Y0)
+    st = p.solve_two_stage(3, 5, 12, Y, Yh)
+    assert st["n_solves"] == 3 * 5 + 12
+    ost = O.two_stage(g, Y0, 3, 5, 12)
+    assert relerr(Y, ost.Y) <= tol
+    assert relerr(Yh, O.embedding(g, ost)) <= tol
+    p.close()

@@ -344,3 +344,28 @@ def test_zero_degree_vertex_rejected():
     X = np.zeros((4, 2))
     with pytest.raises(ValueError):
         O.build_graph(X, np.array([0, 1]), np.array([1, 2]), 1.0)
+
+
+def test_two_stage_stage2_minimises_the_relaxed_y_problem():
+    """Stage II (Sec. IV) runs Alg. 2 with P, B held: its iterates approach
+    the minimiser of |MY|_1 + (r/2 lam) ... the Y-step objective of Alg. 2
+    step 5 with P, B fixed.  Split Bregman for that convex problem converges,
+    so after many iterations the objective is below its value at Stage I's Y
+    and at random perturbations of the result."""
+    X, a, b, sigma = _random_graph(40, 0.15, 21)
+    g = O.build_graph(X, a, b, sigma)
+    rng = np.random.default_rng(2)
+    Y0 = rng.standard_normal((g.n, 3))
+    st1 = O.soc_pfe(g, Y0, 3, 4)
+    st2 = O.two_stage(g, Y0, 3, 4, 400)
+    np.testing.assert_allclose(st2.P, st1.P)          # P, B held in Stage II
+    np.testing.assert_allclose(st2.B, st1.B)
+    sq = np.sqrt(g.dvec)[:, None]
+
+    def f(Y):  # the Y-step objective (Alg. 2 step 5; Eq. 5 in compact form)
+        return np.abs(g.M @ Y).sum() + 0.5 * g.r * np.sum((sq * Y - st1.P + st1.B) ** 2)
+
+    f2 = f(st2.Y)
+    assert f2 <= f(st1.Y) + 1e-12
+    for _ in range(20):
+        assert f2 <= f(st2.Y + 1e-3 * rng.standard_normal(st2.Y.shape)) + 1e-12
