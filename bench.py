@@ -86,12 +86,12 @@ def cpu_sample_worker(arg: str):
         g = O.build_grid_graph(X, spec.H, spec.W, spec.radius, spec.sigma)
     else:
         spec = CONFIGS[cfg["workload"]]
-        win = cfg["window"]
-        x0 = (spec.W - win) // 2
-        y0 = (spec.H - win) // 2
-        wspec = replace(spec, crop=(x0, y0, win, win))
+        win_w, win_h = min(cfg["window"], spec.W), min(cfg["window"], spec.H)  # the whole image when smaller
+        x0 = (spec.W - win_w) // 2
+        y0 = (spec.H - win_h) // 2
+        wspec = replace(spec, crop=(x0, y0, win_w, win_h))
         X, Y0 = make_problem(wspec)
-        g = O.build_grid_graph(X, win, win, spec.radius, spec.sigma, lam=cfg["lambda"])
+        g = O.build_grid_graph(X, win_h, win_w, spec.radius, spec.sigma, lam=cfg["lambda"])
     st = O.init_state(g, Y0)
     solve = O.PCGSolver(g.A, spec.tol, 5000, 50)
     times, iters = [], []
@@ -257,8 +257,11 @@ def cpu_sample_text(spec, window: int, out: dict) -> str:
         return (f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration per step on the smallest image "
                 f"of the batch ({out['n']} pixels, its own lambda, {out['iters'][0]:.0f} PCG iterations per solve), "
                 f"scaled to the whole batch by the nnz_A ratio {out['scale']:.1f}")
+    if window >= spec.W and window >= spec.H:
+        return (f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration per step on the whole image "
+                f"({out['iters'][0]:.0f} PCG iterations per solve)")
     return (f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration per step on the central "
-            f"{window}x{window} window of the same image with the full image's lambda "
+            f"{min(window, spec.W)}x{min(window, spec.H)} window of the same image with the full image's lambda "
             f"({out['iters'][0]:.0f} PCG iterations per solve), scaled by nnz_A ratio {out['scale']:.1f}")
 
 
