@@ -457,7 +457,7 @@ def main():
     upd_ms = p.time_kernel("update", 20)
     pup_ms = p.time_kernel("pupdate", 20)
     edge_ms = p.time_kernel("edge", 10)
-    n, d, nnz = info["n"], info["d"], info["nnz_A"]
+    n, d, nnz, ne = info["n"], info["d"], info["nnz_A"], info["n_edges"]
     fsai_k = {}
     if args.precond == "learned":
         # lower (upper) slots: FP32 G value + int32 column each, kb and G_ii per row;
@@ -482,7 +482,10 @@ def main():
                                   "k_update_GBps": round((3 * 4 * n * d + 4 * n) / (upd_ms * 1e-3) / 1e9, 1),
                                   "k_pupdate_ms": round(pup_ms, 5),
                                   "k_pupdate_GBps": round((7 * 4 * n * d + 4 * n) / (pup_ms * 1e-3) / 1e9, 1),
-                                  "k_edge_ms": round(edge_ms, 5), **fsai_k}}
+                                  "k_edge_ms": round(edge_ms, 5),
+                                  # b read + written (FP32), w, column + edge id per directed slot, Y, C in, RHS out
+                                  "k_edge_GBps": round((8 * d * ne + 4 * ne + 8 * 2 * ne + 12 * n * d)
+                                                       / (edge_ms * 1e-3) / 1e9, 1), **fsai_k}}
     p.close()
 
     # --- the FP32 path with the other preconditioner

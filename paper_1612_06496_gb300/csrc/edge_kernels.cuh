@@ -157,6 +157,92 @@ __global__ void __launch_bounds__(kBlock) k_edge(EdgeArgs<T> a) {
     }
 }
 
+// Slots [P0, P1) of a fixed-position row (compile-time range): on a grid the
+// lower half [0, K/2) holds the neighbours before i (i is the second endpoint
+// of those edges) and the upper half [K/2, K) those after i (i owns the edge
+// and writes its b').  Padding slots carry edge id -1.
+template <typename T, int D, int V, int P0, int P1, bool FIRST>
+__device__ __forceinline__ void edge_half(const EdgeArgs<T> &a, int64_t base, int c0, const T (&yi)[V], T gam,
+                                          T (&acc)[V]) {
+    constexpr int A0 = P0 & ~3, A1 = (P1 + 3) & ~3, NG = A1 - A0, NS = P1 - P0;
+    int ee[NG], jj[NG];
+    T ww[NG];
+#pragma unroll
+    for (int g4 = 0; g4 < NG / 4; ++g4) {
+        const int k = A0 + 4 * g4;
+        const int4 e4 = __ldg(reinterpret_cast<const int4 *>(a.eid + base + k));
+        const int4 c4 = __ldg(reinterpret_cast<const int4 *>(a.col + base + k));
+        ee[4 * g4] = e4.x; ee[4 * g4 + 1] = e4.y; ee[4 * g4 + 2] = e4.z; ee[4 * g4 + 3] = e4.w;
+        jj[4 * g4] = c4.x; jj[4 * g4 + 1] = c4.y; jj[4 * g4 + 2] = c4.z; jj[4 * g4 + 3] = c4.w;
+        if constexpr (sizeof(T) == 4) {
+            const float4 w4 = __ldg(reinterpret_cast<const float4 *>(a.w + base + k));
+            ww[4 * g4] = w4.x; ww[4 * g4 + 1] = w4.y; ww[4 * g4 + 2] = w4.z; ww[4 * g4 + 3] = w4.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ww[4 * g4 + u] = __ldg(a.w + base + k + u);
+        }
+    }
+    T yj[NS][V], bo[NS][V];
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+        const int q = P0 - A0 + u;
+        const int e = ee[q] < 0 ? 0 : ee[q];  // padding slots read a valid dummy
+        eldv<T, V>(a.y + (int64_t)jj[q] * D + c0, yj[u]);
+        eldv<T, V>(a.bs_old + (int64_t)e * D + c0, bo[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+        const int q = P0 - A0 + u;
+        if (ee[q] < 0) continue;  // padding slot
+        T bn[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const T diff = FIRST ? (yi[k] - yj[u][k]) : (yj[u][k] - yi[k]);  // y_a - y_b
+            const T t = ww[q] * diff + bo[u][k];                              // (M Y + b)_e
+            const T z = shrink<T>(t, gam);                                    // d_e
+            bn[k] = t - z;                                                    // b'_e
+            const T v = ww[q] * (z - bn[k]);
+            acc[k] = FIRST ? acc[k] + v : acc[k] - v;
+        }
+        if (FIRST) estv<T, V>(a.bs_new + (int64_t)ee[q] * D + c0, bn);
+    }
+}
+
+// The edge pass on fixed-position rows of LEN slots (grid graphs): the same
+// arithmetic as k_edge, each half of a row as straight-line code.
+template <typename T, int D, bool MS, int LEN>
+__global__ void __launch_bounds__(kBlock, 4) k_edge_fixed(EdgeArgs<T> a) {
+    constexpr int V = (sizeof(T) == 4 && D % 4 == 0) ? 4 : (D % 2 == 0 ? 2 : 1);
+    constexpr int L = D / V, RPW = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int rw = lane / L, cg = lane - rw * L, c0 = cg * V;
+    const bool active = lane < RPW * L;
+    const int64_t warp_g = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int64_t warps_total = (int64_t)gridDim.x * kWarps;
+    for (int64_t g = warp_g; g * RPW < a.n; g += warps_total) {
+        const int64_t i = g * RPW + rw;
+        if (!active || i >= a.n) continue;
+        const int64_t base = i * LEN;
+        T lam = a.lambda, gam = a.gamma;
+        if constexpr (MS) {  // batch: lambda of the row's segment
+            const double ls = a.seg_lam[__ldg(a.sg.rseg + i)];
+            lam = (T)ls;
+            gam = (T)(1.0 / ls);
+        }
+        T yi[V], acc[V];
+        eldv<T, V>(a.y + i * D + c0, yi);
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] = T(0);
+        edge_half<T, D, V, 0, LEN / 2, false>(a, base, c0, yi, gam, acc);
+        edge_half<T, D, V, LEN / 2, LEN, true>(a, base, c0, yi, gam, acc);
+        T ci[V];
+        eldv<T, V>(a.cw + i * D + c0, ci);
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] = lam * acc[k] + ci[k];
+        estv<T, V>(a.rhs + i * D + c0, acc);
+    }
+}
+
 template <typename T, int D>
 pfe_status edge_T(pfe_ctx *c, cudaStream_t s) {
     EdgeArgs<T> a;
@@ -182,10 +268,21 @@ pfe_status edge_T(pfe_ctx *c, cudaStream_t s) {
     constexpr int V = (sizeof(T) == 4 && D % 4 == 0) ? 4 : (D % 2 == 0 ? 2 : 1);
     constexpr int RPW = 32 / (D / V);
     const int64_t need = ((c->g.n + RPW - 1) / RPW + kWarps - 1) / kWarps;
-    if (c->nseg > 1)
-        k_edge<T, D, true><<<wave_grid(c, G_EDGE, k_edge<T, D, true>, need), kBlock, 0, s>>>(a);
-    else
-        k_edge<T, D, false><<<wave_grid(c, G_EDGE, k_edge<T, D, false>, need), kBlock, 0, s>>>(a);
+    // fixed-position rows of 12 slots (FP32 radius-2 grids); radius 3 keeps the
+    // general kernel (28 slots in straight-line code need 126 registers)
+    const int rl = std::is_same_v<T, float> ? c->g.row_len : 0;
+    if (c->nseg > 1) {
+        if (rl == 12)
+            k_edge_fixed<T, D, true, 12><<<wave_grid(c, G_EDGE, k_edge_fixed<T, D, true, 12>, need), kBlock, 0, s>>>(a);
+        else
+            k_edge<T, D, true><<<wave_grid(c, G_EDGE, k_edge<T, D, true>, need), kBlock, 0, s>>>(a);
+    } else {
+        if (rl == 12)
+            k_edge_fixed<T, D, false, 12><<<wave_grid(c, G_EDGE, k_edge_fixed<T, D, false, 12>, need), kBlock, 0,
+                                            s>>>(a);
+        else
+            k_edge<T, D, false><<<wave_grid(c, G_EDGE, k_edge<T, D, false>, need), kBlock, 0, s>>>(a);
+    }
     PFE_CUDA_TRY(c, cudaGetLastError());
     c->bs_cur = 1 - c->bs_cur;
     return PFE_OK;
