@@ -220,6 +220,24 @@ PFE_API pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, doubl
 PFE_API pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant);
 
 /*
+ * pfe_kmeans -- the segmentation stage of Sec. IV: k-means clustering of the
+ * rows of X (n x d row-major FP64, host or device; NULL = the context's
+ * embedding D^{-1/2} P, d = its dimension), in FP64.  Start: C0 (k x d, host
+ * or device) or, when NULL, the maximin rule: centroid 0 = row 0, then
+ * repeatedly the row farthest from its nearest chosen centroid (ties to the
+ * smallest row).  Lloyd rounds: every row to its nearest centroid (ties to
+ * the smallest cluster), every centroid to the mean of its rows (an empty
+ * cluster keeps its centroid), until no label changes or max_iter rounds.
+ * Outputs (any may be NULL; host or device): labels[n] (int32), centroids
+ * (k x d), *inertia = sum of squared distances to the assigned centroids,
+ * *rounds.  Squared distances sum the squared column differences in column
+ * order (separately rounded), so results are reproducible.  1 <= d <= 32,
+ * 1 <= k <= 64; not for a batch.  Synchronises.
+ */
+PFE_API pfe_status pfe_kmeans(pfe_ctx *c, const double *X, int32_t d, int32_t k, const double *C0, int32_t max_iter,
+                              int32_t *labels, double *centroids, double *inertia, int32_t *rounds);
+
+/*
  * pfe_objective -- diagnostics of the current embedding (FP64 reductions in a
  * fixed order): *l1 = |M Y|_1 = sum over undirected edges a < b of
  * w_ab |y_a - y_b|_1 (Eq. 1 sums every ordered pair, i.e. twice this), and

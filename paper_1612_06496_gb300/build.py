@@ -22,7 +22,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpfe.so")
 
-SOURCES = ["api.cu", "graph.cu", "pcg.cu", "edge.cu", "pstep.cu", "convert.cu", "fsai.cu", "noalloc.cu", "le.cu", "diag.cu"]
+SOURCES = ["api.cu", "graph.cu", "pcg.cu", "edge.cu", "pstep.cu", "convert.cu", "fsai.cu", "noalloc.cu", "le.cu", "diag.cu", "kmeans.cu"]
 # Template instantiations (precision x groups of d), one generated
 # translation unit each, so that nvcc runs them in parallel.  The d values
 # must match PFE_DISPATCH_D in csrc/dispatch.cuh.

@@ -483,6 +483,36 @@ pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant) {
     return PFE_OK;
 }
 
+pfe_status pfe_kmeans(pfe_ctx *c, const double *X, int32_t d, int32_t k, const double *C0, int32_t max_iter,
+                      int32_t *labels, double *centroids, double *inertia, int32_t *rounds) {
+    if (!c || d < 1 || d > 32 || k < 1 || k > 64 || k > c->n || max_iter < 1) return PFE_EINVAL;
+    if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "k-means of a batch: cluster each problem separately");
+    PFE_TRY(sync(c));
+    const double *dX = X;
+    double *tmp = nullptr;
+    if (!X) {
+        if (!c->inited) return fail(c, PFE_ESTATE, "pfe_kmeans of the embedding before pfe_init");
+        if (d != c->d) return fail(c, PFE_EINVAL, "d differs from the embedding dimension");
+        PFE_TRY(launch_yhat(c, c->stream, c->wk.stage));
+        dX = c->wk.stage;
+    } else if (!is_device_ptr(X)) {
+        const size_t bytes = sizeof(double) * (size_t)c->n * d;
+        if (cudaMalloc((void **)&tmp, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PFE_ENOMEM, "pfe_kmeans: device allocation failed");
+        }
+        cudaError_t e = cudaMemcpyAsync(tmp, X, bytes, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return fail(c, PFE_ECUDA, cudaGetErrorString(e));
+        }
+        dX = tmp;
+    }
+    const pfe_status st = kmeans_run(c, dX, d, k, C0, max_iter, labels, centroids, inertia, rounds);
+    if (tmp) cudaFree(tmp);
+    return st;
+}
+
 pfe_status pfe_objective(pfe_ctx *c, int32_t which, double *l1, double *ortho_err) {
     if (!c || (which != PFE_OBJ_Y && which != PFE_OBJ_YHAT)) return PFE_EINVAL;
     if (!c->inited) return fail(c, PFE_ESTATE, "pfe_objective before pfe_init");

@@ -163,6 +163,9 @@ namespace pfe {
 pfe_status build_grid_graph(pfe_ctx *c, const double *dfeat);
 pfe_status build_edge_graph(pfe_ctx *c, const double *dfeat, const int32_t *dei, const int32_t *dej);
 pfe_status setup_segments(pfe_ctx *c);
+// --- kmeans.cu: k-means segmentation of an n x d FP64 device matrix
+pfe_status kmeans_run(pfe_ctx *c, const double *X, int d, int k, const double *C0, int max_iter, int *labels,
+                      double *centroids, double *inertia, int *rounds);
 // --- diag.cu: |M Y|_1 and |Y^T D Y - I|_F (which: 0 = Y, 1 = Yhat)
 pfe_status diag_objective(pfe_ctx *c, int which, double *l1, double *ortho);
 // --- le.cu: Laplacian-eigenmap start (n x d FP64, row-major, device)

@@ -29,7 +29,7 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
            "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_get_segments",
            "pfe_get_segment_stats", "pfe_laplacian_eigenmap", "pfe_objective", "pfe_autotune",
-           "pfe_set_variant", "pfe_solve_two_stage"]
+           "pfe_set_variant", "pfe_solve_two_stage", "pfe_kmeans"]
 SPMM_NVARIANTS = 4  # PFE_SPMM_GENERAL, _ROW1, _ROW2, _ROW2_4
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3, "fsai_tr": 4, "fsai_z": 5}
 
@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_autotune.argtypes = [vp, i32, vp, vp]
     lib.pfe_set_variant.argtypes = [vp, i32, i32]
     lib.pfe_solve_two_stage.argtypes = [vp, i32, i32, i32, vp, vp, C.POINTER(SolveStats)]
+    lib.pfe_kmeans.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp, C.POINTER(dbl), C.POINTER(i32)]
     for name in EXPORTS:
         if name not in ("pfe_default_params", "pfe_last_error", "pfe_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -281,6 +282,19 @@ class PFE:
 
     def set_variant(self, variant: int, kernel: int = 0):
         self._check(self.lib.pfe_set_variant(self.ctx, int(kernel), int(variant)), "pfe_set_variant")
+
+    def kmeans(self, k: int, X=None, C0=None, max_iter: int = 100):
+        """k-means segmentation of X (n x d) or of the embedding: (labels,
+        centroids, inertia, rounds)."""
+        d = self.d if X is None else X.shape[1]
+        px, kx = _ptr(X) if X is not None else (None, None)
+        pc, kc = _ptr(C0) if C0 is not None else (None, None)
+        labels = np.empty(self.n, dtype=np.int32)
+        cent = np.empty((k, d))
+        inertia, rounds = C.c_double(), C.c_int32()
+        self._check(self.lib.pfe_kmeans(self.ctx, px, int(d), int(k), pc, int(max_iter), labels.ctypes.data,
+                                        cent.ctypes.data, C.byref(inertia), C.byref(rounds)), "pfe_kmeans")
+        return labels, cent, inertia.value, rounds.value
 
     def objective(self, which: str = "yhat"):
         """(|M Y|_1, |Y^T D Y - I|_F) of the iterate ("y") or the embedding ("yhat")."""
