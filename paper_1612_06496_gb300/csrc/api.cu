@@ -485,13 +485,15 @@ pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant) {
 
 pfe_status pfe_kmeans(pfe_ctx *c, const double *X, int32_t d, int32_t k, const double *C0, int32_t max_iter,
                       int32_t *labels, double *centroids, double *inertia, int32_t *rounds) {
-    if (!c || d < 1 || d > 32 || k < 1 || k > 64 || k > c->n || max_iter < 1) return PFE_EINVAL;
+    if (!c) return PFE_EINVAL;
+    if (!X && !c->inited) return fail(c, PFE_ESTATE, "pfe_kmeans of the embedding before pfe_init");
+    if (d < 1 || d > 32 || k < 1 || k > 64 || k > c->n || max_iter < 1)
+        return fail(c, PFE_EINVAL, "pfe_kmeans: needs 1 <= d <= 32, 1 <= k <= min(64, n), max_iter >= 1");
     if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "k-means of a batch: cluster each problem separately");
     PFE_TRY(sync(c));
     const double *dX = X;
     double *tmp = nullptr;
     if (!X) {
-        if (!c->inited) return fail(c, PFE_ESTATE, "pfe_kmeans of the embedding before pfe_init");
         if (d != c->d) return fail(c, PFE_EINVAL, "d differs from the embedding dimension");
         PFE_TRY(launch_yhat(c, c->stream, c->wk.stage));
         dX = c->wk.stage;

@@ -286,7 +286,7 @@ class PFE:
     def kmeans(self, k: int, X=None, C0=None, max_iter: int = 100):
         """k-means segmentation of X (n x d) or of the embedding: (labels,
         centroids, inertia, rounds)."""
-        d = self.d if X is None else X.shape[1]
+        d = (self.d or 1) if X is None else X.shape[1]  # before pfe_init the library reports PFE_ESTATE
         px, kx = _ptr(X) if X is not None else (None, None)
         pc, kc = _ptr(C0) if C0 is not None else (None, None)
         labels = np.empty(self.n, dtype=np.int32)
