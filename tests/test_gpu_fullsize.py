@@ -1,0 +1,76 @@
+"""The 2048x2048 benchmark image at full size, in the benchmark's launch
+configuration (FP32 path, CUDA-graph loop, tuned kernels): outputs the oracle
+can compute one by one (sampled edge weights, degrees, the edge count and
+lambda) and properties that hold at any size (the constraint after every
+P-step, PCG convergence, the Bregman update on sampled edges)."""
+import numpy as np
+import pytest
+
+from oracle import pfe_oracle as O
+from synth import CONFIGS, make_problem
+from tests.gpu_common import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c5():
+    ensure_built()
+    from paper_1612_06496_gb300 import PFE
+    spec = CONFIGS["C5"]
+    X, Y0 = make_problem(spec)
+    p = PFE(X, sigma=spec.sigma, H=spec.H, W=spec.W, radius=spec.radius, precision="mixed", tol=spec.tol)
+    yield spec, X, Y0, p
+    p.close()
+
+
+def test_graph_at_full_size(c5):
+    spec, X, Y0, p = c5
+    a, b = O.grid_edges(spec.H, spec.W, spec.radius)
+    info = p.info()
+    assert info["n_edges"] == a.shape[0] and info["n"] == spec.n
+    w_all = O.heat_kernel_weights(X, a, b, spec.sigma)
+    lam = np.sqrt(2.0 * np.sum(w_all))
+    assert abs(info["lambda_"] - lam) <= 1e-12 * lam
+    ga, gb, gw = p.edges()
+    rng = np.random.default_rng(0)
+    k = rng.choice(ga.shape[0], 4000, replace=False)
+    # each sampled edge's weight from the features, one by one
+    w_ref = np.exp(-np.sum((X[ga[k]] - X[gb[k]]) ** 2, axis=1) / (2 * spec.sigma ** 2))
+    np.testing.assert_allclose(gw[k], w_ref, rtol=2e-13)
+    # degrees of sampled pixels: their stencil neighbours' weights
+    deg = p.get("DEG")
+    offs = O.grid_offsets(spec.radius)
+    for i in rng.choice(spec.n, 200, replace=False):
+        y, x = divmod(int(i), spec.W)
+        s = 0.0
+        for dx, dy in offs:
+            if 0 <= x + dx < spec.W and 0 <= y + dy < spec.H:
+                j = (y + dy) * spec.W + x + dx
+                s += np.exp(-np.sum((X[i] - X[j]) ** 2) / (2 * spec.sigma ** 2))
+        assert abs(deg[i] - s) <= 1e-12 * s
+
+
+def test_iteration_properties_at_full_size(c5):
+    spec, X, Y0, p = c5
+    p.init(Y0)
+    p.autotune(5)
+    _, ortho0 = p.objective("yhat")
+    assert ortho0 <= 1e-9
+    st = p.inner_step(stats=True)
+    assert st["converged"] and st["relres_max"] <= spec.tol
+    # Bregman update on sampled edges (b started at 0): b' = t - Shrink(t, 1/lam), t = w (y_a - y_b)
+    Y = p.get("Y")
+    bs = p.get("BS")
+    ga, gb, gw = p.edges()
+    lam = p.info()["lambda_"]
+    rng = np.random.default_rng(1)
+    k = rng.choice(ga.shape[0], 4000, replace=False)
+    t = gw[k, None] * (Y[ga[k]] - Y[gb[k]])
+    b_ref = t - O.shrink(t, 1.0 / lam)
+    scale = np.max(np.abs(t))
+    assert np.max(np.abs(bs[k] - b_ref)) <= 1e-5 * scale  # FP32 edge pass
+    stats = p.solve(1, 2)
+    assert stats["n_unconverged"] == 0 and stats["relres_max"] <= spec.tol
+    _, ortho1 = p.objective("yhat")
+    assert ortho1 <= 1e-9
