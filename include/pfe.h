@@ -202,7 +202,8 @@ PFE_API pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY
  * CUDA events over `reps` launches on the current iterate (scratch copies,
  * the iteration state is not modified) and the fastest is kept.  Tunable now:
  * the SpMM of the PCG iteration (variants below; the fixed-length ones apply
- * to FP32 single-problem grid graphs of radius 2 or 3).  choice[0] receives
+ * to FP32 grid graphs of radius 2 or 3, for a batch only PFE_SPMM_ROW1 at
+ * radius 2).  choice[0] receives
  * the chosen SpMM variant and ms[v] (at least PFE_SPMM_NVARIANTS entries;
  * either may be NULL) each variant's average time, -1 where it does not
  * apply.  pfe_set_variant sets a choice directly (e.g. from a cache of

@@ -445,8 +445,9 @@ pfe_status pfe_get_info(const pfe_ctx *c, pfe_info *info) {
 // FP32 single-problem graph with 12 or 28 slots per row).
 static bool spmm_variant_applies(const pfe_ctx *c, int v) {
     if (v == PFE_SPMM_GENERAL) return true;
-    return c->mixed && c->nseg == 1 && (c->g.row_len == 12 || c->g.row_len == 28) && v > 0 &&
-           v < PFE_SPMM_NVARIANTS;
+    if (!c->mixed || v <= 0 || v >= PFE_SPMM_NVARIANTS) return false;
+    if (c->nseg > 1) return v == PFE_SPMM_ROW1 && c->g.row_len == 12;  // batches: one row group per step
+    return c->g.row_len == 12 || c->g.row_len == 28;
 }
 
 pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms) {

@@ -781,7 +781,8 @@ int64_t rows_need(const pfe_ctx *c);
 //   PFE_SPMM_ROW2     fixed row length, two row groups per step, >= 5 blocks/SM
 //   PFE_SPMM_ROW2_4   fixed row length, two row groups per step, >= 4 blocks/SM
 // Fixed-length variants exist for the FP32 single-problem path at radius 2
-// and 3 (12 and 28 slots); elsewhere the general kernel runs.
+// and 3 (12 and 28 slots) and, one row group per step, for FP32 batches at
+// radius 2; elsewhere the general kernel runs.
 template <typename T, int D, bool MS, int LEN>
 bool launch_spmm_fixed(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int v) {
     if (v == PFE_SPMM_ROW1)
@@ -807,6 +808,13 @@ void launch_spmm(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int variant = 
     if constexpr (std::is_same_v<T, float> && !MS) {
         if (c->g.row_len == 12) done = launch_spmm_fixed<T, D, MS, 12>(c, s, a, v);
         else if (c->g.row_len == 28) done = launch_spmm_fixed<T, D, MS, 28>(c, s, a, v);
+    } else if constexpr (std::is_same_v<T, float> && MS) {  // batches: the one-row variant
+        if (v == PFE_SPMM_ROW1 && c->g.row_len == 12) {
+            k_spmm_fixed<T, D, MS, 12, 1, 6><<<wave_grid(c, G_SPMM_F1, k_spmm_fixed<T, D, MS, 12, 1, 6>,
+                                                         rows_need<T, D>(c)),
+                                               kBlock, 0, s>>>(a);
+            done = true;
+        }
     }
     if (!done) k_spmm<T, D, MS><<<wave_grid(c, G_SPMM, k_spmm<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
 }
