@@ -313,13 +313,21 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, 
     if (use) cudaGraphSetConditional(h, value ? 1u : 0u);
 }
 
+// The finishing steps below run on warp 0 of the last block (all 32 lanes):
+// lane c handles column c (or segment c, strided), so the FP64 square roots
+// and divisions of the columns run side by side instead of one after the
+// other.  Values other blocks wrote in this launch are read with ld.cg (L2):
+// the block's L1 may hold lines loaded at its start.
+constexpr unsigned kFull = 0xffffffffu;
+
 // Per-segment part of finishing an iteration `it` (or the start of a solve):
-// residual norms -> relres, beta, freezing.  Thread 0 of the segment's last
-// block.
+// residual norms -> relres, beta, freezing.  Ends with a __syncwarp, so lane 0
+// sees every lane's writes.
 static __device__ void finish_seg(PcgCtl *ctl, const SegScal &sc, int seg, const double *rz, const double *rr, int D,
                                   bool start, int it) {
+    const int lane = threadIdx.x & 31;
     int any = 0;
-    for (int c = 0; c < D; ++c) {
+    for (int c = lane; c < D; c += 32) {
         const int k = seg * D + c;
         if (start) {
             sc.rz[k] = rz[c];
@@ -338,15 +346,19 @@ static __device__ void finish_seg(PcgCtl *ctl, const SegScal &sc, int seg, const
         }
         any |= sc.active[k];
     }
-    if (start)
-        sc.seg_iters[seg] = 0;
-    else if (sc.seg_active[seg])
-        sc.seg_iters[seg] = it;
-    sc.seg_active[seg] = any;
+    any = __any_sync(kFull, any);
+    if (lane == 0) {
+        if (start)
+            sc.seg_iters[seg] = 0;
+        else if (__ldcg(sc.seg_active + seg))
+            sc.seg_iters[seg] = it;
+        sc.seg_active[seg] = any;
+    }
+    __syncwarp();
 }
 
-// Thread 0 of a segment's last block, after its segment's work: true for the
-// last segment to get here (the one that finishes the iteration).
+// Lane 0 of warp 0 of a segment's last block, after its segment's work: true
+// for the last segment to get here (the one that finishes the iteration).
 __device__ __forceinline__ bool last_segment_arrives(PcgCtl *ctl, int k, int nseg) {
     __threadfence();
     const unsigned t = atomicAdd(&ctl->ticket[k], 1u);
@@ -356,40 +368,73 @@ __device__ __forceinline__ bool last_segment_arrives(PcgCtl *ctl, int k, int nse
     return true;
 }
 
-// Global part: termination (every segment converged, an error, or max_iter)
-// and the statistics of a finished solve.
+// The same decision for the whole warp (lane 0 takes the ticket).
+__device__ __forceinline__ bool warp_last_segment(PcgCtl *ctl, int k, int nseg) {
+    int last = 0;
+    if ((threadIdx.x & 31) == 0) last = last_segment_arrives(ctl, k, nseg);
+    last = __shfl_sync(kFull, last, 0);
+    __syncwarp();
+    return last != 0;
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Global part (warp 0, all lanes; the control block is written by lane 0):
+// termination (every segment converged, an error, or max_iter) and the
+// statistics of a finished solve.
 static __device__ void finish_all(PcgCtl *ctl, const SegScal &sc, int nseg, int D, cudaGraphConditionalHandle cond,
                                   int use_cond) {
+    const int lane = threadIdx.x & 31;
     int any = 0;
-    for (int s = 0; s < nseg; ++s) any |= sc.seg_active[s];
-    ctl->any_active = any;
-    const int done = (!any) || ctl->error || ctl->iter >= ctl->max_iter;
+    for (int s = lane; s < nseg; s += 32) any |= __ldcg(sc.seg_active + s);
+    any = __any_sync(kFull, any);
+    int done = 0;
+    if (lane == 0) done = (!any) || *(volatile int *)&ctl->error || ctl->iter >= ctl->max_iter;
+    done = __shfl_sync(kFull, done, 0);
     if (done) {
         double mr = 0.0;
         long long tot = 0;
         int mx = 0, nun = 0;
-        for (int s = 0; s < nseg; ++s) {
-            tot += sc.seg_iters[s];
-            sc.seg_iters_tot[s] += sc.seg_iters[s];
-            mx = max(mx, sc.seg_iters[s]);
-            nun += sc.seg_active[s] ? 1 : 0;
-            for (int c = 0; c < D; ++c) mr = fmax(mr, sc.relres[s * D + c]);
+        for (int s = lane; s < nseg; s += 32) {
+            const int it = __ldcg(sc.seg_iters + s);
+            tot += it;
+            sc.seg_iters_tot[s] += it;
+            mx = max(mx, it);
+            nun += __ldcg(sc.seg_active + s) ? 1 : 0;
+            for (int c = 0; c < D; ++c) mr = fmax(mr, __ldcg(sc.relres + (int64_t)s * D + c));
         }
-        ctl->tot_iters += tot;
-        ctl->tot_rounds += ctl->iter;
-        ctl->max_solve_iters = max(ctl->max_solve_iters, mx);
-        ctl->n_solves += nseg;
-        ctl->n_unconv += nun;
-        ctl->last_iters = mx;
-        ctl->last_relres = mr;
-        ctl->last_converged = !any;
-        ctl->max_relres = fmax(ctl->max_relres, mr);
-        const int u = ctl->unroll > 0 ? ctl->unroll : 1;
-        // launches before and after the loop + the loop body's per iteration
-        ctl->launches += ctl->launch_base + (long long)ctl->launch_per_iter * u * ((ctl->iter + u - 1) / u);
+        tot = warp_sum(tot);
+        nun = warp_sum(nun);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+            mr = fmax(mr, __shfl_xor_sync(kFull, mr, o));
+        }
+        if (lane == 0) {
+            ctl->tot_iters += tot;
+            ctl->tot_rounds += ctl->iter;
+            ctl->max_solve_iters = max(ctl->max_solve_iters, mx);
+            ctl->n_solves += nseg;
+            ctl->n_unconv += nun;
+            ctl->last_iters = mx;
+            ctl->last_relres = mr;
+            ctl->last_converged = !any;
+            ctl->max_relres = fmax(ctl->max_relres, mr);
+            const int u = ctl->unroll > 0 ? ctl->unroll : 1;
+            // launches before and after the loop + the loop body's per iteration
+            ctl->launches += ctl->launch_base + (long long)ctl->launch_per_iter * u * ((ctl->iter + u - 1) / u);
+        }
     }
-    ctl->done = done;
-    set_cond(cond, use_cond, !done);
+    if (lane == 0) {
+        ctl->done = done;
+        set_cond(cond, use_cond, !done);
+    }
+    __syncwarp();
 }
 
 // (b - A y) on columns c0 .. c0+V-1 of row i, with y = hi + lo accumulated in
@@ -460,7 +505,7 @@ __device__ __forceinline__ void true_residual(const PcgArgs<T> &a, int64_t i, in
     const BlockSeg bsg = block_seg<MS_>(a.sg);                                                             \
     const int64_t warp_g = (int64_t)(blockIdx.x - bsg.b0) * kWarps + (threadIdx.x >> 5);                   \
     const int64_t warps_total = (int64_t)bsg.nb * kWarps;                                                  \
-    const int64_t seg_rows = ((MS_) && (LIVE_) && !a.sc.seg_active[bsg.seg]) ? 0 : bsg.r1 - bsg.r0;      \
+    const int64_t seg_rows = ((MS_) && (LIVE_) && !__ldcg(a.sc.seg_active + bsg.seg)) ? 0 : bsg.r1 - bsg.r0; \
     for (int64_t g = warp_g; g * SW::RPW < seg_rows; g += warps_total)
 // one problem (FSAI kernels, y = A x)
 #define PFE_ROW_LOOP(T_, D_) PFE_ROW_LOOP_(T_, D_, false, false)
@@ -505,26 +550,29 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(PcgArgs<T> a) {
     // ctl->error was cleared before this launch (segment finishers may set it)
     __shared__ double tot[3 * D];
     if (grid_sum_cols<T, D, 3>(acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 2], tot)) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             PcgCtl *ctl = a.ctl;
             const int seg = bsg.seg;
-            for (int c = 0; c < D; ++c) {
+            for (int c = threadIdx.x; c < D; c += 32) {
                 double bn = sqrt(tot[2 * D + c]);
                 a.sc.bnorm[seg * D + c] = bn > 0.0 ? bn : 1.0;
                 a.sc.alpha[seg * D + c] = 0.0;
             }
+            __syncwarp();
             if (PRE == 0) finish_seg(ctl, a.sc, seg, tot, tot + D, D, true, 0);
-            if (!MS || last_segment_arrives(ctl, 2, a.sg.nseg)) {
-                ctl->iter = 0;
-                ctl->refresh_now = 0;
-                ctl->p_ready = 1;
-                ctl->xpending = 0;
-                if (PRE == 0) {
-                    finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
-                } else {
-                    ctl->zstart = 1;
-                    ctl->done = 0;
+            if (!MS || warp_last_segment(ctl, 2, a.sg.nseg)) {
+                if (threadIdx.x == 0) {
+                    ctl->iter = 0;
+                    ctl->refresh_now = 0;
+                    ctl->p_ready = 1;
+                    ctl->xpending = 0;
+                    if (PRE != 0) {
+                        ctl->zstart = 1;
+                        ctl->done = 0;
+                    }
                 }
+                __syncwarp();
+                if (PRE == 0) finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
             }
         }
     }
@@ -647,7 +695,7 @@ template <typename T, int D, bool MS>
 __device__ __forceinline__ void spmm_finish(const PcgArgs<T> &a, const BlockSeg &bsg, const double *tot) {
     PcgCtl *w = a.ctl;
     const SegScal &sc = a.sc;
-    for (int c = 0; c < D; ++c) {
+    for (int c = threadIdx.x & 31; c < D; c += 32) {
         const int k = bsg.seg * D + c;
         if (!sc.active[k]) {
             sc.alpha[k] = 0.0;
@@ -661,7 +709,7 @@ __device__ __forceinline__ void spmm_finish(const PcgArgs<T> &a, const BlockSeg 
             sc.alpha[k] = sc.rz[k] / pqc;
         }
     }
-    if (!MS || last_segment_arrives(w, 0, a.sg.nseg)) {
+    if ((!MS || warp_last_segment(w, 0, a.sg.nseg)) && (threadIdx.x & 31) == 0) {
         w->p_ready = 0;
         w->xpending = 1;
     }
@@ -709,7 +757,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
     }
     __shared__ double tot[D];
     if (grid_sum_cols<T, D, 1>(pq, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 0], tot))
-        if (threadIdx.x == 0) spmm_finish<T, D, MS>(a, bsg, tot);
+        if (threadIdx.x < 32) spmm_finish<T, D, MS>(a, bsg, tot);
 }
 
 // k_spmm for graphs whose rows all have LEN slots (grid stencils; LEN a
@@ -732,7 +780,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_spmm_fixed(PcgArgs<T> a) {
     const BlockSeg bsg = block_seg<MS>(a.sg);
     const int64_t warp_g = (int64_t)(blockIdx.x - bsg.b0) * kWarps + (threadIdx.x >> 5);
     const int64_t warps_total = (int64_t)bsg.nb * kWarps;
-    const int64_t seg_rows = (MS && !a.sc.seg_active[bsg.seg]) ? 0 : bsg.r1 - bsg.r0;
+    const int64_t seg_rows = (MS && !__ldcg(a.sc.seg_active + bsg.seg)) ? 0 : bsg.r1 - bsg.r0;
     const int c0 = lm.cg * V;
     for (int64_t g = warp_g; g * SW::RPW < seg_rows; g += ROWS * warps_total) {
         int64_t ii[ROWS];
@@ -768,7 +816,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_spmm_fixed(PcgArgs<T> a) {
     }
     __shared__ double tot[D];
     if (grid_sum_cols<T, D, 1>(pq, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 0], tot))
-        if (threadIdx.x == 0) spmm_finish<T, D, MS>(a, bsg, tot);
+        if (threadIdx.x < 32) spmm_finish<T, D, MS>(a, bsg, tot);
 }
 
 template <typename T, int D>
@@ -847,7 +895,7 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
         const SW lm;
         const int64_t warp_g = (int64_t)(blockIdx.x - bsg.b0) * kWarps + (threadIdx.x >> 5);
         const int64_t warps_total = (int64_t)bsg.nb * kWarps;
-        const int64_t seg_rows = (!MS || a.sc.seg_active[bsg.seg]) ? bsg.r1 - bsg.r0 : 0;
+        const int64_t seg_rows = (!MS || __ldcg(a.sc.seg_active + bsg.seg)) ? bsg.r1 - bsg.r0 : 0;
         const int c0 = lm.cg * V;
         T al[V];
 #pragma unroll
@@ -881,18 +929,21 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
     }
     __shared__ double tot[2 * D];
     if (grid_sum_cols<T, D, 2>(acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot)) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             PcgCtl *ctl = a.ctl;
             const int it = ctl->iter + 1;
             // an error here can only come from an earlier kernel while a refresh is due
-            const bool refresh_due = !ctl->error && ctl->refresh > 0 && (it % ctl->refresh) == 0;
+            int due = 0;
+            if (threadIdx.x == 0) due = !*(volatile int *)&ctl->error && ctl->refresh > 0 && (it % ctl->refresh) == 0;
+            const bool refresh_due = __shfl_sync(kFull, due, 0) != 0;
             if (!refresh_due) finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, false, it);
-            if (!MS || last_segment_arrives(ctl, 1, a.sg.nseg)) {
-                ctl->iter = it;
-                if (refresh_due)
-                    ctl->refresh_now = 1;  // k_xflush + k_refresh finish this iteration
-                else
-                    finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
+            if (!MS || warp_last_segment(ctl, 1, a.sg.nseg)) {
+                if (threadIdx.x == 0) {
+                    ctl->iter = it;
+                    if (refresh_due) ctl->refresh_now = 1;  // k_xflush + k_refresh finish this iteration
+                }
+                __syncwarp();
+                if (!refresh_due) finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
             }
         }
     }
@@ -1002,10 +1053,13 @@ __device__ __forceinline__ void gslot_chunk(const int *__restrict__ col, const T
 }
 
 // The FSAI gather kernels are latency-bound: 5 resident blocks of kBlock per SM
-// (48 registers a thread) with up to 2 columns a lane, 4 with 4 (16 bytes).
-template <typename T, int D>
+// (48 registers a thread) with up to 2 columns a lane, 4 with 4 columns.
+// k_fsai_tr and k_fsai_t on 12-slot fixed rows fit 40 registers without
+// spilling and run 6 blocks (k_fsai_z, which also accumulates two dots,
+// measured slower there and keeps 5).
+template <typename T, int D, int LEN = 0>
 constexpr int gather_min_blocks() {
-    return SubWarp<T, D>::V * (int)sizeof(T) >= 16 ? 4 : 5;
+    return SubWarp<T, D>::V * (int)sizeof(T) >= 16 ? 4 : (LEN == 12 ? 6 : 5);
 }
 
 // All slots in [lo, hi): chunks of kGChunk = 8 slots (the 6 lower or upper
@@ -1055,7 +1109,7 @@ __device__ __forceinline__ void gslot_fixed(const int *__restrict__ col, const T
 // uses), the owner writes its r' to the other buffer.
 // LEN > 0: uniform rows of LEN slots, lower slots at positions [0, LEN/2).
 template <typename T, int D, int LEN>
-__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr(PcgArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN>())) k_fsai_tr(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
     __shared__ T salpha[D];  // FSAI runs on one segment
@@ -1094,7 +1148,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr
 // MODE 0: at the start of a solve (residual in r2[0]); MODE 1: only after a
 // residual refresh (residual in the new buffer).
 template <typename T, int D, int MODE, int LEN>
-__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(PcgArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN>())) k_fsai_t(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
     if (MODE == 1 && !*(volatile int *)&a.ctl->refresh_now) return;
     const T *__restrict__ rsrc = MODE == 0 ? a.r2[0] : a.r2[(a.ctl->iter + 1) & 1];
@@ -1163,14 +1217,18 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_z(
     }
     __shared__ double tot[2 * D];
     if (grid_sum_cols<T, D, 2>(acc2, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot)) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             PcgCtl *ctl = a.ctl;
             const bool start = ctl->zstart != 0;
             finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, start, ctl->iter + 1);
-            ctl->zstart = 0;  // FSAI: one problem (its last block finishes the iteration)
-            if (!start) ctl->iter += 1;
+            if (threadIdx.x == 0) {
+                ctl->zstart = 0;  // FSAI: one problem (its last block finishes the iteration)
+                if (!start) ctl->iter += 1;
+            }
+            __syncwarp();
             finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
-            ctl->refresh_now = (ctl->refresh > 0 && ((ctl->iter + 1) % ctl->refresh) == 0) ? 1 : 0;
+            if (threadIdx.x == 0)
+                ctl->refresh_now = (ctl->refresh > 0 && ((ctl->iter + 1) % ctl->refresh) == 0) ? 1 : 0;
         }
     }
 }
@@ -1203,12 +1261,15 @@ __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
     }
     __shared__ double tot[2 * D];
     if (grid_sum_cols<T, D, 2>(acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 3], tot)) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             PcgCtl *ctl = a.ctl;
             finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, false, ctl->iter);
-            if (!MS || last_segment_arrives(ctl, 3, a.sg.nseg)) {
-                ctl->refresh_now = 0;
-                ctl->xpending = 0;
+            if (!MS || warp_last_segment(ctl, 3, a.sg.nseg)) {
+                if (threadIdx.x == 0) {
+                    ctl->refresh_now = 0;
+                    ctl->xpending = 0;
+                }
+                __syncwarp();
                 finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
             }
         }
