@@ -277,6 +277,13 @@ def jacobi_pcg(A: sp.csr_matrix, Bm: np.ndarray, X0: np.ndarray, tol: float, max
     Returns (X, info) with per-column iteration counts and relative residuals.
     """
     diag_inv = 1.0 / A.diagonal()
+    return pcg(A, Bm, X0, tol, max_iter, refresh, lambda R: diag_inv[:, None] * R)
+
+
+def pcg(A: sp.csr_matrix, Bm: np.ndarray, X0: np.ndarray, tol: float, max_iter: int,
+        refresh: int, apply_minv):
+    """The PCG runs of ``jacobi_pcg`` with any preconditioner: apply_minv(R)
+    returns Z = M^{-1} R column by column (for an FSAI factor G, G^T G R)."""
     X = np.array(X0, dtype=np.float64, copy=True)
     Bm = np.asarray(Bm, dtype=np.float64)
     d = Bm.shape[1]
@@ -286,7 +293,7 @@ def jacobi_pcg(A: sp.csr_matrix, Bm: np.ndarray, X0: np.ndarray, tol: float, max
     iters = np.zeros(d, dtype=np.int64)
     relres = np.linalg.norm(R, axis=0) / bnorm_safe
     active = relres > tol
-    Z = diag_inv[:, None] * R
+    Z = apply_minv(R)
     P = Z.copy()
     rz = np.sum(R * Z, axis=0)
     k = 0
@@ -300,7 +307,7 @@ def jacobi_pcg(A: sp.csr_matrix, Bm: np.ndarray, X0: np.ndarray, tol: float, max
         iters[active] = k
         if refresh > 0 and k % refresh == 0:
             R = np.where(active[None, :], Bm - A @ X, R)
-        Z = diag_inv[:, None] * R
+        Z = apply_minv(R)
         rz_new = np.sum(R * Z, axis=0)
         relres = np.linalg.norm(R, axis=0) / bnorm_safe
         now_done = active & (relres <= tol)

@@ -114,3 +114,33 @@ def test_classical_fsai_reduces_pcg_iterations():
             Z = Minv(R); rzn = (R * Z).sum(0); P = Z + rzn / rz * P; rz = rzn
         return 2000
     assert pcg(lambda R: F.fsai_apply(G, R)) < pcg(lambda R: dinv[:, None] * R)
+
+
+def test_oracle_pcg_exact_preconditioner_takes_one_step():
+    """With M^-1 = A^-1 the first direction is the whole error, alpha = 1 and
+    every column converges after one iteration (any start); with M = I the
+    residual norms of CG on a 1-dimensional Krylov space match the closed form
+    of steepest descent."""
+    g = _tiny_graph(9, 8)
+    rng = np.random.default_rng(5)
+    Bm = rng.standard_normal((g.n, 3))
+    X0 = rng.standard_normal((g.n, 3))
+    solve = O.DirectSolver(g.A)
+    X, info = O.pcg(g.A, Bm, X0, 1e-10, 50, 0, lambda R: solve(R)[0])
+    assert info["converged"] and np.all(info["iters"] == 1)
+    np.testing.assert_allclose(X, solve(Bm)[0], rtol=1e-9, atol=1e-12)
+    # one identity-preconditioned step: x1 = x0 + (r.r / r.A r) r
+    X1, _ = O.pcg(g.A, Bm, X0, 0.0, 1, 0, lambda R: R)
+    R0 = Bm - g.A @ X0
+    al = (R0 * R0).sum(0) / (R0 * (g.A @ R0)).sum(0)
+    np.testing.assert_allclose(X1, X0 + al * R0, rtol=1e-12)
+
+
+def test_oracle_pcg_with_fsai_matches_direct_solve():
+    g = _tiny_graph(20, 18, radius=3.0)
+    Bm = np.random.default_rng(8).standard_normal((g.n, 2))
+    G = F.classical_fsai(g.A)
+    X, info = O.pcg(g.A, Bm, np.zeros_like(Bm), 1e-10, 2000, 50, lambda R: F.fsai_apply(G, R))
+    _, ij = O.jacobi_pcg(g.A, Bm, np.zeros_like(Bm), 1e-10, 2000)
+    assert info["converged"] and info["iters"].max() < ij["iters"].max()
+    np.testing.assert_allclose(X, O.DirectSolver(g.A)(Bm)[0], rtol=1e-7, atol=1e-9)
