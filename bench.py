@@ -461,12 +461,13 @@ def main():
     fsai_k = {}
     if args.precond == "learned":
         # lower (upper) slots: FP32 G value + int32 column each, kb and G_ii per row;
-        # t = G r': r, q in, r', t out; z = G^T t: t, r in, z out
-        tr_ms, z_ms = p.time_kernel("fsai_tr", 20), p.time_kernel("fsai_z", 20)
+        # t = G r': r, q in, r', t out; z = G^T t with p = z + beta p and
+        # y += alpha p: t in, p and y (hi, lo) in and out
+        tr_ms, zp_ms = p.time_kernel("fsai_tr", 20), p.time_kernel("fsai_zp", 20)
         tr_b = 4 * (nnz - n) + 8 * n + 16 * n * d
-        z_b = 4 * (nnz - n) + 8 * n + 12 * n * d
+        zp_b = 4 * (nnz - n) + 8 * n + 28 * n * d
         fsai_k = {"k_fsai_tr_ms": round(tr_ms, 5), "k_fsai_tr_GBps": round(tr_b / (tr_ms * 1e-3) / 1e9, 1),
-                  "k_fsai_z_ms": round(z_ms, 5), "k_fsai_z_GBps": round(z_b / (z_ms * 1e-3) / 1e9, 1)}
+                  "k_fsai_zp_ms": round(zp_ms, 5), "k_fsai_zp_GBps": round(zp_b / (zp_ms * 1e-3) / 1e9, 1)}
     # FP32 values + int32 indices of A, p in, q out: 8 nnz_A + 4 (n + 1) + 2 * 4 n d
     spmm_bytes = 8 * nnz + 4 * (n + 1) + 2 * 4 * n * d
     peaks = measured_peaks()

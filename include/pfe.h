@@ -386,8 +386,10 @@ PFE_API pfe_status pfe_solve_system(pfe_ctx *c, const double *RHS, double *Y, pf
  *   PFE_KERNEL_UPDATE   r -= alpha q with the r.z, r.r column dots
  *   PFE_KERNEL_EDGE     fused M Y / Shrink / b update / M^T scatter (Eqs. 7, 9, 10, 13)
  *   PFE_KERNEL_PUPDATE  p = D_A^{-1} r + beta p with the delayed y += alpha p
- *   PFE_KERNEL_FSAI_TR  r -= alpha q fused with t = G r (FSAI preconditioner set)
- *   PFE_KERNEL_FSAI_Z   z = G^T t with the r.z, r.r column dots (FSAI preconditioner set)
+ *   PFE_KERNEL_FSAI_TR  r -= alpha q fused with t = G r and the column dots
+ *                       t.t (= r.z) and r.r (FSAI preconditioner set)
+ *   PFE_KERNEL_FSAI_ZP  z = G^T t fused with p = z + beta p and the delayed
+ *                       y += alpha p; z is not stored (FSAI preconditioner set)
  * The iteration state is not modified (scratch copies and a scratch control
  * block are used; the edge pass rewrites the same right-hand side).  Only
  * the PCG direction p and product q, which every solve re-initialises, are
@@ -401,7 +403,7 @@ enum {
     PFE_KERNEL_EDGE = 2,
     PFE_KERNEL_PUPDATE = 3,
     PFE_KERNEL_FSAI_TR = 4,
-    PFE_KERNEL_FSAI_Z = 5
+    PFE_KERNEL_FSAI_ZP = 5
 };
 PFE_API pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_ms);
 

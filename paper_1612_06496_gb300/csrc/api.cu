@@ -58,7 +58,6 @@ void free_work(pfe_ctx *c) {
     c->work_allocs.clear();
     c->wk = Work{};
     c->fsai.t = nullptr;
-    c->fsai.z = nullptr;
     c->fsai.r1 = nullptr;
     c->sc = SegScal{};
     c->seg_T = nullptr;
@@ -78,15 +77,13 @@ constexpr int kLeMaxIter = 400;
 constexpr double kLeTol = 1e-9;
 constexpr int kLeDegree = 10;
 
-// Work vectors of the FSAI iteration: t = G r, z = G^T t and the second
-// residual buffer (n x d each, work precision float).
+// Work vectors of the FSAI iteration: t = G r and the second residual buffer
+// (n x d each, work precision float).
 pfe_status fsai_vectors(pfe_ctx *c, int64_t nd) {
-    float *t, *z, *r1;
+    float *t, *r1;
     PFE_TRY(walloc(c, &t, nd));
-    PFE_TRY(walloc(c, &z, nd));
     PFE_TRY(walloc(c, &r1, nd));
     c->fsai.t = t;
-    c->fsai.z = z;
     c->fsai.r1 = r1;
     return PFE_OK;
 }
@@ -95,7 +92,7 @@ pfe_status fsai_vectors(pfe_ctx *c, int64_t nd) {
 // iteration (the counts the device reports in pfe_solve_stats).
 void launch_counts(const pfe_ctx *c, int lc[2]) {
     lc[0] = c->fsai.enabled ? 4 : 2;
-    lc[1] = c->fsai.enabled ? 7 : 5;
+    lc[1] = c->fsai.enabled ? 6 : 5;
 }
 
 // After the preconditioner changed: drop the captured loop (its body differs
@@ -946,8 +943,8 @@ pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_
         if (e != cudaSuccess) return fail(c, PFE_ECUDA, cudaGetErrorString(e));
         ms /= (float)reps;
     } else if (which == PFE_KERNEL_SPMM || which == PFE_KERNEL_UPDATE || which == PFE_KERNEL_PUPDATE ||
-               which == PFE_KERNEL_FSAI_TR || which == PFE_KERNEL_FSAI_Z) {
-        const int k = which == PFE_KERNEL_PUPDATE ? 2 : which == PFE_KERNEL_FSAI_TR ? 3 : which == PFE_KERNEL_FSAI_Z ? 4 : which;
+               which == PFE_KERNEL_FSAI_TR || which == PFE_KERNEL_FSAI_ZP) {
+        const int k = which == PFE_KERNEL_PUPDATE ? 2 : which == PFE_KERNEL_FSAI_TR ? 3 : which == PFE_KERNEL_FSAI_ZP ? 4 : which;
         PFE_TRY(time_pcg_kernel(c, c->stream, k, reps, &ms));
     } else {
         return fail(c, PFE_EINVAL, "unknown kernel id");

@@ -295,8 +295,8 @@ __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
 // runs), capped at `need` blocks and rounded down to a multiple of `mult`.
 // Cached per context in c->kgrid[slot].
 enum GridSlot {
-    G_INIT = 0, G_INIT_F, G_PUPD, G_PUPD_F, G_SPMM, G_UPDATE, G_FSAI_TR, G_XFLUSH, G_REFRESH, G_REFRESH_F,
-    G_FSAI_T, G_FSAI_T1, G_FSAI_Z, G_APPLY, G_EDGE, G_PAPPLY, G_TIME_SPMM, G_TIME_UPDATE, G_SPMM_F1, G_SPMM_F2,
+    G_INIT = 0, G_INIT_F, G_PUPD, G_SPMM, G_UPDATE, G_FSAI_TR, G_XFLUSH, G_REFRESH, G_REFRESH_F,
+    G_FSAI_T, G_FSAI_T1, G_FSAI_ZP, G_APPLY, G_EDGE, G_PAPPLY, G_TIME_SPMM, G_TIME_UPDATE, G_SPMM_F1, G_SPMM_F2,
     G_SPMM_F3, G_NSLOTS
 };
 inline Segs seg_view(const pfe_ctx *c) { return Segs{c->nseg, c->g.n, c->seg_off, c->rseg}; }

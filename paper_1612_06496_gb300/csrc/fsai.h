@@ -30,8 +30,8 @@ struct FsaiState {
     unsigned *tick = nullptr;
     float *params = nullptr;   // network parameters in use (device copy)
     float *grad = nullptr;     // last gradient
-    void *t = nullptr, *z = nullptr;  // PCG work vectors t = G r, z = G^T t (n x d)
-    void *r1 = nullptr;               // second residual buffer (n x d)
+    void *t = nullptr;   // PCG work vector t = G r (n x d)
+    void *r1 = nullptr;  // second residual buffer (n x d)
 };
 
 pfe_status fsai_alloc(pfe_ctx *c);

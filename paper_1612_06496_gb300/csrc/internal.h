@@ -56,7 +56,6 @@ struct PcgCtl {
     int pbuf;                         // which direction buffer holds the current p
     int p_ready;                      // 1: p was just set by k_pcg_init (no update in k_spmm)
     int xpending;                     // 1: y += alpha p of the last k_spmm not yet applied
-    int zstart;                       // FSAI: the next k_fsai_z finishes the start of a solve
     int launch_base, launch_per_iter; // kernel launches outside / per iteration of the loop
     int pad2;
 };

@@ -60,9 +60,9 @@ struct PcgArgs {
     SegScal sc;  // per-segment scalars [seg * D + c]
     cudaGraphConditionalHandle cond;
     int use_cond;
-    // FSAI preconditioner (float path): z = G^T t, t = G r; the residual
-    // alternates between r2[0] (= r) and r2[1]
-    T *z, *t;
+    // FSAI preconditioner (float path): t = G r; the residual alternates
+    // between r2[0] (= r) and r2[1]
+    T *t;
     T *r2[2];
     const T *gdiag, *gslot;
     const int *kb;
@@ -206,6 +206,34 @@ __device__ __forceinline__ void load_slots(const int *__restrict__ col, const T 
     }
 }
 
+// Slots [P0, P1) of a fixed-length row (base a multiple of 4 slots): the
+// widest aligned pieces (4, 2 or 1 slots) that tile the range exactly, so no
+// slot outside it is fetched.  4-byte values (the float path).
+template <typename T, int P0, int P1, int K = P0>
+__device__ __forceinline__ void load_slot_range(const int *__restrict__ col, const T *__restrict__ val, int64_t base,
+                                                int (&jj)[P1 - P0], T (&av)[P1 - P0]) {
+    static_assert(sizeof(T) == 4, "4-byte slot values");
+    if constexpr (K < P1) {
+        constexpr int W = (K % 4 == 0 && K + 4 <= P1) ? 4 : (K % 2 == 0 && K + 2 <= P1) ? 2 : 1;
+        constexpr int u = K - P0;
+        if constexpr (W == 4) {
+            const int4 cv = __ldg(reinterpret_cast<const int4 *>(col + base + K));
+            const float4 vv = __ldg(reinterpret_cast<const float4 *>(val + base + K));
+            jj[u] = cv.x; jj[u + 1] = cv.y; jj[u + 2] = cv.z; jj[u + 3] = cv.w;
+            av[u] = vv.x; av[u + 1] = vv.y; av[u + 2] = vv.z; av[u + 3] = vv.w;
+        } else if constexpr (W == 2) {
+            const int2 cv = __ldg(reinterpret_cast<const int2 *>(col + base + K));
+            const float2 vv = __ldg(reinterpret_cast<const float2 *>(val + base + K));
+            jj[u] = cv.x; jj[u + 1] = cv.y;
+            av[u] = vv.x; av[u + 1] = vv.y;
+        } else {
+            jj[u] = __ldg(col + base + K);
+            av[u] = __ldg(val + base + K);
+        }
+        load_slot_range<T, P0, P1, K + W>(col, val, base, jj, av);
+    }
+}
+
 // ---- reductions -------------------------------------------------------------
 
 template <typename A, typename AT>
@@ -289,6 +317,73 @@ __device__ __forceinline__ bool grid_sum_cols(typename Acc<T>::type (&v)[NQ][Sub
     if (threadIdx.x == 0) *ticket = 0u;
     __syncthreads();
     return true;
+}
+
+// Column sums of non-negative terms x*y (squared norms, r.D^{-1}r): no
+// cancellation, so the float path adds each lane's terms in FP32 over runs of
+// at most kSqChunk rows (relative error of a run <= (kSqChunk - 1) u) and
+// adds the runs to a double-FP32 sum kept in shared memory (one slot per
+// thread, so the registers of the gathers stay free): one FMA a term instead
+// of the ~10 operations of an exact product.  FP64 adds every term with one
+// FMA in registers.  `sh` holds NQ * V * kBlock DF (float path).
+constexpr int kSqChunk = 16;
+template <typename T, int NQ, int V>
+struct SqSum {
+    using AT = typename Acc<T>::type;
+    static constexpr bool kFloat = std::is_same_v<T, float>;
+    AT acc[NQ][V];  // FP64: the sums; float: filled by finish()
+    float run[NQ][V];  // float: the current runs
+    DF *sh;
+    int cnt;
+    __device__ __forceinline__ explicit SqSum(DF *shared_base) : sh(shared_base + threadIdx.x), cnt(0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                acc[q][k] = Acc<T>::zero();
+                run[q][k] = 0.f;
+                if constexpr (kFloat) sh[(q * V + k) * kBlock] = DF{0.f, 0.f};
+            }
+    }
+    __device__ __forceinline__ void add(int q, int k, T x, T y) {
+        if constexpr (kFloat)
+            run[q][k] = __fmaf_rn(x, y, run[q][k]);
+        else
+            acc[q][k] = fma(x, y, acc[q][k]);
+    }
+    __device__ __forceinline__ void flush() {
+        if constexpr (kFloat) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    DF d = sh[(q * V + k) * kBlock];
+                    df_add_f(d, run[q][k]);
+                    sh[(q * V + k) * kBlock] = d;
+                    run[q][k] = 0.f;
+                }
+            cnt = 0;
+        }
+    }
+    // after each row (or group of rows) a lane has added
+    __device__ __forceinline__ void row_done() {
+        if constexpr (kFloat)
+            if (++cnt == kSqChunk) flush();
+    }
+    // the thread's sums in acc, for grid_sum_cols
+    __device__ __forceinline__ void finish() {
+        if constexpr (kFloat) {
+            flush();
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int k = 0; k < V; ++k) acc[q][k] = sh[(q * V + k) * kBlock];
+        }
+    }
+};
+template <typename T, int NQ, int V>
+constexpr int sqsum_slots() {
+    return std::is_same_v<T, float> ? NQ * V * kBlock : 1;
 }
 
 // (hi, lo) += alpha * p for the float path (product and sum errors kept in
@@ -519,8 +614,8 @@ __device__ __forceinline__ void true_residual(const PcgArgs<T> &a, int64_t i, in
 // ---- kernels ----------------------------------------------------------------
 
 // Start of a solve: r = b - A y, norms of b and r, r.z with z = D_A^{-1} r.
-// With the FSAI preconditioner (PRE = 1) z = G^T G r is made by k_fsai_t /
-// k_fsai_z, which also finish the start of the solve.
+// With the FSAI preconditioner (PRE = 1) k_fsai_t makes t = G r and r.z =
+// t.t and finishes the start of the solve; k_fsai_zp then sets p = G^T t.
 template <typename T, int D, int PRE, bool MS>
 __global__ void __launch_bounds__(kBlock) k_pcg_init(PcgArgs<T> a) {
     using A = Acc<T>;
@@ -566,10 +661,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(PcgArgs<T> a) {
                     ctl->refresh_now = 0;
                     ctl->p_ready = 1;
                     ctl->xpending = 0;
-                    if (PRE != 0) {
-                        ctl->zstart = 1;
-                        ctl->done = 0;
-                    }
+                    if (PRE != 0) ctl->done = 0;  // k_fsai_t finishes the start
                 }
                 __syncwarp();
                 if (PRE == 0) finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
@@ -602,9 +694,10 @@ struct Vec<double> {
 
 // p = z + beta p (p = z right after k_pcg_init) and the delayed solution
 // update y += alpha_prev p_prev, elementwise and in place (flat float4 /
-// double2 traversal; the grid makes every thread meet fixed columns).
-// z = D_A^{-1} r (Jacobi) or the stored G^T G r (FSAI, PRE = 1).
-template <typename T, int D, int PRE, bool MS>
+// double2 traversal; the grid makes every thread meet fixed columns), with
+// the Jacobi z = D_A^{-1} r.  (The FSAI iteration makes this update in
+// k_fsai_zp.)
+template <typename T, int D, bool MS>
 __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
@@ -631,7 +724,7 @@ __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
     }
     using V4 = typename VT::V;
     V4 *p4 = reinterpret_cast<V4 *>(a.p[0]);
-    const V4 *z4 = reinterpret_cast<const V4 *>(PRE == 0 ? a.r : a.z);
+    const V4 *z4 = reinterpret_cast<const V4 *>(a.r);
     V4 *x4 = reinterpret_cast<V4 *>(a.x);
     float4 *xl4 = reinterpret_cast<float4 *>(a.xlo);  // float path: VN == 4
     for (int64_t v = tid; v < nvec; v += nthr) {
@@ -648,10 +741,8 @@ __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
         }
         VT::get(p4[v], pv);
         VT::get(z4[v], zv);
-        if constexpr (PRE == 0) {
 #pragma unroll
-            for (int u = 0; u < VN; ++u) zv[u] = a.A.dinv[(v * VN + u) / D] * zv[u];
-        }
+        for (int u = 0; u < VN; ++u) zv[u] = a.A.dinv[(v * VN + u) / D] * zv[u];
         if (xpending) {
             T xv[VN];
             float xl[VN];
@@ -675,7 +766,7 @@ __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
         const int sgm = multi ? row_seg(a.sg, e / D) : 0;
         const T bt = p_ready ? T(0) : (multi ? (T)a.sc.beta[sgm * D + c] : sbeta[c]);
         const T at = multi ? (T)a.sc.alpha[sgm * D + c] : salpha[c];
-        const T z = PRE == 0 ? a.A.dinv[e / D] * a.r[e] : a.z[e];
+        const T z = a.A.dinv[e / D] * a.r[e];
         T po = a.p[0][e];
         if (xpending) {
             T xh = a.x[e];
@@ -877,18 +968,13 @@ void launch_spmm(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int variant = 
 template <typename T, int D, bool MS>
 __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
-    using A = Acc<T>;
-    using AT = typename A::type;
     using SWt = SubWarp<T, D>;
     const BlockSeg bsg = block_seg<MS>(a.sg);
     __shared__ T salpha[D];
     if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.sc.alpha[bsg.seg * D + threadIdx.x];
     __syncthreads();
-    AT acc[2][SWt::V];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int k = 0; k < SWt::V; ++k) acc[q][k] = A::zero();
+    __shared__ DF sq_sh[sqsum_slots<T, 2, SWt::V>()];
+    SqSum<T, 2, SWt::V> sq(sq_sh);  // r.z (= r.D_A^{-1}r) | r.r
     {
         using SW = SWt;
         constexpr int V = SW::V;
@@ -919,16 +1005,18 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
 #pragma unroll
                 for (int k = 0; k < V; ++k) {
                     const T ri = fma(-al[k], qv[h][k], rv[h][k]);
-                    A::add_prod(acc[0][k], ri, dv[h] * ri);
-                    A::add_prod(acc[1][k], ri, ri);
+                    sq.add(0, k, ri, dv[h] * ri);
+                    sq.add(1, k, ri, ri);
                     rv[h][k] = ri;
                 }
                 stv<T, V>(a.r + i * D + c0, rv[h]);
             }
+            sq.row_done();
         }
     }
+    sq.finish();
     __shared__ double tot[2 * D];
-    if (grid_sum_cols<T, D, 2>(acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot)) {
+    if (grid_sum_cols<T, D, 2>(sq.acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot)) {
         if (threadIdx.x < 32) {
             PcgCtl *ctl = a.ctl;
             const int it = ctl->iter + 1;
@@ -985,13 +1073,19 @@ __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush
 }
 
 // ---- FSAI preconditioner, z = G^T (G r) --------------------------------------
-// An FSAI iteration is k_pupdate<PRE=1>, k_spmm, k_fsai_tr (r -= alpha q and
-// t = G r in one pass), then on refresh iterations only k_xflush, k_refresh_f
-// and k_fsai_t<1> (t from the true residual), and k_fsai_z (z = G^T t, the dots
-// r.z and r.r, end of the iteration).
+// With t = G r the PCG dot is r.z = r^T G^T G r = t.t, so it is known as soon
+// as t is; z itself is needed only for p = z + beta p.  An FSAI iteration is
+//   k_spmm     q = A p, partials of p.q -> alpha
+//   k_fsai_tr  r -= alpha q and t = G r in one pass, the dots t.t and r.r ->
+//              beta, convergence (skipped on refresh iterations)
+//   k_xflush, k_refresh_f, k_fsai_t<1>  (refresh iterations) y += alpha p,
+//              r = b - A y, t = G r with the dots
+//   k_fsai_zp  z = G^T t fused with p = z + beta p and the delayed y +=
+//              alpha p_prev (z is never stored)
+// and a solve starts with k_pcg_init<PRE = 1>, k_fsai_t<0>, k_fsai_zp.
 
-// Residual replacement without dots (k_fsai_z makes them); it overwrites the
-// residual that k_fsai_tr has just written.
+// Residual replacement without dots (k_fsai_t<1> makes them); it writes the
+// buffer of the new residual (k_fsai_tr does not run on refresh iterations).
 template <typename T, int D>
 __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
     if (!*(volatile int *)&a.ctl->refresh_now) return;
@@ -1013,7 +1107,8 @@ __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
 
 // In FSAI mode the residual is double-buffered: during iteration k (k =
 // ctl->iter) the current residual is r2[k & 1] and the new one is written to
-// r2[(k + 1) & 1]; k_fsai_z ends the iteration by incrementing k.
+// r2[(k + 1) & 1]; the finisher of k_fsai_tr (k_fsai_t<1> on refresh
+// iterations) ends the iteration by incrementing k.
 
 // acc += sum of g_k * v(j_k) over the slots k in [lo, hi) among the CH slots
 // from k0 on (k0 a multiple of 4; 16-byte slot loads, slots outside the range
@@ -1053,13 +1148,24 @@ __device__ __forceinline__ void gslot_chunk(const int *__restrict__ col, const T
 }
 
 // The FSAI gather kernels are latency-bound: 5 resident blocks of kBlock per SM
-// (48 registers a thread) with up to 2 columns a lane, 4 with 4 columns.
-// k_fsai_tr and k_fsai_t on 12-slot fixed rows fit 40 registers without
-// spilling and run 6 blocks (k_fsai_z, which also accumulates two dots,
-// measured slower there and keeps 5).
-template <typename T, int D, int LEN = 0>
+// (48 registers a thread) with up to 2 columns a lane, 4 with 4 columns; 6
+// (40 registers) for the 12-slot fixed rows with up to 2 columns a lane
+// (LEN6 = true: k_fsai_zp, which fits there without spilling; k_fsai_tr,
+// with the second gather and the dots, does not).
+template <typename T, int D, int LEN = 0, bool LEN6 = false>
 constexpr int gather_min_blocks() {
-    return SubWarp<T, D>::V * (int)sizeof(T) >= 16 ? 4 : (LEN == 12 ? 6 : 5);
+    return SubWarp<T, D>::V * (int)sizeof(T) >= 16 ? 4 : (LEN6 && LEN == 12 ? 6 : 5);
+}
+
+// End of an FSAI iteration (or of the start of a solve) from the dots
+// tot = [t.t | r.r]: warp 0 of the last block.
+template <typename T>
+__device__ void fsai_finish(const PcgArgs<T> &a, const BlockSeg &bsg, const double *tot, int D, bool start) {
+    PcgCtl *ctl = a.ctl;
+    finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, start, ctl->iter + 1);
+    if (threadIdx.x == 0 && !start) ctl->iter += 1;
+    __syncwarp();
+    finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
 }
 
 // All slots in [lo, hi): chunks of kGChunk = 8 slots (the 6 lower or upper
@@ -1077,22 +1183,22 @@ __device__ __forceinline__ void gslot_range(const int *__restrict__ col, const T
 
 // acc += sum of g_k * v(j_k) over the slots k in [P0, P1) of a row with
 // compile-time positions (uniform-length rows; padding slots carry g = 0):
-// 16-byte loads of the slot groups covering the range, then the gathers.
+// exact-range slot loads, then the gathers.
 template <typename T, int D, int V, int P0, int P1, bool QS>
 __device__ __forceinline__ void gslot_fixed(const int *__restrict__ col, const T *__restrict__ gs, int64_t base,
                                             int c0, const T *__restrict__ src, const T *__restrict__ qsrc,
                                             const T (&al)[V], T (&acc)[V]) {
-    constexpr int A0 = P0 & ~3, A1 = (P1 + 3) & ~3, NG = A1 - A0, NS = P1 - P0;
-    int jj[NG];
-    T gv[NG];
-    load_slots<T, NG>(col, gs, base, A0, A1, 0, jj, gv);
+    constexpr int NS = P1 - P0;
+    int jj[NS];
+    T gv[NS];
+    load_slot_range<T, P0, P1>(col, gs, base, jj, gv);
     T vj[NS][V];
 #pragma unroll
-    for (int u = 0; u < NS; ++u) ldv<T, V>(src + (int64_t)jj[P0 - A0 + u] * D + c0, vj[u]);
+    for (int u = 0; u < NS; ++u) ldv<T, V>(src + (int64_t)jj[u] * D + c0, vj[u]);
     if constexpr (QS) {
         T qj[NS][V];
 #pragma unroll
-        for (int u = 0; u < NS; ++u) ldv<T, V>(qsrc + (int64_t)jj[P0 - A0 + u] * D + c0, qj[u]);
+        for (int u = 0; u < NS; ++u) ldv<T, V>(qsrc + (int64_t)jj[u] * D + c0, qj[u]);
 #pragma unroll
         for (int u = 0; u < NS; ++u)
 #pragma unroll
@@ -1101,20 +1207,25 @@ __device__ __forceinline__ void gslot_fixed(const int *__restrict__ col, const T
 #pragma unroll
     for (int u = 0; u < NS; ++u)
 #pragma unroll
-        for (int k = 0; k < V; ++k) acc[k] = fma(gv[P0 - A0 + u], vj[u][k], acc[k]);
+        for (int k = 0; k < V; ++k) acc[k] = fma(gv[u], vj[u][k], acc[k]);
 }
 
 // r' = r - alpha q and t = G r' in one pass: r' is recomputed at each
 // gathered lower neighbour from the old r and q (the same FMA its owner
-// uses), the owner writes its r' to the other buffer.
+// uses), the owner writes its r' to the other buffer; then the dots t.t
+// (= r'.z') and r'.r' and the end of the iteration.  On refresh iterations
+// it does nothing (k_refresh_f and k_fsai_t<1> make r and t).
 // LEN > 0: uniform rows of LEN slots, lower slots at positions [0, LEN/2).
 template <typename T, int D, int LEN>
-__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN>())) k_fsai_tr(PcgArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
+    if (ctl->refresh_now) return;
     __shared__ T salpha[D];  // FSAI runs on one segment
     if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
     __syncthreads();
+    __shared__ DF sq_sh[sqsum_slots<T, 2, SubWarp<T, D>::V>()];
+    SqSum<T, 2, SubWarp<T, D>::V> sq(sq_sh);  // t.t (= r.z) | r.r
     const int par = ctl->iter & 1;
     const T *__restrict__ rold = a.r2[par];
     T *__restrict__ rnew = a.r2[1 - par];
@@ -1141,17 +1252,30 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN>())) k_fs
         else
             gslot_range<T, D, V, true>(a.A.col, a.gslot, base, len, 0, a.kb[i], (int)i, c0, rold, a.q, al, acc);
         stv<T, V>(a.t + i * D + c0, acc);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            sq.add(0, k, acc[k], acc[k]);
+            sq.add(1, k, ri[k], ri[k]);
+        }
+        sq.row_done();
     }
+    sq.finish();
+    __shared__ double tot[2 * D];
+    if (grid_sum_cols<T, D, 2>(sq.acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot))
+        if (threadIdx.x < 32) fsai_finish(a, bsg, tot, D, false);
 }
 
-// t = G r: t_i = G_ii r_i + sum over the lower slots (j < i) of G_ij r_j.
-// MODE 0: at the start of a solve (residual in r2[0]); MODE 1: only after a
-// residual refresh (residual in the new buffer).
+// t = G r: t_i = G_ii r_i + sum over the lower slots (j < i) of G_ij r_j, with
+// the dots t.t (= r.z) and r.r.  MODE 0: the start of a solve (residual in
+// r2[0]); MODE 1: only after a residual refresh (residual in the new buffer),
+// ending the iteration.
 template <typename T, int D, int MODE, int LEN>
-__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN>())) k_fsai_t(PcgArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
     if (MODE == 1 && !*(volatile int *)&a.ctl->refresh_now) return;
     const T *__restrict__ rsrc = MODE == 0 ? a.r2[0] : a.r2[(a.ctl->iter + 1) & 1];
+    __shared__ DF sq_sh[sqsum_slots<T, 2, SubWarp<T, D>::V>()];
+    SqSum<T, 2, SubWarp<T, D>::V> sq(sq_sh);  // t.t (= r.z) | r.r
     PFE_ROW_LOOP(T, D) {
         PFE_ROW_I;
         const int c0 = lm.cg * V;
@@ -1170,33 +1294,44 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN>())) k_fs
             gslot_range<T, D, V, false>(a.A.col, a.gslot, base, len, 0, a.kb[i], (int)i, c0, rsrc, nullptr, nal,
                                         acc);
         stv<T, V>(a.t + i * D + c0, acc);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            sq.add(0, k, acc[k], acc[k]);
+            sq.add(1, k, ri[k], ri[k]);
+        }
+        sq.row_done();
     }
+    sq.finish();
+    __shared__ double tot[2 * D];
+    if (grid_sum_cols<T, D, 2>(sq.acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot))
+        if (threadIdx.x < 32) fsai_finish(a, bsg, tot, D, MODE == 0);
 }
 
-// z = G^T t: z_i = G_ii t_i + sum over the upper slots (j > i) of G_ji t_j,
-// then the dots r.z, r.r; the last block ends the iteration (or the start of
-// the solve) and decides whether the next iteration refreshes r.
+// z = G^T t (z_i = G_ii t_i + sum over the upper slots (j > i) of G_ji t_j)
+// fused with the direction update p = z + beta p (p = z at the start of a
+// solve) and the delayed solution update y += alpha p_prev, all in place on
+// the row's own entries; z is never stored.  Block 0 also decides whether the
+// next iteration refreshes the residual.
 template <typename T, int D, int LEN>
-__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_z(PcgArgs<T> a) {
-    if (*(volatile int *)&a.ctl->done) return;
-    // the residual of this iteration: r2[0] at the start of a solve, else the
-    // buffer k_fsai_tr (or k_refresh_f) wrote
-    const T *__restrict__ rcur = a.ctl->zstart ? a.r2[0] : a.r2[(a.ctl->iter + 1) & 1];
-    using A = Acc<T>;
-    using AT = typename A::type;
-    using SWt = SubWarp<T, D>;
-    AT acc2[2][SWt::V];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int k = 0; k < SWt::V; ++k) acc2[q][k] = A::zero();
+__global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())) k_fsai_zp(PcgArgs<T> a) {
+    PcgCtl *ctl = a.ctl;
+    if (*(volatile int *)&ctl->done) return;
+    const int p_ready = ctl->p_ready, xpending = ctl->xpending;
+    __shared__ T sbeta[D], salpha[D];
+    if (threadIdx.x < D) {
+        sbeta[threadIdx.x] = p_ready ? T(0) : (T)a.sc.beta[threadIdx.x];
+        salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        ctl->refresh_now = (ctl->refresh > 0 && ((ctl->iter + 1) % ctl->refresh) == 0) ? 1 : 0;
+    __syncthreads();
     PFE_ROW_LOOP(T, D) {
         PFE_ROW_I;
         const int c0 = lm.cg * V;
         int64_t base;
         int len;
         sell_row(a.A.slice_ptr, a.A.row_len, i, base, len);
-        T acc[V], ti[V], ri[V];
+        T acc[V], ti[V], pv[V];
         const T nal[V] = {};
         ldv<T, V>(a.t + i * D + c0, ti);
         const T gd = a.gdiag[i];
@@ -1207,29 +1342,21 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_z(
         else
             gslot_range<T, D, V, false>(a.A.col, a.gslot, base, len, a.kb[i], len, (int)i, c0, a.t, nullptr, nal,
                                         acc);
-        stv<T, V>(a.z + i * D + c0, acc);
-        ldv<T, V>(rcur + i * D + c0, ri);
+        const int64_t ic = i * D + c0;
+        ldv_rw<T, V>(a.p[0] + ic, pv);
+        if (xpending) {
+            T xh[V];
+            float xl[V] = {};
+            ldv_rw<T, V>(a.x + ic, xh);
+            if constexpr (std::is_same_v<T, float>) ldv_rw<float, V>(a.xlo + ic, xl);
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
-            A::add_prod(acc2[0][k], ri[k], acc[k]);
-            A::add_prod(acc2[1][k], ri[k], ri[k]);
+            for (int k = 0; k < V; ++k) axpy_hilo<T>(xh[k], xl[k], salpha[c0 + k], pv[k]);
+            stv<T, V>(a.x + ic, xh);
+            if constexpr (std::is_same_v<T, float>) stv<float, V>(a.xlo + ic, xl);
         }
-    }
-    __shared__ double tot[2 * D];
-    if (grid_sum_cols<T, D, 2>(acc2, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot)) {
-        if (threadIdx.x < 32) {
-            PcgCtl *ctl = a.ctl;
-            const bool start = ctl->zstart != 0;
-            finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, start, ctl->iter + 1);
-            if (threadIdx.x == 0) {
-                ctl->zstart = 0;  // FSAI: one problem (its last block finishes the iteration)
-                if (!start) ctl->iter += 1;
-            }
-            __syncwarp();
-            finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
-            if (threadIdx.x == 0)
-                ctl->refresh_now = (ctl->refresh > 0 && ((ctl->iter + 1) % ctl->refresh) == 0) ? 1 : 0;
-        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) pv[k] = p_ready ? acc[k] : acc[k] + sbeta[c0 + k] * pv[k];
+        stv<T, V>(a.p[0] + ic, pv);
     }
 }
 
@@ -1325,7 +1452,6 @@ PcgArgs<T> pcg_args(pfe_ctx *c, PcgLaunch L) {
     a.sc = c->sc;
     a.cond = L.cond;
     a.use_cond = L.use_cond;
-    a.z = (T *)c->fsai.z;
     a.t = (T *)c->fsai.t;
     a.r2[0] = a.r;
     a.r2[1] = (T *)c->fsai.r1;
@@ -1376,7 +1502,7 @@ void init_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a) {
 template <typename T, int D, bool MS>
 void body_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int iters) {
     for (int u = 0; u < iters; ++u) {
-        k_pupdate<T, D, 0, MS><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0, MS>, flat_need<T, D>(c), flat_mult<T, D>()),
+        k_pupdate<T, D, MS><<<wave_grid(c, G_PUPD, k_pupdate<T, D, MS>, flat_need<T, D>(c), flat_mult<T, D>()),
                                  kBlock, 0, s>>>(a);
         launch_spmm<T, D, MS>(c, s, a);
         k_update<T, D, MS><<<wave_grid(c, G_UPDATE, k_update<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
@@ -1387,7 +1513,7 @@ void body_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int iters) {
 
 // The FSAI kernels with the compile-time row length of the layout (FP32 grid
 // graphs of radius 2 or 3; else the general kernels).
-// which: 0 = k_fsai_tr, 1 = k_fsai_t (start of a solve), 2 = k_fsai_t (after a refresh), 3 = k_fsai_z
+// which: 0 = k_fsai_tr, 1 = k_fsai_t (start of a solve), 2 = k_fsai_t (after a refresh), 3 = k_fsai_zp
 template <typename T, int D, int LEN>
 void fsai_kernels_len(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int which) {
     if (which == 0)
@@ -1398,7 +1524,7 @@ void fsai_kernels_len(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int which
         k_fsai_t<T, D, 1, LEN><<<wave_grid(c, G_FSAI_T1, k_fsai_t<T, D, 1, LEN>, rows_need<T, D>(c)), kBlock, 0, s>>>(
             a);
     else
-        k_fsai_z<T, D, LEN><<<wave_grid(c, G_FSAI_Z, k_fsai_z<T, D, LEN>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        k_fsai_zp<T, D, LEN><<<wave_grid(c, G_FSAI_ZP, k_fsai_zp<T, D, LEN>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
 }
 template <typename T, int D>
 void launch_fsai(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int which) {
@@ -1439,9 +1565,6 @@ pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
     if constexpr (std::is_same_v<T, float>) {
         if (use_fsai<T>(c)) {
             for (int u = 0; u < iters; ++u) {
-                k_pupdate<T, D, 1, false><<<wave_grid(c, G_PUPD_F, k_pupdate<T, D, 1, false>, flat_need<T, D>(c),
-                                                      flat_mult<T, D>()),
-                                            kBlock, 0, s>>>(a);
                 launch_spmm<T, D, false>(c, s, a);
                 launch_fsai<T, D>(c, s, a, 0);
                 k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c)), kBlock, 0,
@@ -1486,7 +1609,7 @@ pfe_status apply_T(pfe_ctx *c, cudaStream_t s, const void *x, void *y) {
 // control block (every column active, a steady-state iteration: direction
 // update and delayed solution update both on) and scratch copies of y, r and
 // the direction buffers, so the iteration state is left as it was.
-// which: 0 = k_spmm, 1 = k_update, 2 = k_pupdate, 3 = k_fsai_tr, 4 = k_fsai_z.
+// which: 0 = k_spmm, 1 = k_update, 2 = k_pupdate, 3 = k_fsai_tr, 4 = k_fsai_zp.
 template <typename T, int D>
 pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, int variant) {
     PcgCtl h;
@@ -1519,13 +1642,13 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
         return PFE_EUNSUPPORTED;
     }
     PcgCtl *dctl = nullptr;
-    T *xs = nullptr, *rs = nullptr, *p0 = nullptr, *p1 = nullptr, *r1s = nullptr, *ts = nullptr, *zs = nullptr;
+    T *xs = nullptr, *rs = nullptr, *p0 = nullptr, *p1 = nullptr, *r1s = nullptr, *ts = nullptr;
     float *xls = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     pfe_status st = PFE_OK;
     auto cleanup = [&]() {
         for (void *q : {(void *)dctl, (void *)xs, (void *)rs, (void *)p0, (void *)p1, (void *)xls, (void *)r1s,
-                        (void *)ts, (void *)zs, dsc})
+                        (void *)ts, dsc})
             if (q) cudaFree(q);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
@@ -1536,8 +1659,7 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
         cudaMalloc((void **)&p1, nd * sizeof(T)) != cudaSuccess ||
         (std::is_same_v<T, float> && cudaMalloc((void **)&xls, nd * sizeof(float)) != cudaSuccess) ||
         (fsai && (cudaMalloc((void **)&r1s, nd * sizeof(T)) != cudaSuccess ||
-                  cudaMalloc((void **)&ts, nd * sizeof(T)) != cudaSuccess ||
-                  cudaMalloc((void **)&zs, nd * sizeof(T)) != cudaSuccess))) {
+                  cudaMalloc((void **)&ts, nd * sizeof(T)) != cudaSuccess))) {
         cudaGetLastError();
         cleanup();
         c->err = "pfe_time_kernel: scratch allocation failed";
@@ -1554,7 +1676,6 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
     a.r2[0] = rs;
     a.r2[1] = r1s;
     a.t = ts;
-    a.z = zs;
     cudaMemcpyAsync(dctl, &h, sizeof(h), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dsc, hsc.data(), sc_bytes, cudaMemcpyHostToDevice, s);
     if (fsai) {
@@ -1579,11 +1700,11 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
         else if (which == 1)
             k_update<T, D, false><<<wave_grid(c, G_UPDATE, k_update<T, D, false>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
         else if (which == 2 && multi)
-            k_pupdate<T, D, 0, true><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0, true>, flat_need<T, D>(c),
+            k_pupdate<T, D, true><<<wave_grid(c, G_PUPD, k_pupdate<T, D, true>, flat_need<T, D>(c),
                                                  flat_mult<T, D>()),
                                        kBlock, 0, s>>>(a);
         else if (which == 2)
-            k_pupdate<T, D, 0, false><<<wave_grid(c, G_PUPD, k_pupdate<T, D, 0, false>, flat_need<T, D>(c),
+            k_pupdate<T, D, false><<<wave_grid(c, G_PUPD, k_pupdate<T, D, false>, flat_need<T, D>(c),
                                                   flat_mult<T, D>()),
                                         kBlock, 0, s>>>(a);
         else if constexpr (std::is_same_v<T, float>) {

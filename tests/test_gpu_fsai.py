@@ -97,3 +97,27 @@ def test_classical_fsai_matches_oracle_and_cuts_iterations():
     assert st["converged"] and st["pcg_iters"] < it_jacobi
     assert relerr(Y, O.DirectSolver(g.A)(R)[0]) < 1e-4
     p.close()
+
+
+@pytest.mark.parametrize("radius", [2.0, 3.0])
+def test_fsai_pcg_iterations_match_oracle(radius):
+    """PCG with M^-1 = G^T G for the classical FSAI factor: the number of
+    iterations the GPU needs to reach the tolerance (its r.z taken as |G r|^2)
+    against the oracle's FP64 PCG with the same G (r.z taken directly), and
+    the solutions.  Radius 2 and 3 run the fixed-row kernels of 12 and 28 slots."""
+    spec = small_spec(H=31, W=29, d=3, radius=radius)
+    p, X, Y0 = gpu_problem(spec, "mixed", tol=1e-6)
+    g = oracle_graph(spec, X)
+    p.init(Y0)
+    p.fsai_classical()
+    G = F.classical_fsai(g.A).tocsr()
+    rng = np.random.default_rng(23)
+    R = rng.standard_normal((g.n, 3))
+    Y = np.zeros_like(R)
+    st = p.solve_system(R, Y)
+    Yo, info = O.pcg(g.A, R, np.zeros_like(R), 1e-6, 5000, 50, lambda Rm: F.fsai_apply(G, Rm))
+    assert st["converged"] and info["converged"]
+    # FP32 vectors against FP64: the counts may differ by a step or two
+    assert abs(st["pcg_iters"] - int(info["iters"].max())) <= 2, (st["pcg_iters"], info["iters"])
+    assert relerr(Y, Yo) < 1e-4
+    p.close()
