@@ -461,13 +461,17 @@ def main():
     fsai_k = {}
     if args.precond == "learned":
         # lower (upper) slots: FP32 G value + int32 column each, kb and G_ii per row;
-        # t = G r': r, q in, r', t out; z = G^T t with p = z + beta p and
-        # y += alpha p: t in, p and y (hi, lo) in and out
-        tr_ms, zp_ms = p.time_kernel("fsai_tr", 20), p.time_kernel("fsai_zp", 20)
+        # t = G r': r, q in, r', t out; z = G^T t with p_new = z + beta p: t
+        # and p in, p_new out, and every other iteration y += alpha_prev
+        # p_prev + alpha p: p_prev and y (hi, lo) in, y out
+        tr_ms = p.time_kernel("fsai_tr", 20)
+        zf_ms, zh_ms = p.time_kernel("fsai_zp", 20), p.time_kernel("fsai_zp_hold", 20)
         tr_b = 4 * (nnz - n) + 8 * n + 16 * n * d
-        zp_b = 4 * (nnz - n) + 8 * n + 28 * n * d
+        zh_b = 4 * (nnz - n) + 8 * n + 12 * n * d
+        zf_b = zh_b + 20 * n * d
         fsai_k = {"k_fsai_tr_ms": round(tr_ms, 5), "k_fsai_tr_GBps": round(tr_b / (tr_ms * 1e-3) / 1e9, 1),
-                  "k_fsai_zp_ms": round(zp_ms, 5), "k_fsai_zp_GBps": round(zp_b / (zp_ms * 1e-3) / 1e9, 1)}
+                  "k_fsai_zp_fold_ms": round(zf_ms, 5), "k_fsai_zp_fold_GBps": round(zf_b / (zf_ms * 1e-3) / 1e9, 1),
+                  "k_fsai_zp_hold_ms": round(zh_ms, 5), "k_fsai_zp_hold_GBps": round(zh_b / (zh_ms * 1e-3) / 1e9, 1)}
     # FP32 values + int32 indices of A, p in, q out: 8 nnz_A + 4 (n + 1) + 2 * 4 n d
     spmm_bytes = 8 * nnz + 4 * (n + 1) + 2 * 4 * n * d
     peaks = measured_peaks()

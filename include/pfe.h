@@ -388,8 +388,12 @@ PFE_API pfe_status pfe_solve_system(pfe_ctx *c, const double *RHS, double *Y, pf
  *   PFE_KERNEL_PUPDATE  p = D_A^{-1} r + beta p with the delayed y += alpha p
  *   PFE_KERNEL_FSAI_TR  r -= alpha q fused with t = G r and the column dots
  *                       t.t (= r.z) and r.r (FSAI preconditioner set)
- *   PFE_KERNEL_FSAI_ZP  z = G^T t fused with p = z + beta p and the delayed
- *                       y += alpha p; z is not stored (FSAI preconditioner set)
+ *   PFE_KERNEL_FSAI_ZP  z = G^T t fused with p_new = z + beta p and the two
+ *                       delayed solution updates y += alpha_prev p_prev +
+ *                       alpha p (every other iteration); z is not stored
+ *                       (FSAI preconditioner set)
+ *   PFE_KERNEL_FSAI_ZP_HOLD  the same launch on the other iterations, which
+ *                       hold the solution update (no pass over y)
  * The iteration state is not modified (scratch copies and a scratch control
  * block are used; the edge pass rewrites the same right-hand side).  Only
  * the PCG direction p and product q, which every solve re-initialises, are
@@ -403,7 +407,8 @@ enum {
     PFE_KERNEL_EDGE = 2,
     PFE_KERNEL_PUPDATE = 3,
     PFE_KERNEL_FSAI_TR = 4,
-    PFE_KERNEL_FSAI_ZP = 5
+    PFE_KERNEL_FSAI_ZP = 5,
+    PFE_KERNEL_FSAI_ZP_HOLD = 6
 };
 PFE_API pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_ms);
 

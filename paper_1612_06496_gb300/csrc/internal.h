@@ -29,6 +29,7 @@ struct Segs {
 // last block of a segment in a reduction kernel.
 struct SegScal {
     double *bnorm, *rz, *alpha, *beta, *relres;  // nseg * d
+    double *alpha_prev;                           // nseg * d: alpha of a held solution update (FSAI)
     int *active;                                  // nseg * d: column still iterating
     int *seg_active;                              // nseg: any column of the segment iterating
     int *seg_iters;                               // nseg: iterations of the segment in this solve
@@ -53,11 +54,11 @@ struct PcgCtl {
     double max_relres, last_relres;
     int last_converged, unroll;       // unroll: iterations per graph body / host poll
     long long launches;               // PCG kernel launches (early-exited ones included)
-    int pbuf;                         // which direction buffer holds the current p
+    int xheld;                        // FSAI: y += alpha_prev p_prev of the iteration before is also pending
     int p_ready;                      // 1: p was just set by k_pcg_init (no update in k_spmm)
     int xpending;                     // 1: y += alpha p of the last k_spmm not yet applied
     int launch_base, launch_per_iter; // kernel launches outside / per iteration of the loop
-    int pad2;
+    int xfold;                        // FSAI: this iteration's k_fsai_zp applies both pending updates
 };
 
 // Control block of the P-step (Alg. 1 steps 6-7).  G, T and evals are

@@ -661,6 +661,8 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(PcgArgs<T> a) {
                     ctl->refresh_now = 0;
                     ctl->p_ready = 1;
                     ctl->xpending = 0;
+                    ctl->xheld = 0;
+                    ctl->xfold = 0;
                     if (PRE != 0) ctl->done = 0;  // k_fsai_t finishes the start
                 }
                 __syncwarp();
@@ -815,7 +817,7 @@ __global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
     using A = Acc<T>;
     using AT = typename A::type;
     using SWt = SubWarp<T, D>;
-    const T *__restrict__ pp = a.p[0];
+    const T *__restrict__ pp = a.p[ctl->iter & 1];  // FSAI alternates the buffers
     AT pq[1][SWt::V];
 #pragma unroll
     for (int k = 0; k < SWt::V; ++k) pq[0][k] = A::zero();
@@ -863,7 +865,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_spmm_fixed(PcgArgs<T> a) {
     using SW = SubWarp<T, D>;
     constexpr int V = SW::V;
     static_assert(LEN % 4 == 0, "rows are read 4 slots at a time");
-    const T *__restrict__ pp = a.p[0];
+    const T *__restrict__ pp = a.p[ctl->iter & 1];  // FSAI alternates the buffers
     AT pq[1][V];
 #pragma unroll
     for (int k = 0; k < V; ++k) pq[0][k] = A::zero();
@@ -1042,30 +1044,43 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
 template <typename T, int D, bool MS>
 __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush) {
     const PcgCtl *ctl = a.ctl;
-    if (!*(volatile const int *)&ctl->xpending) return;
+    const int xp = *(volatile const int *)&ctl->xpending, xh = *(volatile const int *)&ctl->xheld;
+    if (!xp && !xh) return;
     if (!final_flush && !*(volatile const int *)&ctl->refresh_now) return;
     constexpr bool multi = MS;
-    __shared__ T salpha[D];
-    if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
+    __shared__ T salpha[D], salpha_prev[D];
+    if (threadIdx.x < D) {
+        salpha[threadIdx.x] = xp ? (T)a.sc.alpha[threadIdx.x] : T(0);
+        salpha_prev[threadIdx.x] = (T)a.sc.alpha_prev[threadIdx.x];  // held updates: one problem (FSAI)
+    }
     __syncthreads();
-    const T *__restrict__ pc = a.p[0];
+    // the direction of the last k_spmm (FSAI: buffer iter & 1 before the
+    // iteration's finisher counted it, the other one after) and the one before
+    const int kc = final_flush ? ((ctl->iter & 1) ^ 1) : (ctl->iter & 1);
+    const T *__restrict__ pc = a.p[kc];
+    const T *__restrict__ pprev = a.p[kc ^ 1];
     const int64_t nel = a.A.n * D;
     for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < nel; e += (int64_t)gridDim.x * kBlock) {
-        T xh = a.x[e];
+        T xv = a.x[e];
         float xl = 0.f;
         if constexpr (std::is_same_v<T, float>) xl = a.xlo[e];
         const int c = (int)(e % D);
-        const T al = multi ? (T)a.sc.alpha[__ldg(a.sg.rseg + e / D) * D + c] : salpha[c];
-        axpy_hilo<T>(xh, xl, al, pc[e]);
-        a.x[e] = xh;
+        if (xh) axpy_hilo<T>(xv, xl, salpha_prev[c], pprev[e]);
+        if (xp) {
+            const T al = multi ? (T)a.sc.alpha[__ldg(a.sg.rseg + e / D) * D + c] : salpha[c];
+            axpy_hilo<T>(xv, xl, al, pc[e]);
+        }
+        a.x[e] = xv;
         if constexpr (std::is_same_v<T, float>) a.xlo[e] = xl;
     }
-    // the flag is cleared by whoever reads it next: k_refresh's last block, or
+    // the flags are cleared by whoever reads them next: k_refresh's last
+    // block (xpending) and the finisher of the refresh iteration (xheld), or
     // k_pcg_init of the next solve
     if (final_flush) {
         if (last_block_arrives(&a.ctl->ticket[3])) {
             if (threadIdx.x == 0) {
                 a.ctl->xpending = 0;
+                a.ctl->xheld = 0;
                 a.ctl->ticket[3] = 0u;
             }
         }
@@ -1158,14 +1173,37 @@ constexpr int gather_min_blocks() {
 }
 
 // End of an FSAI iteration (or of the start of a solve) from the dots
-// tot = [t.t | r.r]: warp 0 of the last block.
+// tot = [t.t | r.r]: warp 0 of the last block.  MODE 0: start of a solve,
+// 1: a refresh iteration (k_xflush applied every pending update), 2: an
+// ordinary iteration.
+// The solution update y += alpha p of an ordinary iteration is held and
+// applied together with the next one (y += alpha_prev p_prev + alpha p in
+// one pass of k_fsai_zp, the directions in alternating buffers): the hi/lo
+// solution is read and written every other iteration.  Once the solve is
+// done the held state stays for the final k_xflush.
 template <typename T>
-__device__ void fsai_finish(const PcgArgs<T> &a, const BlockSeg &bsg, const double *tot, int D, bool start) {
+__device__ void fsai_finish(const PcgArgs<T> &a, const BlockSeg &bsg, const double *tot, int D, int mode) {
     PcgCtl *ctl = a.ctl;
-    finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, start, ctl->iter + 1);
-    if (threadIdx.x == 0 && !start) ctl->iter += 1;
+    finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, mode == 0, ctl->iter + 1);
+    if (threadIdx.x == 0 && mode != 0) ctl->iter += 1;
     __syncwarp();
     finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
+    int hold = 0;
+    if (threadIdx.x == 0) {
+        if (mode != 2) {
+            ctl->xheld = 0;
+            ctl->xfold = 0;
+        } else if (!ctl->done) {
+            const int fold = ctl->xheld;
+            ctl->xfold = fold;
+            ctl->xheld = !fold;
+            hold = !fold;
+        }
+    }
+    hold = __shfl_sync(kFull, hold, 0);
+    if (hold)
+        for (int c = threadIdx.x; c < D; c += 32) a.sc.alpha_prev[c] = a.sc.alpha[c];
+    __syncwarp();
 }
 
 // All slots in [lo, hi): chunks of kGChunk = 8 slots (the 6 lower or upper
@@ -1262,7 +1300,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr
     sq.finish();
     __shared__ double tot[2 * D];
     if (grid_sum_cols<T, D, 2>(sq.acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot))
-        if (threadIdx.x < 32) fsai_finish(a, bsg, tot, D, false);
+        if (threadIdx.x < 32) fsai_finish(a, bsg, tot, D, 2);
 }
 
 // t = G r: t_i = G_ii r_i + sum over the lower slots (j < i) of G_ij r_j, with
@@ -1304,23 +1342,30 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(
     sq.finish();
     __shared__ double tot[2 * D];
     if (grid_sum_cols<T, D, 2>(sq.acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot))
-        if (threadIdx.x < 32) fsai_finish(a, bsg, tot, D, MODE == 0);
+        if (threadIdx.x < 32) fsai_finish(a, bsg, tot, D, MODE == 0 ? 0 : 1);
 }
 
 // z = G^T t (z_i = G_ii t_i + sum over the upper slots (j > i) of G_ji t_j)
-// fused with the direction update p = z + beta p (p = z at the start of a
-// solve) and the delayed solution update y += alpha p_prev, all in place on
-// the row's own entries; z is never stored.  Block 0 also decides whether the
+// fused with the direction update p_new = z + beta p (p = z at the start of a
+// solve) into the other direction buffer, and on folding iterations the two
+// pending solution updates y += alpha_prev p_prev + alpha p (p_prev is the
+// old content of the buffer p_new goes to); each thread reads and writes only
+// its row's own entries; z is never stored.  Block 0 also decides whether the
 // next iteration refreshes the residual.
 template <typename T, int D, int LEN>
 __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())) k_fsai_zp(PcgArgs<T> a) {
     PcgCtl *ctl = a.ctl;
     if (*(volatile int *)&ctl->done) return;
-    const int p_ready = ctl->p_ready, xpending = ctl->xpending;
-    __shared__ T sbeta[D], salpha[D];
+    const int p_ready = ctl->p_ready, fold = ctl->xpending && ctl->xfold;
+    // p of this iteration in buffer iter & 1 before the finisher counted the
+    // iteration (at the start of a solve: no old p), the new one in the other
+    T *__restrict__ pdst = a.p[ctl->iter & 1];
+    const T *__restrict__ psrc = a.p[(ctl->iter & 1) ^ 1];
+    __shared__ T sbeta[D], salpha[D], salpha_prev[D];
     if (threadIdx.x < D) {
         sbeta[threadIdx.x] = p_ready ? T(0) : (T)a.sc.beta[threadIdx.x];
         salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
+        salpha_prev[threadIdx.x] = (T)a.sc.alpha_prev[threadIdx.x];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0)
         ctl->refresh_now = (ctl->refresh > 0 && ((ctl->iter + 1) % ctl->refresh) == 0) ? 1 : 0;
@@ -1331,7 +1376,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())
         int64_t base;
         int len;
         sell_row(a.A.slice_ptr, a.A.row_len, i, base, len);
-        T acc[V], ti[V], pv[V];
+        T acc[V], ti[V], pv[V] = {};
         const T nal[V] = {};
         ldv<T, V>(a.t + i * D + c0, ti);
         const T gd = a.gdiag[i];
@@ -1343,20 +1388,24 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())
             gslot_range<T, D, V, false>(a.A.col, a.gslot, base, len, a.kb[i], len, (int)i, c0, a.t, nullptr, nal,
                                         acc);
         const int64_t ic = i * D + c0;
-        ldv_rw<T, V>(a.p[0] + ic, pv);
-        if (xpending) {
-            T xh[V];
+        if (!p_ready) ldv_rw<T, V>(psrc + ic, pv);
+        if (fold) {
+            T xh[V], pp[V];
             float xl[V] = {};
+            ldv_rw<T, V>(pdst + ic, pp);
             ldv_rw<T, V>(a.x + ic, xh);
             if constexpr (std::is_same_v<T, float>) ldv_rw<float, V>(a.xlo + ic, xl);
 #pragma unroll
-            for (int k = 0; k < V; ++k) axpy_hilo<T>(xh[k], xl[k], salpha[c0 + k], pv[k]);
+            for (int k = 0; k < V; ++k) {
+                axpy_hilo<T>(xh[k], xl[k], salpha_prev[c0 + k], pp[k]);
+                axpy_hilo<T>(xh[k], xl[k], salpha[c0 + k], pv[k]);
+            }
             stv<T, V>(a.x + ic, xh);
             if constexpr (std::is_same_v<T, float>) stv<float, V>(a.xlo + ic, xl);
         }
 #pragma unroll
         for (int k = 0; k < V; ++k) pv[k] = p_ready ? acc[k] : acc[k] + sbeta[c0 + k] * pv[k];
-        stv<T, V>(a.p[0] + ic, pv);
+        stv<T, V>(pdst + ic, pv);
     }
 }
 
@@ -1443,7 +1492,8 @@ PcgArgs<T> pcg_args(pfe_ctx *c, PcgLaunch L) {
     a.xlo = c->wk.Ylo;
     a.r = (T *)c->wk.R;
     a.p[0] = (T *)c->wk.Pd;
-    a.p[1] = (T *)c->wk.Pd;
+    // FSAI (float path) alternates the direction buffers
+    a.p[1] = (std::is_same_v<T, float> && c->fsai.enabled) ? (T *)c->wk.Pd2 : (T *)c->wk.Pd;
     a.q = (T *)c->wk.Q;
     a.b = (const T *)c->wk.RHS;
     a.part = c->wk.partials;
@@ -1609,7 +1659,8 @@ pfe_status apply_T(pfe_ctx *c, cudaStream_t s, const void *x, void *y) {
 // control block (every column active, a steady-state iteration: direction
 // update and delayed solution update both on) and scratch copies of y, r and
 // the direction buffers, so the iteration state is left as it was.
-// which: 0 = k_spmm, 1 = k_update, 2 = k_pupdate, 3 = k_fsai_tr, 4 = k_fsai_zp.
+// which: 0 = k_spmm, 1 = k_update, 2 = k_pupdate, 3 = k_fsai_tr, 4 = k_fsai_zp
+// folding two solution updates, 5 = k_fsai_zp holding one.
 template <typename T, int D>
 pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, int variant) {
     PcgCtl h;
@@ -1619,6 +1670,7 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
     h.tol = 0.0;
     h.p_ready = 0;
     h.xpending = 1;
+    h.xfold = which == 4 ? 1 : 0;
     // scratch per-segment scalars: every column active
     const int nseg = c->nseg;
     const size_t sc_bytes = segscal_bytes(nseg, D);
@@ -1708,7 +1760,7 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
                                                   flat_mult<T, D>()),
                                         kBlock, 0, s>>>(a);
         else if constexpr (std::is_same_v<T, float>) {
-            launch_fsai<T, D>(c, s, a, which == 3 ? 0 : 3);
+            launch_fsai<T, D>(c, s, a, which == 3 ? 0 : 3);  // 4, 5: k_fsai_zp
         }
     };
     launch();  // warm-up
