@@ -202,9 +202,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload: str, kernel: str, units_full: float) -> float | None:
+def ncu_traffic(workload: str, kernel: str, units_full: float, variant: int | None = None) -> float | None:
     """DRAM bytes per launch from the committed ncu summary, scaled to the
-    full launch; None when the kernel source changed since the capture."""
+    full launch; None when the kernel source changed since the capture or
+    the capture was of another kernel variant than the one timed."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -215,6 +216,8 @@ def ncu_traffic(workload: str, kernel: str, units_full: float) -> float | None:
                 k, v = ln.split("=", 1)
                 kv[k.strip()] = v.strip()
     if kv.get("kernel_sha") != kernel_source_hash():
+        return None
+    if variant is not None and "variant" in kv and kv["variant"] != str(variant):
         return None
     try:
         return float(kv["dram_bytes_per_launch"]) * units_full / float(kv["units"])
@@ -472,14 +475,24 @@ def main():
         fsai_k = {"k_fsai_tr_ms": round(tr_ms, 5), "k_fsai_tr_GBps": round(tr_b / (tr_ms * 1e-3) / 1e9, 1),
                   "k_fsai_zp_fold_ms": round(zf_ms, 5), "k_fsai_zp_fold_GBps": round(zf_b / (zf_ms * 1e-3) / 1e9, 1),
                   "k_fsai_zp_hold_ms": round(zh_ms, 5), "k_fsai_zp_hold_GBps": round(zh_b / (zh_ms * 1e-3) / 1e9, 1)}
-    # FP32 values + int32 indices of A, p in, q out: 8 nnz_A + 4 (n + 1) + 2 * 4 n d
-    spmm_bytes = 8 * nnz + 4 * (n + 1) + 2 * 4 * n * d
+    # the SpMM variant the autotuner chose for this arm
+    variant = tuned.get("mixed/" + args.precond, (0, {}))[0]
+    kname = {0: "k_spmm", 1: "k_spmm_fixed", 2: "k_spmm_fixed", 3: "k_spmm_fixed", 4: "k_spmm_tma",
+             5: "k_spmm_stencil"}.get(variant, "k_spmm")
+    if variant == 5:
+        # stencil form: FP32 value of every nonzero (no column index, no row
+        # pointer), p in, q out: 4 nnz_A + 2 * 4 n d
+        spmm_bytes = 4 * nnz + 2 * 4 * n * d
+    else:
+        # FP32 values + int32 indices of A, p in, q out: 8 nnz_A + 4 (n + 1) + 2 * 4 n d
+        spmm_bytes = 8 * nnz + 4 * (n + 1) + 2 * 4 * n * d
     peaks = measured_peaks()
     achieved = spmm_bytes / (spmm_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_spmm<float,%d>" % d, "achieved": round(achieved, 1),
+    roofline = {"bound": "hbm", "kernel": "%s<float,%d> (SpMM variant %d)" % (kname, d, variant),
+                "achieved": round(achieved, 1),
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                 "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": ncu_traffic(args.workload, "spmm", nnz),
+                "traffic": ncu_traffic(args.workload, "spmm", nnz, variant),
                 "algorithmic_bytes_per_launch": spmm_bytes, "avg_launch_ms": round(spmm_ms, 5),
                 "launches_in_timed_region": rounds,
                 "share_of_timed_region": round(rounds * spmm_ms / ms, 4),

@@ -214,7 +214,13 @@ enum {
     PFE_SPMM_ROW1 = 1,    /* uniform rows: one row group per step, >= 6 blocks per SM */
     PFE_SPMM_ROW2 = 2,    /* uniform rows: two row groups per step, >= 5 blocks per SM */
     PFE_SPMM_ROW2_4 = 3,  /* uniform rows: two row groups per step, >= 4 blocks per SM */
-    PFE_SPMM_NVARIANTS = 4
+    PFE_SPMM_TMA = 4,     /* uniform rows: the slots of tiles of rows staged in shared memory by
+                             bulk asynchronous (TMA) copies, two tiles ahead (one problem only) */
+    PFE_SPMM_STENCIL = 5, /* one grid image: the stencil form; a block walks a strip of the image
+                             down, a ring of row bands of p and the rows' matrix values staged
+                             in shared memory (cp.async, several rows ahead); the column array
+                             is not read and no gather leaves the SM */
+    PFE_SPMM_NVARIANTS = 6
 };
 enum { PFE_TUNE_SPMM = 0 };
 PFE_API pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms);

@@ -444,6 +444,10 @@ static bool spmm_variant_applies(const pfe_ctx *c, int v) {
     if (v == PFE_SPMM_GENERAL) return true;
     if (!c->mixed || v <= 0 || v >= PFE_SPMM_NVARIANTS) return false;
     if (c->nseg > 1) return v == PFE_SPMM_ROW1 && c->g.row_len == 12;  // batches: one row group per step
+    // the stencil form: one grid image whose rows start on 16-byte boundaries
+    if (v == PFE_SPMM_STENCIL &&
+        (c->kind != PFE_GRAPH_GRID || c->W < 1 || c->W % 4 != 0 || stencil_strip(c->d, c->g.row_len, kStencilSteps) == 0))
+        return false;
     return c->g.row_len == 12 || c->g.row_len == 28;
 }
 

@@ -297,8 +297,29 @@ __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
 enum GridSlot {
     G_INIT = 0, G_INIT_F, G_PUPD, G_SPMM, G_UPDATE, G_FSAI_TR, G_XFLUSH, G_REFRESH, G_REFRESH_F,
     G_FSAI_T, G_FSAI_T1, G_FSAI_ZP, G_APPLY, G_EDGE, G_PAPPLY, G_TIME_SPMM, G_TIME_UPDATE, G_SPMM_F1, G_SPMM_F2,
-    G_SPMM_F3, G_NSLOTS
+    G_SPMM_F3, G_SPMM_TMA, G_SPMM_STENCIL, G_NSLOTS
 };
+// Strip width of the stencil SpMM pipeline for d columns, rows of len
+// slots (radius 2: 12, radius 3: 28) and p steps in flight: the widest
+// multiple of 4 of whole row groups of the float sub-warp mapping (V = 4, 2
+// or 1 columns a lane) up to one pass of kWarps warps whose shared memory
+// (a ring of 2R + 1 + p row bands, p + 1 rows of matrix values and
+// diagonal) fits 41 KB with every copy 16-byte aligned; 0 if none does.
+constexpr int kStencilSteps = 3;  // steps of the stencil SpMM pipeline in flight (5 measured slower)
+constexpr int stencil_strip(int d, int len, int p) {
+    const int r = len == 12 ? 2 : 3;
+    const int v = d % 4 == 0 ? 4 : (d % 2 == 0 ? 2 : 1);
+    const int rpw = 32 / (d / v);
+    const int q = d % 4 == 0 ? 1 : (d % 2 == 0 ? 2 : 4);  // pixels per 16 bytes
+    const int padl = (r % q == 0) ? 0 : q - r % q;
+    for (int ts = kWarps * rpw; ts >= rpw; ts -= rpw) {
+        const int brows = (ts + 2 * r + padl + q - 1 + q - 1) / q * q;
+        const int bytes = 4 * ((2 * r + 1 + p) * brows * d + (p + 1) * ts * len + (p + 1) * ts);
+        if (ts % 4 == 0 && bytes <= 41 * 1024) return ts;
+    }
+    return 0;
+}
+
 inline Segs seg_view(const pfe_ctx *c) { return Segs{c->nseg, c->g.n, c->seg_off, c->rseg}; }
 
 // One allocation holds every array of a SegScal: bytes needed, and the

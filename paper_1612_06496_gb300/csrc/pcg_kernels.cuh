@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace pfe {
 namespace pcgk {
@@ -60,6 +61,7 @@ struct PcgArgs {
     SegScal sc;  // per-segment scalars [seg * D + c]
     cudaGraphConditionalHandle cond;
     int use_cond;
+    int grid_w;  // width of the image of a one-image grid graph (0 otherwise)
     // FSAI preconditioner (float path): t = G r; the residual alternates
     // between r2[0] (= r) and r2[1]
     T *t;
@@ -912,6 +914,371 @@ __global__ void __launch_bounds__(kBlock, MINB) k_spmm_fixed(PcgArgs<T> a) {
         if (threadIdx.x < 32) spmm_finish<T, D, MS>(a, bsg, tot);
 }
 
+// k_spmm for fixed-length rows with the matrix slots staged in shared
+// memory by bulk asynchronous copies.  The block walks tiles of TR rows (its
+// tiles t, t + gridDim.x, ...); S tiles are requested ahead, so every SM
+// keeps S x (its blocks) x TR x LEN x 8 bytes of the slot stream in flight
+// while its warps gather p, and a warp's row no longer waits for its slot
+// loads before it can gather.  One barrier per tile (it also releases the
+// previous tile's stage for refilling).  One problem (no segments).
+template <typename T, int D, int LEN, int S>
+struct SpmmTma {
+    // rows per tile (one pass of the block's warps at d = 10; any d works,
+    // some warps idle where a pass holds more rows).  Small tiles leave most
+    // of the SM's unified L1/shared memory to L1, which the gathers of p hit.
+    static constexpr int TR = 48;
+    static constexpr int STAGE = 2 * TR * LEN * 4;  // bytes: columns, then values
+    static constexpr int SMEM = S * STAGE;
+};
+
+template <typename T, int D, int LEN, int S, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_spmm_tma(PcgArgs<T> a) {
+    static_assert(sizeof(T) == 4 && LEN % 4 == 0, "FP32 rows of a multiple of 4 slots (16-byte copies)");
+    using P = SpmmTma<T, D, LEN, S>;
+    const PcgCtl *ctl = a.ctl;
+    if (*(volatile const int *)&ctl->done) return;
+    extern __shared__ __align__(16) unsigned char smem_tiles[];
+    __shared__ __align__(8) uint64_t bars[S];
+    using A = Acc<T>;
+    using AT = typename A::type;
+    using SW = SubWarp<T, D>;
+    constexpr int V = SW::V;
+    const T *__restrict__ pp = a.p[ctl->iter & 1];  // FSAI alternates the buffers
+    AT pq[1][V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) pq[0][k] = A::zero();
+    const SW lm;
+    const BlockSeg bsg = block_seg<false>(a.sg);
+    const int64_t n = bsg.r1 - bsg.r0;
+    const int64_t ntiles = (n + P::TR - 1) / P::TR;
+    const int64_t nmine = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int warp = threadIdx.x >> 5;
+    const int c0 = lm.cg * V;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S; ++q) mbar_init(&bars[q], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    // thread 0: request this block's tile k into stage k % S (sizes and
+    // offsets are multiples of LEN * 4 bytes, a multiple of 16)
+    auto issue = [&](int64_t k) {
+        const int64_t r0 = bsg.r0 + ((int64_t)blockIdx.x + k * gridDim.x) * P::TR;
+        const uint32_t bytes = (uint32_t)(min((int64_t)P::TR, bsg.r1 - r0) * LEN * 4);
+        unsigned char *st = smem_tiles + (int)(k % S) * P::STAGE;
+        uint64_t *bar = &bars[k % S];
+        mbar_arrive_expect_tx(bar, 2 * bytes);
+        bulk_copy_g2s(st, a.A.col + r0 * LEN, bytes, bar);
+        bulk_copy_g2s(st + P::STAGE / 2, a.A.aoff + r0 * LEN, bytes, bar);
+    };
+    if (threadIdx.x == 0)
+        for (int64_t k = 0; k < S && k < nmine; ++k) issue(k);
+    int64_t k = 0;
+    bool failed = false;
+    for (; k < nmine; ++k) {
+        const int st = (int)(k % S);
+        const bool got = mbar_wait(&bars[st], (uint32_t)((k / S) & 1));
+        // every thread's wait result; every thread is also done with tile
+        // k - 1, whose stage is refilled
+        if (__syncthreads_or(!got)) {
+            failed = true;
+            break;
+        }
+        if (threadIdx.x == 0 && k >= 1 && k - 1 + S < nmine) issue(k - 1 + S);
+        const int64_t r0 = bsg.r0 + ((int64_t)blockIdx.x + k * gridDim.x) * P::TR;
+        const int rows = (int)min((int64_t)P::TR, bsg.r1 - r0);
+        const int *__restrict__ cs = reinterpret_cast<const int *>(smem_tiles + st * P::STAGE);
+        const T *__restrict__ vs = reinterpret_cast<const T *>(smem_tiles + st * P::STAGE + P::STAGE / 2);
+        for (int g = warp; g * SW::RPW < rows; g += kWarps) {
+            const int il = g * SW::RPW + lm.r;
+            if (!lm.active || il >= rows) continue;
+            const int64_t i = r0 + il;
+            int jj[LEN];
+            T av[LEN];
+#pragma unroll
+            for (int g4 = 0; g4 < LEN / 4; ++g4) {
+                const int4 cv = *reinterpret_cast<const int4 *>(cs + il * LEN + 4 * g4);
+                const float4 vv = *reinterpret_cast<const float4 *>(vs + il * LEN + 4 * g4);
+                jj[4 * g4] = cv.x; jj[4 * g4 + 1] = cv.y; jj[4 * g4 + 2] = cv.z; jj[4 * g4 + 3] = cv.w;
+                av[4 * g4] = vv.x; av[4 * g4 + 1] = vv.y; av[4 * g4 + 2] = vv.z; av[4 * g4 + 3] = vv.w;
+            }
+            const int64_t ic = i * D + c0;
+            T pi[V], acc[V], pj[LEN][V];
+            ldv<T, V>(pp + ic, pi);
+            const T ad = a.A.adiag[i];
+#pragma unroll
+            for (int q = 0; q < V; ++q) acc[q] = ad * pi[q];
+#pragma unroll
+            for (int u = 0; u < LEN; ++u) ldv<T, V>(pp + (int64_t)jj[u] * D + c0, pj[u]);
+#pragma unroll
+            for (int u = 0; u < LEN; ++u)
+#pragma unroll
+                for (int q = 0; q < V; ++q) acc[q] = fma(av[u], pj[u][q], acc[q]);
+            stv<T, V>(a.q + ic, acc);
+#pragma unroll
+            for (int q = 0; q < V; ++q) A::add_prod(pq[0][q], pi[q], acc[q]);
+        }
+    }
+    if (failed) {
+        // report, then let the copies this block requested land before it
+        // leaves (each wait bounded); the partials still go to the reduction
+        if (threadIdx.x == 0) atomicMax(&a.ctl->error, (int)PFE_ETIMEOUT);
+        const int64_t refills = max((int64_t)0, min(k - 1, nmine - (int64_t)S));
+        const int64_t issued = min(nmine, (int64_t)S) + refills;
+        for (int64_t j = k; j < issued; ++j) mbar_wait(&bars[j % S], (uint32_t)((j / S) & 1));
+    }
+    __shared__ double tot[D];
+    if (grid_sum_cols<T, D, 1>(pq, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 0], tot))
+        if (threadIdx.x < 32) spmm_finish<T, D, false>(a, bsg, tot);
+}
+
+// Stencil of a grid graph with fixed slot positions: slot t of every row is
+// the t-th offset (dy, dx), 0 < dx^2 + dy^2 <= R^2, in (dy, dx) order (the
+// order the graph builder lists them); 12 slots at radius 2, 28 at radius 3.
+template <int LEN>
+struct Stencil {
+    static constexpr int R = LEN == 12 ? 2 : 3;
+    int dx[LEN], dy[LEN];
+};
+template <int LEN>
+constexpr Stencil<LEN> make_stencil() {
+    Stencil<LEN> st{};
+    constexpr int R = Stencil<LEN>::R;
+    int k = 0;
+    for (int y = -R; y <= R; ++y)
+        for (int x = -R; x <= R; ++x)
+            if (x * x + y * y > 0 && x * x + y * y <= R * R && k < LEN) {
+                st.dy[k] = y;
+                st.dx[k] = x;
+                ++k;
+            }
+    return st;
+}
+template <int LEN>
+constexpr int stencil_count() {
+    constexpr int R = Stencil<LEN>::R;
+    int k = 0;
+    for (int y = -R; y <= R; ++y)
+        for (int x = -R; x <= R; ++x) k += (x * x + y * y > 0 && x * x + y * y <= R * R) ? 1 : 0;
+    return k;
+}
+
+__device__ __forceinline__ void cp_async_8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait_newest() {  // all but the N newest groups have landed
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Layout of the stencil pipeline of a one-image grid graph of width W: the
+// image is cut into vertical strips of TS pixels (the last one narrower) and
+// each strip into chunks of image rows; a block walks a chunk top to bottom,
+// one image row (a step: up to TS pixels, one pass of its warps) at a time.
+// A ring of NSLOT = 2R + 1 + P bands holds image rows y - R .. y + R of the
+// vector, each band the strip's pixels plus R (and PADL, for alignment) on
+// the left and R (plus rounding) on the right; the next P steps' bands, matrix
+// values and diagonals are in flight as bulk asynchronous (TMA) copies that
+// one thread requests, completing on one mbarrier per step (P + 1 of them,
+// reused).  Every vector element and matrix value is copied from memory once
+// per chunk (plus halo rows and columns) and every stencil neighbour is read
+// from shared memory at a compile-time offset.
+// Needs W * D, W, TS and TS * D multiples of 4 (16-byte aligned copies).
+template <typename T, int D, int LEN, int P>
+struct StencilPipe {
+    static constexpr int R = Stencil<LEN>::R;
+    static constexpr int NSLOT = 2 * R + 1 + P, NBAR = P + 1;
+    static constexpr int RPW = SubWarp<T, D>::RPW;
+    // pixels per 16 bytes of a row of D floats
+    static constexpr int Q = D % 4 == 0 ? 1 : (D % 2 == 0 ? 2 : 4);
+    // left pad so a band starts on a 16-byte boundary: ((R + PADL) D) % 4 == 0
+    static constexpr int PADL = (R % Q == 0) ? 0 : Q - R % Q;
+    static constexpr int brows(int ts) { return (ts + 2 * R + PADL + Q - 1 + Q - 1) / Q * Q; }
+    static constexpr int TS = stencil_strip(D, LEN, P);  // 0: no aligned layout fits
+    static constexpr int BROWS = brows(TS);
+    static constexpr int SMEM = 4 * (NSLOT * BROWS * D + NBAR * TS * LEN + NBAR * TS);
+    static constexpr bool kAligned = TS > 0 && TS % 4 == 0 && (TS * D) % 4 == 0;
+};
+
+// k_spmm for a one-image grid graph in the stencil form: q_i = A_ii p_i +
+// sum over the slots t of A_i,t p(i + dy_t W + dx_t), every neighbour read
+// from the band ring (the column array is not read: the neighbour of slot t
+// is a compile-time offset in its band, and padding slots have A_i,t = 0,
+// with pixels outside the image zero-filled).  Summation in slot order: the
+// same results as k_spmm_fixed.  nchunk: chunks per strip (the host makes
+// strips x chunks <= the grid).  A wait that runs out sets PFE_ETIMEOUT,
+// lets the copies already requested land (bounded) and skips the rest.
+template <typename T, int D, int LEN, int P, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_spmm_stencil(PcgArgs<T> a, int nchunk) {
+    static_assert(sizeof(T) == 4 && LEN % 4 == 0 && stencil_count<LEN>() == LEN, "FP32 stencil rows");
+    using SP = StencilPipe<T, D, LEN, P>;
+    static_assert(SP::kAligned, "strip width");
+    constexpr int R = SP::R, TS = SP::TS, NSLOT = SP::NSLOT, NBAR = SP::NBAR, BROWS = SP::BROWS;
+    constexpr int PADL = SP::PADL, Q = SP::Q;
+    constexpr Stencil<LEN> stn = make_stencil<LEN>();
+    const PcgCtl *ctl = a.ctl;
+    if (*(volatile const int *)&ctl->done) return;
+    extern __shared__ __align__(16) float pipe_smem[];
+    __shared__ __align__(8) uint64_t bars[NBAR];
+    float *band = pipe_smem;                 // NSLOT x BROWS x D
+    float *aof = band + NSLOT * BROWS * D;   // NBAR x TS x LEN
+    float *adg = aof + NBAR * TS * LEN;      // NBAR x TS
+    using A = Acc<T>;
+    using AT = typename A::type;
+    using SW = SubWarp<T, D>;
+    constexpr int V = SW::V;
+    const T *__restrict__ pp = a.p[ctl->iter & 1];  // FSAI alternates the buffers
+    AT pq[1][V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) pq[0][k] = A::zero();
+    const SW lm;
+    const BlockSeg bsg = block_seg<false>(a.sg);
+    const int64_t n = bsg.r1, W = a.grid_w, H = n / W;
+    const int64_t NS = (W + TS - 1) / TS, units = NS * (int64_t)nchunk, CH = (H + nchunk - 1) / nchunk;
+    const int il = (threadIdx.x >> 5) * SW::RPW + lm.r;  // this lane's pixel of a step
+    const int c0 = lm.cg * V;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NBAR; ++b) mbar_init(&bars[b], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    uint32_t phase = 0;  // bit b: parity of barrier b's next phase (the same in every thread)
+    bool failed = false;
+    for (int64_t u = blockIdx.x; u < units && !failed; u += gridDim.x) {
+        const int64_t x0 = (u % NS) * TS, y0 = (u / NS) * CH;
+        const int w = (int)min((int64_t)TS, W - x0);
+        const int64_t L = min(H, y0 + CH) - y0;  // steps (image rows) of this chunk
+        if (L <= 0) continue;
+        const int m = (w + 2 * R + PADL + Q - 1) / Q * Q;  // pixels copied per band
+        // band k: image row y0 - R + k, pixels from x0 - R - PADL (at the image's
+        // left and right edges these wrap into the next or previous row: read
+        // only by padding slots), into slot k % NSLOT; [lo, hi) is the part in
+        // [0, n) (the rest is zero-filled)
+        auto band_span = [&](int64_t k, int64_t &jb, int64_t &lo, int64_t &hi) {
+            jb = (y0 - R + k) * W + x0 - R - PADL;
+            lo = max(jb, (int64_t)0);
+            hi = max(lo, min(jb + m, n));
+        };
+        // thread 0: request step q's group (bands kb0 .. q + 2R, row data of
+        // image row y0 + q) on bars[q % NBAR]
+        auto issue = [&](int64_t q, int64_t kb0) {
+            uint64_t *bar = &bars[q % NBAR];
+            const int64_t pix0 = (y0 + q) * W + x0;
+            uint32_t bytes = (uint32_t)w * (LEN + 1) * 4;
+            for (int64_t k = kb0; k <= q + 2 * R; ++k) {
+                int64_t jb, lo, hi;
+                band_span(k, jb, lo, hi);
+                bytes += (uint32_t)((hi - lo) * D * 4);
+            }
+            mbar_arrive_expect_tx(bar, bytes);
+            // order the block's earlier generic writes to these slots (zero
+            // fills) before the copies' writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int64_t k = kb0; k <= q + 2 * R; ++k) {
+                int64_t jb, lo, hi;
+                band_span(k, jb, lo, hi);
+                if (hi > lo)
+                    bulk_copy_g2s(band + (int)(k % NSLOT) * BROWS * D + (lo - jb) * D, pp + lo * D,
+                                  (uint32_t)((hi - lo) * D * 4), bar);
+            }
+            const int slot = (int)(q % NBAR);
+            bulk_copy_g2s(aof + slot * TS * LEN, a.A.aoff + pix0 * LEN, (uint32_t)w * LEN * 4, bar);
+            bulk_copy_g2s(adg + slot * TS, a.A.adiag + pix0, (uint32_t)w * 4, bar);
+        };
+        // every thread: zero the parts of bands kb0 .. q + 2R outside [0, n)
+        auto zero_clipped = [&](int64_t q, int64_t kb0) {
+            for (int64_t k = kb0; k <= q + 2 * R; ++k) {
+                int64_t jb, lo, hi;
+                band_span(k, jb, lo, hi);
+                if (lo == jb && hi == jb + m) continue;
+                float *dst = band + (int)(k % NSLOT) * BROWS * D;
+                for (int e = threadIdx.x; e < m * D; e += kBlock) {
+                    const int64_t j = jb + e / D;
+                    if (j < lo || j >= hi) dst[e] = 0.f;
+                }
+            }
+        };
+        const int64_t npro = min(L, (int64_t)P);
+        zero_clipped(0, 0);
+        for (int64_t q = 1; q < npro; ++q) zero_clipped(q, q + 2 * R);
+        if (threadIdx.x == 0) {
+            issue(0, 0);
+            for (int64_t q = 1; q < npro; ++q) issue(q, q + 2 * R);
+        }
+        int st = 0;
+        const bool lane_on = lm.active && il < w;
+        const int lane_off = (il + R + PADL) * D + c0;  // the lane's pixel (dx = 0) within a band slot
+        T *qrow = a.q + ((y0 * W + x0 + il) * D + c0);              // its output row at step 0
+        for (; st < (int)L; ++st) {
+            const int b = st % NBAR;
+            // thread 0 waits for step st's copies; the block barrier then also
+            // means every thread is done with step st - 1, whose band slot,
+            // row-data slot and barrier are reused; every other thread then
+            // observes the completed phase itself (no spinning)
+            bool got = true;
+            if (threadIdx.x == 0) got = mbar_wait(&bars[b], (phase >> b) & 1u);
+            if (__syncthreads_or(!got)) {
+                failed = true;
+                break;
+            }
+            if (threadIdx.x != 0) mbar_wait(&bars[b], (phase >> b) & 1u);
+            phase ^= 1u << b;
+            if (st + P < L) {
+                zero_clipped(st + P, st + P + 2 * R);
+                if (threadIdx.x == 0) issue(st + P, st + P + 2 * R);
+            }
+            if (lane_on) {
+                const float *av = aof + b * TS * LEN + il * LEN;
+                const T ad = adg[b * TS + il];
+                // the 2R + 1 bands of this step (image rows y - R .. y + R), as
+                // 32-bit offsets into shared memory
+                int bo[2 * R + 1];
+#pragma unroll
+                for (int k = 0; k <= 2 * R; ++k) bo[k] = ((st + k) % NSLOT) * (BROWS * D) + lane_off;
+                T pi[V], acc[V];
+#pragma unroll
+                for (int q = 0; q < V; ++q) pi[q] = band[bo[R] + q];
+#pragma unroll
+                for (int q = 0; q < V; ++q) acc[q] = ad * pi[q];
+#pragma unroll
+                for (int g4 = 0; g4 < LEN / 4; ++g4) {
+                    const float4 a4 = *reinterpret_cast<const float4 *>(av + 4 * g4);
+                    const float aw[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int t = 4 * g4 + h;
+                        const int o = bo[stn.dy[t] + R] + stn.dx[t] * D;
+#pragma unroll
+                        for (int q = 0; q < V; ++q) acc[q] = fma(aw[h], band[o + q], acc[q]);
+                    }
+                }
+                stv<T, V>(qrow, acc);
+#pragma unroll
+                for (int q = 0; q < V; ++q) A::add_prod(pq[0][q], pi[q], acc[q]);
+            }
+            qrow += W * D;
+        }
+        if (failed) {
+            // report; let the groups already requested (steps st .. min(L, st + P) - 1) land
+            if (threadIdx.x == 0) atomicMax(&a.ctl->error, (int)PFE_ETIMEOUT);
+            for (int64_t g = st; g < min(L, (int64_t)st + P); ++g) {
+                const int b = (int)(g % NBAR);
+                mbar_wait(&bars[b], (phase >> b) & 1u);
+                phase ^= 1u << b;
+            }
+        }
+        __syncthreads();  // the next chunk refills every buffer
+    }
+    __shared__ double tot[D];
+    if (grid_sum_cols<T, D, 1>(pq, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 0], tot))
+        if (threadIdx.x < 32) spmm_finish<T, D, false>(a, bsg, tot);
+}
+
 template <typename T, int D>
 int64_t rows_need(const pfe_ctx *c);
 
@@ -921,11 +1288,53 @@ int64_t rows_need(const pfe_ctx *c);
 //   PFE_SPMM_ROW1     fixed row length, one row group per step, >= 6 blocks/SM
 //   PFE_SPMM_ROW2     fixed row length, two row groups per step, >= 5 blocks/SM
 //   PFE_SPMM_ROW2_4   fixed row length, two row groups per step, >= 4 blocks/SM
+//   PFE_SPMM_TMA      fixed row length, slots of row tiles staged by bulk copies
+//   PFE_SPMM_STENCIL  one grid image: stencil form, p and A staged by a ring of row bands
 // Fixed-length variants exist for the FP32 single-problem path at radius 2
 // and 3 (12 and 28 slots) and, one row group per step, for FP32 batches at
 // radius 2; elsewhere the general kernel runs.
 template <typename T, int D, bool MS, int LEN>
 bool launch_spmm_fixed(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int v) {
+    if constexpr (!MS) {
+        if (v == PFE_SPMM_STENCIL) {
+            constexpr int P = kStencilSteps;
+            using SP = StencilPipe<T, D, LEN, P>;
+            if constexpr (SP::kAligned) {
+                constexpr int MB = 4;  // 64 registers: the pipeline bookkeeping and the row math stay in registers
+                auto kern = k_spmm_stencil<T, D, LEN, P, MB>;
+                const int64_t W = c->W, H = c->g.n / W, NS = (W + SP::TS - 1) / SP::TS;
+                int &grid = c->kgrid[G_SPMM_STENCIL];
+                if (grid == 0) {
+                    // dynamic shared memory past the default 48 KB less the kernel's static arrays
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SP::SMEM);
+                    int occ = 0;
+                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, SP::SMEM) != cudaSuccess ||
+                        occ < 1) {
+                        cudaGetLastError();
+                        occ = 1;
+                    }
+                    const int64_t maxb = (int64_t)occ * c->num_sms;
+                    const int64_t nch = std::max<int64_t>(1, std::min<int64_t>(H, maxb / NS));
+                    grid = (int)std::min<int64_t>(maxb, NS * nch);
+                }
+                const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(H, grid / NS));
+                kern<<<grid, kBlock, SP::SMEM, s>>>(a, nchunk);
+                return true;
+            }
+        }
+        if (v == PFE_SPMM_TMA) {
+            constexpr int S = 2;
+            using P = SpmmTma<T, D, LEN, S>;
+            // with the kernel's static arrays (block reduction, < 8 KB) within
+            // the 48 KB a block gets without opting in
+            static_assert(P::SMEM <= 40 * 1024, "shared-memory budget");
+            const int64_t ntiles = (c->g.n + P::TR - 1) / P::TR;
+            constexpr int MB = SubWarp<T, D>::V * (int)sizeof(T) >= 16 ? 4 : 6;  // 40 registers up to 2 columns a lane
+            k_spmm_tma<T, D, LEN, S, MB><<<wave_grid(c, G_SPMM_TMA, k_spmm_tma<T, D, LEN, S, MB>, ntiles, 1, P::SMEM),
+                                           kBlock, P::SMEM, s>>>(a);
+            return true;
+        }
+    }
     if (v == PFE_SPMM_ROW1)
         k_spmm_fixed<T, D, MS, LEN, 1, 6><<<wave_grid(c, G_SPMM_F1, k_spmm_fixed<T, D, MS, LEN, 1, 6>,
                                                       rows_need<T, D>(c)),
@@ -1502,6 +1911,7 @@ PcgArgs<T> pcg_args(pfe_ctx *c, PcgLaunch L) {
     a.sc = c->sc;
     a.cond = L.cond;
     a.use_cond = L.use_cond;
+    a.grid_w = (c->kind == PFE_GRAPH_GRID && c->nseg == 1) ? (int)c->W : 0;
     a.t = (T *)c->fsai.t;
     a.r2[0] = a.r;
     a.r2[1] = (T *)c->fsai.r1;

@@ -5,12 +5,12 @@ import pytest
 
 from oracle import pfe_oracle as O
 from synth import CONFIGS
-from tests.gpu_common import gpu_problem, oracle_graph, relerr
+from tests.gpu_common import gpu_problem, oracle_graph, relerr, small_spec
 
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_spmm_variants_match_oracle(variant):
     spec = CONFIGS["C1"]  # radius 2: 12 slots per row, the fixed-length kernels apply
     p, X, Y0 = gpu_problem(spec, "mixed")
@@ -29,7 +29,7 @@ def test_autotune_chooses_an_applicable_variant():
     p, X, Y0 = gpu_problem(spec, "mixed")
     p.init(Y0)
     choice, ms = p.autotune(5)
-    assert set(ms) == {0, 1, 2, 3} and all(t > 0 for t in ms.values())
+    assert set(ms) == {0, 1, 2, 3, 4, 5} and all(t > 0 for t in ms.values())
     assert ms[choice] == min(ms.values())
     st = p.solve(1, 2)
     assert st["n_unconverged"] == 0
@@ -40,3 +40,42 @@ def test_autotune_chooses_an_applicable_variant():
     choice, ms = q.autotune(3)
     assert choice == 0 and list(ms) == [0]
     q.close()
+
+
+@pytest.mark.parametrize("H,W,d,radius", [(23, 20, 3, 2.0), (29, 32, 4, 3.0), (64, 64, 10, 2.0), (7, 132, 10, 3.0),
+                                          (41, 100, 10, 2.0)])
+def test_stencil_spmm_equals_fixed_spmm_bitwise(H, W, d, radius):
+    """The stencil-form SpMM (a ring of row bands of p and the rows' matrix
+    values staged by bulk copies; no column array) adds the same products in
+    the same order as the fixed-length kernel: whole solves agree bit for
+    bit (odd d: a left pad for 16-byte alignment; d = 4: four columns a
+    lane; a 7-row image: bands clipped at both ends; W = 100: a narrower
+    last strip)."""
+    spec = small_spec(H=H, W=W, d=d, radius=radius)
+    out = []
+    for variant in (1, 5):
+        p, X, Y0 = gpu_problem(spec, "mixed")
+        p.init(Y0)
+        p.set_variant(variant)
+        Y = np.empty_like(Y0)
+        st = p.solve(2, 3, Y, None)
+        assert st["n_unconverged"] == 0
+        out.append(Y)
+        p.close()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_stencil_spmm_needs_aligned_rows():
+    """Image rows that do not start on 16-byte boundaries (W % 4 != 0) leave
+    the stencil SpMM out: choosing it is PFE_EUNSUPPORTED, the autotuner
+    skips it."""
+    from paper_1612_06496_gb300 import PFEError
+    spec = small_spec(H=16, W=18, d=5)
+    p, X, Y0 = gpu_problem(spec, "mixed")
+    p.init(Y0)
+    with pytest.raises(PFEError) as ei:
+        p.set_variant(5)
+    assert ei.value.status == 8
+    choice, ms = p.autotune(3)
+    assert 5 not in ms and choice != 5
+    p.close()
