@@ -196,7 +196,7 @@ def measured_peaks() -> dict:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("pcg_kernels.cuh", "common.cuh"):
+    for f in ("pcg_kernels.cuh", "common.cuh", "tma.cuh"):
         with open(os.path.join(ROOT, "paper_1612_06496_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -486,20 +486,36 @@ def main():
     else:
         # FP32 values + int32 indices of A, p in, q out: 8 nnz_A + 4 (n + 1) + 2 * 4 n d
         spmm_bytes = 8 * nnz + 4 * (n + 1) + 2 * 4 * n * d
+    upd_b, pup_b = 3 * 4 * n * d + 4 * n, 7 * 4 * n * d + 4 * n
+    # candidates for the dominant kernel of the PCG iteration: (name, traffic
+    # key, ms per launch, algorithmic bytes per launch); one launch each per
+    # iteration (k_fsai_zp: folding and holding launches alternate)
+    cands = [("%s<float,%d> (SpMM variant %d)" % (kname, d, variant), "spmm", spmm_ms, spmm_bytes)]
+    if args.precond == "learned":
+        cands += [("k_fsai_tr<float,%d>" % d, "fsai_tr", tr_ms, tr_b),
+                  ("k_fsai_zp<float,%d> (folding and holding launches averaged)" % d, "fsai_zp",
+                   0.5 * (zf_ms + zh_ms), 0.5 * (zf_b + zh_b))]
+    else:
+        cands += [("k_update<float,%d>" % d, "update", upd_ms, upd_b),
+                  ("k_pupdate<float,%d>" % d, "pupdate", pup_ms, pup_b)]
+    dom_name, dom_key, dom_ms, dom_bytes = max(cands, key=lambda c: c[2])
     peaks = measured_peaks()
-    achieved = spmm_bytes / (spmm_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "%s<float,%d> (SpMM variant %d)" % (kname, d, variant),
-                "achieved": round(achieved, 1),
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1),
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                 "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": ncu_traffic(args.workload, "spmm", nnz, variant),
-                "algorithmic_bytes_per_launch": spmm_bytes, "avg_launch_ms": round(spmm_ms, 5),
+                "traffic": ncu_traffic(args.workload, dom_key, nnz, variant if dom_key == "spmm" else None),
+                "algorithmic_bytes_per_launch": int(dom_bytes), "avg_launch_ms": round(dom_ms, 5),
                 "launches_in_timed_region": rounds,
-                "share_of_timed_region": round(rounds * spmm_ms / ms, 4),
+                "share_of_timed_region": round(rounds * dom_ms / ms, 4),
+                "spmm": {"kernel": cands[0][0], "ms": round(spmm_ms, 5), "algorithmic_bytes": spmm_bytes,
+                         "GBps": round(spmm_bytes / (spmm_ms * 1e-3) / 1e9, 1),
+                         "share_of_timed_region": round(rounds * spmm_ms / ms, 4),
+                         "traffic": ncu_traffic(args.workload, "spmm", nnz, variant)},
                 "other_kernels": {"k_update_ms": round(upd_ms, 5),
-                                  "k_update_GBps": round((3 * 4 * n * d + 4 * n) / (upd_ms * 1e-3) / 1e9, 1),
+                                  "k_update_GBps": round(upd_b / (upd_ms * 1e-3) / 1e9, 1),
                                   "k_pupdate_ms": round(pup_ms, 5),
-                                  "k_pupdate_GBps": round((7 * 4 * n * d + 4 * n) / (pup_ms * 1e-3) / 1e9, 1),
+                                  "k_pupdate_GBps": round(pup_b / (pup_ms * 1e-3) / 1e9, 1),
                                   "k_edge_ms": round(edge_ms, 5),
                                   # b read + written (FP32), w, column + edge id per directed slot, Y, C in, RHS out
                                   "k_edge_GBps": round((8 * d * ne + 4 * ne + 8 * 2 * ne + 12 * n * d)
