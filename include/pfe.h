@@ -391,7 +391,11 @@ PFE_API pfe_status pfe_solve_system(pfe_ctx *c, const double *RHS, double *Y, pf
  *   PFE_KERNEL_SPMM     q = A p with the p.q column dots (one per PCG iteration)
  *   PFE_KERNEL_UPDATE   r -= alpha q with the r.z, r.r column dots
  *   PFE_KERNEL_EDGE     fused M Y / Shrink / b update / M^T scatter (Eqs. 7, 9, 10, 13)
- *   PFE_KERNEL_PUPDATE  p = D_A^{-1} r + beta p with the delayed y += alpha p
+ *   PFE_KERNEL_PUPDATE  p_new = D_A^{-1} r + beta p with the two delayed
+ *                       solution updates y += alpha_prev p_prev + alpha p
+ *                       (every other iteration)
+ *   PFE_KERNEL_PUPDATE_HOLD  the same launch on the other iterations, which
+ *                       hold the solution update (no pass over y)
  *   PFE_KERNEL_FSAI_TR  r -= alpha q fused with t = G r and the column dots
  *                       t.t (= r.z) and r.r (FSAI preconditioner set)
  *   PFE_KERNEL_FSAI_ZP  z = G^T t fused with p_new = z + beta p and the two
@@ -414,7 +418,8 @@ enum {
     PFE_KERNEL_PUPDATE = 3,
     PFE_KERNEL_FSAI_TR = 4,
     PFE_KERNEL_FSAI_ZP = 5,
-    PFE_KERNEL_FSAI_ZP_HOLD = 6
+    PFE_KERNEL_FSAI_ZP_HOLD = 6,
+    PFE_KERNEL_PUPDATE_HOLD = 7
 };
 PFE_API pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_ms);
 

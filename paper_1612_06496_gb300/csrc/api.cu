@@ -947,12 +947,14 @@ pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_
         if (e != cudaSuccess) return fail(c, PFE_ECUDA, cudaGetErrorString(e));
         ms /= (float)reps;
     } else if (which == PFE_KERNEL_SPMM || which == PFE_KERNEL_UPDATE || which == PFE_KERNEL_PUPDATE ||
-               which == PFE_KERNEL_FSAI_TR || which == PFE_KERNEL_FSAI_ZP || which == PFE_KERNEL_FSAI_ZP_HOLD) {
-        const int k = which == PFE_KERNEL_PUPDATE    ? 2
-                      : which == PFE_KERNEL_FSAI_TR  ? 3
-                      : which == PFE_KERNEL_FSAI_ZP  ? 4
+               which == PFE_KERNEL_FSAI_TR || which == PFE_KERNEL_FSAI_ZP || which == PFE_KERNEL_FSAI_ZP_HOLD ||
+               which == PFE_KERNEL_PUPDATE_HOLD) {
+        const int k = which == PFE_KERNEL_PUPDATE        ? 2
+                      : which == PFE_KERNEL_FSAI_TR      ? 3
+                      : which == PFE_KERNEL_FSAI_ZP      ? 4
                       : which == PFE_KERNEL_FSAI_ZP_HOLD ? 5
-                                                       : which;
+                      : which == PFE_KERNEL_PUPDATE_HOLD ? 6
+                                                         : which;
         PFE_TRY(time_pcg_kernel(c, c->stream, k, reps, &ms));
     } else {
         return fail(c, PFE_EINVAL, "unknown kernel id");

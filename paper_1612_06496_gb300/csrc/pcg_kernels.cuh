@@ -696,28 +696,35 @@ struct Vec<double> {
     __device__ static __forceinline__ V make(const double (&o)[2]) { return make_double2(o[0], o[1]); }
 };
 
-// p = z + beta p (p = z right after k_pcg_init) and the delayed solution
-// update y += alpha_prev p_prev, elementwise and in place (flat float4 /
-// double2 traversal; the grid makes every thread meet fixed columns), with
-// the Jacobi z = D_A^{-1} r.  (The FSAI iteration makes this update in
-// k_fsai_zp.)
+// p_new = z + beta p (p = z right after k_pcg_init) with the Jacobi z =
+// D_A^{-1} r, into the other direction buffer, and on folding iterations the
+// two delayed solution updates y += alpha_prev p_prev + alpha p (p_prev is
+// the old content of the buffer p_new goes to; every other iteration holds
+// its update, so y is read and written every other iteration).  Elementwise
+// (flat float4 / double2 traversal; the grid makes every thread meet fixed
+// columns).  (The FSAI iteration makes this update in k_fsai_zp.)
 template <typename T, int D, bool MS>
 __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
-    const int p_ready = ctl->p_ready, xpending = ctl->xpending;
+    const int p_ready = ctl->p_ready, fold = ctl->xpending && ctl->xfold;
+    // p of the previous iteration in buffer (iter & 1) ^ 1 (its finisher has
+    // counted it), the new one into iter & 1
+    T *__restrict__ pdst = a.p[ctl->iter & 1];
+    const T *__restrict__ psrc = a.p[(ctl->iter & 1) ^ 1];
     constexpr bool multi = MS;  // batch: beta, alpha of each row's segment
-    __shared__ T sbeta[D], salpha[D];
+    __shared__ T sbeta[D], salpha[D], salpha_prev[D];
     if (threadIdx.x < D) {
         sbeta[threadIdx.x] = p_ready ? T(0) : (T)a.sc.beta[threadIdx.x];
         salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
+        salpha_prev[threadIdx.x] = (T)a.sc.alpha_prev[threadIdx.x];
     }
     __syncthreads();
     using VT = Vec<T>;
     constexpr int VN = VT::N;
     const int64_t nel = a.A.n * D, nvec = nel / VN;
     const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
-    T be[VN], al[VN];
+    T be[VN], al[VN], ap[VN];
     int cu[VN];
 #pragma unroll
     for (int u = 0; u < VN; ++u) {
@@ -725,9 +732,11 @@ __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
         cu[u] = c;
         be[u] = sbeta[c];
         al[u] = salpha[c];
+        ap[u] = salpha_prev[c];
     }
     using V4 = typename VT::V;
-    V4 *p4 = reinterpret_cast<V4 *>(a.p[0]);
+    V4 *p4 = reinterpret_cast<V4 *>(pdst);
+    const V4 *ps4 = reinterpret_cast<const V4 *>(psrc);
     const V4 *z4 = reinterpret_cast<const V4 *>(a.r);
     V4 *x4 = reinterpret_cast<V4 *>(a.x);
     float4 *xl4 = reinterpret_cast<float4 *>(a.xlo);  // float path: VN == 4
@@ -741,22 +750,27 @@ __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
                 const int sgm = __ldg(a.sg.rseg + row0 + (cu[0] + u) / D);
                 be[u] = p_ready ? T(0) : (T)a.sc.beta[sgm * D + cu[u]];
                 al[u] = (T)a.sc.alpha[sgm * D + cu[u]];
+                ap[u] = (T)a.sc.alpha_prev[sgm * D + cu[u]];
             }
         }
-        VT::get(p4[v], pv);
+        VT::get(ps4[v], pv);
         VT::get(z4[v], zv);
 #pragma unroll
         for (int u = 0; u < VN; ++u) zv[u] = a.A.dinv[(v * VN + u) / D] * zv[u];
-        if (xpending) {
-            T xv[VN];
+        if (fold) {
+            T xv[VN], pp[VN];
             float xl[VN];
+            VT::get(p4[v], pp);
             VT::get(x4[v], xv);
             if constexpr (std::is_same_v<T, float>) {
                 const float4 t = xl4[v];
                 xl[0] = t.x; xl[1] = t.y; xl[2] = t.z; xl[3] = t.w;
             }
 #pragma unroll
-            for (int u = 0; u < VN; ++u) axpy_hilo<T>(xv[u], xl[u], al[u], pv[u]);
+            for (int u = 0; u < VN; ++u) {
+                axpy_hilo<T>(xv[u], xl[u], ap[u], pp[u]);
+                axpy_hilo<T>(xv[u], xl[u], al[u], pv[u]);
+            }
             x4[v] = VT::make(xv);
             if constexpr (std::is_same_v<T, float>) xl4[v] = make_float4(xl[0], xl[1], xl[2], xl[3]);
         }
@@ -770,17 +784,19 @@ __global__ void __launch_bounds__(kBlock) k_pupdate(PcgArgs<T> a) {
         const int sgm = multi ? row_seg(a.sg, e / D) : 0;
         const T bt = p_ready ? T(0) : (multi ? (T)a.sc.beta[sgm * D + c] : sbeta[c]);
         const T at = multi ? (T)a.sc.alpha[sgm * D + c] : salpha[c];
+        const T apv = multi ? (T)a.sc.alpha_prev[sgm * D + c] : salpha_prev[c];
         const T z = a.A.dinv[e / D] * a.r[e];
-        T po = a.p[0][e];
-        if (xpending) {
+        const T po = psrc[e];
+        if (fold) {
             T xh = a.x[e];
             float xl = 0.f;
             if constexpr (std::is_same_v<T, float>) xl = a.xlo[e];
+            axpy_hilo<T>(xh, xl, apv, pdst[e]);
             axpy_hilo<T>(xh, xl, at, po);
             a.x[e] = xh;
             if constexpr (std::is_same_v<T, float>) a.xlo[e] = xl;
         }
-        a.p[0][e] = p_ready ? z : z + bt * po;
+        pdst[e] = p_ready ? z : z + bt * po;
     }
 }
 
@@ -1436,13 +1452,26 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
             if (threadIdx.x == 0) due = !*(volatile int *)&ctl->error && ctl->refresh > 0 && (it % ctl->refresh) == 0;
             const bool refresh_due = __shfl_sync(kFull, due, 0) != 0;
             if (!refresh_due) finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, false, it);
+            // the next k_pupdate holds this iteration's solution update when
+            // none is held now (xheld changes only in the last finisher below):
+            // each segment keeps its alpha for the fold
+            if (!refresh_due && !*(volatile int *)&ctl->xheld)
+                for (int c = threadIdx.x; c < D; c += 32) a.sc.alpha_prev[bsg.seg * D + c] = a.sc.alpha[bsg.seg * D + c];
+            __syncwarp();
             if (!MS || warp_last_segment(ctl, 1, a.sg.nseg)) {
                 if (threadIdx.x == 0) {
                     ctl->iter = it;
                     if (refresh_due) ctl->refresh_now = 1;  // k_xflush + k_refresh finish this iteration
                 }
                 __syncwarp();
-                if (!refresh_due) finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
+                if (!refresh_due) {
+                    finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
+                    if (threadIdx.x == 0 && !ctl->done) {  // once done the held state stays for the final k_xflush
+                        const int fold = ctl->xheld;
+                        ctl->xfold = fold;
+                        ctl->xheld = !fold;
+                    }
+                }
             }
         }
     }
@@ -1451,7 +1480,7 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
 // y += alpha p with the direction of the last k_spmm.  In the loop body it
 // runs only before a refresh; after the loop it applies the final update.
 template <typename T, int D, bool MS>
-__global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush) {
+__global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush, int counted) {
     const PcgCtl *ctl = a.ctl;
     const int xp = *(volatile const int *)&ctl->xpending, xh = *(volatile const int *)&ctl->xheld;
     if (!xp && !xh) return;
@@ -1460,12 +1489,14 @@ __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush
     __shared__ T salpha[D], salpha_prev[D];
     if (threadIdx.x < D) {
         salpha[threadIdx.x] = xp ? (T)a.sc.alpha[threadIdx.x] : T(0);
-        salpha_prev[threadIdx.x] = (T)a.sc.alpha_prev[threadIdx.x];  // held updates: one problem (FSAI)
+        salpha_prev[threadIdx.x] = (T)a.sc.alpha_prev[threadIdx.x];
     }
     __syncthreads();
-    // the direction of the last k_spmm (FSAI: buffer iter & 1 before the
-    // iteration's finisher counted it, the other one after) and the one before
-    const int kc = final_flush ? ((ctl->iter & 1) ^ 1) : (ctl->iter & 1);
+    // the direction of the last k_spmm: buffer iter & 1 before the iteration's
+    // finisher counted it (FSAI refresh iterations), the other one after
+    // (counted: Jacobi refresh iterations and the flush after the loop); the
+    // direction before it in the other buffer
+    const int kc = counted ? ((ctl->iter & 1) ^ 1) : (ctl->iter & 1);
     const T *__restrict__ pc = a.p[kc];
     const T *__restrict__ pprev = a.p[kc ^ 1];
     const int64_t nel = a.A.n * D;
@@ -1474,7 +1505,10 @@ __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush
         float xl = 0.f;
         if constexpr (std::is_same_v<T, float>) xl = a.xlo[e];
         const int c = (int)(e % D);
-        if (xh) axpy_hilo<T>(xv, xl, salpha_prev[c], pprev[e]);
+        if (xh) {
+            const T ap = multi ? (T)a.sc.alpha_prev[__ldg(a.sg.rseg + e / D) * D + c] : salpha_prev[c];
+            axpy_hilo<T>(xv, xl, ap, pprev[e]);
+        }
         if (xp) {
             const T al = multi ? (T)a.sc.alpha[__ldg(a.sg.rseg + e / D) * D + c] : salpha[c];
             axpy_hilo<T>(xv, xl, al, pc[e]);
@@ -1853,6 +1887,8 @@ __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
                 if (threadIdx.x == 0) {
                     ctl->refresh_now = 0;
                     ctl->xpending = 0;
+                    ctl->xheld = 0;  // k_xflush applied every pending update
+                    ctl->xfold = 0;
                 }
                 __syncwarp();
                 finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
@@ -1901,8 +1937,7 @@ PcgArgs<T> pcg_args(pfe_ctx *c, PcgLaunch L) {
     a.xlo = c->wk.Ylo;
     a.r = (T *)c->wk.R;
     a.p[0] = (T *)c->wk.Pd;
-    // FSAI (float path) alternates the direction buffers
-    a.p[1] = (std::is_same_v<T, float> && c->fsai.enabled) ? (T *)c->wk.Pd2 : (T *)c->wk.Pd;
+    a.p[1] = (T *)c->wk.Pd2;  // the direction buffers alternate between iterations
     a.q = (T *)c->wk.Q;
     a.b = (const T *)c->wk.RHS;
     a.part = c->wk.partials;
@@ -1966,7 +2001,7 @@ void body_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int iters) {
                                  kBlock, 0, s>>>(a);
         launch_spmm<T, D, MS>(c, s, a);
         k_update<T, D, MS><<<wave_grid(c, G_UPDATE, k_update<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-        k_xflush<T, D, MS><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, MS>, flat_need<T, D>(c)), kBlock, 0, s>>>(a, 0);
+        k_xflush<T, D, MS><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, MS>, flat_need<T, D>(c)), kBlock, 0, s>>>(a, 0, 1);
         k_refresh<T, D, MS><<<wave_grid(c, G_REFRESH, k_refresh<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
     }
 }
@@ -2028,7 +2063,7 @@ pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
                 launch_spmm<T, D, false>(c, s, a);
                 launch_fsai<T, D>(c, s, a, 0);
                 k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c)), kBlock, 0,
-                                        s>>>(a, 0);
+                                        s>>>(a, 0, 0);
                 k_refresh_f<T, D><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
                 launch_fsai<T, D>(c, s, a, 2);
                 launch_fsai<T, D>(c, s, a, 3);
@@ -2049,10 +2084,10 @@ template <typename T, int D>
 pfe_status final_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
     if (c->nseg > 1)
         k_xflush<T, D, true><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, true>, flat_need<T, D>(c)), kBlock, 0, s>>>(
-            pcg_args<T>(c, L), 1);
+            pcg_args<T>(c, L), 1, 1);
     else
         k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c)), kBlock, 0, s>>>(
-            pcg_args<T>(c, L), 1);
+            pcg_args<T>(c, L), 1, 1);
     PFE_CUDA_TRY(c, cudaGetLastError());
     return PFE_OK;
 }
@@ -2069,8 +2104,9 @@ pfe_status apply_T(pfe_ctx *c, cudaStream_t s, const void *x, void *y) {
 // control block (every column active, a steady-state iteration: direction
 // update and delayed solution update both on) and scratch copies of y, r and
 // the direction buffers, so the iteration state is left as it was.
-// which: 0 = k_spmm, 1 = k_update, 2 = k_pupdate, 3 = k_fsai_tr, 4 = k_fsai_zp
-// folding two solution updates, 5 = k_fsai_zp holding one.
+// which: 0 = k_spmm, 1 = k_update, 2 = k_pupdate folding two solution
+// updates, 3 = k_fsai_tr, 4 = k_fsai_zp folding, 5 = k_fsai_zp holding one,
+// 6 = k_pupdate holding.
 template <typename T, int D>
 pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, int variant) {
     PcgCtl h;
@@ -2080,7 +2116,7 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
     h.tol = 0.0;
     h.p_ready = 0;
     h.xpending = 1;
-    h.xfold = which == 4 ? 1 : 0;
+    h.xfold = (which == 2 || which == 4) ? 1 : 0;  // 2, 4: the folding launch; 5, 6: the holding one
     // scratch per-segment scalars: every column active
     const int nseg = c->nseg;
     const size_t sc_bytes = segscal_bytes(nseg, D);
@@ -2098,7 +2134,7 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
     }
     void *dsc = nullptr;
     const int64_t nd = c->g.n * (int64_t)D;
-    const bool fsai = which >= 3;
+    const bool fsai = which >= 3 && which <= 5;
     if (fsai && !use_fsai<T>(c)) {
         c->err = "pfe_time_kernel: the FSAI kernels need the FSAI preconditioner on the mixed path";
         return PFE_EUNSUPPORTED;
@@ -2161,11 +2197,11 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
             k_update<T, D, true><<<wave_grid(c, G_UPDATE, k_update<T, D, true>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
         else if (which == 1)
             k_update<T, D, false><<<wave_grid(c, G_UPDATE, k_update<T, D, false>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-        else if (which == 2 && multi)
+        else if ((which == 2 || which == 6) && multi)
             k_pupdate<T, D, true><<<wave_grid(c, G_PUPD, k_pupdate<T, D, true>, flat_need<T, D>(c),
                                                  flat_mult<T, D>()),
                                        kBlock, 0, s>>>(a);
-        else if (which == 2)
+        else if (which == 2 || which == 6)
             k_pupdate<T, D, false><<<wave_grid(c, G_PUPD, k_pupdate<T, D, false>, flat_need<T, D>(c),
                                                   flat_mult<T, D>()),
                                         kBlock, 0, s>>>(a);
