@@ -263,11 +263,21 @@ __device__ __forceinline__ void block_sum_cols(typename Acc<T>::type (&v)[NQ][Su
 #pragma unroll
         for (int k = 0; k < SW::V; ++k) red[q][warp][lane][k] = v[q][k];
     __syncthreads();
-    for (int t = threadIdx.x; t < NQ * D; t += blockDim.x) {
+    // two stages (shorter dependent chains than one thread a value): thread
+    // (t, w) adds warp w's rows of value t, then thread t adds the warps, in
+    // a fixed order
+    __shared__ AT wsum[kWarps][NQ * D];
+    for (int e = threadIdx.x; e < kWarps * NQ * D; e += blockDim.x) {
+        const int w = e / (NQ * D), t = e - w * (NQ * D);
         const int q = t / D, c = t - q * D, cg = c / SW::V, k = c - cg * SW::V;
         AT s = A::zero();
-        for (int w = 0; w < kWarps; ++w)
-            for (int r = 0; r < SW::RPW; ++r) A::add(s, red[q][w][r * SW::L + cg][k]);
+        for (int r = 0; r < SW::RPW; ++r) A::add(s, red[q][w][r * SW::L + cg][k]);
+        wsum[w][t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NQ * D; t += blockDim.x) {
+        AT s = wsum[0][t];
+        for (int w = 1; w < kWarps; ++w) A::add(s, wsum[w][t]);
         sh[t] = s;
     }
     __syncthreads();
@@ -296,16 +306,16 @@ __device__ __forceinline__ bool grid_sum_cols(typename Acc<T>::type (&v)[NQ][Sub
         const int v = threadIdx.x % NV, h = threadIdx.x / NV;
         const int nb = bsg.nb;
         AT s = A::zero();
-        // eight independent loads in flight, then the additions in block order
-        for (int b0 = h; b0 < nb; b0 += 8 * G) {
-            AT vals[8];
+        // sixteen independent loads in flight, then the additions in block order
+        for (int b0 = h; b0 < nb; b0 += 16 * G) {
+            AT vals[16];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 16; ++u) {
                 const int b = b0 + u * G;
                 vals[u] = b < nb ? ld_part<A, AT>(part + (int64_t)b * NV + v) : A::zero();
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
+            for (int u = 0; u < 16; ++u)
                 if (b0 + u * G < nb) A::add(s, vals[u]);
         }
         pr[h][v] = s;
