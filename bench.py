@@ -206,7 +206,8 @@ def ncu_traffic(workload: str, kernel: str, units_full: float, variant: int | No
     """DRAM bytes per launch from the committed ncu summary, scaled to the
     full launch; None when the kernel source changed since the capture or
     the capture was of another kernel variant than the one timed."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    name = f"{kernel}_v{variant}" if variant is not None else kernel  # SpMM: one file per variant
+    path = os.path.join(ROOT, "profiles", f"{name}_traffic.txt")
     if not os.path.exists(path):
         return None
     kv = {}
