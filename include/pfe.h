@@ -455,6 +455,20 @@ PFE_API pfe_status pfe_fsai_set(pfe_ctx *c, const float *params);
  * row has more than 23 lower neighbours.  Synchronises. */
 PFE_API pfe_status pfe_fsai_classical(pfe_ctx *c);
 
+/* The paper's preconditioner (Sec. III: conjugate gradients with an
+ * incomplete Cholesky factorisation), in its zero-fill form IC(0): L lower
+ * triangular on the pattern of tril(A) with (L L^T)_ij = A_ij on the
+ * pattern, factored in FP64 on the GPU; later PCG solves use
+ * M^{-1} = L^{-T} L^{-1}.  The triangular solves are sequential along a
+ * wavefront: they run one launch per level (W + c (H - 1) levels, c = 2 at
+ * radius 2 and 3 at radius 3), which is why the FSAI forms are the fast
+ * path; IC(0) is the comparator.  L is readable with pfe_fsai_get (L_ii and
+ * L_ba per edge).  One grid image of radius 2 or 3 on the mixed-precision
+ * path; PFE_EUNSUPPORTED otherwise, PFE_ENUMERIC on a non-positive pivot
+ * (not possible for this system matrix, an M-matrix).  pfe_fsai_set(c, NULL)
+ * switches back to Jacobi.  Synchronises. */
+PFE_API pfe_status pfe_ic0(pfe_ctx *c);
+
 /* Training criterion: Kaporin's condition number of G A G^T,
  *   *loss = log(tr(G A G^T) / n) - (2/n) sum_i log G_ii,
  * and its gradient with respect to params (written to grad when non-NULL,

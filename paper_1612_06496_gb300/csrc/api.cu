@@ -91,6 +91,19 @@ pfe_status fsai_vectors(pfe_ctx *c, int64_t nd) {
 // Launches per solve: the init kernels plus the final flush, and per
 // iteration (the counts the device reports in pfe_solve_stats).
 void launch_counts(const pfe_ctx *c, int lc[2]) {
+    if (c->fsai.enabled && c->fsai.ic) {
+        // the triangular solves: one launch per level that holds a row
+        int64_t nl = 0;
+        const int64_t W = c->W, H = c->g.n / W;
+        for (int64_t l = 0; l < c->fsai.ic_levels; ++l) {
+            int64_t y0 = 0, rows = 0;
+            ic_level_rows(l, W, H, c->fsai.ic_cl, y0, rows);
+            nl += rows > 0;
+        }
+        lc[0] = (int)(2 * nl + 3);
+        lc[1] = (int)(2 * nl + 5);
+        return;
+    }
     lc[0] = c->fsai.enabled ? 4 : 2;
     lc[1] = c->fsai.enabled ? 6 : 5;
 }
@@ -980,6 +993,7 @@ pfe_status pfe_fsai_set(pfe_ctx *c, const float *params) {
         if (c->inited && !c->fsai.t) PFE_TRY(fsai_vectors(c, c->n * (int64_t)c->d));
         c->fsai.enabled = true;
     }
+    c->fsai.ic = false;
     return fsai_switched(c);
 }
 
@@ -992,6 +1006,22 @@ pfe_status pfe_fsai_classical(pfe_ctx *c) {
     PFE_TRY(fsai_classical(c));
     if (c->inited && !c->fsai.t) PFE_TRY(fsai_vectors(c, c->n * (int64_t)c->d));
     c->fsai.enabled = true;
+    c->fsai.ic = false;
+    return fsai_switched(c);
+}
+
+pfe_status pfe_ic0(pfe_ctx *c) {
+    if (!c) return PFE_EINVAL;
+    if (c->nseg > 1 || c->kind != PFE_GRAPH_GRID || c->W < 1 || (c->g.row_len != 12 && c->g.row_len != 28))
+        return fail(c, PFE_EUNSUPPORTED, "IC(0) is built for one grid image of radius 2 or 3");
+    if (!c->mixed) return fail(c, PFE_EUNSUPPORTED, "IC(0) runs on the mixed-precision path");
+    PFE_TRY(sync(c));
+    PFE_TRY(fsai_alloc(c));
+    c->fsai.enabled = false;
+    PFE_TRY(ic0_factor(c));
+    if (c->inited && !c->fsai.t) PFE_TRY(fsai_vectors(c, c->n * (int64_t)c->d));
+    c->fsai.enabled = true;
+    c->fsai.ic = true;
     return fsai_switched(c);
 }
 

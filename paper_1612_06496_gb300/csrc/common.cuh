@@ -297,7 +297,7 @@ __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
 enum GridSlot {
     G_INIT = 0, G_INIT_F, G_PUPD, G_SPMM, G_UPDATE, G_FSAI_TR, G_XFLUSH, G_REFRESH, G_REFRESH_F,
     G_FSAI_T, G_FSAI_T1, G_FSAI_ZP, G_APPLY, G_EDGE, G_PAPPLY, G_TIME_SPMM, G_TIME_UPDATE, G_SPMM_F1, G_SPMM_F2,
-    G_SPMM_F3, G_SPMM_TMA, G_SPMM_STENCIL, G_NSLOTS
+    G_SPMM_F3, G_SPMM_TMA, G_SPMM_STENCIL, G_IC_R, G_IC_DOTS, G_NSLOTS
 };
 // Strip width of the stencil SpMM pipeline for d columns, rows of len
 // slots (radius 2: 12, radius 3: 28) and p steps in flight: the widest
@@ -305,6 +305,67 @@ enum GridSlot {
 // or 1 columns a lane) up to one pass of kWarps warps whose shared memory
 // (a ring of 2R + 1 + p row bands, p + 1 rows of matrix values and
 // diagonal) fits 41 KB with every copy 16-byte aligned; 0 if none does.
+// Stencil of a grid graph with fixed slot positions: slot t of every row is
+// the t-th offset (dy, dx), 0 < dx^2 + dy^2 <= R^2, in (dy, dx) order (the
+// order the graph builder lists them); 12 slots at radius 2, 28 at radius 3.
+template <int LEN>
+struct Stencil {
+    static constexpr int R = LEN == 12 ? 2 : 3;
+    int dx[LEN], dy[LEN];
+};
+template <int LEN>
+constexpr Stencil<LEN> make_stencil() {
+    Stencil<LEN> st{};
+    constexpr int R = Stencil<LEN>::R;
+    int k = 0;
+    for (int y = -R; y <= R; ++y)
+        for (int x = -R; x <= R; ++x)
+            if (x * x + y * y > 0 && x * x + y * y <= R * R && k < LEN) {
+                st.dy[k] = y;
+                st.dx[k] = x;
+                ++k;
+            }
+    return st;
+}
+template <int LEN>
+constexpr int stencil_count() {
+    constexpr int R = Stencil<LEN>::R;
+    int k = 0;
+    for (int y = -R; y <= R; ++y)
+        for (int x = -R; x <= R; ++x) k += (x * x + y * y > 0 && x * x + y * y <= R * R) ? 1 : 0;
+    return k;
+}
+
+// Level schedule of the incomplete-Cholesky triangular solves on a grid
+// image in raster order: pixel (x, y) gets level x + CL y, so every lower
+// stencil neighbour (dy < 0, or dy = 0 and dx < 0) has a smaller level and
+// the rows of one level are independent.  CL = 1 + the largest dx among the
+// offsets with dy = -1 (2 at radius 2, 3 at radius 3).
+template <int LEN>
+constexpr int ic_level_coef() {
+    constexpr Stencil<LEN> st = make_stencil<LEN>();
+    int m = 0;
+    for (int t = 0; t < LEN; ++t)
+        if (st.dy[t] == -1 && st.dx[t] > m) m = st.dx[t];
+    return m + 1;
+}
+template <int LEN>
+constexpr bool ic_levels_ok() {
+    constexpr Stencil<LEN> st = make_stencil<LEN>();
+    constexpr int cl = ic_level_coef<LEN>();
+    for (int t = 0; t < LEN / 2; ++t)  // the lower offsets
+        if (!(cl * -st.dy[t] - st.dx[t] > 0)) return false;
+    return true;
+}
+// rows of level l of a W x H image: y in [y0, y0 + count), x = l - cl y
+__host__ __device__ inline void ic_level_rows(int64_t l, int64_t W, int64_t H, int cl, int64_t &y0, int64_t &count) {
+    const int64_t lo = l - (W - 1) <= 0 ? 0 : (l - (W - 1) + cl - 1) / cl;
+    const int64_t hi = l / cl < H - 1 ? l / cl : H - 1;
+    y0 = lo;
+    count = hi >= lo ? hi - lo + 1 : 0;
+}
+inline int64_t ic_levels(int64_t W, int64_t H, int cl) { return (W - 1) + cl * (H - 1) + 1; }
+
 constexpr int kStencilSteps = 3;  // steps of the stencil SpMM pipeline in flight (5 measured slower)
 constexpr int stencil_strip(int d, int len, int p) {
     const int r = len == 12 ? 2 : 3;

@@ -803,6 +803,145 @@ pfe_status fsai_classical(pfe_ctx *c) {
     return PFE_OK;
 }
 
+// ---- incomplete Cholesky IC(0) (Sec. III's preconditioner) ------------------
+// L lower triangular on the pattern of tril(A) with (L L^T)_ij = A_ij on the
+// pattern, row by row: L_ij = (A_ij - sum_k L_ik L_jk) / L_jj for the lower
+// neighbours j of i in increasing order, L_ii = sqrt(A_ii - sum_j L_ij^2).  On
+// a grid image with fixed slot positions the common lower neighbours k of i
+// and j (slot t) are the slot pairs (s, u) with offset_s = offset_t +
+// offset_u, a compile-time table; a pair whose slot is padding (outside the
+// image) carries L = 0.  Rows of one level of the raster wavefront
+// (ic_level_rows) are independent and run in parallel; a launch per level.
+template <int LEN>
+struct IcPairs {
+    int cnt[LEN / 2];
+    int s[LEN / 2][LEN / 2], u[LEN / 2][LEN / 2];
+};
+template <int LEN>
+constexpr IcPairs<LEN> make_ic_pairs() {
+    constexpr Stencil<LEN> st = make_stencil<LEN>();
+    IcPairs<LEN> p{};
+    for (int t = 0; t < LEN / 2; ++t) {
+        p.cnt[t] = 0;
+        for (int s = 0; s < LEN / 2; ++s)  // ascending s: ascending column k
+            for (int u = 0; u < LEN / 2; ++u)
+                if (st.dy[s] == st.dy[t] + st.dy[u] && st.dx[s] == st.dx[t] + st.dx[u]) {
+                    p.s[t][p.cnt[t]] = s;
+                    p.u[t][p.cnt[t]] = u;
+                    ++p.cnt[t];
+                }
+    }
+    return p;
+}
+
+template <int LEN>
+__global__ void k_ic_factor(int64_t W, int64_t y0, int64_t rows, int64_t level, int cl, const int *__restrict__ col,
+                            const int *__restrict__ eid, const double *__restrict__ aoff,
+                            const double *__restrict__ adiag, double *__restrict__ Llow, double *__restrict__ Ldiag,
+                            int *err) {
+    constexpr int NL = LEN / 2;
+    constexpr IcPairs<LEN> pr = make_ic_pairs<LEN>();
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= rows) return;
+    const int64_t y = y0 + k, x = level - cl * y;
+    const int64_t i = y * W + x;
+    double li[NL];
+    double sq = 0.0;
+#pragma unroll
+    for (int t = 0; t < NL; ++t) {
+        const int64_t slot = i * LEN + t;
+        li[t] = 0.0;
+        if (eid[slot] < 0) continue;  // padding
+        const int64_t j = col[slot];
+        double v = aoff[slot];
+#pragma unroll
+        for (int q = 0; q < pr.cnt[t]; ++q) v -= li[pr.s[t][q]] * Llow[j * NL + pr.u[t][q]];
+        li[t] = v / Ldiag[j];
+        sq += li[t] * li[t];
+    }
+    double piv = adiag[i] - sq;
+    if (!(piv > 0.0)) {
+        atomicMax(err, 1);
+        piv = 1.0;
+    }
+    Ldiag[i] = sqrt(piv);
+#pragma unroll
+    for (int t = 0; t < NL; ++t) Llow[i * NL + t] = li[t];
+}
+
+// L into the FSAI buffers: gdiag = L_ii, gE[edge] = L_ba (b > a), so that the
+// slot copy gives each row its lower entries and, mirrored, the upper ones.
+template <int LEN>
+__global__ void k_ic_pack(int64_t n, const int *__restrict__ eid, const double *__restrict__ Llow,
+                          const double *__restrict__ Ldiag, float *gdiag, float *gE) {
+    constexpr int NL = LEN / 2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    gdiag[i] = (float)Ldiag[i];
+    for (int t = 0; t < NL; ++t) {
+        const int e = eid[i * LEN + t];
+        if (e >= 0) gE[e] = (float)Llow[i * NL + t];
+    }
+}
+
+template <int LEN>
+pfe_status ic0_len(pfe_ctx *c) {
+    static_assert(ic_levels_ok<LEN>(), "level schedule");
+    auto &f = c->fsai;
+    cudaStream_t s = c->stream;
+    const int64_t n = c->g.n, W = c->W, H = n / W;
+    constexpr int cl = ic_level_coef<LEN>();
+    double *Llow = nullptr, *Ldiag = nullptr;
+    if (cudaMalloc((void **)&Llow, sizeof(double) * n * (LEN / 2)) != cudaSuccess ||
+        cudaMalloc((void **)&Ldiag, sizeof(double) * n) != cudaSuccess) {
+        cudaGetLastError();
+        if (Llow) cudaFree(Llow);
+        c->err = "IC(0): scratch allocation failed";
+        return PFE_ENOMEM;
+    }
+    int *derr = reinterpret_cast<int *>(f.tick + 2);
+    cudaError_t e = cudaMemsetAsync(derr, 0, sizeof(int), s);
+    const int64_t L = ic_levels(W, H, cl);
+    for (int64_t l = 0; l < L && e == cudaSuccess; ++l) {
+        int64_t y0 = 0, rows = 0;
+        ic_level_rows(l, W, H, cl, y0, rows);
+        if (rows == 0) continue;
+        k_ic_factor<LEN><<<nblk(rows, 128), 128, 0, s>>>(W, y0, rows, l, cl, c->g.col, c->g.eid, c->g.aoff64,
+                                                         c->g.adiag64, Llow, Ldiag, derr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        View v = view(c);
+        k_ic_pack<LEN><<<nblk(n, 256), 256, 0, s>>>(n, c->g.eid, Llow, Ldiag, f.gdiag, f.gE);
+        k_gslots<<<nblk(c->g.n_slices * 32, 256), 256, 0, s>>>(v, f.gE, f.gslot);
+        e = cudaGetLastError();
+    }
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(Llow);
+    cudaFree(Ldiag);
+    if (e != cudaSuccess) {
+        c->err = std::string("IC(0): ") + cudaGetErrorString(e);
+        return PFE_ECUDA;
+    }
+    if (h) {
+        c->err = "IC(0): a non-positive pivot (the matrix is not an M-matrix)";
+        return PFE_ENUMERIC;
+    }
+    f.ic_cl = cl;
+    f.ic_levels = L;
+    return PFE_OK;
+}
+
+// IC(0) factor of A into the FSAI buffers (one grid image, fixed slot positions).
+pfe_status ic0_factor(pfe_ctx *c) {
+    if (c->g.row_len == 12) return ic0_len<12>(c);
+    if (c->g.row_len == 28) return ic0_len<28>(c);
+    c->err = "IC(0) is built for grid images of radius 2 or 3";
+    return PFE_EUNSUPPORTED;
+}
+
 // G entries as FP64: od[i] = G_ii (n), oe[k] = G_{b_k a_k} for external edge k.
 pfe_status fsai_export(pfe_ctx *c, double *od, double *oe) {
     const int64_t m = std::max<int64_t>(c->g.n, c->g.n_edges);

@@ -30,6 +30,9 @@ struct FsaiState {
     unsigned *tick = nullptr;
     float *params = nullptr;   // network parameters in use (device copy)
     float *grad = nullptr;     // last gradient
+    bool ic = false;           // the factor is IC(0)'s L: M^{-1} = L^{-T} L^{-1} (triangular solves)
+    int ic_cl = 0;             // IC level schedule: pixel (x, y) has level x + ic_cl y
+    int64_t ic_levels = 0;
     void *t = nullptr;   // PCG work vector t = G r (n x d)
     void *r1 = nullptr;  // second residual buffer (n x d)
 };
@@ -39,6 +42,7 @@ pfe_status fsai_infer(pfe_ctx *c);
 pfe_status fsai_loss_grad(pfe_ctx *c, double *loss);
 pfe_status fsai_export(pfe_ctx *c, double *od, double *oe);
 pfe_status fsai_classical(pfe_ctx *c);
+pfe_status ic0_factor(pfe_ctx *c);
 pfe_status adam_step(float *p, const float *gr, float *m, float *v, int64_t cnt, int step, double lr, double b1,
                      double b2, double eps, cudaStream_t s);
 

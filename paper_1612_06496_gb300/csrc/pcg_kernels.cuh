@@ -1057,37 +1057,6 @@ __global__ void __launch_bounds__(kBlock, MINB) k_spmm_tma(PcgArgs<T> a) {
         if (threadIdx.x < 32) spmm_finish<T, D, false>(a, bsg, tot);
 }
 
-// Stencil of a grid graph with fixed slot positions: slot t of every row is
-// the t-th offset (dy, dx), 0 < dx^2 + dy^2 <= R^2, in (dy, dx) order (the
-// order the graph builder lists them); 12 slots at radius 2, 28 at radius 3.
-template <int LEN>
-struct Stencil {
-    static constexpr int R = LEN == 12 ? 2 : 3;
-    int dx[LEN], dy[LEN];
-};
-template <int LEN>
-constexpr Stencil<LEN> make_stencil() {
-    Stencil<LEN> st{};
-    constexpr int R = Stencil<LEN>::R;
-    int k = 0;
-    for (int y = -R; y <= R; ++y)
-        for (int x = -R; x <= R; ++x)
-            if (x * x + y * y > 0 && x * x + y * y <= R * R && k < LEN) {
-                st.dy[k] = y;
-                st.dx[k] = x;
-                ++k;
-            }
-    return st;
-}
-template <int LEN>
-constexpr int stencil_count() {
-    constexpr int R = Stencil<LEN>::R;
-    int k = 0;
-    for (int y = -R; y <= R; ++y)
-        for (int x = -R; x <= R; ++x) k += (x * x + y * y > 0 && x * x + y * y <= R * R) ? 1 : 0;
-    return k;
-}
-
 __device__ __forceinline__ void cp_async_8(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
@@ -1862,6 +1831,127 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())
     }
 }
 
+// ---- incomplete Cholesky IC(0), M^{-1} = L^{-T} L^{-1} --------------------------
+// The FSAI iteration with G = L^{-1}: t = L^{-1} r (forward solve), r.z = t.t,
+// z = L^{-T} t (backward solve, in place in t) fused with the direction and
+// solution updates.  L is held like G (lower entries in a row's lower slots,
+// the mirrored upper ones in its upper slots, L_ii in gdiag).  The solves run
+// level by level over the raster wavefront (one launch per level, rows of a
+// level in parallel, one thread per row and column).  An IC iteration:
+//   k_spmm, k_ic_r (r -= alpha q; not on refresh iterations), k_xflush and
+//   k_refresh_f (refresh iterations), k_ic_fwd per level, k_ic_dots (t.t,
+//   r.r -> beta, convergence; decides the next refresh), k_ic_bwd per level
+//   in reverse.  A solve starts with k_pcg_init<PRE = 1>, the forward levels,
+//   k_ic_dots (start) and the backward levels.
+
+// r' = r - alpha q into the other residual buffer (elementwise).
+template <typename T, int D>
+__global__ void __launch_bounds__(kBlock) k_ic_r(PcgArgs<T> a) {
+    const PcgCtl *ctl = a.ctl;
+    if (*(volatile const int *)&ctl->done) return;
+    if (ctl->refresh_now) return;
+    const int par = ctl->iter & 1;
+    const T *__restrict__ rold = a.r2[par];
+    T *__restrict__ rnew = a.r2[1 - par];
+    const int64_t nel = a.A.n * D;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < nel; e += (int64_t)gridDim.x * kBlock)
+        rnew[e] = fma(-(T)a.sc.alpha[e % D], a.q[e], rold[e]);
+}
+
+// Forward level: t_i = (r_i - sum over the lower slots of L_ij t_j) / L_ii for
+// the rows y0 .. y0 + rows - 1 of level `level` (x = level - cl y).
+template <typename T, int D, int LEN>
+__global__ void __launch_bounds__(kBlock) k_ic_fwd(PcgArgs<T> a, int64_t level, int64_t y0, int64_t rows, int start) {
+    const PcgCtl *ctl = a.ctl;
+    if (*(volatile const int *)&ctl->done) return;
+    constexpr int cl = ic_level_coef<LEN>();
+    const int64_t k = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    if (k >= rows * D) return;
+    const int64_t y = y0 + k / D, i = y * a.grid_w + (level - cl * y);
+    const int c = (int)(k % D);
+    const T *__restrict__ src = start ? a.r2[0] : a.r2[(ctl->iter + 1) & 1];
+    T acc = src[i * D + c];
+#pragma unroll
+    for (int t = 0; t < LEN / 2; ++t) {
+        const int64_t j = a.A.col[i * LEN + t];
+        if (j != i) acc = fma(-a.gslot[i * LEN + t], a.t[j * D + c], acc);
+    }
+    a.t[i * D + c] = acc / a.gdiag[i];
+}
+
+// t.t (= r.z) and r.r over all rows, then the end of the iteration (or of
+// the start of the solve) and the refresh decision for the next iteration.
+template <typename T, int D>
+__global__ void __launch_bounds__(kBlock) k_ic_dots(PcgArgs<T> a, int start) {
+    if (*(volatile int *)&a.ctl->done) return;
+    const int mode = start ? 0 : (*(volatile int *)&a.ctl->refresh_now ? 1 : 2);
+    const T *__restrict__ rsrc = start ? a.r2[0] : a.r2[(a.ctl->iter + 1) & 1];
+    __shared__ DF sq_sh[sqsum_slots<T, 2, SubWarp<T, D>::V>()];
+    SqSum<T, 2, SubWarp<T, D>::V> sq(sq_sh);  // t.t | r.r
+    __syncthreads();
+    PFE_ROW_LOOP(T, D) {
+        PFE_ROW_I;
+        const int c0 = lm.cg * V;
+        T ti[V], ri[V];
+        ldv_rw<T, V>(a.t + i * D + c0, ti);
+        ldv<T, V>(rsrc + i * D + c0, ri);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            sq.add(0, k, ti[k], ti[k]);
+            sq.add(1, k, ri[k], ri[k]);
+        }
+        sq.row_done();
+    }
+    sq.finish();
+    __shared__ double tot[2 * D];
+    if (grid_sum_cols<T, D, 2>(sq.acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot)) {
+        if (threadIdx.x < 32) {
+            fsai_finish(a, bsg, tot, D, mode);
+            if (threadIdx.x == 0) {
+                PcgCtl *ctl = a.ctl;
+                ctl->refresh_now = (ctl->refresh > 0 && ((ctl->iter + 1) % ctl->refresh) == 0) ? 1 : 0;
+            }
+        }
+    }
+}
+
+// Backward level: z_i = (t_i - sum over the upper slots of L_ji z_j) / L_ii
+// in place, fused with the row's p_new = z + beta p and, on folding
+// iterations, y += alpha_prev p_prev + alpha p (as k_fsai_zp).
+template <typename T, int D, int LEN>
+__global__ void __launch_bounds__(kBlock) k_ic_bwd(PcgArgs<T> a, int64_t level, int64_t y0, int64_t rows) {
+    const PcgCtl *ctl = a.ctl;
+    if (*(volatile const int *)&ctl->done) return;
+    constexpr int cl = ic_level_coef<LEN>();
+    const int64_t k = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    if (k >= rows * D) return;
+    const int64_t y = y0 + k / D, i = y * a.grid_w + (level - cl * y);
+    const int c = (int)(k % D);
+    const int64_t e = i * D + c;
+    T acc = a.t[e];
+#pragma unroll
+    for (int t = LEN / 2; t < LEN; ++t) {
+        const int64_t j = a.A.col[i * LEN + t];
+        if (j != i) acc = fma(-a.gslot[i * LEN + t], a.t[j * D + c], acc);
+    }
+    const T z = acc / a.gdiag[i];
+    a.t[e] = z;
+    const int p_ready = ctl->p_ready, fold = ctl->xpending && ctl->xfold;
+    T *__restrict__ pdst = a.p[ctl->iter & 1];
+    const T *__restrict__ psrc = a.p[(ctl->iter & 1) ^ 1];
+    const T pv = p_ready ? T(0) : psrc[e];
+    if (fold) {
+        T xh = a.x[e];
+        float xl = 0.f;
+        if constexpr (std::is_same_v<T, float>) xl = a.xlo[e];
+        axpy_hilo<T>(xh, xl, (T)a.sc.alpha_prev[c], pdst[e]);
+        axpy_hilo<T>(xh, xl, (T)a.sc.alpha[c], pv);
+        a.x[e] = xh;
+        if constexpr (std::is_same_v<T, float>) a.xlo[e] = xl;
+    }
+    pdst[e] = p_ready ? z : z + (T)a.sc.beta[c] * pv;
+}
+
 // Residual replacement: r = b - A y (extended precision), then finish the
 // iteration with the true residual.
 template <typename T, int D, bool MS>
@@ -2041,12 +2131,47 @@ void launch_fsai(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int which) {
         fsai_kernels_len<T, D, 0>(c, s, a, which);
 }
 
+// The IC(0) triangular solves: one launch per level of the raster wavefront
+// (forward: levels ascending into t; backward: descending, z in place).
+template <typename T, int D, int LEN>
+void ic_solve_len(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, bool fwd, int start) {
+    constexpr int cl = ic_level_coef<LEN>();
+    const int64_t W = c->W, H = c->g.n / W, L = ic_levels(W, H, cl);
+    for (int64_t q = 0; q < L; ++q) {
+        const int64_t l = fwd ? q : L - 1 - q;
+        int64_t y0 = 0, rows = 0;
+        ic_level_rows(l, W, H, cl, y0, rows);
+        if (rows == 0) continue;
+        const unsigned g = (unsigned)((rows * D + kBlock - 1) / kBlock);
+        if (fwd)
+            k_ic_fwd<T, D, LEN><<<g, kBlock, 0, s>>>(a, l, y0, rows, start);
+        else
+            k_ic_bwd<T, D, LEN><<<g, kBlock, 0, s>>>(a, l, y0, rows);
+    }
+}
+template <typename T, int D>
+void ic_solve(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, bool fwd, int start) {
+    if (c->g.row_len == 12)
+        ic_solve_len<T, D, 12>(c, s, a, fwd, start);
+    else
+        ic_solve_len<T, D, 28>(c, s, a, fwd, start);
+}
+
 template <typename T, int D>
 pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
     PcgArgs<T> a = pcg_args<T>(c, L);
     // the error flag of the solve starts clear (the segments' finishers only raise it)
     PFE_CUDA_TRY(c, cudaMemsetAsync(&c->ctl->error, 0, sizeof(int), s));
     if constexpr (std::is_same_v<T, float>) {
+        if (use_fsai<T>(c) && c->fsai.ic) {
+            k_pcg_init<T, D, 1, false><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1, false>, rows_need<T, D>(c)), kBlock,
+                                         0, s>>>(a);
+            ic_solve<T, D>(c, s, a, true, 1);
+            k_ic_dots<T, D><<<wave_grid(c, G_IC_DOTS, k_ic_dots<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a, 1);
+            ic_solve<T, D>(c, s, a, false, 0);
+            PFE_CUDA_TRY(c, cudaGetLastError());
+            return PFE_OK;
+        }
         if (use_fsai<T>(c)) {
             k_pcg_init<T, D, 1, false><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1, false>, rows_need<T, D>(c)), kBlock,
                                          0, s>>>(a);
@@ -2068,6 +2193,20 @@ template <typename T, int D>
 pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
     PcgArgs<T> a = pcg_args<T>(c, L);
     if constexpr (std::is_same_v<T, float>) {
+        if (use_fsai<T>(c) && c->fsai.ic) {
+            for (int u = 0; u < iters; ++u) {
+                launch_spmm<T, D, false>(c, s, a);
+                k_ic_r<T, D><<<wave_grid(c, G_IC_R, k_ic_r<T, D>, flat_need<T, D>(c)), kBlock, 0, s>>>(a);
+                k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c)), kBlock, 0,
+                                        s>>>(a, 0, 0);
+                k_refresh_f<T, D><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+                ic_solve<T, D>(c, s, a, true, 0);
+                k_ic_dots<T, D><<<wave_grid(c, G_IC_DOTS, k_ic_dots<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a, 0);
+                ic_solve<T, D>(c, s, a, false, 0);
+            }
+            PFE_CUDA_TRY(c, cudaGetLastError());
+            return PFE_OK;
+        }
         if (use_fsai<T>(c)) {
             for (int u = 0; u < iters; ++u) {
                 launch_spmm<T, D, false>(c, s, a);
@@ -2145,7 +2284,7 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
     void *dsc = nullptr;
     const int64_t nd = c->g.n * (int64_t)D;
     const bool fsai = which >= 3 && which <= 5;
-    if (fsai && !use_fsai<T>(c)) {
+    if (fsai && (!use_fsai<T>(c) || c->fsai.ic)) {
         c->err = "pfe_time_kernel: the FSAI kernels need the FSAI preconditioner on the mixed path";
         return PFE_EUNSUPPORTED;
     }

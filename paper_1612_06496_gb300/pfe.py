@@ -27,7 +27,7 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_destroy", "pfe_last_error", "pfe_status_string", "pfe_get_info", "pfe_set_stream",
            "pfe_get_array", "pfe_set_array", "pfe_get_edges", "pfe_apply_A", "pfe_solve_system",
            "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
-           "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_get_segments",
+           "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_ic0", "pfe_get_segments",
            "pfe_get_segment_stats", "pfe_laplacian_eigenmap", "pfe_objective", "pfe_autotune",
            "pfe_set_variant", "pfe_solve_two_stage", "pfe_kmeans"]
 SPMM_NVARIANTS = 6  # PFE_SPMM_GENERAL, _ROW1, _ROW2, _ROW2_4, _TMA, _STENCIL
@@ -406,6 +406,10 @@ class PFE:
             return
         pp, keep = _ptr_f32(params)
         self._check(self.lib.pfe_fsai_set(self.ctx, pp), "pfe_fsai_set")
+
+    def ic0(self):
+        """The paper's incomplete-Cholesky preconditioner, IC(0), for later solves."""
+        self._check(self.lib.pfe_ic0(self.ctx), "pfe_ic0")
 
     def fsai_classical(self):
         """Use the classical FSAI factor (per-row dense solves) as preconditioner."""
