@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--precond", default="learned", choices=["learned", "jacobi"],
-                    help="preconditioner of the timed FP32 arm (learned FSAI or Jacobi)")
+    ap.add_argument("--precond", default="learned", choices=["learned", "jacobi", "classical", "ic0"],
+                    help="preconditioner of the timed FP32 arm (learned FSAI, Jacobi, classical FSAI or "
+                         "the paper's incomplete Cholesky IC(0))")
     ap.add_argument("--no-alt", action="store_true", help="skip the FP32 arm with the other preconditioner")
     ap.add_argument("--alt-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-worker", default=None, help=argparse.SUPPRESS)
@@ -408,6 +409,10 @@ def main():
                 stream=stream, loop=args.loop, **geom)
         if precond == "learned":
             p.fsai_set(fsai_params)  # network inference of G runs inside the timed setup
+        elif precond == "classical":
+            p.fsai_classical()
+        elif precond == "ic0":
+            p.ic0()
         p.init(Y0d)
         tuned[precision + "/" + precond] = p.autotune(10)  # kernel variants for this problem (setup)
         torch.cuda.synchronize()
@@ -607,9 +612,11 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(spec, world),
             "precision_path": "FP32 edge/SpMM/vectors, double-FP32 dots and PCG solution, FP64 P-step; "
-                              + ("learned FSAI preconditioner (BF16 tensor-core MLP, weights "
-                                 "paper_1612_06496_gb300/fsai_weights.npz)" if args.precond == "learned"
-                                 else "Jacobi preconditioner"),
+                              + {"learned": "learned FSAI preconditioner (BF16 tensor-core MLP, weights "
+                                            "paper_1612_06496_gb300/fsai_weights.npz)",
+                                 "jacobi": "Jacobi preconditioner",
+                                 "classical": "classical FSAI preconditioner",
+                                 "ic0": "IC(0) preconditioner (level-scheduled triangular solves)"}[args.precond],
             "precond": args.precond,
             "pcg_iters_mean": iters_total / max(n_solves, 1),
             "pcg_iters_max": max(s["pcg_iters_max"] for s in stats),
