@@ -468,7 +468,8 @@ def main():
     edge_ms = p.time_kernel("edge", 10)
     n, d, nnz, ne = info["n"], info["d"], info["nnz_A"], info["n_edges"]
     fsai_k = {}
-    if args.precond == "learned":
+    fsai_arm = args.precond in ("learned", "classical")  # the FSAI kernels run (any factor G)
+    if fsai_arm:
         # lower (upper) slots: FP32 G value + int32 column each, kb and G_ii per row;
         # t = G r': r, q in, r', t out; z = G^T t with p_new = z + beta p: t
         # and p in, p_new out, and every other iteration y += alpha_prev
@@ -500,11 +501,11 @@ def main():
     # key, ms per launch, algorithmic bytes per launch); one launch each per
     # iteration (k_fsai_zp: folding and holding launches alternate)
     cands = [("%s<float,%d> (SpMM variant %d)" % (kname, d, variant), "spmm", spmm_ms, spmm_bytes)]
-    if args.precond == "learned":
+    if fsai_arm:
         cands += [("k_fsai_tr<float,%d>" % d, "fsai_tr", tr_ms, tr_b),
                   ("k_fsai_zp<float,%d> (folding and holding launches averaged)" % d, "fsai_zp",
                    0.5 * (zf_ms + zh_ms), 0.5 * (zf_b + zh_b))]
-    else:
+    elif args.precond == "jacobi":
         cands += [("k_update<float,%d>" % d, "update", upd_ms, upd_b),
                   ("k_pupdate<float,%d> (folding and holding launches averaged)" % d, "pupdate",
                    0.5 * (pup_ms + puph_ms), 0.5 * (pup_b + puph_b))]
@@ -580,6 +581,10 @@ def main():
                     stream=stream, **geom)
             if args.precond == "learned":
                 r.fsai_set(fsai_params)  # host copy of the network weights
+            elif args.precond == "classical":
+                r.fsai_classical()
+            elif args.precond == "ic0":
+                r.ic0()
             r.init(Y0h)
             r.solve(1, spec.n_inner, Yo, Yho)
             r.close()
