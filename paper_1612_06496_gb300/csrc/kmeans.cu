@@ -213,7 +213,7 @@ pfe_status kmeans_run(pfe_ctx *c, const double *X, int d, int k, const double *C
     double *dres = reinterpret_cast<double *>(dch) + 2;
     cudaError_t e = cudaMemsetAsync(ac, 0, sizeof(ArgCtl), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dch, 0, sizeof(unsigned long long) + 64, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dlab, 0xff, sizeof(int) * n, s);  // labels -1: all change in round 1
+    if (e == cudaSuccess) e = cudaMemsetAsync(dlab, 0xff, sizeof(int) * n, s);  // labels -1: every label changes in the first Lloyd round
     if (e == cudaSuccess) {
         if (C0) {
             e = cudaMemcpyAsync(dC, C0, sizeof(double) * k * d, cudaMemcpyDefault, s);

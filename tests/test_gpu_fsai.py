@@ -121,3 +121,32 @@ def test_fsai_pcg_iterations_match_oracle(radius):
     assert abs(st["pcg_iters"] - int(info["iters"].max())) <= 2, (st["pcg_iters"], info["iters"])
     assert relerr(Y, Yo) < 1e-4
     p.close()
+
+
+def test_trained_network_cuts_pcg_iterations_on_the_gpu():
+    """The committed weights through the GPU's BF16 tensor-core network and
+    FSAI kernels: fewer PCG iterations than Jacobi on an image the network
+    was not trained on (the oracle needs 0.54x), about as many as the oracle
+    with the same weights, and the exact solution."""
+    from paper_1612_06496_gb300.learned import load_weights
+    spec = small_spec(H=40, W=48, d=4, seed=11, regions=4)
+    p, X, Y0 = gpu_problem(spec, "mixed", tol=1e-6)
+    g = oracle_graph(spec, X)
+    p.init(Y0)
+    R = np.random.default_rng(31).standard_normal((g.n, 4))
+    Yj = np.zeros_like(R)
+    it_j = p.solve_system(R, Yj)["pcg_iters"]
+    p.fsai_set(load_weights())
+    Y = np.zeros_like(R)
+    st = p.solve_system(R, Y)
+    th = load_weights().astype(np.float64)
+    Fd, Fe = F.entry_features(g)
+    od, _ = F.mlp_forward(th, Fd)
+    oe, _ = F.mlp_forward(th, Fe)
+    G, _, _ = F.assemble_G(g, od, oe)
+    _, info = O.pcg(g.A, R, np.zeros_like(R), 1e-6, 5000, 50, lambda Q: F.fsai_apply(G, Q))
+    n_o = int(info["iters"].max())
+    assert st["converged"] and st["pcg_iters"] <= 0.8 * it_j, (st["pcg_iters"], it_j)
+    assert abs(st["pcg_iters"] - n_o) <= max(3, 0.25 * n_o), (st["pcg_iters"], n_o)
+    assert relerr(Y, O.DirectSolver(g.A)(R)[0]) < 1e-4
+    p.close()
