@@ -43,7 +43,6 @@ notes of the repository):
 """
 from __future__ import annotations
 
-import time
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -428,31 +427,3 @@ def two_stage(g: Graph, Y0: np.ndarray, n_outer: int, n_inner: int, n_stage2: in
 def embedding(g: Graph, st: State) -> np.ndarray:
     """Yhat = D^{-1/2} P, the D-orthonormal embedding."""
     return st.P / np.sqrt(g.dvec)[:, None]
-
-
-# --------------------------------------------------------------------------
-# Timing helper (CPU baseline): the oracle as it stands, Jacobi-PCG mode
-# --------------------------------------------------------------------------
-
-
-def time_inner_sample(g: Graph, Y0: np.ndarray, tol: float, pcg_iters: int,
-                      max_iter: int = 5000) -> dict:
-    """Time one split-Bregman step with a PCG capped at ``pcg_iters`` iterations.
-
-    Returns seconds for the edge/right-hand-side work and per PCG iteration,
-    so that a caller can scale to a whole outer iteration.
-    """
-    st = init_state(g, Y0)
-    sq = np.sqrt(g.dvec)[:, None]
-    t0 = time.perf_counter()
-    rhs = g.lam * (g.M.T @ (st.ds - st.bs)) + g.r * sq * (st.P - st.B)
-    t1 = time.perf_counter()
-    Y, info = jacobi_pcg(g.A, rhs, st.Y, tol, min(pcg_iters, max_iter), refresh=0)
-    t2 = time.perf_counter()
-    MY = g.M @ Y
-    ds = shrink(MY + st.bs, 1.0 / g.lam)
-    _ = st.bs + MY - ds
-    t3 = time.perf_counter()
-    n_it = int(info["iters"].max()) if info["iters"].size else 0
-    return {"edge_s": (t1 - t0) + (t3 - t2), "pcg_s": t2 - t1, "pcg_iters": n_it,
-            "per_pcg_iter_s": (t2 - t1) / max(n_it, 1)}

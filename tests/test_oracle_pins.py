@@ -90,6 +90,23 @@ def test_heat_kernel_closed_form():
     assert w[2] == pytest.approx(np.exp(-25.0 / (2 * sigma * sigma)), rel=1e-13)
 
 
+def test_system_matrix_and_lambda_on_a_path():
+    """Three points on a line, edges 0-1 and 1-2: every entry of
+    A = lam (D2 - W o W) + r D and lam = sqrt(vol W) written out by hand."""
+    sigma = 0.5
+    X = np.array([[0.0, 0.0], [0.3, 0.0], [0.3, 0.8]])
+    w1, w2 = np.exp(-0.09 / (2 * sigma ** 2)), np.exp(-0.64 / (2 * sigma ** 2))
+    g = O.build_graph(X, np.array([0, 1]), np.array([1, 2]), sigma, r=0.7)
+    lam, r = np.sqrt(2.0 * (w1 + w2)), 0.7        # vol W counts each edge from both ends
+    assert g.lam == pytest.approx(lam, rel=1e-15)
+    expect = np.array([[lam * w1 ** 2 + r * w1, -lam * w1 ** 2, 0.0],
+                       [-lam * w1 ** 2, lam * (w1 ** 2 + w2 ** 2) + r * (w1 + w2), -lam * w2 ** 2],
+                       [0.0, -lam * w2 ** 2, lam * w2 ** 2 + r * w2]])
+    np.testing.assert_allclose(g.A.toarray(), expect, rtol=1e-14, atol=0.0)
+    # an explicit lambda is kept as given
+    assert O.build_graph(X, np.array([0, 1]), np.array([1, 2]), sigma, lam=2.5).lam == 2.5
+
+
 def test_degrees_and_edge_operator_laplacian():
     """M^T M is the Laplacian of the squared weights; d is the row sum of W."""
     X, a, b, sigma = _random_graph(9, 0.4, 3)
