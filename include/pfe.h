@@ -11,7 +11,8 @@
  *
  * Conventions for every entry point:
  *  - Returns a pfe_status; PFE_OK is 0.  No C++ exception crosses the ABI.
- *    pfe_last_error() returns a message for the last failing call on a ctx.
+ *    pfe_last_error() returns a message for the last failing call on a ctx
+ *    (pfe_last_error(NULL): for the calling thread's last failed build).
  *  - Array arguments are plain pointers.  Unless a parameter says otherwise
  *    a pointer may address host memory (pageable or pinned) or device
  *    memory of the context's GPU; the library detects which and copies host
@@ -318,7 +319,9 @@ PFE_API pfe_status pfe_solve_two_stage(pfe_ctx *c, int32_t n_outer, int32_t n_in
 /* Frees every library allocation of the context (NULL is allowed). */
 PFE_API pfe_status pfe_destroy(pfe_ctx *c);
 
-/* Message of the last failed call on c (never NULL; "" when none). */
+/* Message of the last failed call on c (never NULL; "" when none).  With
+ * c = NULL: the message of the last pfe_build_graph on the calling thread
+ * that failed (its context no longer exists), "" if that call succeeded. */
 PFE_API const char *pfe_last_error(const pfe_ctx *c);
 
 /* Human-readable name of a status code (static storage). */

@@ -279,7 +279,11 @@ const char *pfe_status_string(pfe_status s) {
     return "PFE_?";
 }
 
-const char *pfe_last_error(const pfe_ctx *c) { return c ? c->err.c_str() : "null context"; }
+// Message of the last pfe_build_graph on this thread that failed (its
+// context is gone by then, so the message cannot live in one).
+static thread_local std::string t_build_err;
+
+const char *pfe_last_error(const pfe_ctx *c) { return c ? c->err.c_str() : t_build_err.c_str(); }
 
 pfe_status pfe_destroy(pfe_ctx *c) {
     if (!c) return PFE_OK;
@@ -294,7 +298,8 @@ pfe_status pfe_destroy(pfe_ctx *c) {
     return PFE_OK;
 }
 
-pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_params *p, pfe_stream_t stream) {
+static pfe_status build_graph_impl(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_params *p,
+                                   pfe_stream_t stream) {
     if (!out) return PFE_EINVAL;
     *out = nullptr;
     if (!gd || !p) return PFE_EINVAL;
@@ -358,9 +363,8 @@ pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_pa
     c->h_seg_h = sh;
     c->h_seg_w = sw;
     auto bail = [&](pfe_status s) {
-        std::string msg = c->err;
+        t_build_err = c->err;  // kept for pfe_last_error(NULL)
         pfe_destroy(c);
-        (void)msg;
         return s;
     };
     cudaError_t e = cudaGetDevice(&c->device);
@@ -425,6 +429,13 @@ pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_pa
     c->grid_rows = (int)std::max<int64_t>(1, std::min(want, need));
     *out = c;
     return PFE_OK;
+}
+
+pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_params *p, pfe_stream_t stream) {
+    t_build_err.clear();
+    const pfe_status st = build_graph_impl(out, gd, p, stream);
+    if (st != PFE_OK && t_build_err.empty()) t_build_err = pfe_status_string(st);
+    return st;
 }
 
 pfe_status pfe_set_stream(pfe_ctx *c, pfe_stream_t stream) {

@@ -207,7 +207,8 @@ class PFE:
         st = self.lib.pfe_build_graph(C.byref(self.ctx), C.byref(gd), C.byref(p), _stream_ptr(stream))
         self._feat = self._ei = self._ej = None
         if st != PFE_OK:
-            raise PFEError(st, f"pfe_build_graph failed: {self.lib.pfe_status_string(st).decode()}")
+            raise PFEError(st, f"pfe_build_graph failed: {self.lib.pfe_status_string(st).decode()}: "
+                               f"{self.lib.pfe_last_error(None).decode()}")
 
     # -- helpers
     def _check(self, st: int, what: str, ok=(PFE_OK,)):

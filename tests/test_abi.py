@@ -66,3 +66,21 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert L.pfe_inner_step(None, None) == 1
     assert L.pfe_solve(None, 1, 1, None, None, None) == 1
     assert L.pfe_destroy(None) == 0
+
+
+def test_failed_build_leaves_its_message(lib):
+    """pfe_last_error(NULL) reports the calling thread's last failed build
+    (its context is gone); a later failure replaces it."""
+    from paper_1612_06496_gb300.pfe import GraphDesc, Params, load_library
+    L = load_library()
+    ctx = ctypes.c_void_p()
+    p = Params()
+    L.pfe_default_params(ctypes.byref(p))
+    g = GraphDesc()
+    g.n = 1
+    assert L.pfe_build_graph(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(p), None) == 1
+    assert L.pfe_last_error(None) == b"PFE_EINVAL" and not ctx.value
+    g.n, g.m, g.sigma, g.kind, g.features, g.radius, g.H, g.W = 16, 5, 0.1, 0, 8, 2.0, 4, 4
+    p.precond = 7  # not a preconditioner the build takes
+    assert L.pfe_build_graph(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(p), None) == 8
+    assert L.pfe_last_error(None) == b"PFE_EUNSUPPORTED"

@@ -105,6 +105,7 @@ def test_zero_degree_vertex_is_rejected():
     with pytest.raises(PFEError) as ei:
         PFE(X, sigma=0.1, H=8, W=9, radius=2.0)
     assert ei.value.status == 1
+    assert "zero degree" in str(ei.value)  # the build's message outlives its context
 
 
 @pytest.mark.parametrize("bad", ["self", "dup", "range"])
@@ -121,6 +122,7 @@ def test_bad_edge_lists_are_rejected(bad):
     with pytest.raises(PFEError) as ei:
         _pfe(X, a, b, 1.0)
     assert ei.value.status == 1
+    assert {"self": "self-loop", "dup": "same pair", "range": "outside"}[bad] in str(ei.value)
 
 
 def test_dimension_and_call_order_errors():
