@@ -136,6 +136,13 @@ def test_shrink_closed_form_and_prox():
     z = O.shrink(y, g)
     np.testing.assert_array_equal(z, [-0.75, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.26 - 0.25, 0.75, 0.5])
     assert np.isnan(O.shrink(np.array([np.nan]), g)[0])
+    # subnormals: below any positive threshold they shrink to zero; with
+    # gamma = 0 Shrink is the identity on them
+    tiny = np.array([5e-324, -5e-324, 2.2e-308, -1e-310])
+    np.testing.assert_array_equal(O.shrink(tiny, g), np.zeros(4))
+    np.testing.assert_array_equal(O.shrink(tiny, 0.0), tiny)
+    assert O.shrink(np.array([1e-310]), 1e-310)[0] == 0.0
+    assert O.shrink(np.array([3e-310]), 1e-310)[0] == 3e-310 - 1e-310
     # odd function
     rng = np.random.default_rng(0)
     v = rng.standard_normal(1000)
