@@ -330,21 +330,43 @@ def full_graph_size_and_lambda(spec):
     return spec.n + 2 * a.shape[0], float(np.sqrt(vol))
 
 
+L2_BYTES = 129 * 2 ** 20  # GB300 L2
+
+
+def stencil_size(radius: float) -> int:
+    """Neighbours of an interior pixel: offsets (dx, dy) != 0 with dx^2 + dy^2 <= radius^2."""
+    r = int(radius)
+    return sum(1 for dy in range(-r, r + 1) for dx in range(-r, r + 1)
+               if (dx or dy) and dx * dx + dy * dy <= radius * radius)
+
+
+def l2_note(n: int, d: int, radius: float) -> str:
+    """Whether the PCG loop's data (FP32 matrix value + column per stored
+    nonzero, about eight n x d FP32 vectors) outgrows the L2 between timed
+    iterations; no flush is done either way."""
+    ws = 8 * n * (1 + stencil_size(radius)) + 32 * n * d
+    if ws > L2_BYTES:
+        return f"PCG working set ~{ws / 2 ** 20:.0f} MiB > {L2_BYTES >> 20} MiB L2: inputs larger than L2, no flush"
+    return (f"PCG working set ~{ws / 2 ** 20:.0f} MiB fits in the {L2_BYTES >> 20} MiB L2: no flush, so this "
+            f"workload's figures are L2-warm, not HBM-bound")
+
+
 def workload_config(spec, gpus: int) -> dict:
     if spec.name == "C3":
         from synth import batch_specs
         specs = batch_specs()
+        n = sum(s.n for s in specs)
         return {"workload": f"C3: batch of {len(specs)} synthetic Voronoi images, 96..481 x 96..321 pixels, "
                             f"3-12 regions, radius-2 graphs, sigma=0.1, d=5, 10 inner iterations per outer step "
                             f"(every image), PCG rel-res 1e-06, one launch per kernel for the whole batch",
-                "n": sum(s.n for s in specs), "images": len(specs), "d": 5, "n_inner": 10, "tol": 1e-6,
-                "l2": "working set per step >> L2 (inputs larger than L2, no flush)",
+                "n": n, "images": len(specs), "d": 5, "n_inner": 10, "tol": 1e-6,
+                "l2": l2_note(n, 5, specs[0].radius),
                 "parallelism": f"replicas x{gpus}" if gpus > 1 else "single GPU"}
     return {"workload": f"{spec.name}: {spec.W}x{spec.H} synthetic Voronoi image, radius-{spec.radius:g} graph, "
                         f"sigma={spec.sigma:g}, d={spec.d}, {spec.n_inner} inner iterations per outer step, "
                         f"PCG rel-res {spec.tol:g}",
             "n": spec.n, "d": spec.d, "n_inner": spec.n_inner, "tol": spec.tol,
-            "l2": "working set per step >> L2 (inputs larger than L2, no flush)",
+            "l2": l2_note(spec.n, spec.d, spec.radius),
             "parallelism": f"replicas x{gpus}" if gpus > 1 else "single GPU"}
 
 

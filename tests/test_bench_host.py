@@ -69,3 +69,33 @@ def test_stale_capture_reads_null(bench, tmp_path, monkeypatch):
 def test_measured_peaks_are_read(bench):
     pk = bench.measured_peaks()
     assert pk["hbm_gbs"] > 1000 and pk["source"] in ("measured", "fallback")
+
+
+def test_l2_note_follows_the_working_set(bench):
+    from synth import CONFIGS
+    assert bench.stencil_size(2.0) == 12 and bench.stencil_size(3.0) == 28 and bench.stencil_size(1.0) == 4
+    # the 2048^2 benchmark image and the batch outgrow the L2; the small images do not
+    for name, big in (("C1", False), ("C2", False), ("C3", True), ("C5", True)):
+        note = bench.workload_config(CONFIGS[name], 1)["l2"]
+        assert ("inputs larger than L2" in note) == big, (name, note)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference on the small image: one JSON line with the
+    oracle's timing, its CPU baseline and end-to-end objects."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(os.path.dirname(os.path.dirname(__file__)), "bench.py"),
+                        "--impl", "reference", "--workload", "C1", "--steps", "2", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "s/outer-iter" and d["higher_is_better"] is False
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["dtype"] == "f64" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("C1: 32x32")
