@@ -21,6 +21,9 @@ M^{-1} = G^T G with G lower triangular on the pattern of tril(A):
       L = log(tr(G A G^T) / n) - (2/n) sum_i log G_ii   (+ log det A / n, constant),
   which classical FSAI minimises over the same pattern.
 
+Training takes Adam steps (Kingma and Ba, ICLR 2015, Algorithm 1) on the
+loss averaged over a mini-batch of images: ``adam_step``.
+
 Parameter vector layout (float64 here, float32 on the GPU):
   W1 (4 x 64, row-major), b1 (64), W2 (64 x 64), b2 (64), W3 (64 x 2), b3 (2).
 """
@@ -169,3 +172,17 @@ def classical_fsai(A) -> sp.csr_matrix:
 def fsai_apply(G, R):
     """z = G^T (G r), column by column."""
     return G.T @ (G @ R)
+
+
+def adam_step(theta, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8):
+    """One step of Adam (Kingma and Ba, ICLR 2015, Algorithm 1), the
+    optimiser of the network's training: exponential moving averages of the
+    gradient and of its square, each divided by its bias correction
+    1 - beta^step, and a step of lr * mhat / (sqrt(vhat) + eps).
+    Returns (theta, m, v) after the step; the inputs are not changed."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mhat = m / (1.0 - beta1 ** step)
+    vhat = v / (1.0 - beta2 ** step)
+    return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v

@@ -173,3 +173,39 @@ def test_trained_network_cuts_pcg_iterations(H, W, radius, seed):
     assert n_l <= 1.1 * n_c, (n_l, n_c)
     Xd = O.DirectSolver(g.A)(R)[0]
     assert np.linalg.norm(Xl - Xd) <= 1e-4 * np.linalg.norm(Xd)
+
+
+def test_adam_moves_by_lr_sign_of_a_constant_gradient():
+    """Adam's bias corrections make both moment estimates exact when the
+    gradient is constant, so every step moves a parameter by
+    lr g / (|g| + eps): about lr against the sign of its gradient, whatever
+    the gradient's scale."""
+    rng = np.random.default_rng(3)
+    g = rng.choice([-1.0, 1.0], 60) * np.logspace(-3, 3, 60)
+    th0 = rng.standard_normal(60)
+    th, m, v = th0.copy(), np.zeros(60), np.zeros(60)
+    for step in range(1, 21):
+        th, m, v = F.adam_step(th, g, m, v, step, lr=0.01)
+    np.testing.assert_allclose(th, th0 - 20 * 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-12)
+    # no gradient, no moments: no movement
+    th2, _, _ = F.adam_step(th0, np.zeros(60), np.zeros(60), np.zeros(60), 1, lr=0.01)
+    np.testing.assert_array_equal(th2, th0)
+
+
+def test_adam_moments_are_the_weighted_sums_of_past_gradients():
+    """After T steps m = (1 - b1) sum_k b1^(T-k) g_k and v likewise with g_k^2
+    (the recursion unrolled); the T-th step is lr mhat / (sqrt(vhat) + eps)."""
+    rng = np.random.default_rng(4)
+    T, n, lr, b1, b2, eps = 6, 40, 3e-3, 0.8, 0.95, 1e-6
+    gs = rng.standard_normal((T, n))
+    th, m, v = rng.standard_normal(n), np.zeros(n), np.zeros(n)
+    for t in range(1, T + 1):
+        prev = th
+        th, m, v = F.adam_step(th, gs[t - 1], m, v, t, lr, b1, b2, eps)
+    w1 = (1 - b1) * b1 ** np.arange(T - 1, -1, -1)
+    w2 = (1 - b2) * b2 ** np.arange(T - 1, -1, -1)
+    m_sum, v_sum = w1 @ gs, w2 @ gs ** 2
+    np.testing.assert_allclose(m, m_sum, rtol=1e-13)
+    np.testing.assert_allclose(v, v_sum, rtol=1e-13)
+    last = lr * (m_sum / (1 - b1 ** T)) / (np.sqrt(v_sum / (1 - b2 ** T)) + eps)
+    np.testing.assert_allclose(prev - th, last, rtol=1e-12, atol=1e-15)  # prev - th cancels: |theta| ~ 1

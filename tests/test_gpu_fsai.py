@@ -150,3 +150,35 @@ def test_trained_network_cuts_pcg_iterations_on_the_gpu():
     assert abs(st["pcg_iters"] - n_o) <= max(3, 0.25 * n_o), (st["pcg_iters"], n_o)
     assert relerr(Y, O.DirectSolver(g.A)(R)[0]) < 1e-4
     p.close()
+
+
+def test_adam_kernel_matches_oracle():
+    """pfe_adam_update (FP32, in place on device arrays) against the oracle's
+    FP64 Adam step, on a length that is not a multiple of the block, at step
+    3 from non-zero moments.  FP32 bounds: m from its two terms' sizes (they
+    may cancel), v (non-negative terms) relative, the parameter to its own
+    rounding plus the update's error at the scale of its terms."""
+    import torch
+    from paper_1612_06496_gb300.pfe import adam_update
+    from tests.gpu_common import ensure_built
+    ensure_built()
+    rng = np.random.default_rng(9)
+    # hyper-parameters that FP32 holds exactly, so both sides use the same
+    # values (FP32 rounding of 0.999 alone would move 1 - b2 by 5e-5)
+    n, step, lr, b1, b2, eps = 1000, 3, 2.0 ** -7, 0.875, 1 - 2.0 ** -10, 2.0 ** -27
+    p0 = rng.standard_normal(n).astype(np.float32)
+    g = (rng.standard_normal(n) * np.logspace(-3, 1, n)).astype(np.float32)
+    m0 = (0.1 * rng.standard_normal(n)).astype(np.float32)
+    v0 = rng.uniform(0.0, 1.0, n).astype(np.float32)
+    P, G, M, V = (torch.from_numpy(a.copy()).cuda() for a in (p0, g, m0, v0))
+    adam_update(P, G, M, V, step, lr, b1, b2, eps)
+    torch.cuda.synchronize()
+    f64 = [a.astype(np.float64) for a in (p0, g, m0, v0)]
+    th, m, v = F.adam_step(*f64, step, lr, b1, b2, eps)
+    u32 = 2.0 ** -23
+    m_terms = np.abs(b1 * f64[2]) + np.abs((1 - b1) * f64[1])
+    assert np.all(np.abs(M.cpu().numpy() - m) <= 4 * u32 * m_terms)
+    np.testing.assert_allclose(V.cpu().numpy(), v, rtol=4 * u32)
+    u_terms = lr * (m_terms / (1 - b1 ** step)) / (np.sqrt(v / (1 - b2 ** step)) + eps)
+    err = np.abs(P.cpu().numpy().astype(np.float64) - th)
+    assert np.all(err <= u32 * np.abs(th) + 16 * u32 * u_terms)
