@@ -330,7 +330,9 @@ PFE_API const char *pfe_status_string(pfe_status s);
 /* Sizes and parameters of a context. Never synchronises. */
 PFE_API pfe_status pfe_get_info(const pfe_ctx *c, pfe_info *info);
 
-/* Changes the stream later calls enqueue on. */
+/* Changes the stream later calls enqueue on.  Work already queued on the
+ * previous stream is ordered before them (the new stream waits for it on
+ * the device; the call does not block the host). */
 PFE_API pfe_status pfe_set_stream(pfe_ctx *c, pfe_stream_t stream);
 
 /* Segments of a batch (host arrays, either may be NULL): off[0..nseg] first

@@ -440,7 +440,18 @@ pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_pa
 
 pfe_status pfe_set_stream(pfe_ctx *c, pfe_stream_t stream) {
     if (!c) return PFE_EINVAL;
-    c->stream = (cudaStream_t)stream;
+    const cudaStream_t ns = (cudaStream_t)stream;
+    if (ns != c->stream) {
+        // work already queued on the old stream stays first: the new stream
+        // waits for it on the device (the host does not block)
+        cudaEvent_t ev;
+        PFE_CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ns, ev, 0);
+        cudaEventDestroy(ev);  // released once the recorded work completes
+        if (e != cudaSuccess) return fail(c, PFE_ECUDA, "pfe_set_stream: ordering the old stream before the new");
+    }
+    c->stream = ns;
     return PFE_OK;
 }
 
