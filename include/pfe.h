@@ -55,7 +55,7 @@ typedef enum pfe_status {
     PFE_ENOTCONV = 4,      /* a PCG solve hit max_iter; results are still written */
     PFE_ENUMERIC = 5,      /* NaN/Inf or a non-positive curvature p^T A p in PCG */
     PFE_ESINGULAR = 6,     /* the P-step's Gram matrix is numerically singular */
-    PFE_ETIMEOUT = 7,      /* reserved: a bounded device wait ran out */
+    PFE_ETIMEOUT = 7,      /* a bounded device wait ran out (a bulk copy of the TMA-staged SpMM never landed) */
     PFE_EUNSUPPORTED = 8,  /* embedding dimension or option not built into this library */
     PFE_ESTATE = 9         /* call out of order (e.g. pfe_inner_step before pfe_init) */
 } pfe_status;
@@ -217,10 +217,11 @@ enum {
     PFE_SPMM_ROW2_4 = 3,  /* uniform rows: two row groups per step, >= 4 blocks per SM */
     PFE_SPMM_TMA = 4,     /* uniform rows: the slots of tiles of rows staged in shared memory by
                              bulk asynchronous (TMA) copies, two tiles ahead (one problem only) */
-    PFE_SPMM_STENCIL = 5, /* one grid image: the stencil form; a block walks a strip of the image
-                             down, a ring of row bands of p and the rows' matrix values staged
-                             in shared memory (cp.async, several rows ahead); the column array
-                             is not read and no gather leaves the SM */
+    PFE_SPMM_STENCIL = 5, /* one grid image whose width is a multiple of 4: the stencil form; a
+                             block walks a strip of the image down, a ring of row bands of p and
+                             the rows' matrix values staged in shared memory by bulk asynchronous
+                             (TMA) copies three rows ahead; the column array is not read and no
+                             gather leaves the SM */
     PFE_SPMM_NVARIANTS = 6
 };
 enum { PFE_TUNE_SPMM = 0 };
