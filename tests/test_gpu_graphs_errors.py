@@ -1,6 +1,5 @@
 """Edge-list graphs on the GPU and the error paths of the C ABI (every
 failure is made on the host or through the inputs; nothing faults a GPU)."""
-import ctypes
 
 import numpy as np
 import pytest

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import pfe_oracle as O
-from synth import CONFIGS, make_problem
+from synth import CONFIGS
 from tests.gpu_common import ensure_built, gpu_problem, oracle_graph, relerr
 
 pytestmark = pytest.mark.gpu

@@ -8,7 +8,6 @@ import os
 import numpy as np
 import pytest
 import scipy.linalg as sla
-import scipy.sparse as sp
 
 from oracle import pfe_oracle as O
 
