@@ -50,7 +50,7 @@ typedef void *pfe_stream_t;
 typedef enum pfe_status {
     PFE_OK = 0,
     PFE_EINVAL = 1,        /* bad argument (NULL, size, zero-degree vertex, duplicate edge, ...) */
-    PFE_ENOMEM = 2,        /* a device or host allocation failed */
+    PFE_ENOMEM = 2,        /* a device or host allocation failed, or would pass max_device_bytes */
     PFE_ECUDA = 3,         /* a CUDA runtime call failed */
     PFE_ENOTCONV = 4,      /* a PCG solve hit max_iter; results are still written */
     PFE_ENUMERIC = 5,      /* NaN/Inf or a non-positive curvature p^T A p in PCG */
@@ -130,6 +130,10 @@ typedef struct pfe_params {
     int32_t loop_mode;    /* PFE_LOOP_GRAPH (default) or PFE_LOOP_HOST */
     int32_t check_every;  /* iterations per graph body / host poll; default 4 */
     int32_t blocks_per_sm;/* persistent-grid occupancy of the row kernels; 0 = auto */
+    int64_t max_device_bytes; /* cap on the device memory the context keeps (pfe_info.device_bytes):
+                                 an allocation that would pass it fails with PFE_ENOMEM and
+                                 allocates nothing; temporaries of a single call are not
+                                 counted; 0 (default) = no cap */
 } pfe_params;
 
 /* Fills *p with the defaults listed above.  Never fails. */

@@ -33,6 +33,8 @@ pfe_status fail(pfe_ctx *c, pfe_status s, const char *msg) {
 template <typename P>
 pfe_status walloc(pfe_ctx *c, P **p, int64_t count) {
     size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(P);
+    *p = nullptr;
+    if (over_device_cap(c, bytes)) return PFE_ENOMEM;
     cudaError_t e = cudaMalloc((void **)p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -42,6 +44,7 @@ pfe_status walloc(pfe_ctx *c, P **p, int64_t count) {
     }
     c->work_allocs.push_back((void *)*p);
     c->bytes += (int64_t)bytes;
+    c->work_bytes += (int64_t)bytes;
     return PFE_OK;
 }
 
@@ -56,6 +59,8 @@ void free_work(pfe_ctx *c) {
     free_pcg_graph(c);
     for (void *p : c->work_allocs) cudaFree(p);
     c->work_allocs.clear();
+    c->bytes -= c->work_bytes;
+    c->work_bytes = 0;
     c->wk = Work{};
     c->fsai.t = nullptr;
     c->fsai.r1 = nullptr;
@@ -611,8 +616,7 @@ pfe_status pfe_get_segment_stats(pfe_ctx *c, int32_t *iters, double *relres, int
     return PFE_OK;
 }
 
-pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
-    if (!c) return PFE_EINVAL;
+static pfe_status init_impl(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
     if (d < 1 || d > c->n) return fail(c, PFE_EINVAL, "d must be in [1, n]");
     if (Y0 && ldY0 < d) return fail(c, PFE_EINVAL, "ldY0 < d");
     if (!d_supported(d)) return fail(c, PFE_EUNSUPPORTED, "embedding dimension not built into libpfe");
@@ -714,6 +718,19 @@ pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
     PFE_TRY(check_pstep(c));
     c->inited = true;
     return PFE_OK;
+}
+
+pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
+    if (!c) return PFE_EINVAL;
+    const pfe_status st = init_impl(c, d, Y0, ldY0);
+    // a failure after the previous state was released leaves no work buffers
+    // behind (one rejected by the argument checks keeps that state)
+    if (st != PFE_OK && !c->inited) {
+        const std::string msg = c->err;
+        free_work(c);
+        c->err = msg;
+    }
+    return st;
 }
 
 pfe_status pfe_inner_step(pfe_ctx *c, pfe_step_stats *st) {

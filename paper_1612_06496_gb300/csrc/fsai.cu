@@ -714,9 +714,19 @@ pfe_status fsai_alloc(pfe_ctx *c) {
     auto &f = c->fsai;
     if (f.gdiag) return PFE_OK;
     const int64_t n = c->g.n, ne = c->g.n_edges, N = n + ne;
+    // all or nothing: a failure frees what this call allocated, so a later
+    // call starts again from no buffers
+    const size_t n_allocs0 = c->dev_allocs.size();
+    const int64_t bytes0 = c->bytes;
+    bool capped = false;
     auto al = [&](void **p, size_t bytes) -> bool {
+        if (over_device_cap(c, bytes)) {
+            capped = true;
+            return false;
+        }
         if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
             cudaGetLastError();
+            *p = nullptr;
             return false;
         }
         c->dev_allocs.push_back(*p);
@@ -734,7 +744,14 @@ pfe_status fsai_alloc(pfe_ctx *c) {
         !al((void **)&f.gpart, (size_t)f.mlp_blocks * kNParam * sizeof(float)) ||
         !al((void **)&f.tick, 4 * sizeof(unsigned)) || !al((void **)&f.params, kNParam * sizeof(float)) ||
         !al((void **)&f.grad, kNParam * sizeof(float))) {
-        c->err = "FSAI buffers: cudaMalloc failed";
+        for (size_t k = n_allocs0; k < c->dev_allocs.size(); ++k) cudaFree(c->dev_allocs[k]);
+        c->dev_allocs.resize(n_allocs0);
+        c->bytes = bytes0;
+        f.gdiag = f.gE = f.gslot = f.srow = f.hraw = f.dq = f.gpart = f.params = f.grad = nullptr;
+        f.kb = f.ent_of_slot = nullptr;
+        f.qrow = f.logd = f.sums = f.part = nullptr;
+        f.tick = nullptr;
+        if (!capped) c->err = "FSAI buffers: cudaMalloc failed";
         return PFE_ENOMEM;
     }
     cudaStream_t s = c->stream;

@@ -418,6 +418,7 @@ __global__ void k_values_seg(int64_t n, int64_t n_slices, const int *slice_ptr, 
 template <typename P>
 pfe_status dalloc(pfe_ctx *c, P **p, int64_t count) {
     size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(P);
+    if (over_device_cap(c, bytes)) return PFE_ENOMEM;
     cudaError_t e = cudaMalloc((void **)p, bytes);
     if (e != cudaSuccess) {
         c->err = std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e);

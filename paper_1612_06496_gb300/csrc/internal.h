@@ -151,13 +151,24 @@ struct pfe_ctx {
     std::string err;
     std::vector<void *> dev_allocs;   // graph-lifetime allocations
     std::vector<void *> work_allocs;  // d-dependent allocations
-    int64_t bytes = 0;
+    int64_t bytes = 0;       // device memory the context keeps (pfe_info.device_bytes)
+    int64_t work_bytes = 0;  // the part of it in work_allocs
     int spmm_variant = PFE_SPMM_ROW1;  // SpMM kernel variant (pfe_autotune)
     int le_iters = 0;                 // last Laplacian-eigenmap computation
     double le_residual = 0.0;
 };
 
 namespace pfe {
+
+// pfe_params.max_device_bytes: true (with the message set) when keeping
+// `bytes` more would pass the context's cap; nothing is allocated then.
+inline bool over_device_cap(pfe_ctx *c, size_t bytes) {
+    const int64_t cap = c->prm.max_device_bytes;
+    if (cap <= 0 || c->bytes + (int64_t)bytes <= cap) return false;
+    c->err = "max_device_bytes: keeping " + std::to_string(bytes) + " more bytes would pass the cap of " +
+             std::to_string(cap) + " (" + std::to_string(c->bytes) + " held)";
+    return true;
+}
 
 // --- graph.cu
 pfe_status build_grid_graph(pfe_ctx *c, const double *dfeat);

@@ -46,7 +46,7 @@ class Params(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("r", C.c_double), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("tol", C.c_double), ("max_iter", C.c_int32), ("refresh", C.c_int32),
                 ("reset_inner_each_outer", C.c_int32), ("loop_mode", C.c_int32), ("check_every", C.c_int32),
-                ("blocks_per_sm", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("max_device_bytes", C.c_int64)]
 
 
 class Info(C.Structure):
@@ -168,7 +168,7 @@ class PFE:
                  radius: float | None = None, edges=None, lam: float = 0.0, r: float = 1.0,
                  precision: str = "mixed", tol: float = 1e-6, max_iter: int = 5000, refresh: int = 50,
                  reset_inner: bool = True, loop: str = "graph", check_every: int = 4,
-                 blocks_per_sm: int = 0, stream=None, shapes=None, seg_off=None):
+                 blocks_per_sm: int = 0, stream=None, shapes=None, seg_off=None, max_device_bytes: int = 0):
         self.lib = load_library()
         self.ctx = C.c_void_p()
         fp, self._feat = _ptr(features)
@@ -201,6 +201,7 @@ class PFE:
         p.reset_inner_each_outer = 1 if reset_inner else 0
         p.loop_mode = PFE_LOOP_GRAPH if loop == "graph" else PFE_LOOP_HOST
         p.check_every, p.blocks_per_sm = int(check_every), int(blocks_per_sm)
+        p.max_device_bytes = int(max_device_bytes)
         self.params = p
         self.n = n
         self.d = 0

@@ -84,3 +84,40 @@ def test_failed_build_leaves_its_message(lib):
     p.precond = 7  # not a preconditioner the build takes
     assert L.pfe_build_graph(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(p), None) == 8
     assert L.pfe_last_error(None) == b"PFE_EUNSUPPORTED"
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets that
+    the C compiler gives the header's struct (gcc compiles a probe of
+    sizeof/offsetof; nothing of the library runs)."""
+    import shutil
+    import subprocess
+    from paper_1612_06496_gb300 import pfe as B
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    pairs = {"pfe_graph_desc": B.GraphDesc, "pfe_params": B.Params, "pfe_info": B.Info,
+             "pfe_step_stats": B.StepStats, "pfe_solve_stats": B.SolveStats}
+    lines, want = [], []
+    for cname, cls in pairs.items():
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(cls))
+        for fname, _ in cls._fields_:
+            field = "lambda" if fname == "lambda_" else fname
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {field}));')
+            want.append(getattr(cls, fname).offset)
+    src = tmp_path / "probe.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "pfe.h"\nint main(void) {\n'
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "probe"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == want
+
+
+def test_default_params_have_no_device_cap(lib):
+    from paper_1612_06496_gb300.pfe import Params, load_library
+    p = Params()
+    p.max_device_bytes = 123
+    load_library().pfe_default_params(ctypes.byref(p))
+    assert p.max_device_bytes == 0

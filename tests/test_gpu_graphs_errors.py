@@ -180,3 +180,48 @@ def test_nan_right_hand_side_is_reported():
             p.inner_step(stats=True)
         assert ei.value.status == 5, loop
         p.close()
+
+
+def test_device_memory_cap():
+    """pfe_params.max_device_bytes bounds the memory a context keeps: a build
+    or pfe_init that would pass it fails with PFE_ENOMEM and keeps nothing
+    of the failed call; the FSAI buffers are all or nothing; a re-init
+    returns the previous dimension's buffers."""
+    from paper_1612_06496_gb300 import PFE, PFEError
+    from synth import make_problem
+    ensure_built()
+    spec = small_spec(H=14, W=15, d=3)
+    X, Y0 = make_problem(spec)
+    kw = dict(sigma=spec.sigma, H=14, W=15, radius=spec.radius, precision="mixed")
+    p = PFE(X, **kw)
+    b_graph = p.info()["device_bytes"]
+    p.init(Y0)
+    b3 = p.info()["device_bytes"]
+    p.init(np.ascontiguousarray(Y0[:, :2]))
+    b2 = p.info()["device_bytes"]
+    assert b_graph < b2 < b3
+    p.close()
+    with pytest.raises(PFEError) as ei:
+        PFE(X, **kw, max_device_bytes=b_graph // 2)
+    assert ei.value.status == 2 and "max_device_bytes" in str(ei.value)
+    q = PFE(X, **kw, max_device_bytes=b_graph)
+    assert q.info()["device_bytes"] == b_graph
+    with pytest.raises(PFEError) as ei:
+        q.init(Y0)
+    assert ei.value.status == 2 and "max_device_bytes" in str(ei.value)
+    assert q.info()["device_bytes"] == b_graph
+    with pytest.raises(PFEError) as ei:
+        q.inner_step()
+    assert ei.value.status == 9  # still not initialised
+    q.close()
+    # room for the d = 3 state and the first FSAI buffer (G_ii, n floats) only
+    r = PFE(X, **kw, max_device_bytes=b3 + 4 * spec.n)
+    r.init(Y0)
+    assert r.info()["device_bytes"] == b3
+    with pytest.raises(PFEError) as ei:
+        r.fsai_classical()
+    assert ei.value.status == 2
+    assert r.info()["device_bytes"] == b3  # the buffer that fitted was released again
+    Y = np.empty((spec.n, 3))
+    assert r.solve(1, 2, Y, None)["n_unconverged"] == 0  # Jacobi still runs
+    r.close()
