@@ -233,12 +233,18 @@ pfe_status pcg_status(pfe_ctx *c) {
 size_t elem_size(const pfe_ctx *c) { return c->mixed ? sizeof(float) : sizeof(double); }
 
 pfe_status inner_step_enqueue(pfe_ctx *c) {
-    PFE_TRY(run_pcg(c, false));
+    NvtxRange r("pfe inner step");
+    {
+        NvtxRange r1("pcg");
+        PFE_TRY(run_pcg(c, false));
+    }
+    NvtxRange r2("edge pass");
     PFE_TRY(launch_edge(c, c->stream));
     return PFE_OK;
 }
 
 pfe_status pstep_enqueue(pfe_ctx *c) {
+    NvtxRange r("pfe P-step");
     const bool reset = c->prm.reset_inner_each_outer != 0;
     PFE_TRY(launch_pstep(c, c->stream, reset ? PSTEP_RESET : PSTEP_CARRY));
     if (reset) {
@@ -437,6 +443,7 @@ static pfe_status build_graph_impl(pfe_ctx **out, const pfe_graph_desc *gd, cons
 }
 
 pfe_status pfe_build_graph(pfe_ctx **out, const pfe_graph_desc *gd, const pfe_params *p, pfe_stream_t stream) {
+    NvtxRange r("pfe build graph");
     t_build_err.clear();
     const pfe_status st = build_graph_impl(out, gd, p, stream);
     if (st != PFE_OK && t_build_err.empty()) t_build_err = pfe_status_string(st);
@@ -722,6 +729,7 @@ static pfe_status init_impl(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY
 
 pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY0) {
     if (!c) return PFE_EINVAL;
+    NvtxRange r("pfe init");
     const pfe_status st = init_impl(c, d, Y0, ldY0);
     // a failure after the previous state was released leaves no work buffers
     // behind (one rejected by the argument checks keeps that state)
@@ -760,6 +768,7 @@ static pfe_status solve_stages(pfe_ctx *c, int32_t n_outer, int32_t n_inner, int
                                double *Yhat_out, pfe_solve_stats *st) {
     if (!c->inited) return fail(c, PFE_ESTATE, "pfe_solve before pfe_init");
     if (n_outer < 0 || n_inner < 0 || n_stage2 < 0) return fail(c, PFE_EINVAL, "negative iteration count");
+    NvtxRange r("pfe solve");
     PFE_TRY(clear_stats(c));
     for (int k = 0; k < n_outer; ++k) {
         for (int l = 0; l < n_inner; ++l) PFE_TRY(inner_step_enqueue(c));
@@ -1019,6 +1028,7 @@ int32_t pfe_fsai_param_count(void) { return kNParam; }
 
 pfe_status pfe_fsai_set(pfe_ctx *c, const float *params) {
     if (!c) return PFE_EINVAL;
+    NvtxRange r("pfe learned FSAI set-up");
     if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner is built for one problem, not a batch");
     PFE_TRY(sync(c));
     if (!params) {
@@ -1038,6 +1048,7 @@ pfe_status pfe_fsai_set(pfe_ctx *c, const float *params) {
 
 pfe_status pfe_fsai_classical(pfe_ctx *c) {
     if (!c) return PFE_EINVAL;
+    NvtxRange r("pfe classical FSAI set-up");
     if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner is built for one problem, not a batch");
     if (!c->mixed) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner runs on the mixed-precision path");
     PFE_TRY(sync(c));
@@ -1051,6 +1062,7 @@ pfe_status pfe_fsai_classical(pfe_ctx *c) {
 
 pfe_status pfe_ic0(pfe_ctx *c) {
     if (!c) return PFE_EINVAL;
+    NvtxRange r("pfe IC(0) set-up");
     if (c->nseg > 1 || c->kind != PFE_GRAPH_GRID || c->W < 1 || (c->g.row_len != 12 && c->g.row_len != 28))
         return fail(c, PFE_EUNSUPPORTED, "IC(0) is built for one grid image of radius 2 or 3");
     if (!c->mixed) return fail(c, PFE_EUNSUPPORTED, "IC(0) runs on the mixed-precision path");

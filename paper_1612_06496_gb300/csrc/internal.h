@@ -7,6 +7,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pfe.h"
 #include "fsai.h"
@@ -159,6 +160,16 @@ struct pfe_ctx {
 };
 
 namespace pfe {
+
+// NVTX range over one stage of the method (build, init, inner step with its
+// PCG and edge pass, P-step, solve, preconditioner set-up), for profilers
+// that select kernels by range (ncu --nvtx); a no-op unless a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // pfe_params.max_device_bytes: true (with the message set) when keeping
 // `bytes` more would pass the context's cap; nothing is allocated then.
