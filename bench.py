@@ -165,9 +165,16 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        self.thread.join(timeout=5)  # every line the sampler printed
+        return self.summarise(self.lines)
+
+    @staticmethod
+    def summarise(lines) -> dict | None:
+        """Median and largest SM clock over the samples of FIELDS, and every
+        throttle reason that was active in any of them."""
         sms, maxs, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue

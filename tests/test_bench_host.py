@@ -99,3 +99,19 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("C1: 32x32")
+
+
+def test_clock_samples_are_summarised(bench):
+    """nvidia-smi lines (FIELDS order, csv, no units): median SM clock, the
+    largest max clock, every reason active in any sample; unreadable lines
+    are skipped and no readable sample gives None."""
+    lines = ["0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 1100.2, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "garbage"]
+    out = bench.ClockSampler.summarise(lines)
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = lines[:1] + ["0, 1500, 2070, 800, 0x40, Not Active, Active, Not Active, Not Active"]
+    assert bench.ClockSampler.summarise(hot)["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.ClockSampler.summarise(["garbage"]) is None
