@@ -656,7 +656,7 @@ def main():
             "pcg_iters_max": max(s["pcg_iters_max"] for s in stats),
             "pcg_relres_max": max(s["relres_max"] for s in stats),
             "gnnz_rhs_per_s": nnz_iters * d / (ms / 1e3) / 1e9,
-            "setup_s": setup_s, "lambda": info["lambda_"],
+            "setup_s": setup_s, "lambda": info["lambda_"], "r": info["r"],
             "fp32_other_precond": alt,
             "fp64": fp64,
             "speedup_vs_fp64": (fp64["sec_per_outer_iter"] / sec_per_outer) if fp64 else None,
