@@ -392,3 +392,18 @@ def test_two_stage_stage2_minimises_the_relaxed_y_problem():
     assert f2 <= f(st1.Y) + 1e-12
     for _ in range(20):
         assert f2 <= f(st2.Y + 1e-3 * rng.standard_normal(st2.Y.shape)) + 1e-12
+
+
+def test_edge_count_fixture_is_what_its_script_writes():
+    """tests/golden/edge_counts.json is the closed-form output of
+    tests/golden/make_edge_counts.py, entry for entry."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_edge_counts", os.path.join(GOLD, "make_edge_counts.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with open(os.path.join(GOLD, "edge_counts.json")) as f:
+        gold = json.load(f)
+    shapes = {"C1": (32, 32, 2.0), "C2": (481, 321, 3.0), "C5": (2048, 2048, 2.0), "grid128_4nn": (128, 128, 1.0)}
+    assert set(gold) == set(shapes)
+    for key, (W, H, R) in shapes.items():
+        assert mod.counts(W, H, R) == gold[key], key
