@@ -115,3 +115,12 @@ def test_clock_samples_are_summarised(bench):
     hot = lines[:1] + ["0, 1500, 2070, 800, 0x40, Not Active, Active, Not Active, Not Active"]
     assert bench.ClockSampler.summarise(hot)["reasons"] == ["hw_thermal_slowdown"]
     assert bench.ClockSampler.summarise(["garbage"]) is None
+
+
+def test_reference_arm_runs_on_rank_zero_only(bench, capsys):
+    """Under torchrun the other ranks of the reference arm exit at once,
+    without work or output."""
+    import argparse
+    args = argparse.Namespace(workload="C1", steps=1, warmup=1, gpus=2, cpu_window=192)
+    assert bench.run_reference(args, rank=1, world=2) is None
+    assert capsys.readouterr().out == ""
