@@ -386,7 +386,7 @@ inline Segs seg_view(const pfe_ctx *c) { return Segs{c->nseg, c->g.n, c->seg_off
 // One allocation holds every array of a SegScal: bytes needed, and the
 // arrays carved from a base pointer (doubles first, then ints).
 inline size_t segscal_bytes(int nseg, int d) {
-    return sizeof(double) * 6 * (size_t)nseg * d + sizeof(long long) * (size_t)nseg +
+    return sizeof(double) * 9 * (size_t)nseg * d + sizeof(long long) * (size_t)nseg +
            sizeof(int) * ((size_t)nseg * d + 2 * (size_t)nseg) + sizeof(unsigned) * 4 * (size_t)nseg;
 }
 inline SegScal segscal_carve(void *base, int nseg, int d) {
@@ -399,7 +399,10 @@ inline SegScal segscal_carve(void *base, int nseg, int d) {
     sc.beta = dp + 3 * nd;
     sc.relres = dp + 4 * nd;
     sc.alpha_prev = dp + 5 * nd;
-    sc.seg_iters_tot = reinterpret_cast<long long *>(dp + 6 * nd);
+    sc.rel_ref = dp + 6 * nd;
+    sc.rec2 = dp + 7 * nd;
+    sc.devr = dp + 8 * nd;
+    sc.seg_iters_tot = reinterpret_cast<long long *>(dp + 9 * nd);
     int *ip = reinterpret_cast<int *>(sc.seg_iters_tot + nseg);
     sc.active = ip;
     sc.seg_active = ip + nd;

@@ -31,6 +31,9 @@ struct Segs {
 struct SegScal {
     double *bnorm, *rz, *alpha, *beta, *relres;  // nseg * d
     double *alpha_prev;                           // nseg * d: alpha of a held solution update (FSAI)
+    double *rel_ref;                              // nseg * d: relative residual at the last replacement (or the start)
+    double *rec2;                                 // nseg * d: |r|^2 of the recurrence residual a replacement replaces
+    double *devr;                                 // nseg * d: |r_true - r_rec|^2 / |r_rec|^2 of the last replacement
     int *active;                                  // nseg * d: column still iterating
     int *seg_active;                              // nseg: any column of the segment iterating
     int *seg_iters;                               // nseg: iterations of the segment in this solve
@@ -60,6 +63,8 @@ struct PcgCtl {
     int xpending;                     // 1: y += alpha p of the last k_spmm not yet applied
     int launch_base, launch_per_iter; // kernel launches outside / per iteration of the loop
     int xfold;                        // FSAI: this iteration's k_fsai_zp applies both pending updates
+    int refresh_want;                 // set during an iteration: a column asks for a residual replacement
+    int refresh_next;                 // Jacobi: refresh_want latched at the end of an iteration for the next one
 };
 
 // Control block of the P-step (Alg. 1 steps 6-7).  G, T and evals are

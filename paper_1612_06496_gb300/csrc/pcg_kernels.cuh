@@ -427,39 +427,69 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, 
 // the block's L1 may hold lines loaded at its start.
 constexpr unsigned kFull = 0xffffffffu;
 
-// Per-segment part of finishing an iteration `it` (or the start of a solve):
-// residual norms -> relres, beta, freezing.  Ends with a __syncwarp, so lane 0
-// sees every lane's writes.
+// Residual replacement (van der Vorst and Ye, "Residual replacement
+// strategies for Krylov subspace iterative methods", 2000): the recurrence
+// r -= alpha q drifts from b - A y by about eps |r_0| (FP32: 6e-8 |r_0|), so
+// with a warm start (|r_0| >> |b|) it can report 1e-6 while b - A y is far
+// larger.  Replacing r by b - A y keeps the iteration sound only while that
+// drift is small against r: a replacement made after the drift has outgrown
+// r makes beta huge, the new direction copies the old one and the iteration
+// stalls.  So a column asks for a replacement once its recurrence residual
+// has fallen kRefreshDrop below its value at the last one (the drift stays
+// below ~eps / kRefreshDrop of r), and when it reaches tol: a column is
+// frozen only on a replaced (true) residual.  A replacement that still moved
+// r by more than sqrt(kRestartDev) of its norm restarts that column's
+// direction (beta = 0).  Periodic replacements (every `refresh` iterations)
+// come on top; refresh = 0 turns replacement off and freezes on the
+// recurrence.
+constexpr double kRefreshDrop = 1e-3;
+constexpr double kRestartDev = 1e-2;
+
+// Per-segment part of finishing iteration `it` (or the start of a solve):
+// residual norms -> relres, beta, freezing, replacement requests.  MODE 0:
+// the start of a solve (r = b - A y); 1: a replacement iteration (r = b - A y,
+// sc.devr holds the replacement's relative deviation); 2: an ordinary
+// iteration (recurrence residual).  Ends with a __syncwarp, so lane 0 sees
+// every lane's writes.
 static __device__ void finish_seg(PcgCtl *ctl, const SegScal &sc, int seg, const double *rz, const double *rr, int D,
-                                  bool start, int it) {
+                                  int mode, int it) {
     const int lane = threadIdx.x & 31;
-    int any = 0;
+    const bool replace = ctl->refresh > 0;
+    int any = 0, want = 0;
     for (int c = lane; c < D; c += 32) {
         const int k = seg * D + c;
-        if (start) {
+        if (mode == 0) {
             sc.rz[k] = rz[c];
             sc.beta[k] = 0.0;
             const double rel = sqrt(rr[c]) / sc.bnorm[k];
             sc.relres[k] = rel;
+            sc.rel_ref[k] = rel;
             if (!(rel == rel) || !(rz[c] == rz[c])) atomicMax(&ctl->error, (int)PFE_ENUMERIC);
             sc.active[k] = rel > ctl->tol;
         } else if (sc.active[k]) {
             const double rel = sqrt(rr[c]) / sc.bnorm[k];
-            sc.beta[k] = rz[c] / sc.rz[k];
+            sc.beta[k] = (mode == 1 && sc.devr[k] > kRestartDev) ? 0.0 : rz[c] / sc.rz[k];
             sc.rz[k] = rz[c];
             sc.relres[k] = rel;
             if (!(rel == rel) || !(rz[c] == rz[c])) atomicMax(&ctl->error, (int)PFE_ENUMERIC);
-            if (rel <= ctl->tol) sc.active[k] = 0;
+            if (mode == 1 || !replace) {
+                if (rel <= ctl->tol) sc.active[k] = 0;
+                if (mode == 1) sc.rel_ref[k] = rel;
+            } else if (rel <= ctl->tol || rel <= kRefreshDrop * sc.rel_ref[k]) {
+                want = 1;
+            }
         }
         any |= sc.active[k];
     }
     any = __any_sync(kFull, any);
+    want = __any_sync(kFull, want);
     if (lane == 0) {
-        if (start)
+        if (mode == 0)
             sc.seg_iters[seg] = 0;
         else if (__ldcg(sc.seg_active + seg))
             sc.seg_iters[seg] = it;
         sc.seg_active[seg] = any;
+        if (want) ctl->refresh_want = 1;
     }
     __syncwarp();
 }
@@ -666,7 +696,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(PcgArgs<T> a) {
                 a.sc.alpha[seg * D + c] = 0.0;
             }
             __syncwarp();
-            if (PRE == 0) finish_seg(ctl, a.sc, seg, tot, tot + D, D, true, 0);
+            if (PRE == 0) finish_seg(ctl, a.sc, seg, tot, tot + D, D, 0, 0);
             if (!MS || warp_last_segment(ctl, 2, a.sg.nseg)) {
                 if (threadIdx.x == 0) {
                     ctl->iter = 0;
@@ -675,6 +705,8 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(PcgArgs<T> a) {
                     ctl->xpending = 0;
                     ctl->xheld = 0;
                     ctl->xfold = 0;
+                    ctl->refresh_want = 0;
+                    ctl->refresh_next = 0;
                     if (PRE != 0) ctl->done = 0;  // k_fsai_t finishes the start
                 }
                 __syncwarp();
@@ -1427,10 +1459,17 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
             PcgCtl *ctl = a.ctl;
             const int it = ctl->iter + 1;
             // an error here can only come from an earlier kernel while a refresh is due
+            // (periodic, or asked for by a column at the end of the last iteration)
             int due = 0;
-            if (threadIdx.x == 0) due = !*(volatile int *)&ctl->error && ctl->refresh > 0 && (it % ctl->refresh) == 0;
+            if (threadIdx.x == 0)
+                due = !*(volatile int *)&ctl->error && ctl->refresh > 0 &&
+                      ((it % ctl->refresh) == 0 || *(volatile int *)&ctl->refresh_next);
             const bool refresh_due = __shfl_sync(kFull, due, 0) != 0;
-            if (!refresh_due) finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, false, it);
+            if (!refresh_due) finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, 2, it);
+            // |r_rec|^2 of the residual the replacement will replace (k_refresh
+            // measures how far the true residual lies from it)
+            if (refresh_due)
+                for (int c = threadIdx.x; c < D; c += 32) a.sc.rec2[bsg.seg * D + c] = tot[D + c];
             // the next k_pupdate holds this iteration's solution update when
             // none is held now (xheld changes only in the last finisher below):
             // each segment keeps its alpha for the fold
@@ -1449,6 +1488,10 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
                         const int fold = ctl->xheld;
                         ctl->xfold = fold;
                         ctl->xheld = !fold;
+                    }
+                    if (threadIdx.x == 0) {  // every segment's request of this iteration, for the next
+                        ctl->refresh_next = ctl->refresh_want;
+                        ctl->refresh_want = 0;
                     }
                 }
             }
@@ -1521,23 +1564,48 @@ __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush
 //              alpha p_prev (z is never stored)
 // and a solve starts with k_pcg_init<PRE = 1>, k_fsai_t<0>, k_fsai_zp.
 
-// Residual replacement without dots (k_fsai_t<1> makes them); it writes the
-// buffer of the new residual (k_fsai_tr does not run on refresh iterations).
+// Residual replacement without the preconditioned dots (k_fsai_t<1> makes
+// them); it writes the buffer of the new residual (k_fsai_tr does not run on
+// replacement iterations).  It also measures how far the true residual lies
+// from the recurrence residual r - alpha q it replaces (|r - r_rec|^2 /
+// |r_rec|^2 per column -> sc.devr, for the restart test).
 template <typename T, int D>
 __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
     if (!*(volatile int *)&a.ctl->refresh_now) return;
-    T *__restrict__ rdst = a.r2[(a.ctl->iter + 1) & 1];
+    const int par = a.ctl->iter & 1;
+    const T *__restrict__ rold = a.r2[par];
+    T *__restrict__ rdst = a.r2[par ^ 1];
+    __shared__ T salpha[D];
+    if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
+    __syncthreads();
+    __shared__ DF sq_sh[sqsum_slots<T, 2, SubWarp<T, D>::V>()];
+    SqSum<T, 2, SubWarp<T, D>::V> sq(sq_sh);  // |r - r_rec|^2 | |r_rec|^2
     PFE_ROW_LOOP(T, D) {
         PFE_ROW_I;
         const int c0 = lm.cg * V;
-        T ri[V];
+        T ri[V], ro[V], qi[V];
+        ldv<T, V>(rold + i * D + c0, ro);
+        ldv<T, V>(a.q + i * D + c0, qi);
         true_residual<T, D, V>(a, i, c0, ri);
         stv<T, V>(rdst + i * D + c0, ri);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const T rrec = fma(-salpha[c0 + k], qi[k], ro[k]);
+            const T dr = ri[k] - rrec;
+            sq.add(0, k, dr, dr);
+            sq.add(1, k, rrec, rrec);
+        }
+        sq.row_done();
     }
-    if (last_block_arrives(&a.ctl->ticket[3])) {
-        if (threadIdx.x == 0) {
-            a.ctl->xpending = 0;
-            a.ctl->ticket[3] = 0u;
+    sq.finish();
+    __shared__ double tot[2 * D];
+    if (grid_sum_cols<T, D, 2>(sq.acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 3], tot)) {
+        if (threadIdx.x < 32) {
+            for (int c = threadIdx.x; c < D; c += 32) {
+                const double rec = tot[D + c];
+                a.sc.devr[c] = rec > 0.0 ? tot[c] / rec : (tot[c] > 0.0 ? INFINITY : 0.0);
+            }
+            if (threadIdx.x == 0) a.ctl->xpending = 0;
         }
     }
 }
@@ -1606,7 +1674,7 @@ constexpr int gather_min_blocks() {
 template <typename T>
 __device__ void fsai_finish(const PcgArgs<T> &a, const BlockSeg &bsg, const double *tot, int D, int mode) {
     PcgCtl *ctl = a.ctl;
-    finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, mode == 0, ctl->iter + 1);
+    finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, mode, ctl->iter + 1);
     if (threadIdx.x == 0 && mode != 0) ctl->iter += 1;
     __syncwarp();
     finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
@@ -1789,8 +1857,10 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())
         salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
         salpha_prev[threadIdx.x] = (T)a.sc.alpha_prev[threadIdx.x];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        ctl->refresh_now = (ctl->refresh > 0 && ((ctl->iter + 1) % ctl->refresh) == 0) ? 1 : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // periodic, or asked for by a column in this iteration
+        ctl->refresh_now = (ctl->refresh > 0 && (((ctl->iter + 1) % ctl->refresh) == 0 || ctl->refresh_want)) ? 1 : 0;
+        ctl->refresh_want = 0;
+    }
     __syncthreads();
     PFE_ROW_LOOP(T, D) {
         PFE_ROW_I;
@@ -1907,9 +1977,11 @@ __global__ void __launch_bounds__(kBlock) k_ic_dots(PcgArgs<T> a, int start) {
     if (grid_sum_cols<T, D, 2>(sq.acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot)) {
         if (threadIdx.x < 32) {
             fsai_finish(a, bsg, tot, D, mode);
-            if (threadIdx.x == 0) {
+            if (threadIdx.x == 0) {  // periodic, or asked for by a column in this iteration
                 PcgCtl *ctl = a.ctl;
-                ctl->refresh_now = (ctl->refresh > 0 && ((ctl->iter + 1) % ctl->refresh) == 0) ? 1 : 0;
+                ctl->refresh_now =
+                    (ctl->refresh > 0 && (((ctl->iter + 1) % ctl->refresh) == 0 || ctl->refresh_want)) ? 1 : 0;
+                ctl->refresh_want = 0;
             }
         }
     }
@@ -1953,42 +2025,55 @@ __global__ void __launch_bounds__(kBlock) k_ic_bwd(PcgArgs<T> a, int64_t level, 
 }
 
 // Residual replacement: r = b - A y (extended precision), then finish the
-// iteration with the true residual.
+// iteration with the true residual.  Also |r - r_rec|^2, the squared
+// distance of the true residual from the recurrence residual k_update left
+// in r (its |r_rec|^2 is in sc.rec2), for the restart test.
 template <typename T, int D, bool MS>
 __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
     if (!*(volatile int *)&a.ctl->refresh_now) return;
     using A = Acc<T>;
     using AT = typename A::type;
     using SWt = SubWarp<T, D>;
-    AT acc[2][SWt::V];
+    AT acc[3][SWt::V];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < 3; ++q)
 #pragma unroll
         for (int k = 0; k < SWt::V; ++k) acc[q][k] = A::zero();
     PFE_ROW_LOOP_LIVE(T, D, MS) {
         PFE_ROW_I;
         const int c0 = lm.cg * V;
-        T ri[V];
+        T ri[V], rr[V];
+        ldv_rw<T, V>(a.r + i * D + c0, rr);
         true_residual<T, D, V>(a, i, c0, ri);
         const T dv = a.A.dinv[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             A::add_prod(acc[0][k], ri[k], dv * ri[k]);
             A::add_prod(acc[1][k], ri[k], ri[k]);
+            const T dr = ri[k] - rr[k];
+            A::add_prod(acc[2][k], dr, dr);
         }
         stv<T, V>(a.r + i * D + c0, ri);
     }
-    __shared__ double tot[2 * D];
-    if (grid_sum_cols<T, D, 2>(acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 3], tot)) {
+    __shared__ double tot[3 * D];
+    if (grid_sum_cols<T, D, 3>(acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 3], tot)) {
         if (threadIdx.x < 32) {
             PcgCtl *ctl = a.ctl;
-            finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, false, ctl->iter);
+            for (int c = threadIdx.x; c < D; c += 32) {
+                const int k = bsg.seg * D + c;
+                const double rec = a.sc.rec2[k];
+                a.sc.devr[k] = rec > 0.0 ? tot[2 * D + c] / rec : (tot[2 * D + c] > 0.0 ? INFINITY : 0.0);
+            }
+            __syncwarp();
+            finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, 1, ctl->iter);
             if (!MS || warp_last_segment(ctl, 3, a.sg.nseg)) {
                 if (threadIdx.x == 0) {
                     ctl->refresh_now = 0;
                     ctl->xpending = 0;
                     ctl->xheld = 0;  // k_xflush applied every pending update
                     ctl->xfold = 0;
+                    ctl->refresh_next = 0;
+                    ctl->refresh_want = 0;
                 }
                 __syncwarp();
                 finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);

@@ -1,0 +1,142 @@
+"""The benchmarked configuration against the oracle: the FP32 path with the
+learned FSAI preconditioner (the committed network weights, BF16 tensor-core
+inference), the 2048x2048 generator's radius-2 graph at d = 10 (the
+compile-time instantiations k_fsai_tr<float,10,12>, k_fsai_zp<float,10,12>
+and every SpMM variant at d = 10) and the paper-scale 481x321 image at
+radius 3, d = 8 (the 28-slot instantiations).  Whole nested loops (Alg. 1
+with Alg. 2's inner steps) against the oracle's exact solves at the PCG
+tolerance the benchmark uses (relative residual 1e-6): relative Frobenius
+error of Y and of the embedding within 2e-4, the constraint Y^T D Y = I to
+1e-10.  And the FSAI iteration's counts at d = 10 against the oracle's FP64
+PCG with the same factor G."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import pfe_oracle as O
+from synth import CONFIGS, crop_specs, make_problem
+from tests.gpu_common import gpu_problem, oracle_graph, oracle_run, relerr
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 2e-4
+N_OUTER, N_INNER = 2, 5
+
+
+def _crop(idx):
+    return crop_specs(CONFIGS["C5"])[idx]
+
+
+_oracle_cache = {}
+
+
+def _oracle_crop(idx):
+    if idx not in _oracle_cache:
+        spec = _crop(idx)
+        X, Y0 = make_problem(spec)
+        g = oracle_graph(spec, X)
+        st = O.soc_pfe(g, Y0, N_OUTER, N_INNER, solver="direct")
+        _oracle_cache[idx] = (g, st, O.embedding(g, st))
+    return _oracle_cache[idx]
+
+
+def _learned(spec, variant=None, tune=False):
+    from paper_1612_06496_gb300.learned import load_weights
+    p, X, Y0 = gpu_problem(spec, "mixed", tol=spec.tol)
+    p.fsai_set(load_weights())
+    p.init(Y0)
+    if tune:
+        p.autotune(5)
+    elif variant is not None:
+        p.set_variant(variant)
+    return p, Y0
+
+
+@pytest.mark.parametrize("crop_idx", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, "tuned"])
+def test_c5_crops_learned_fsai_parity(crop_idx, variant):
+    """Seeded 64x64 windows of the 2048x2048 image, d = 10, radius 2, the
+    learned factor, each SpMM variant forced (and the autotuner's pick)."""
+    spec = _crop(crop_idx)
+    assert spec.d == 10 and spec.radius == 2.0 and spec.tol == 1e-6
+    g, ost, Yh_o = _oracle_crop(crop_idx)
+    p, Y0 = _learned(spec, None if variant == "tuned" else variant, tune=variant == "tuned")
+    Y = np.empty((spec.n, spec.d))
+    Yhat = np.empty((spec.n, spec.d))
+    st = p.solve(N_OUTER, N_INNER, Y, Yhat)
+    assert st["n_unconverged"] == 0 and st["relres_max"] <= spec.tol
+    assert relerr(Y, ost.Y) <= MIXED_TOL
+    assert relerr(Yhat, Yh_o) <= MIXED_TOL
+    assert np.max(np.abs(Yhat.T @ (g.dvec[:, None] * Yhat) - np.eye(spec.d))) <= 1e-10
+    p.close()
+
+
+def test_c5_crop_learned_fsai_fixed_variants_bitwise():
+    """The SpMM variants on fixed-length rows that take one row group per
+    step (the slot-loading kernel, its TMA-tile form and the stencil form)
+    add the same products in the same order: the learned-FSAI solves agree
+    bit for bit at d = 10."""
+    spec = _crop(1)
+    out = []
+    for variant in (1, 4, 5):
+        p, Y0 = _learned(spec, variant)
+        Y = np.empty((spec.n, spec.d))
+        p.solve(N_OUTER, N_INNER, Y, None)
+        out.append(Y)
+        p.close()
+    np.testing.assert_array_equal(out[0], out[1])
+    np.testing.assert_array_equal(out[0], out[2])
+
+
+def test_c2_learned_fsai_matches_oracle():
+    """The 481x321 image (radius 3, d = 8, 4.45 M nonzeros of A) with the
+    learned factor and the autotuned SpMM, one outer iteration of two inner
+    steps, against the oracle's sparse-LU solves."""
+    spec = CONFIGS["C2"]
+    g, ost, Yh_o = oracle_run("C2", 1, 2)
+    p, _ = _learned(spec, tune=True)
+    Y = np.empty((spec.n, spec.d))
+    Yhat = np.empty((spec.n, spec.d))
+    st = p.solve(1, 2, Y, Yhat)
+    assert st["n_unconverged"] == 0
+    assert relerr(Y, ost.Y) <= MIXED_TOL
+    assert relerr(Yhat, Yh_o) <= MIXED_TOL
+    assert np.max(np.abs(Yhat.T @ (g.dvec[:, None] * Yhat) - np.eye(spec.d))) <= 1e-10
+    p.close()
+
+
+def _G_from_gpu(p, g):
+    """The factor the GPU holds, G_ii on the diagonal and G_ij (i > j) below."""
+    gd, ge = p.fsai_get()
+    return (sp.diags(gd) + sp.csr_matrix((ge, (g.b, g.a)), shape=(g.n, g.n))).tocsr()
+
+
+def _fsai_apply(G, R):
+    return G.T @ (G @ R)
+
+
+@pytest.mark.parametrize("kind", ["classical", "learned"])
+def test_fsai_iterations_at_d10_match_oracle_pcg(kind):
+    """PCG with M^-1 = G^T G at d = 10 (the benchmark's instantiations): the
+    GPU's iteration count against the oracle's FP64 PCG given the same G
+    (read back from the GPU for the learned factor, so both sides run the
+    same preconditioner), and both solutions against the exact solve."""
+    from paper_1612_06496_gb300.learned import load_weights
+    spec = _crop(2)
+    p, X, Y0 = gpu_problem(spec, "mixed", tol=1e-6)
+    g = oracle_graph(spec, X)
+    p.init(Y0)
+    if kind == "classical":
+        p.fsai_classical()
+    else:
+        p.fsai_set(load_weights())
+    G = _G_from_gpu(p, g)
+    R = np.random.default_rng(41).standard_normal((g.n, 10))
+    Y = np.zeros_like(R)
+    st = p.solve_system(R, Y)
+    Yo, info = O.pcg(g.A, R, np.zeros_like(R), 1e-6, 5000, 50, lambda Q: _fsai_apply(G, Q))
+    assert st["converged"] and info["converged"]
+    assert abs(st["pcg_iters"] - int(info["iters"].max())) <= 2, (st["pcg_iters"], info["iters"])
+    Yd = O.DirectSolver(g.A)(R)[0]
+    assert relerr(Y, Yd) < 1e-4 and relerr(Yo, Yd) < 1e-4
+    p.close()
