@@ -489,6 +489,13 @@ def main():
         nnz_iters = float(info["nnz_A"]) * iters_total
     launches = sum(s["kernel_launches"] for s in stats)
     sec_per_outer = job_seconds_per_outer(ms_max, args.steps, world)
+    # after the timed region: the next system of Eq. 13 solved from its warm
+    # start by the same path, and |b - A y| / |b| per column with A in FP64
+    # (pfe_residual), the problem's matrix rather than the FP32 rounding the
+    # iteration multiplies by
+    b_next, y_next = p.get("RHS"), p.get("Y")
+    p.solve_system(b_next, y_next)
+    true_relres = float(p.residual(b_next, y_next).max())
 
     # --- roofline of the dominant kernel: k_spmm (q = A p with the p.q dots)
     spmm_ms = p.time_kernel("spmm", 20)
@@ -655,6 +662,7 @@ def main():
             "pcg_iters_mean": iters_total / max(n_solves, 1),
             "pcg_iters_max": max(s["pcg_iters_max"] for s in stats),
             "pcg_relres_max": max(s["relres_max"] for s in stats),
+            "true_relres_fp64_max": true_relres,
             "gnnz_rhs_per_s": nnz_iters * d / (ms / 1e3) / 1e9,
             "setup_s": setup_s, "lambda": info["lambda_"], "r": info["r"],
             "fp32_other_precond": alt,

@@ -55,7 +55,8 @@ typedef enum pfe_status {
     PFE_ENOTCONV = 4,      /* a PCG solve hit max_iter; results are still written */
     PFE_ENUMERIC = 5,      /* NaN/Inf or a non-positive curvature p^T A p in PCG */
     PFE_ESINGULAR = 6,     /* the P-step's Gram matrix is numerically singular */
-    PFE_ETIMEOUT = 7,      /* a bounded device wait ran out (a bulk copy of the TMA-staged SpMM never landed) */
+    PFE_ETIMEOUT = 7,      /* a bounded device wait ran out (a bulk copy of the TMA-staged SpMM never landed), or the
+                              PCG loop ran max_iter + 24 rounds without its iterations advancing */
     PFE_EUNSUPPORTED = 8,  /* embedding dimension or option not built into this library */
     PFE_ESTATE = 9         /* call out of order (e.g. pfe_inner_step before pfe_init) */
 } pfe_status;
@@ -170,6 +171,8 @@ typedef struct pfe_solve_stats {
     int64_t pcg_rounds;       /* PCG iterations the kernels ran, summed over inner steps: for a
                                  batch the longest problem's count per step (= pcg_iters_total
                                  for one problem) */
+    int64_t replacements;     /* of those, iterations that replaced the recurrence residual by
+                                 b - A y (periodic, after a 1e3-fold fall, or to confirm tol) */
 } pfe_solve_stats;
 
 /*
@@ -262,6 +265,20 @@ PFE_API pfe_status pfe_kmeans(pfe_ctx *c, const double *X, int32_t d, int32_t k,
  */
 enum { PFE_OBJ_Y = 0, PFE_OBJ_YHAT = 1 };
 PFE_API pfe_status pfe_objective(pfe_ctx *c, int32_t which, double *l1, double *ortho_err);
+
+/*
+ * pfe_residual -- how well X solves the linear systems of Eq. 13 (Sec. III:
+ * the d systems A x_c = b_c that PCG solves, A = lambda M^T M + r D):
+ * relres[s * d + c] = |b_c - A x_c|_2 / |b_c|_2 over the rows of problem s
+ * (|b_c - A x_c|_2 where b_c = 0), computed in FP64 with the FP64 values of
+ * A whatever the context's precision -- so it states a mixed-precision
+ * solve's residual against the problem's matrix, not against the FP32
+ * rounding of A that its iteration multiplies by.  B and X: n x d row-major
+ * FP64, host or device (host arrays are copied through a temporary device
+ * buffer); relres: host, nseg * d.  Sums in a fixed order.  Needs pfe_init
+ * (d); synchronises.
+ */
+PFE_API pfe_status pfe_residual(pfe_ctx *c, const double *B, const double *X, double *relres);
 
 /*
  * pfe_laplacian_eigenmap -- the Laplacian-eigenmap embedding of the graph

@@ -67,25 +67,48 @@ def sigmoid(x):
     return 1.0 / (1.0 + np.exp(-x))
 
 
-def mlp_forward(theta, F):
+def bf16_round(x):
+    """Round to the nearest bfloat16 (8 significant bits, ties to even), via
+    FP32: the rounding the GPU's tensor-core layer applies to its operands.
+    Returned as float64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def mlp_forward(theta, F, bf16: bool = False):
+    """out = ReLU(ReLU(F W1 + b1) W2 + b2) W3 + b3.  bf16: the 64 x 64 layer's
+    operands (h1 and W2) rounded to bfloat16 first, as the GPU's tensor cores
+    take them (everything else in FP64)."""
     W1, b1, W2, b2, W3, b3 = unpack(theta)
     a1 = F @ W1 + b1
     h1 = np.maximum(a1, 0.0)
+    if bf16:
+        h1 = bf16_round(h1)
+        W2 = bf16_round(W2)
     a2 = h1 @ W2 + b2
     h2 = np.maximum(a2, 0.0)
     out = h2 @ W3 + b3
     return out, (F, a1, h1, a2, h2)
 
 
-def mlp_backward(theta, cache, dout):
+def mlp_backward(theta, cache, dout, bf16: bool = False):
+    """Gradient of sum(out * dout) w.r.t. theta, back through mlp_forward's
+    cache.  bf16: the 64 x 64 layer's backward products take bfloat16
+    operands (da2, and W2 for dh1 = da2 W2^T; h1 is already rounded), as the
+    GPU's tensor cores do."""
     W1, b1, W2, b2, W3, b3 = unpack(theta)
     F, a1, h1, a2, h2 = cache
     gW3 = h2.T @ dout
     gb3 = dout.sum(0)
     dh2 = dout @ W3.T
     da2 = dh2 * (a2 > 0)
-    gW2 = h1.T @ da2
     gb2 = da2.sum(0)
+    if bf16:
+        da2 = bf16_round(da2)
+        W2 = bf16_round(W2)
+    gW2 = h1.T @ da2
     dh1 = da2 @ W2.T
     da1 = dh1 * (a1 > 0)
     gW1 = F.T @ da1
@@ -129,11 +152,12 @@ def kaporin(g, G):
     return L, dG, T
 
 
-def loss_and_grad(theta, g):
-    """Kaporin loss of the network's G on graph g and its gradient w.r.t. theta."""
+def loss_and_grad(theta, g, bf16: bool = False):
+    """Kaporin loss of the network's G on graph g and its gradient w.r.t.
+    theta (bf16: the hidden layer's operands rounded as on the GPU)."""
     Fd, Fe = entry_features(g)
-    od, cd = mlp_forward(theta, Fd)
-    oe, ce = mlp_forward(theta, Fe)
+    od, cd = mlp_forward(theta, Fd, bf16)
+    oe, ce = mlp_forward(theta, Fe, bf16)
     G, gd, ge = assemble_G(g, od, oe)
     L, dG, T = kaporin(g, G)
     Ad = g.A.diagonal()
@@ -144,7 +168,7 @@ def loss_and_grad(theta, g):
     dout_d[:, 1] = dgd * sigmoid(od[:, 1]) / np.sqrt(Ad)
     dout_e = np.zeros_like(oe)
     dout_e[:, 0] = dge / np.sqrt(Ad[g.a])
-    grad = mlp_backward(theta, cd, dout_d) + mlp_backward(theta, ce, dout_e)
+    grad = mlp_backward(theta, cd, dout_d, bf16) + mlp_backward(theta, ce, dout_e, bf16)
     return L, grad, {"T": T, "gd": gd, "ge": ge, "G": G}
 
 

@@ -93,9 +93,12 @@ pfe_status fsai_vectors(pfe_ctx *c, int64_t nd) {
     return PFE_OK;
 }
 
-// Launches per solve: the init kernels plus the final flush, and per
-// iteration (the counts the device reports in pfe_solve_stats).
-void launch_counts(const pfe_ctx *c, int lc[2]) {
+// Launches per solve: the init kernels plus the final flush, per iteration
+// those that run every iteration, and those of a residual replacement (k_xflush
+// and the replacement kernels, which run only on replacement iterations when
+// the captured loop puts them in IF nodes; the device adds them up in
+// pfe_solve_stats).
+void launch_counts(const pfe_ctx *c, int lc[3]) {
     if (c->fsai.enabled && c->fsai.ic) {
         // the triangular solves: one launch per level that holds a row
         int64_t nl = 0;
@@ -106,41 +109,78 @@ void launch_counts(const pfe_ctx *c, int lc[2]) {
             nl += rows > 0;
         }
         lc[0] = (int)(2 * nl + 3);
-        lc[1] = (int)(2 * nl + 5);
+        lc[1] = (int)(2 * nl + 3);
+        lc[2] = 2;
         return;
     }
     lc[0] = c->fsai.enabled ? 4 : 2;
-    lc[1] = c->fsai.enabled ? 6 : 5;
+    lc[1] = 3;
+    lc[2] = c->fsai.enabled ? 3 : 2;
+}
+
+pfe_status write_launch_counts(pfe_ctx *c) {
+    int lc[3];
+    launch_counts(c, lc);
+    PFE_CUDA_TRY(c, cudaMemcpyAsync((char *)c->ctl + offsetof(PcgCtl, launch_base), lc, 2 * sizeof(int),
+                                    cudaMemcpyHostToDevice, c->stream));
+    PFE_CUDA_TRY(c, cudaMemcpyAsync((char *)c->ctl + offsetof(PcgCtl, launch_cond), lc + 2, sizeof(int),
+                                    cudaMemcpyHostToDevice, c->stream));
+    return PFE_OK;
 }
 
 // After the preconditioner changed: drop the captured loop (its body differs
 // between preconditioners) and update the launch counts.
 pfe_status fsai_switched(pfe_ctx *c) {
     free_pcg_graph(c);
-    if (c->inited) {
-        int lc[2];
-        launch_counts(c, lc);
-        PFE_CUDA_TRY(c, cudaMemcpyAsync((char *)c->ctl + offsetof(PcgCtl, launch_base), lc, sizeof(lc),
-                                        cudaMemcpyHostToDevice, c->stream));
-    }
+    if (c->inited) PFE_TRY(write_launch_counts(c));
     return sync(c);
 }
 
 // Build the CUDA graph {init kernel -> WHILE(body of check_every iterations)}.
+// The replacement kernels of each iteration of the body sit in a conditional
+// IF node (handles made on the top graph, values set by the kernel that
+// decides each replacement, cleared when the solve ends).
 pfe_status build_pcg_graph(pfe_ctx *c) {
     free_pcg_graph(c);
-    cudaStream_t cs;
+    cudaStream_t cs, side;
     PFE_CUDA_TRY(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        PFE_CUDA_TRY(c, cudaGetLastError());
+        return fail(c, PFE_ECUDA, "PCG graph: stream creation failed");
+    }
     struct StreamGuard {
-        cudaStream_t s;
-        ~StreamGuard() { cudaStreamDestroy(s); }
-    } guard{cs};
+        cudaStream_t s, t;
+        ~StreamGuard() {
+            cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+            for (cudaStream_t q : {s, t})
+                if (cudaStreamIsCapturing(q, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+                    cudaGraph_t g = nullptr;
+                    cudaStreamEndCapture(q, &g);  // an abandoned capture (error path)
+                }
+            cudaGetLastError();
+            cudaStreamDestroy(s);
+            cudaStreamDestroy(t);
+        }
+    } guard{cs, side};
     cudaGraph_t g = nullptr;
     PFE_CUDA_TRY(c, cudaGraphCreate(&g, 0));
     c->pcg_graph = g;
     cudaGraphConditionalHandle h;
     PFE_CUDA_TRY(c, cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
     PcgLaunch L{h, 1};
+    const int iters = std::max(1, c->prm.check_every);
+    if (iters <= kPcgMaxIf) {
+        L.n_if = iters;
+        L.side = side;
+        for (int k = 0; k < iters; ++k)
+            PFE_CUDA_TRY(c, cudaGraphConditionalHandleCreate(&L.ifh[k], g, 0, cudaGraphCondAssignDefault));
+    }
+    PFE_CUDA_TRY(c, cudaMemcpyAsync((char *)c->ctl + offsetof(PcgCtl, ifh), L.ifh, sizeof(L.ifh),
+                                    cudaMemcpyHostToDevice, c->stream));
+    PFE_CUDA_TRY(c, cudaMemcpyAsync((char *)c->ctl + offsetof(PcgCtl, n_if), &L.n_if, sizeof(int),
+                                    cudaMemcpyHostToDevice, c->stream));
+    PFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // L lives on this stack frame
     PFE_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     pfe_status st = launch_pcg_init(c, cs, L);
     cudaGraph_t g2 = g;
@@ -160,7 +200,7 @@ pfe_status build_pcg_graph(pfe_ctx *c) {
     PFE_CUDA_TRY(c, cudaGraphAddNode(&cn, g, nodes.data(), nullptr, nn, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     PFE_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    st = launch_pcg_body(c, cs, L, std::max(1, c->prm.check_every));
+    st = launch_pcg_body(c, cs, L, iters);
     cudaGraph_t b2 = body;
     ce = cudaStreamEndCapture(cs, &b2);
     if (st != PFE_OK) return st;
@@ -223,9 +263,16 @@ pfe_status check_pstep(pfe_ctx *c) {
     return PFE_OK;
 }
 
+// The device's PCG error word (host copy must be fresh) as a status.
+pfe_status pcg_error(pfe_ctx *c) {
+    if (c->h_ctl->error == PFE_ETIMEOUT)
+        return fail(c, PFE_ETIMEOUT, "PCG: a bounded device wait ran out, or the loop stopped advancing");
+    return fail(c, PFE_ENUMERIC, "PCG: NaN/Inf or non-positive p^T A p");
+}
+
 // status of the solves since the last clear_stats (host copy must be fresh)
 pfe_status pcg_status(pfe_ctx *c) {
-    if (c->h_ctl->error) return fail(c, PFE_ENUMERIC, "PCG: NaN/Inf or non-positive p^T A p");
+    if (c->h_ctl->error) return pcg_error(c);
     if (c->h_ctl->n_unconv > 0) return fail(c, PFE_ENOTCONV, "PCG: max_iter reached before tol");
     return PFE_OK;
 }
@@ -571,6 +618,44 @@ pfe_status pfe_objective(pfe_ctx *c, int32_t which, double *l1, double *ortho_er
     return diag_objective(c, which, l1, ortho_err);
 }
 
+pfe_status pfe_residual(pfe_ctx *c, const double *B, const double *X, double *relres) {
+    if (!c || !B || !X || !relres) return PFE_EINVAL;
+    if (!c->inited) return fail(c, PFE_ESTATE, "pfe_residual before pfe_init");
+    PFE_TRY(sync(c));
+    const size_t bytes = (size_t)c->g.n * c->d * sizeof(double);
+    const bool hb = !is_device_ptr(B), hx = !is_device_ptr(X);
+    double *tmp = nullptr;
+    if (hb || hx) {
+        if (cudaMalloc((void **)&tmp, (hb + hx) * bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PFE_ENOMEM, "pfe_residual: device allocation failed");
+        }
+    }
+    const double *Bd = B, *Xd = X;
+    cudaError_t e = cudaSuccess;
+    if (hb) {
+        e = cudaMemcpyAsync(tmp, B, bytes, cudaMemcpyHostToDevice, c->stream);
+        Bd = tmp;
+    }
+    if (hx && e == cudaSuccess) {
+        e = cudaMemcpyAsync(tmp + (hb ? c->g.n * c->d : 0), X, bytes, cudaMemcpyHostToDevice, c->stream);
+        Xd = tmp + (hb ? c->g.n * c->d : 0);
+    }
+    pfe_status st = PFE_OK;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->err = std::string("pfe_residual: ") + cudaGetErrorString(e);
+        st = PFE_ECUDA;
+    } else {
+        st = diag_residual(c, Bd, Xd, relres);
+    }
+    if (tmp) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+    }
+    return st;
+}
+
 pfe_status pfe_laplacian_eigenmap(pfe_ctx *c, int32_t d, double *V, int32_t max_iter, double tol, int32_t *iters,
                                   double *residual) {
     if (!c || !V || d < 1 || max_iter < 0 || !(tol >= 0.0)) return PFE_EINVAL;
@@ -700,10 +785,11 @@ static pfe_status init_impl(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY
     h.tol = c->prm.tol;
     h.done = 1;
     h.unroll = std::max(1, c->prm.check_every);
-    int lc[2];
+    int lc[3];
     launch_counts(c, lc);
     h.launch_base = lc[0];
     h.launch_per_iter = lc[1];
+    h.launch_cond = lc[2];
     PFE_CUDA_TRY(c, cudaMemcpyAsync(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
     PFE_CUDA_TRY(c, cudaMemsetAsync(c->pctl, 0, sizeof(PstepCtl), c->stream));
     // Y0 (or the eigenmap) -> stage (contiguous FP64), then D-orthonormalise
@@ -750,7 +836,7 @@ pfe_status pfe_inner_step(pfe_ctx *c, pfe_step_stats *st) {
         st->pcg_iters = c->h_ctl->last_iters;
         st->converged = c->h_ctl->last_converged;
         st->relres_max = c->h_ctl->last_relres;
-        if (c->h_ctl->error) return fail(c, PFE_ENUMERIC, "PCG: NaN/Inf or non-positive p^T A p");
+        if (c->h_ctl->error) return pcg_error(c);
         if (!st->converged) return fail(c, PFE_ENOTCONV, "PCG: max_iter reached before tol");
     }
     return PFE_OK;
@@ -799,6 +885,7 @@ static pfe_status solve_stages(pfe_ctx *c, int32_t n_outer, int32_t n_inner, int
     if (st) {
         st->pcg_iters_total = c->h_ctl->tot_iters;
         st->pcg_rounds = c->h_ctl->tot_rounds;
+        st->replacements = c->h_ctl->tot_refreshes;
         st->pcg_iters_max = c->h_ctl->max_solve_iters;
         st->n_solves = c->h_ctl->n_solves;
         st->n_unconverged = c->h_ctl->n_unconv;
@@ -975,7 +1062,7 @@ pfe_status pfe_solve_system(pfe_ctx *c, const double *RHS, double *Y, pfe_step_s
         st->converged = c->h_ctl->last_converged;
         st->relres_max = c->h_ctl->last_relres;
     }
-    if (c->h_ctl->error) return fail(c, PFE_ENUMERIC, "PCG: NaN/Inf or non-positive p^T A p");
+    if (c->h_ctl->error) return pcg_error(c);
     if (!c->h_ctl->last_converged) return fail(c, PFE_ENOTCONV, "PCG: max_iter reached before tol");
     return PFE_OK;
 }

@@ -2,7 +2,10 @@
 //   |M Y|_1 = sum over undirected edges (a < b) of w_ab |y_a - y_b|_1, the
 //             objective of Eq. 1 (which counts every pair twice);
 //   |Y^T D Y - I|_F, the distance from the constraint of Eq. 1, for each
-//             problem of a batch (the largest is reported).
+//             problem of a batch (the largest is reported);
+//   |b_c - A x_c| / |b_c| per column (and problem of a batch) of a solve of
+//             Eq. 13, with the FP64 system matrix whatever the iteration's
+//             precision.
 #include <algorithm>
 #include <cmath>
 
@@ -105,7 +108,91 @@ __global__ void k_obj_gram(Segs sg, const double *deg, const double *y, int d, d
     }
 }
 
+// Residual norms of the columns of B - A X (FP64 values of A): threads own
+// one column (block of kRes = d * floor(256 / d) threads; thread t: column
+// t % d of rows t / d, t / d + kRes / d, ...), add r^2 and b^2 of their rows,
+// the block sums them per column in thread order, and the segment's last
+// block adds the blocks' partials in block order: out[seg * d + c] = |r_c| /
+// |b_c| (|r_c| where b_c = 0).
+__global__ void k_resid(Segs sg, const int *slice_ptr, const int *col, const double *aoff, const double *adiag,
+                        const double *B, const double *X, int d, double *part, unsigned *tickets, double *out) {
+    extern __shared__ double smr[];  // 2 * blockDim.x
+    const BlockSeg bsg = block_seg(sg);
+    const int per = blockDim.x / d;  // rows a block holds at once
+    const int c = threadIdx.x % d, rr = threadIdx.x / d;
+    double r2 = 0.0, b2 = 0.0;
+    if (rr < per) {
+        for (int64_t i = bsg.r0 + (int64_t)(blockIdx.x - bsg.b0) * per + rr; i < bsg.r1; i += (int64_t)bsg.nb * per) {
+            const int64_t s = i >> 5;
+            const int s0 = slice_ptr[s];
+            const int len = (slice_ptr[s + 1] - s0) >> 5;
+            const int64_t base = (int64_t)s0 + (i & 31) * (int64_t)len;
+            double ax = adiag[i] * X[i * d + c];
+            for (int k = 0; k < len; ++k) ax = fma(aoff[base + k], X[(int64_t)col[base + k] * d + c], ax);
+            const double b = B[i * d + c], r = b - ax;
+            r2 = fma(r, r, r2);
+            b2 = fma(b, b, b2);
+        }
+    }
+    smr[threadIdx.x] = r2;
+    smr[blockDim.x + threadIdx.x] = b2;
+    __syncthreads();
+    if (threadIdx.x < d) {
+        double sr = 0.0, sb = 0.0;
+        for (int q = 0; q < per; ++q) {
+            sr += smr[q * d + threadIdx.x];
+            sb += smr[blockDim.x + q * d + threadIdx.x];
+        }
+        part[(int64_t)blockIdx.x * 2 * d + threadIdx.x] = sr;
+        part[(int64_t)blockIdx.x * 2 * d + d + threadIdx.x] = sb;
+    }
+    if (!last_block_arrives(tickets + bsg.seg, (unsigned)bsg.nb)) return;
+    if (threadIdx.x < d) {
+        double sr = 0.0, sb = 0.0;
+        for (int b = 0; b < bsg.nb; ++b) {
+            sr += __ldcg(part + (int64_t)(bsg.b0 + b) * 2 * d + threadIdx.x);
+            sb += __ldcg(part + (int64_t)(bsg.b0 + b) * 2 * d + d + threadIdx.x);
+        }
+        out[bsg.seg * d + threadIdx.x] = sb > 0.0 ? sqrt(sr) / sqrt(sb) : sqrt(sr);
+    }
+    if (threadIdx.x == 0) tickets[bsg.seg] = 0u;
+}
+
 }  // namespace
+
+// Relative residuals |B - A X| / |B| per column (and problem), FP64 A; B, X
+// device n x d FP64 arrays; relres: host, nseg * d.
+pfe_status diag_residual(pfe_ctx *c, const double *B, const double *X, double *relres) {
+    cudaStream_t s = c->stream;
+    const int d = c->d;
+    const int64_t n = c->g.n;
+    const int threads = d * (256 / d);
+    const int per = threads / d;
+    const int grid = (int)std::max<int64_t>(c->nseg, std::min<int64_t>((n + per - 1) / per, (int64_t)c->num_sms * 8));
+    const size_t npart = (size_t)grid * 2 * d, nout = (size_t)c->nseg * d;
+    double *buf = nullptr;
+    if (cudaMalloc((void **)&buf, (npart + nout + c->nseg) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "pfe_residual: device allocation failed";
+        return PFE_ENOMEM;
+    }
+    double *part = buf, *out = buf + npart;
+    unsigned *tick = reinterpret_cast<unsigned *>(out + nout);
+    cudaError_t e = cudaMemsetAsync(tick, 0, sizeof(unsigned) * c->nseg, s);
+    if (e == cudaSuccess) {
+        k_resid<<<grid, threads, 2 * threads * sizeof(double), s>>>(seg_view(c), c->g.slice_ptr, c->g.col, c->g.aoff64,
+                                                                    c->g.adiag64, B, X, d, part, tick, out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(relres, out, nout * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        c->err = std::string("pfe_residual: ") + cudaGetErrorString(e);
+        return PFE_ECUDA;
+    }
+    return PFE_OK;
+}
 
 // Objective and constraint distance of Y (which = 0: the iterate Y of
 // Alg. 2; 1: the embedding Yhat = D^{-1/2} P).

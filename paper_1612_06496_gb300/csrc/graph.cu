@@ -360,6 +360,15 @@ __global__ void k_values_rows(int64_t n, double lam, double r, const double *deg
     dinv32[i] = (float)(1.0 / a);
 }
 
+// FP32 low parts of A's values: a = hi + lo with hi = the FP32 value the
+// iteration multiplies by and lo = FP32(a - hi), so the residual replacement
+// of the FP32 path works with A's FP64 values in FP32 arithmetic.
+__global__ void k_values_lo(int64_t count, const double *a64, const float *a32, float *lo32) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    lo32[k] = (float)(a64[k] - (double)a32[k]);
+}
+
 // Segment of each row (binary search over the offsets).
 __global__ void k_fill_rseg(int64_t n, int nseg, const int64_t *off, int *rseg) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -510,6 +519,7 @@ pfe_status alloc_slots(pfe_ctx *c, cudaStream_t s, const int64_t *slice_ptr64, c
     PFE_TRY(dalloc(c, &g.w32, slots));
     PFE_TRY(dalloc(c, &g.aoff64, slots));
     PFE_TRY(dalloc(c, &g.aoff32, slots));
+    PFE_TRY(dalloc(c, &g.aofflo32, slots));
     PFE_TRY(dalloc(c, &g.ext_slot, g.n_edges));
     PFE_TRY(dalloc(c, &g.ea, g.n_edges));
     PFE_TRY(dalloc(c, &g.eb, g.n_edges));
@@ -519,6 +529,7 @@ pfe_status alloc_slots(pfe_ctx *c, cudaStream_t s, const int64_t *slice_ptr64, c
     PFE_TRY(dalloc(c, &g.sqrtdeg, g.n));
     PFE_TRY(dalloc(c, &g.adiag64, g.n));
     PFE_TRY(dalloc(c, &g.adiag32, g.n));
+    PFE_TRY(dalloc(c, &g.adiaglo32, g.n));
     PFE_TRY(dalloc(c, &g.dinv64, g.n));
     PFE_TRY(dalloc(c, &g.dinv32, g.n));
     return PFE_OK;
@@ -740,6 +751,8 @@ pfe_status finish_graph_values(pfe_ctx *c) {
                                                                  g.sqrtdeg, g.adiag64, g.adiag32, g.dinv64, g.dinv32,
                                                                  derr);
     }
+    if (g.slots > 0) k_values_lo<<<nblk(g.slots, 256), 256, 0, s>>>(g.slots, g.aoff64, g.aoff32, g.aofflo32);
+    k_values_lo<<<nblk(g.n, 256), 256, 0, s>>>(g.n, g.adiag64, g.adiag32, g.adiaglo32);
     PFE_CUDA_TRY(c, cudaGetLastError());
     int herr = 0;
     PFE_CUDA_TRY(c, cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -35,11 +35,16 @@ struct SegScal {
     double *rec2;                                 // nseg * d: |r|^2 of the recurrence residual a replacement replaces
     double *devr;                                 // nseg * d: |r_true - r_rec|^2 / |r_rec|^2 of the last replacement
     int *active;                                  // nseg * d: column still iterating
+    int *pending;                                 // nseg * d: reached tol on the recurrence, waiting for a replacement
     int *seg_active;                              // nseg: any column of the segment iterating
     int *seg_iters;                               // nseg: iterations of the segment in this solve
     long long *seg_iters_tot;                     // nseg: summed over solves until the host clears it
     unsigned *ticket;                             // nseg * 4: per-segment reduction tickets
 };
+
+// Most iterations in one captured loop body that get their own conditional
+// node for the replacement kernels (a longer body launches them every time).
+constexpr int kPcgMaxIf = 8;
 
 // Device-resident control block of one d-column PCG solve (all segments).
 // The per-segment finishers of a reduction kernel count themselves on
@@ -53,7 +58,7 @@ struct PcgCtl {
     int max_iter, refresh, ncols, any_active;
     double tol;
     // statistics accumulated over solves until the host clears them
-    long long tot_iters, tot_rounds;
+    long long tot_iters, tot_rounds, tot_refreshes;
     int max_solve_iters, n_solves, n_unconv, last_iters;
     double max_relres, last_relres;
     int last_converged, unroll;       // unroll: iterations per graph body / host poll
@@ -65,6 +70,11 @@ struct PcgCtl {
     int xfold;                        // FSAI: this iteration's k_fsai_zp applies both pending updates
     int refresh_want;                 // set during an iteration: a column asks for a residual replacement
     int refresh_next;                 // Jacobi: refresh_want latched at the end of an iteration for the next one
+    int refreshes;                    // replacement iterations of the current solve
+    int rounds;                       // q = A p launches of the current solve (bounds the loop)
+    int launch_cond;                  // launches of a replacement iteration that run only then (IF node body)
+    int n_if;                         // IF nodes of the captured loop body (0: no graph built)
+    cudaGraphConditionalHandle ifh[kPcgMaxIf];  // their handles, by position in the body
 };
 
 // Control block of the P-step (Alg. 1 steps 6-7).  G, T and evals are
@@ -94,8 +104,10 @@ struct DevGraph {
     float *w32 = nullptr;
     double *aoff64 = nullptr;   // per slot: A_ij = -lambda w_ij^2
     float *aoff32 = nullptr;
+    float *aofflo32 = nullptr;  // per slot: A_ij - aoff32 rounded to FP32 (aoff32 + aofflo32 = A_ij to ~2^-48)
     double *adiag64 = nullptr;  // A_ii = lambda d2_i + r d_i
     float *adiag32 = nullptr;
+    float *adiaglo32 = nullptr;
     double *dinv64 = nullptr;   // 1 / A_ii
     float *dinv32 = nullptr;
     double *deg = nullptr, *deg2 = nullptr, *sqrtdeg = nullptr;
@@ -195,6 +207,7 @@ pfe_status kmeans_run(pfe_ctx *c, const double *X, int d, int k, const double *C
                       double *centroids, double *inertia, int *rounds);
 // --- diag.cu: |M Y|_1 and |Y^T D Y - I|_F (which: 0 = Y, 1 = Yhat)
 pfe_status diag_objective(pfe_ctx *c, int which, double *l1, double *ortho);
+pfe_status diag_residual(pfe_ctx *c, const double *B, const double *X, double *relres);
 // --- le.cu: Laplacian-eigenmap start (n x d FP64, row-major, device)
 int le_block(int d);
 pfe_status launch_le(pfe_ctx *c, int d, double *yout, int max_iter, double tol, int degree, int *iters,
@@ -206,6 +219,12 @@ pfe_status finish_graph_values(pfe_ctx *c);
 struct PcgLaunch {
     cudaGraphConditionalHandle cond;
     int use_cond;
+    // graph capture of the loop body: the kernels of replacement iterations
+    // go into one conditional IF node per iteration of the body (n_if > 0),
+    // captured on the side stream
+    int n_if = 0;
+    cudaGraphConditionalHandle ifh[kPcgMaxIf] = {};
+    cudaStream_t side = nullptr;
 };
 pfe_status launch_pcg_init(pfe_ctx *c, cudaStream_t s, PcgLaunch L);
 pfe_status launch_pcg_body(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters);

@@ -45,6 +45,8 @@ struct SysView {
     const T *__restrict__ aoff;
     const T *__restrict__ adiag;
     const T *__restrict__ dinv;
+    const float *__restrict__ aofflo;    // FP32 low parts of A's values (the float path's residual replacement)
+    const float *__restrict__ adiaglo;
 };
 
 template <typename T>
@@ -61,6 +63,7 @@ struct PcgArgs {
     SegScal sc;  // per-segment scalars [seg * D + c]
     cudaGraphConditionalHandle cond;
     int use_cond;
+    int if_pos;  // >= 0: this launch decides the replacement of the body's iteration if_pos (its IF node)
     int grid_w;  // width of the image of a one-image grid graph (0 otherwise)
     // FSAI preconditioner (float path): t = G r; the residual alternates
     // between r2[0] (= r) and r2[1]
@@ -87,6 +90,8 @@ SysView<T> sys_view(pfe_ctx *c) {
         v.adiag = c->g.adiag64;
         v.dinv = c->g.dinv64;
     }
+    v.aofflo = c->g.aofflo32;
+    v.adiaglo = c->g.adiaglo32;
     return v;
 }
 
@@ -420,6 +425,13 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, int use, 
     if (use) cudaGraphSetConditional(h, value ? 1u : 0u);
 }
 
+// Whether the replacement kernels of the loop body's iteration a.if_pos run
+// (the value of its IF node; graph launches only).
+template <typename T>
+__device__ __forceinline__ void set_if(const PcgArgs<T> &a, int value) {
+    if (a.use_cond && a.if_pos >= 0) cudaGraphSetConditional(a.ctl->ifh[a.if_pos], value ? 1u : 0u);
+}
+
 // The finishing steps below run on warp 0 of the last block (all 32 lanes):
 // lane c handles column c (or segment c, strided), so the FP64 square roots
 // and divisions of the columns run side by side instead of one after the
@@ -436,12 +448,14 @@ constexpr unsigned kFull = 0xffffffffu;
 // r makes beta huge, the new direction copies the old one and the iteration
 // stalls.  So a column asks for a replacement once its recurrence residual
 // has fallen kRefreshDrop below its value at the last one (the drift stays
-// below ~eps / kRefreshDrop of r), and when it reaches tol: a column is
-// frozen only on a replaced (true) residual.  A replacement that still moved
-// r by more than sqrt(kRestartDev) of its norm restarts that column's
-// direction (beta = 0).  Periodic replacements (every `refresh` iterations)
-// come on top; refresh = 0 turns replacement off and freezes on the
-// recurrence.
+// below ~eps / kRefreshDrop of r).  A column whose recurrence residual
+// reaches tol stops (pending) and is confirmed on the next replacement's true
+// residual -- one is made as soon as no column is left iterating -- or, if
+// that residual is still above tol, resumes with a restarted direction.  A
+// replacement that moved r by more than sqrt(kRestartDev) of its norm
+// restarts that column too (beta = 0).  Periodic replacements (every
+// `refresh` iterations) come on top; refresh = 0 turns replacement off and
+// freezes columns on the recurrence.
 constexpr double kRefreshDrop = 1e-3;
 constexpr double kRestartDev = 1e-2;
 
@@ -455,7 +469,7 @@ static __device__ void finish_seg(PcgCtl *ctl, const SegScal &sc, int seg, const
                                   int mode, int it) {
     const int lane = threadIdx.x & 31;
     const bool replace = ctl->refresh > 0;
-    int any = 0, want = 0;
+    int live = 0, iterating = 0, want = 0;
     for (int c = lane; c < D; c += 32) {
         const int k = seg * D + c;
         if (mode == 0) {
@@ -466,30 +480,43 @@ static __device__ void finish_seg(PcgCtl *ctl, const SegScal &sc, int seg, const
             sc.rel_ref[k] = rel;
             if (!(rel == rel) || !(rz[c] == rz[c])) atomicMax(&ctl->error, (int)PFE_ENUMERIC);
             sc.active[k] = rel > ctl->tol;
-        } else if (sc.active[k]) {
+            sc.pending[k] = 0;
+        } else if (mode == 1 && (sc.active[k] || sc.pending[k])) {
             const double rel = sqrt(rr[c]) / sc.bnorm[k];
-            sc.beta[k] = (mode == 1 && sc.devr[k] > kRestartDev) ? 0.0 : rz[c] / sc.rz[k];
+            const bool restart = sc.pending[k] || sc.devr[k] > kRestartDev;
+            sc.beta[k] = restart ? 0.0 : rz[c] / sc.rz[k];
+            sc.rz[k] = rz[c];
+            sc.relres[k] = rel;
+            sc.rel_ref[k] = rel;
+            if (!(rel == rel) || !(rz[c] == rz[c])) atomicMax(&ctl->error, (int)PFE_ENUMERIC);
+            sc.active[k] = rel > ctl->tol;
+            sc.pending[k] = 0;
+        } else if (mode == 2 && sc.active[k]) {
+            const double rel = sqrt(rr[c]) / sc.bnorm[k];
+            sc.beta[k] = rz[c] / sc.rz[k];
             sc.rz[k] = rz[c];
             sc.relres[k] = rel;
             if (!(rel == rel) || !(rz[c] == rz[c])) atomicMax(&ctl->error, (int)PFE_ENUMERIC);
-            if (mode == 1 || !replace) {
-                if (rel <= ctl->tol) sc.active[k] = 0;
-                if (mode == 1) sc.rel_ref[k] = rel;
-            } else if (rel <= ctl->tol || rel <= kRefreshDrop * sc.rel_ref[k]) {
+            if (rel <= ctl->tol) {
+                sc.active[k] = 0;
+                sc.pending[k] = replace ? 1 : 0;
+            } else if (replace && rel <= kRefreshDrop * sc.rel_ref[k]) {
                 want = 1;
             }
         }
-        any |= sc.active[k];
+        live |= sc.active[k] | sc.pending[k];
+        iterating |= sc.active[k];
     }
-    any = __any_sync(kFull, any);
-    want = __any_sync(kFull, want);
+    live = __any_sync(kFull, live);
+    iterating = __any_sync(kFull, iterating);
+    want = __any_sync(kFull, want) || (live && !iterating);  // only pending columns left: confirm them
     if (lane == 0) {
         if (mode == 0)
             sc.seg_iters[seg] = 0;
         else if (__ldcg(sc.seg_active + seg))
             sc.seg_iters[seg] = it;
-        sc.seg_active[seg] = any;
-        if (want) ctl->refresh_want = 1;
+        sc.seg_active[seg] = live;
+        if (want && mode == 2) ctl->refresh_want = 1;
     }
     __syncwarp();
 }
@@ -555,6 +582,7 @@ static __device__ void finish_all(PcgCtl *ctl, const SegScal &sc, int nseg, int 
         if (lane == 0) {
             ctl->tot_iters += tot;
             ctl->tot_rounds += ctl->iter;
+            ctl->tot_refreshes += ctl->refreshes;
             ctl->max_solve_iters = max(ctl->max_solve_iters, mx);
             ctl->n_solves += nseg;
             ctl->n_unconv += nun;
@@ -563,9 +591,17 @@ static __device__ void finish_all(PcgCtl *ctl, const SegScal &sc, int nseg, int 
             ctl->last_converged = !any;
             ctl->max_relres = fmax(ctl->max_relres, mr);
             const int u = ctl->unroll > 0 ? ctl->unroll : 1;
-            // launches before and after the loop + the loop body's per iteration
-            ctl->launches += ctl->launch_base + (long long)ctl->launch_per_iter * u * ((ctl->iter + u - 1) / u);
+            // launches before and after the loop + the loop body's per
+            // iteration; the replacement kernels run on replacement iterations
+            // only when they sit in IF nodes, else every iteration
+            const long long body_iters = (long long)u * ((ctl->iter + u - 1) / u);
+            const bool by_if = use_cond && ctl->n_if > 0;
+            ctl->launches += ctl->launch_base + (long long)ctl->launch_per_iter * body_iters +
+                             (long long)ctl->launch_cond * (by_if ? (long long)ctl->refreshes : body_iters);
         }
+        // the rest of the body's IF nodes stay closed
+        if (use_cond)
+            for (int k = lane; k < ctl->n_if; k += 32) cudaGraphSetConditional(ctl->ifh[k], 0u);
     }
     if (lane == 0) {
         ctl->done = done;
@@ -574,37 +610,64 @@ static __device__ void finish_all(PcgCtl *ctl, const SegScal &sc, int nseg, int 
     __syncwarp();
 }
 
-// (b - A y) on columns c0 .. c0+V-1 of row i, with y = hi + lo accumulated in
-// double-FP32 (float path) or FP64.
-template <typename T, int D, int V>
+// acc += a * (xh + xl) with a = ah + al: the exact product ah * xh plus the
+// cross terms (al * xl is below the pair's precision).
+__device__ __forceinline__ void df_add_prod2(DF &acc, float ah, float al, float xh, float xl) {
+    df_add_prod(acc, ah, xh);
+    df_add_f(acc, __fmaf_rn(al, xh, __fmul_rn(ah, xl)));
+}
+
+// (b - A y) on columns c0 .. c0+V-1 of row i.  Float path: y = hi + lo and
+// A's FP64 values as FP32 pairs (aoff + aofflo, set when the graph is
+// built), accumulated in double-FP32, so the replaced residual is that of the
+// FP64 system matrix (not of the FP32 rounding the iteration's q = A p uses)
+// to about 2^-44 of |A||y|.  FP64 path: plain FP64.  LEN > 0: uniform rows
+// of LEN slots (row i's at i * LEN), loaded as vectors.
+template <typename T, int D, int V, int LEN = 0>
 __device__ __forceinline__ void true_residual(const PcgArgs<T> &a, int64_t i, int c0, T (&out)[V]) {
-    int64_t base;
-    int len;
-    sell_row(a.A.slice_ptr, a.A.row_len, i, base, len);
     T bi[V];
     ldv_rw<T, V>(a.b + i * D + c0, bi);
     if constexpr (std::is_same_v<T, float>) {
         DF acc[V];
         float xh[V], xl[V];
-        const float ad = a.A.adiag[i];
+        const float ah = a.A.adiag[i], al = a.A.adiaglo[i];
         ldv_rw<float, V>(a.x + i * D + c0, xh);
         ldv_rw<float, V>(a.xlo + i * D + c0, xl);
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             acc[k] = DF{0.f, 0.f};
-            df_add_prod(acc[k], ad, xh[k]);
-            df_add_f(acc[k], ad * xl[k]);
+            df_add_prod2(acc[k], ah, al, xh[k], xl[k]);
         }
-        for (int s = 0; s < len; ++s) {
-            const int64_t idx = base + s;
-            const int j = a.A.col[idx];
-            const float av = a.A.aoff[idx];
-            ldv_rw<float, V>(a.x + (int64_t)j * D + c0, xh);
-            ldv_rw<float, V>(a.xlo + (int64_t)j * D + c0, xl);
+        if constexpr (LEN > 0) {
+            static_assert(LEN % 4 == 0, "fixed rows hold a multiple of 4 slots");
+            const int4 *c4 = reinterpret_cast<const int4 *>(a.A.col + i * LEN);
+            const float4 *h4 = reinterpret_cast<const float4 *>(a.A.aoff + i * LEN);
+            const float4 *l4 = reinterpret_cast<const float4 *>(a.A.aofflo + i * LEN);
 #pragma unroll
-            for (int k = 0; k < V; ++k) {
-                df_add_prod(acc[k], av, xh[k]);
-                df_add_f(acc[k], av * xl[k]);
+            for (int q = 0; q < LEN / 4; ++q) {
+                const int4 jc = __ldg(c4 + q);
+                const float4 vh = __ldg(h4 + q), vl = __ldg(l4 + q);
+                const int jj[4] = {jc.x, jc.y, jc.z, jc.w};
+                const float sh[4] = {vh.x, vh.y, vh.z, vh.w}, sl[4] = {vl.x, vl.y, vl.z, vl.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    ldv_rw<float, V>(a.x + (int64_t)jj[u] * D + c0, xh);
+                    ldv_rw<float, V>(a.xlo + (int64_t)jj[u] * D + c0, xl);
+#pragma unroll
+                    for (int k = 0; k < V; ++k) df_add_prod2(acc[k], sh[u], sl[u], xh[k], xl[k]);
+                }
+            }
+        } else {
+            int64_t base;
+            int len;
+            sell_row(a.A.slice_ptr, a.A.row_len, i, base, len);
+            for (int s = 0; s < len; ++s) {
+                const int64_t idx = base + s;
+                const int j = a.A.col[idx];
+                ldv_rw<float, V>(a.x + (int64_t)j * D + c0, xh);
+                ldv_rw<float, V>(a.xlo + (int64_t)j * D + c0, xl);
+#pragma unroll
+                for (int k = 0; k < V; ++k) df_add_prod2(acc[k], a.A.aoff[idx], a.A.aofflo[idx], xh[k], xl[k]);
             }
         }
 #pragma unroll
@@ -614,6 +677,9 @@ __device__ __forceinline__ void true_residual(const PcgArgs<T> &a, int64_t i, in
             out[k] = __fadd_rn(sh, __fsub_rn(se, acc[k].lo));
         }
     } else {
+        int64_t base;
+        int len;
+        sell_row(a.A.slice_ptr, a.A.row_len, i, base, len);
         double acc[V], xv[V];
         const double ad = a.A.adiag[i];
         ldv_rw<double, V>(a.x + i * D + c0, xv);
@@ -707,6 +773,8 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(PcgArgs<T> a) {
                     ctl->xfold = 0;
                     ctl->refresh_want = 0;
                     ctl->refresh_next = 0;
+                    ctl->refreshes = 0;
+                    ctl->rounds = 0;
                     if (PRE != 0) ctl->done = 0;  // k_fsai_t finishes the start
                 }
                 __syncwarp();
@@ -865,6 +933,15 @@ __device__ __forceinline__ void spmm_finish(const PcgArgs<T> &a, const BlockSeg 
     if ((!MS || warp_last_segment(w, 0, a.sg.nseg)) && (threadIdx.x & 31) == 0) {
         w->p_ready = 0;
         w->xpending = 1;
+        // a loop whose iterations stopped advancing (no finisher ran) ends
+        // here with PFE_ETIMEOUT instead of running on
+        if (++w->rounds > w->max_iter + 2 * kPcgMaxIf + 8) {
+            atomicMax(&w->error, (int)PFE_ETIMEOUT);
+            w->done = 1;
+            set_cond(a.cond, a.use_cond, 0);
+            if (a.use_cond)
+                for (int k = 0; k < w->n_if; ++k) cudaGraphSetConditional(w->ifh[k], 0u);
+        }
     }
 }
 
@@ -1480,6 +1557,7 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
                 if (threadIdx.x == 0) {
                     ctl->iter = it;
                     if (refresh_due) ctl->refresh_now = 1;  // k_xflush + k_refresh finish this iteration
+                    set_if(a, refresh_due);
                 }
                 __syncwarp();
                 if (!refresh_due) {
@@ -1499,8 +1577,11 @@ __global__ void __launch_bounds__(kBlock) k_update(PcgArgs<T> a) {
     }
 }
 
-// y += alpha p with the direction of the last k_spmm.  In the loop body it
-// runs only before a refresh; after the loop it applies the final update.
+// y += alpha p with the direction of the last k_spmm (and y += alpha_prev
+// p_prev when an update is held).  In the loop body it runs only on
+// replacement iterations; after the loop it applies the final update.  Flat
+// float4 / double2 traversal like k_pupdate (the grid makes every thread meet
+// fixed columns).
 template <typename T, int D, bool MS>
 __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush, int counted) {
     const PcgCtl *ctl = a.ctl;
@@ -1511,7 +1592,7 @@ __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush
     __shared__ T salpha[D], salpha_prev[D];
     if (threadIdx.x < D) {
         salpha[threadIdx.x] = xp ? (T)a.sc.alpha[threadIdx.x] : T(0);
-        salpha_prev[threadIdx.x] = (T)a.sc.alpha_prev[threadIdx.x];
+        salpha_prev[threadIdx.x] = xh ? (T)a.sc.alpha_prev[threadIdx.x] : T(0);
     }
     __syncthreads();
     // the direction of the last k_spmm: buffer iter & 1 before the iteration's
@@ -1521,20 +1602,62 @@ __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush
     const int kc = counted ? ((ctl->iter & 1) ^ 1) : (ctl->iter & 1);
     const T *__restrict__ pc = a.p[kc];
     const T *__restrict__ pprev = a.p[kc ^ 1];
-    const int64_t nel = a.A.n * D;
-    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < nel; e += (int64_t)gridDim.x * kBlock) {
+    using VT = Vec<T>;
+    constexpr int VN = VT::N;
+    const int64_t nel = a.A.n * D, nvec = nel / VN;
+    const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
+    T al[VN], ap[VN];
+    int cu[VN];
+#pragma unroll
+    for (int u = 0; u < VN; ++u) {
+        cu[u] = (int)((tid * VN + u) % D);
+        al[u] = salpha[cu[u]];
+        ap[u] = salpha_prev[cu[u]];
+    }
+    using V4 = typename VT::V;
+    const V4 *pc4 = reinterpret_cast<const V4 *>(pc);
+    const V4 *pp4 = reinterpret_cast<const V4 *>(pprev);
+    V4 *x4 = reinterpret_cast<V4 *>(a.x);
+    float4 *xl4 = reinterpret_cast<float4 *>(a.xlo);  // float path: VN == 4
+    for (int64_t v = tid; v < nvec; v += nthr) {
+        if constexpr (multi) {
+            const int64_t row0 = v * VN / D;
+#pragma unroll
+            for (int u = 0; u < VN; ++u) {
+                const int sgm = __ldg(a.sg.rseg + row0 + (cu[0] + u) / D);
+                al[u] = xp ? (T)a.sc.alpha[sgm * D + cu[u]] : T(0);
+                ap[u] = xh ? (T)a.sc.alpha_prev[sgm * D + cu[u]] : T(0);
+            }
+        }
+        T xv[VN], pv[VN], qv[VN];
+        float xl[VN] = {};
+        VT::get(x4[v], xv);
+        if constexpr (std::is_same_v<T, float>) {
+            const float4 t = xl4[v];
+            xl[0] = t.x; xl[1] = t.y; xl[2] = t.z; xl[3] = t.w;
+        }
+        if (xh) {
+            VT::get(pp4[v], qv);
+#pragma unroll
+            for (int u = 0; u < VN; ++u) axpy_hilo<T>(xv[u], xl[u], ap[u], qv[u]);
+        }
+        if (xp) {
+            VT::get(pc4[v], pv);
+#pragma unroll
+            for (int u = 0; u < VN; ++u) axpy_hilo<T>(xv[u], xl[u], al[u], pv[u]);
+        }
+        x4[v] = VT::make(xv);
+        if constexpr (std::is_same_v<T, float>) xl4[v] = make_float4(xl[0], xl[1], xl[2], xl[3]);
+    }
+    if (tid < nel - nvec * VN) {  // tail elements
+        const int64_t e = nvec * VN + tid;
+        const int c = (int)(e % D);
+        const int sgm = multi ? row_seg(a.sg, e / D) : 0;
         T xv = a.x[e];
         float xl = 0.f;
         if constexpr (std::is_same_v<T, float>) xl = a.xlo[e];
-        const int c = (int)(e % D);
-        if (xh) {
-            const T ap = multi ? (T)a.sc.alpha_prev[__ldg(a.sg.rseg + e / D) * D + c] : salpha_prev[c];
-            axpy_hilo<T>(xv, xl, ap, pprev[e]);
-        }
-        if (xp) {
-            const T al = multi ? (T)a.sc.alpha[__ldg(a.sg.rseg + e / D) * D + c] : salpha[c];
-            axpy_hilo<T>(xv, xl, al, pc[e]);
-        }
+        if (xh) axpy_hilo<T>(xv, xl, multi ? (T)a.sc.alpha_prev[sgm * D + c] : salpha_prev[c], pprev[e]);
+        if (xp) axpy_hilo<T>(xv, xl, multi ? (T)a.sc.alpha[sgm * D + c] : salpha[c], pc[e]);
         a.x[e] = xv;
         if constexpr (std::is_same_v<T, float>) a.xlo[e] = xl;
     }
@@ -1569,9 +1692,9 @@ __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush
 // replacement iterations).  It also measures how far the true residual lies
 // from the recurrence residual r - alpha q it replaces (|r - r_rec|^2 /
 // |r_rec|^2 per column -> sc.devr, for the restart test).
-template <typename T, int D>
+template <typename T, int D, int LEN>
 __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
-    if (!*(volatile int *)&a.ctl->refresh_now) return;
+    if (*(volatile int *)&a.ctl->done || !*(volatile int *)&a.ctl->refresh_now) return;
     const int par = a.ctl->iter & 1;
     const T *__restrict__ rold = a.r2[par];
     T *__restrict__ rdst = a.r2[par ^ 1];
@@ -1586,7 +1709,7 @@ __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
         T ri[V], ro[V], qi[V];
         ldv<T, V>(rold + i * D + c0, ro);
         ldv<T, V>(a.q + i * D + c0, qi);
-        true_residual<T, D, V>(a, i, c0, ri);
+        true_residual<T, D, V, LEN>(a, i, c0, ri);
         stv<T, V>(rdst + i * D + c0, ri);
 #pragma unroll
         for (int k = 0; k < V; ++k) {
@@ -1676,6 +1799,7 @@ __device__ void fsai_finish(const PcgArgs<T> &a, const BlockSeg &bsg, const doub
     PcgCtl *ctl = a.ctl;
     finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, mode, ctl->iter + 1);
     if (threadIdx.x == 0 && mode != 0) ctl->iter += 1;
+    if (threadIdx.x == 0 && mode == 1) ctl->refreshes += 1;
     __syncwarp();
     finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
     int hold = 0;
@@ -1860,6 +1984,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // periodic, or asked for by a column in this iteration
         ctl->refresh_now = (ctl->refresh > 0 && (((ctl->iter + 1) % ctl->refresh) == 0 || ctl->refresh_want)) ? 1 : 0;
         ctl->refresh_want = 0;
+        set_if(a, ctl->refresh_now);
     }
     __syncthreads();
     PFE_ROW_LOOP(T, D) {
@@ -1982,6 +2107,7 @@ __global__ void __launch_bounds__(kBlock) k_ic_dots(PcgArgs<T> a, int start) {
                 ctl->refresh_now =
                     (ctl->refresh > 0 && (((ctl->iter + 1) % ctl->refresh) == 0 || ctl->refresh_want)) ? 1 : 0;
                 ctl->refresh_want = 0;
+                if (!ctl->done) set_if(a, ctl->refresh_now);
             }
         }
     }
@@ -2028,7 +2154,7 @@ __global__ void __launch_bounds__(kBlock) k_ic_bwd(PcgArgs<T> a, int64_t level, 
 // iteration with the true residual.  Also |r - r_rec|^2, the squared
 // distance of the true residual from the recurrence residual k_update left
 // in r (its |r_rec|^2 is in sc.rec2), for the restart test.
-template <typename T, int D, bool MS>
+template <typename T, int D, bool MS, int LEN>
 __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
     if (!*(volatile int *)&a.ctl->refresh_now) return;
     using A = Acc<T>;
@@ -2044,7 +2170,7 @@ __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
         const int c0 = lm.cg * V;
         T ri[V], rr[V];
         ldv_rw<T, V>(a.r + i * D + c0, rr);
-        true_residual<T, D, V>(a, i, c0, ri);
+        true_residual<T, D, V, LEN>(a, i, c0, ri);
         const T dv = a.A.dinv[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) {
@@ -2074,6 +2200,7 @@ __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
                     ctl->xfold = 0;
                     ctl->refresh_next = 0;
                     ctl->refresh_want = 0;
+                    ctl->refreshes += 1;
                 }
                 __syncwarp();
                 finish_all(ctl, a.sc, a.sg.nseg, D, a.cond, a.use_cond);
@@ -2131,6 +2258,7 @@ PcgArgs<T> pcg_args(pfe_ctx *c, PcgLaunch L) {
     a.sc = c->sc;
     a.cond = L.cond;
     a.use_cond = L.use_cond;
+    a.if_pos = -1;
     a.grid_w = (c->kind == PFE_GRAPH_GRID && c->nseg == 1) ? (int)c->W : 0;
     a.t = (T *)c->fsai.t;
     a.r2[0] = a.r;
@@ -2179,16 +2307,76 @@ template <typename T, int D, bool MS>
 void init_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a) {
     k_pcg_init<T, D, 0, MS><<<wave_grid(c, G_INIT, k_pcg_init<T, D, 0, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
 }
-template <typename T, int D, bool MS>
-void body_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int iters) {
-    for (int u = 0; u < iters; ++u) {
-        k_pupdate<T, D, MS><<<wave_grid(c, G_PUPD, k_pupdate<T, D, MS>, flat_need<T, D>(c), flat_mult<T, D>()),
-                                 kBlock, 0, s>>>(a);
-        launch_spmm<T, D, MS>(c, s, a);
-        k_update<T, D, MS><<<wave_grid(c, G_UPDATE, k_update<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-        k_xflush<T, D, MS><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, MS>, flat_need<T, D>(c)), kBlock, 0, s>>>(a, 0, 1);
-        k_refresh<T, D, MS><<<wave_grid(c, G_REFRESH, k_refresh<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+// The replacement kernels of iteration `pos` of the loop body.  Capturing a
+// graph with IF nodes (L.n_if > 0): a conditional IF node is appended to the
+// capture of stream s (its value is set on the device by the kernel that
+// decides the replacement) and its body is captured on the side stream, so
+// ordinary iterations launch none of these kernels.  Otherwise they are
+// launched on s and return at once outside replacement iterations.
+static pfe_status if_begin(pfe_ctx *c, cudaStream_t s, const PcgLaunch &L, int pos, cudaStream_t &ks) {
+    ks = s;
+    if (L.n_if == 0) return PFE_OK;
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    PFE_CUDA_TRY(c, cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &ndeps));
+    if (cst != cudaStreamCaptureStatusActive) {
+        c->err = "PCG loop body: the stream is not capturing";
+        return PFE_ECUDA;
     }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = L.ifh[pos];
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t n;
+    PFE_CUDA_TRY(c, cudaGraphAddNode(&n, g, deps, nullptr, ndeps, &cp));
+    PFE_CUDA_TRY(c, cudaStreamUpdateCaptureDependencies(s, &n, nullptr, 1, cudaStreamSetCaptureDependencies));
+    PFE_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(L.side, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal));
+    ks = L.side;
+    return PFE_OK;
+}
+static pfe_status if_end(pfe_ctx *c, const PcgLaunch &L) {
+    if (L.n_if == 0) return PFE_OK;
+    PFE_CUDA_TRY(c, cudaGetLastError());
+    cudaGraph_t g = nullptr;
+    PFE_CUDA_TRY(c, cudaStreamEndCapture(L.side, &g));
+    return PFE_OK;
+}
+
+// The replacement kernels with the compile-time row length of fixed-length
+// layouts (12 or 28 slots), else the general slot loop.
+template <typename T, int D, bool MS>
+void launch_refresh(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a) {
+    if (c->g.row_len == 12)
+        k_refresh<T, D, MS, 12><<<wave_grid(c, G_REFRESH, k_refresh<T, D, MS, 12>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+    else if (c->g.row_len == 28)
+        k_refresh<T, D, MS, 28><<<wave_grid(c, G_REFRESH, k_refresh<T, D, MS, 28>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+    else
+        k_refresh<T, D, MS, 0><<<wave_grid(c, G_REFRESH, k_refresh<T, D, MS, 0>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+}
+template <typename T, int D>
+void launch_refresh_f(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a) {
+    if (c->g.row_len == 12)
+        k_refresh_f<T, D, 12><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 12>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+    else if (c->g.row_len == 28)
+        k_refresh_f<T, D, 28><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 28>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+    else
+        k_refresh_f<T, D, 0><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 0>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+}
+
+template <typename T, int D, bool MS>
+pfe_status body_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, const PcgLaunch &L, int u, cudaStream_t &ks) {
+    k_pupdate<T, D, MS><<<wave_grid(c, G_PUPD, k_pupdate<T, D, MS>, flat_need<T, D>(c), flat_mult<T, D>()),
+                             kBlock, 0, s>>>(a);
+    launch_spmm<T, D, MS>(c, s, a);
+    k_update<T, D, MS><<<wave_grid(c, G_UPDATE, k_update<T, D, MS>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+    PFE_TRY(if_begin(c, s, L, u, ks));
+    k_xflush<T, D, MS><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, MS>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0, ks>>>(a, 0, 1);
+    launch_refresh<T, D, MS>(c, ks, a);
+    return if_end(c, L);
 }
 
 // The FSAI kernels with the compile-time row length of the layout (FP32 grid
@@ -2252,7 +2440,9 @@ pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
             k_pcg_init<T, D, 1, false><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1, false>, rows_need<T, D>(c)), kBlock,
                                          0, s>>>(a);
             ic_solve<T, D>(c, s, a, true, 1);
-            k_ic_dots<T, D><<<wave_grid(c, G_IC_DOTS, k_ic_dots<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a, 1);
+            PcgArgs<T> ad = a;
+            ad.if_pos = L.n_if > 0 ? 0 : -1;  // decides the replacement of the body's first iteration
+            k_ic_dots<T, D><<<wave_grid(c, G_IC_DOTS, k_ic_dots<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(ad, 1);
             ic_solve<T, D>(c, s, a, false, 0);
             PFE_CUDA_TRY(c, cudaGetLastError());
             return PFE_OK;
@@ -2261,7 +2451,9 @@ pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
             k_pcg_init<T, D, 1, false><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1, false>, rows_need<T, D>(c)), kBlock,
                                          0, s>>>(a);
             launch_fsai<T, D>(c, s, a, 1);
-            launch_fsai<T, D>(c, s, a, 3);
+            PcgArgs<T> az = a;
+            az.if_pos = L.n_if > 0 ? 0 : -1;  // decides the replacement of the body's first iteration
+            launch_fsai<T, D>(c, s, az, 3);
             PFE_CUDA_TRY(c, cudaGetLastError());
             return PFE_OK;
         }
@@ -2277,16 +2469,21 @@ pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
 template <typename T, int D>
 pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
     PcgArgs<T> a = pcg_args<T>(c, L);
+    cudaStream_t ks = s;
     if constexpr (std::is_same_v<T, float>) {
         if (use_fsai<T>(c) && c->fsai.ic) {
             for (int u = 0; u < iters; ++u) {
                 launch_spmm<T, D, false>(c, s, a);
                 k_ic_r<T, D><<<wave_grid(c, G_IC_R, k_ic_r<T, D>, flat_need<T, D>(c)), kBlock, 0, s>>>(a);
-                k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c)), kBlock, 0,
-                                        s>>>(a, 0, 0);
-                k_refresh_f<T, D><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+                PFE_TRY(if_begin(c, s, L, u, ks));
+                k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0,
+                                        ks>>>(a, 0, 0);
+                launch_refresh_f<T, D>(c, ks, a);
+                PFE_TRY(if_end(c, L));
                 ic_solve<T, D>(c, s, a, true, 0);
-                k_ic_dots<T, D><<<wave_grid(c, G_IC_DOTS, k_ic_dots<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a, 0);
+                PcgArgs<T> ad = a;
+                ad.if_pos = L.n_if > 0 ? (u + 1) % iters : -1;  // decides the next iteration's replacement
+                k_ic_dots<T, D><<<wave_grid(c, G_IC_DOTS, k_ic_dots<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(ad, 0);
                 ic_solve<T, D>(c, s, a, false, 0);
             }
             PFE_CUDA_TRY(c, cudaGetLastError());
@@ -2296,20 +2493,28 @@ pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
             for (int u = 0; u < iters; ++u) {
                 launch_spmm<T, D, false>(c, s, a);
                 launch_fsai<T, D>(c, s, a, 0);
-                k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c)), kBlock, 0,
-                                        s>>>(a, 0, 0);
-                k_refresh_f<T, D><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
-                launch_fsai<T, D>(c, s, a, 2);
-                launch_fsai<T, D>(c, s, a, 3);
+                PFE_TRY(if_begin(c, s, L, u, ks));
+                k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0,
+                                        ks>>>(a, 0, 0);
+                launch_refresh_f<T, D>(c, ks, a);
+                launch_fsai<T, D>(c, ks, a, 2);
+                PFE_TRY(if_end(c, L));
+                PcgArgs<T> az = a;
+                az.if_pos = L.n_if > 0 ? (u + 1) % iters : -1;  // decides the next iteration's replacement
+                launch_fsai<T, D>(c, s, az, 3);
             }
             PFE_CUDA_TRY(c, cudaGetLastError());
             return PFE_OK;
         }
     }
-    if (c->nseg > 1)
-        body_ms<T, D, true>(c, s, a, iters);
-    else
-        body_ms<T, D, false>(c, s, a, iters);
+    for (int u = 0; u < iters; ++u) {
+        PcgArgs<T> au = a;
+        au.if_pos = L.n_if > 0 ? u : -1;  // k_update decides this iteration's replacement
+        if (c->nseg > 1)
+            PFE_TRY((body_ms<T, D, true>(c, s, au, L, u, ks)));
+        else
+            PFE_TRY((body_ms<T, D, false>(c, s, au, L, u, ks)));
+    }
     PFE_CUDA_TRY(c, cudaGetLastError());
     return PFE_OK;
 }
@@ -2317,10 +2522,10 @@ pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
 template <typename T, int D>
 pfe_status final_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
     if (c->nseg > 1)
-        k_xflush<T, D, true><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, true>, flat_need<T, D>(c)), kBlock, 0, s>>>(
+        k_xflush<T, D, true><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, true>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0, s>>>(
             pcg_args<T>(c, L), 1, 1);
     else
-        k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c)), kBlock, 0, s>>>(
+        k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0, s>>>(
             pcg_args<T>(c, L), 1, 1);
     PFE_CUDA_TRY(c, cudaGetLastError());
     return PFE_OK;

@@ -29,7 +29,7 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
            "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_ic0", "pfe_get_segments",
            "pfe_get_segment_stats", "pfe_laplacian_eigenmap", "pfe_objective", "pfe_autotune",
-           "pfe_set_variant", "pfe_solve_two_stage", "pfe_kmeans"]
+           "pfe_set_variant", "pfe_solve_two_stage", "pfe_kmeans", "pfe_residual"]
 SPMM_NVARIANTS = 6  # PFE_SPMM_GENERAL, _ROW1, _ROW2, _ROW2_4, _TMA, _STENCIL
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3, "fsai_tr": 4, "fsai_zp": 5, "fsai_zp_hold": 6,
           "pupdate_hold": 7}
@@ -63,7 +63,7 @@ class StepStats(C.Structure):
 class SolveStats(C.Structure):
     _fields_ = [("pcg_iters_total", C.c_int64), ("pcg_iters_max", C.c_int32), ("n_solves", C.c_int32),
                 ("n_unconverged", C.c_int32), ("relres_max", C.c_double), ("kernel_launches", C.c_int64),
-                ("pcg_rounds", C.c_int64)]
+                ("pcg_rounds", C.c_int64), ("replacements", C.c_int64)]
 
 
 _lib = None
@@ -112,6 +112,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_set_variant.argtypes = [vp, i32, i32]
     lib.pfe_solve_two_stage.argtypes = [vp, i32, i32, i32, vp, vp, C.POINTER(SolveStats)]
     lib.pfe_kmeans.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp, C.POINTER(dbl), C.POINTER(i32)]
+    lib.pfe_residual.argtypes = [vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("pfe_default_params", "pfe_last_error", "pfe_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -299,6 +300,14 @@ class PFE:
                                         cent.ctypes.data, C.byref(inertia), C.byref(rounds)), "pfe_kmeans")
         return labels, cent, inertia.value, rounds.value
 
+    def residual(self, B, X):
+        """|B - A X| / |B| per problem and column ([nseg, d]) with the FP64 values of A."""
+        pb, kb = _ptr(B)
+        px, kx = _ptr(X)
+        out = np.empty((self.info()["nseg"], X.shape[1]), dtype=np.float64)
+        self._check(self.lib.pfe_residual(self.ctx, pb, px, out.ctypes.data), "pfe_residual")
+        return out
+
     def objective(self, which: str = "yhat"):
         """(|M Y|_1, |Y^T D Y - I|_F) of the iterate ("y") or the embedding ("yhat")."""
         l1, oe = C.c_double(), C.c_double()
@@ -337,7 +346,8 @@ class PFE:
         st = self._check(self.lib.pfe_solve(self.ctx, n_outer, n_inner, py, ph, C.byref(s)), "pfe_solve", ok)
         return {"pcg_iters_total": s.pcg_iters_total, "pcg_iters_max": s.pcg_iters_max, "n_solves": s.n_solves,
                 "n_unconverged": s.n_unconverged, "relres_max": s.relres_max,
-                "kernel_launches": s.kernel_launches, "pcg_rounds": s.pcg_rounds, "status": st}
+                "kernel_launches": s.kernel_launches, "pcg_rounds": s.pcg_rounds,
+                "replacements": s.replacements, "status": st}
 
     def solve_two_stage(self, n_outer: int, n_inner: int, n_stage2: int, Y_out=None, Yhat_out=None,
                         allow_notconv: bool = False):
@@ -351,7 +361,8 @@ class PFE:
                          "pfe_solve_two_stage", ok)
         return {"pcg_iters_total": s.pcg_iters_total, "pcg_iters_max": s.pcg_iters_max, "n_solves": s.n_solves,
                 "n_unconverged": s.n_unconverged, "relres_max": s.relres_max,
-                "kernel_launches": s.kernel_launches, "pcg_rounds": s.pcg_rounds, "status": st}
+                "kernel_launches": s.kernel_launches, "pcg_rounds": s.pcg_rounds,
+                "replacements": s.replacements, "status": st}
 
     def get(self, which: str, out=None):
         if out is None:

@@ -209,3 +209,100 @@ def test_adam_moments_are_the_weighted_sums_of_past_gradients():
     np.testing.assert_allclose(v, v_sum, rtol=1e-13)
     last = lr * (m_sum / (1 - b1 ** T)) / (np.sqrt(v_sum / (1 - b2 ** T)) + eps)
     np.testing.assert_allclose(prev - th, last, rtol=1e-12, atol=1e-15)  # prev - th cancels: |theta| ~ 1
+
+
+# ---------------------------------------------------------------- the network itself
+
+
+def _theta_random(seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(F.NPARAM) * 0.3
+
+
+def _torch_mlp(theta):
+    """The same network as torch.nn layers in FP64 (Linear computes x W^T + b,
+    so each weight is the transpose of the oracle's row-major W)."""
+    torch = pytest.importorskip("torch")
+    W1, b1, W2, b2, W3, b3 = F.unpack(theta)
+    net = torch.nn.Sequential(torch.nn.Linear(4, F.H), torch.nn.ReLU(), torch.nn.Linear(F.H, F.H), torch.nn.ReLU(),
+                              torch.nn.Linear(F.H, 2)).double()
+    with torch.no_grad():
+        for layer, W, b in ((net[0], W1, b1), (net[2], W2, b2), (net[4], W3, b3)):
+            layer.weight.copy_(torch.from_numpy(np.ascontiguousarray(W.T)))
+            layer.bias.copy_(torch.from_numpy(b))
+    return torch, net
+
+
+def test_mlp_forward_matches_torch_nn():
+    """mlp_forward against torch.nn's Linear/ReLU stack in FP64, on inputs of
+    both signs (both ReLUs cut)."""
+    theta = _theta_random(1)
+    Fm = np.random.default_rng(2).standard_normal((300, 4)) * 2.0
+    out, _ = F.mlp_forward(theta, Fm)
+    torch, net = _torch_mlp(theta)
+    ref = net(torch.from_numpy(Fm)).detach().numpy()
+    np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_mlp_backward_matches_torch_autograd():
+    """mlp_backward (the gradient of sum(out * dout) w.r.t. the parameters)
+    against torch's autograd of the same network in FP64."""
+    theta = _theta_random(3)
+    rng = np.random.default_rng(4)
+    Fm = rng.standard_normal((200, 4)) * 2.0
+    dout = rng.standard_normal((200, 2))
+    _, cache = F.mlp_forward(theta, Fm)
+    g = F.mlp_backward(theta, cache, dout)
+    torch, net = _torch_mlp(theta)
+    (net(torch.from_numpy(Fm)) * torch.from_numpy(dout)).sum().backward()
+    parts = [net[0].weight.grad.T, net[0].bias.grad, net[2].weight.grad.T, net[2].bias.grad, net[4].weight.grad.T,
+             net[4].bias.grad]
+    ref = np.concatenate([np.ascontiguousarray(p.numpy()).ravel() for p in parts])
+    np.testing.assert_allclose(g, ref, rtol=1e-11, atol=1e-12)
+
+
+def test_mlp_forward_worked_by_hand():
+    """A network whose output follows by hand.  W1 copies the four inputs to
+    units 0..3; W2 shifts unit k to unit k + 1 (not symmetric, so a transposed
+    W2 reads unit k + 1 instead) and also sends -h1_1 to unit 10; b2 = -0.5
+    makes the second ReLU cut.  Input (1, -2, 3, 0.5): h1 = (1, 0, 3, 0.5)
+    (the first ReLU cuts -2; without it unit 10 would get 2 - 0.5 and out0
+    1.5 more); a2_j = h1_{j-1} - 0.5, so h2 = (0, 0.5, 0, 2.5, 0, ...);
+    out0 = 0.5 * 2 + 2.5 * 4 + 0.25 = 11.25 and out1 = 2.5 * 1 - 1 = 1.5."""
+    W1 = np.zeros((4, F.H))
+    W1[np.arange(4), np.arange(4)] = 1.0
+    W2 = np.zeros((F.H, F.H))
+    W2[np.arange(F.H - 1), np.arange(1, F.H)] = 1.0
+    W2[1, 10] = -1.0
+    b2 = np.full(F.H, -0.5)
+    W3 = np.zeros((F.H, 2))
+    W3[:4, 0] = [1.0, 2.0, 3.0, 4.0]
+    W3[10, 0] = 1.0
+    W3[3, 1] = 1.0
+    theta = np.concatenate([W1.ravel(), np.zeros(F.H), W2.ravel(), b2, W3.ravel(), [0.25, -1.0]])
+    out, _ = F.mlp_forward(theta, np.array([[1.0, -2.0, 3.0, 0.5]]))
+    np.testing.assert_allclose(out, [[11.25, 1.5]], rtol=0, atol=1e-15)
+
+
+def test_bf16_rounding_matches_torch():
+    """bf16_round (nearest, ties to even, via FP32) against torch's bfloat16
+    conversion, ties and a boundary included: 1 + 2^-8 is a tie between 1
+    and 1 + 2^-7 and rounds to the even 1; 1 + 3 * 2^-8 rounds to 1 + 2^-6."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    x = np.concatenate([rng.standard_normal(1000) * 10.0 ** rng.integers(-6, 6, 1000),
+                        [1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8), 0.0, 2.0 ** -126]])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(F.bf16_round(x), ref)
+    assert F.bf16_round(1 + 2.0 ** -8) == 1.0 and F.bf16_round(1 + 3 * 2.0 ** -8) == 1 + 2.0 ** -6
+
+
+def test_bf16_network_stays_within_bf16_rounding_of_fp64():
+    """The BF16 emulation of the hidden layer moves the outputs by about the
+    BF16 unit (2^-8 relative per operand) and no more."""
+    theta = _theta_random(5)
+    Fm = np.random.default_rng(6).standard_normal((500, 4))
+    o64, _ = F.mlp_forward(theta, Fm)
+    o16, _ = F.mlp_forward(theta, Fm, bf16=True)
+    rel = np.linalg.norm(o16 - o64) / np.linalg.norm(o64)
+    assert 1e-5 < rel < 2e-2, rel

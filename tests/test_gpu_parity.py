@@ -111,10 +111,9 @@ def test_init_d_orthonormalises(precision):
 # ---------------------------------------------------------------- one inner step
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_single_inner_step_state(precision):
+def test_single_inner_step_state_fp64():
     spec = small_spec(H=20, W=26, d=3)
-    p, X, Y0 = gpu_problem(spec, precision, tol=1e-12 if precision == "fp64" else 1e-6)
+    p, X, Y0 = gpu_problem(spec, "fp64", tol=1e-12)
     g = oracle_graph(spec, X)
     p.init(Y0)
     st = O.init_state(g, Y0)
@@ -122,11 +121,64 @@ def test_single_inner_step_state(precision):
     for step in range(3):
         p.inner_step()
         O.split_bregman_step(g, st, solve)
-        tol = 1e-9 if precision == "fp64" else 2e-4
-        assert relerr(p.get("Y"), st.Y) < tol, step
-        assert relerr(p.get("BS"), st.bs) < (1e-8 if precision == "fp64" else 5e-3), step
+        assert relerr(p.get("Y"), st.Y) < 1e-9, step
+        assert relerr(p.get("BS"), st.bs) < 1e-8, step
         rhs_next = g.lam * (g.M.T @ (st.ds - st.bs)) + g.r * np.sqrt(g.dvec)[:, None] * (st.P - st.B)
-        assert relerr(p.get("RHS"), rhs_next) < (1e-9 if precision == "fp64" else 1e-3), step
+        assert relerr(p.get("RHS"), rhs_next) < 1e-9, step
+    p.close()
+
+
+def test_single_inner_step_state_mixed():
+    """The FP32 path's edge pass against the oracle, element by element, with
+    bounds that follow from the method.  The Bregman update of Eq. 10 is
+    b' = b + E - Shrink(E + b, 1/lam) = clamp(E + b, -1/lam, 1/lam), a
+    1-Lipschitz map of t = E + b (no jump where the shrink switches on), and
+    E_e = w_e (y_a - y_b).  So an error dY in the solve (bounded by the PCG
+    tolerance, 2e-4 relative) moves b'_e by at most
+    T_e = w_e (|dy_a| + |dy_b|) + (the bound on b_e) + FP32 rounding, and the
+    next right-hand side lam M^T (Z - b') + r D^{1/2} (P - B), Z - b' = t -
+    2 clamp(t), by at most lam sum over the row's edges of 3 w_e T_e plus
+    rounding.  Differences of nearby y are small in smooth regions, so these
+    errors can be large relative to b and the right-hand side (the norm
+    errors are also printed) while every element stays inside its bound."""
+    spec = small_spec(H=20, W=26, d=3)
+    p, X, Y0 = gpu_problem(spec, "mixed", tol=1e-6)
+    g = oracle_graph(spec, X)
+    p.init(Y0)
+    st = O.init_state(g, Y0)
+    solve = O.DirectSolver(g.A)
+    u32 = 2.0 ** -24
+    gam = 1.0 / g.lam
+    absM = abs(g.M)
+    sq = np.sqrt(g.dvec)[:, None]
+    Tb = np.zeros_like(st.bs)  # bound on |db| entering the step
+    for step in range(3):
+        b_old = st.bs.copy()
+        p.inner_step()
+        O.split_bregman_step(g, st, solve)
+        Yg = p.get("Y")
+        assert relerr(Yg, st.Y) < 2e-4, step
+        dy = np.abs(Yg - st.Y)
+        w = g.w[:, None]
+        E = g.M @ st.Y
+        # FP32 rounding of y (hi part), w, the difference, the product and t = E + b
+        rnd = 8 * u32 * (w * (np.abs(st.Y[g.a]) + np.abs(st.Y[g.b])) + np.abs(b_old) + np.abs(E) + gam)
+        Tt = w * (dy[g.a] + dy[g.b]) + Tb + rnd
+        bg = p.get("BS")
+        err_b = np.abs(bg - st.bs)
+        assert np.all(err_b <= Tt), (step, float(np.max(err_b / Tt)))
+        Tb = Tt
+        q = st.ds - st.bs  # Z - b'
+        C = g.r * sq * (st.P - st.B)
+        rhs_next = g.lam * (g.M.T @ q) + C
+        # 12 or fewer FP32 terms a row, each rounded, and C's FP32 rounding
+        rnd_r = 32 * u32 * (g.lam * (absM.T @ np.abs(q)) + np.abs(C))
+        Tr = g.lam * (absM.T @ (3 * Tt)) + rnd_r
+        err_r = np.abs(p.get("RHS") - rhs_next)
+        assert np.all(err_r <= Tr), (step, float(np.max(err_r / Tr)))
+        print(f"step {step}: relerr Y {relerr(Yg, st.Y):.2e} b {relerr(bg, st.bs):.2e} "
+              f"rhs {relerr(p.get('RHS'), rhs_next):.2e}; worst element / bound: b "
+              f"{np.max(err_b / Tt):.2f}, rhs {np.max(err_r / Tr):.2f}")
     p.close()
 
 
