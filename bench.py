@@ -443,7 +443,7 @@ def main():
         elif precond == "ic0":
             p.ic0()
         p.init(Y0d)
-        tuned[precision + "/" + precond] = p.autotune(10)  # kernel variants for this problem (setup)
+        tuned[precision + "/" + precond] = p.autotune(10) + p.get_variant("fsai")  # kernel variants (setup)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         for _ in range(warmup):
@@ -505,15 +505,18 @@ def main():
     n, d, nnz, ne = info["n"], info["d"], info["nnz_A"], info["n_edges"]
     fsai_k = {}
     fsai_arm = args.precond in ("learned", "classical")  # the FSAI kernels run (any factor G)
+    fsai_cols = tuned.get("mixed/" + args.precond, (0, {}, 0, None))[2]  # 1: columns computed from the stencil
     if fsai_arm:
-        # lower (upper) slots: FP32 G value + int32 column each, kb and G_ii per row;
-        # t = G r': r, q in, r', t out; z = G^T t with p_new = z + beta p: t
-        # and p in, p_new out, and every other iteration y += alpha_prev
-        # p_prev + alpha p: p_prev and y (hi, lo) in, y out
+        # lower (upper) slots: FP32 G value (+ int32 column unless computed
+        # from the stencil) each, G_ii per row; t = G r': r, q in, r', t out;
+        # z = G^T t with p_new = z + beta p: t and p in, p_new out, and every
+        # other iteration y += alpha_prev p_prev + alpha p: p_prev and y (hi,
+        # lo) in, y out
         tr_ms = p.time_kernel("fsai_tr", 20)
         zf_ms, zh_ms = p.time_kernel("fsai_zp", 20), p.time_kernel("fsai_zp_hold", 20)
-        tr_b = 4 * (nnz - n) + 8 * n + 16 * n * d
-        zh_b = 4 * (nnz - n) + 8 * n + 12 * n * d
+        slot_b = (2 if fsai_cols == 1 else 4) * (nnz - n)
+        tr_b = slot_b + 4 * n + 16 * n * d
+        zh_b = slot_b + 4 * n + 12 * n * d
         zf_b = zh_b + 20 * n * d
         fsai_k = {"k_fsai_tr_ms": round(tr_ms, 5), "k_fsai_tr_GBps": round(tr_b / (tr_ms * 1e-3) / 1e9, 1),
                   "k_fsai_zp_fold_ms": round(zf_ms, 5), "k_fsai_zp_fold_GBps": round(zf_b / (zf_ms * 1e-3) / 1e9, 1),
@@ -521,10 +524,11 @@ def main():
     # the SpMM variant the autotuner chose for this arm
     variant = tuned.get("mixed/" + args.precond, (0, {}))[0]
     kname = {0: "k_spmm", 1: "k_spmm_fixed", 2: "k_spmm_fixed", 3: "k_spmm_fixed", 4: "k_spmm_tma",
-             5: "k_spmm_stencil"}.get(variant, "k_spmm")
-    if variant == 5:
-        # stencil form: FP32 value of every nonzero (no column index, no row
-        # pointer), p in, q out: 4 nnz_A + 2 * 4 n d
+             5: "k_spmm_stencil", 6: "k_spmm_fixed (stencil columns)", 7: "k_spmm_fixed (stencil columns)"}.get(variant,
+                                                                                                           "k_spmm")
+    if variant in (5, 6, 7):
+        # stencil form and computed columns: FP32 value of every nonzero (no
+        # column index, no row pointer), p in, q out: 4 nnz_A + 2 * 4 n d
         spmm_bytes = 4 * nnz + 2 * 4 * n * d
     else:
         # FP32 values + int32 indices of A, p in, q out: 8 nnz_A + 4 (n + 1) + 2 * 4 n d
@@ -538,8 +542,9 @@ def main():
     # iteration (k_fsai_zp: folding and holding launches alternate)
     cands = [("%s<float,%d> (SpMM variant %d)" % (kname, d, variant), "spmm", spmm_ms, spmm_bytes)]
     if fsai_arm:
-        cands += [("k_fsai_tr<float,%d>" % d, "fsai_tr", tr_ms, tr_b),
-                  ("k_fsai_zp<float,%d> (folding and holding launches averaged)" % d, "fsai_zp",
+        cols = " (stencil columns)" if fsai_cols == 1 else ""
+        cands += [("k_fsai_tr<float,%d>%s" % (d, cols), "fsai_tr", tr_ms, tr_b),
+                  ("k_fsai_zp<float,%d>%s (folding and holding launches averaged)" % (d, cols), "fsai_zp",
                    0.5 * (zf_ms + zh_ms), 0.5 * (zf_b + zh_b))]
     elif args.precond == "jacobi":
         cands += [("k_update<float,%d>" % d, "update", upd_ms, upd_b),
@@ -551,7 +556,8 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1),
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                 "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": ncu_traffic(args.workload, dom_key, nnz, variant if dom_key == "spmm" else None),
+                "traffic": ncu_traffic(args.workload, dom_key, nnz,
+                                       variant if dom_key == "spmm" else (fsai_cols if fsai_arm else None)),
                 "algorithmic_bytes_per_launch": int(dom_bytes), "avg_launch_ms": round(dom_ms, 5),
                 "launches_in_timed_region": rounds,
                 "share_of_timed_region": round(rounds * dom_ms / ms, 4),
@@ -669,7 +675,11 @@ def main():
             "fp64": fp64,
             "speedup_vs_fp64": (fp64["sec_per_outer_iter"] / sec_per_outer) if fp64 else None,
             "roofline": roofline,
-            "autotune": {k: {"spmm_variant": v[0], "spmm_ms": {str(a): round(b, 5) for a, b in v[1].items()}}
+            "autotune": {k: {"spmm_variant": v[0], "spmm_ms": {str(a): round(b, 5) for a, b in v[1].items()},
+                             "fsai_columns": {0: "slots", 1: "stencil"}[v[2]] if v[3] is not None and v[3][0] > 0
+                             else None,
+                             "fsai_ms": [round(float(x), 5) for x in v[3]] if v[3] is not None and v[3][0] > 0
+                             else None}
                          for k, v in tuned.items()},
             "gpu_launches": launches,
             "clocks": clk,

@@ -208,14 +208,21 @@ PFE_API pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY
  * pfe_autotune -- choose the fastest variant of each tunable hot kernel for
  * this context (its graph, d and precision): every candidate is timed with
  * CUDA events over `reps` launches on the current iterate (scratch copies,
- * the iteration state is not modified) and the fastest is kept.  Tunable now:
- * the SpMM of the PCG iteration (variants below; the fixed-length ones apply
- * to FP32 grid graphs of radius 2 or 3, for a batch only PFE_SPMM_ROW1 at
- * radius 2).  choice[0] receives
- * the chosen SpMM variant and ms[v] (at least PFE_SPMM_NVARIANTS entries;
- * either may be NULL) each variant's average time, -1 where it does not
- * apply.  pfe_set_variant sets a choice directly (e.g. from a cache of
- * earlier tuning).  Needs pfe_init; synchronises.
+ * the iteration state is not modified) and the fastest is kept.  Tunable:
+ *  - the SpMM of the PCG iteration (PFE_TUNE_SPMM, variants below; the
+ *    fixed-length ones apply to FP32 grid graphs of radius 2 or 3, for a
+ *    batch only PFE_SPMM_ROW1 at radius 2);
+ *  - with an FSAI factor set (pfe_fsai_set, pfe_fsai_classical) on one FP32
+ *    grid image of radius 2 or 3: the column form of the FSAI kernels
+ *    (PFE_TUNE_FSAI), timed as one iteration's k_fsai_tr and k_fsai_zp.
+ * Every variant of a kernel adds the same products in the same order, so
+ * the choice changes the time, not the results.  choice[0] receives the
+ * chosen SpMM variant and ms[v] (at least PFE_SPMM_NVARIANTS entries; either
+ * may be NULL) each variant's average time, -1 where it does not apply;
+ * pfe_get_variant reads any kernel's current choice (and the FSAI timings).
+ * pfe_set_variant sets a choice directly (e.g. from a cache of earlier
+ * tuning): PFE_EUNSUPPORTED where it does not apply.  Needs pfe_init;
+ * synchronises.
  */
 enum {
     PFE_SPMM_GENERAL = 0, /* any layout: slots fetched 12 at a time, then gathered */
@@ -229,11 +236,22 @@ enum {
                              the rows' matrix values staged in shared memory by bulk asynchronous
                              (TMA) copies three rows ahead; the column array is not read and no
                              gather leaves the SM */
-    PFE_SPMM_NVARIANTS = 6
+    PFE_SPMM_GRID1 = 6,   /* one grid image: uniform rows whose neighbour columns are computed from
+                             the stencil (only the matrix values are read), one row group per step */
+    PFE_SPMM_GRID2 = 7,   /* the same, two row groups per step */
+    PFE_SPMM_NVARIANTS = 8
 };
-enum { PFE_TUNE_SPMM = 0 };
+enum { PFE_TUNE_SPMM = 0, PFE_TUNE_FSAI = 1 };
+enum {
+    PFE_FSAI_SLOTS = 0,   /* FSAI kernels read each slot's column */
+    PFE_FSAI_STENCIL = 1  /* one grid image: the columns are computed from the stencil */
+};
 PFE_API pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms);
 PFE_API pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant);
+/* pfe_get_variant -- the current choice for `kernel` (PFE_TUNE_SPMM or
+ * PFE_TUNE_FSAI); for PFE_TUNE_FSAI, ms (2 entries, may be NULL) receives the
+ * two column forms' times from the last pfe_autotune (-1 if not tuned). */
+PFE_API pfe_status pfe_get_variant(pfe_ctx *c, int32_t kernel, int32_t *variant, double *ms);
 
 /*
  * pfe_kmeans -- the segmentation stage of Sec. IV: k-means clustering of the

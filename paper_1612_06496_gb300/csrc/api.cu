@@ -542,7 +542,24 @@ static bool spmm_variant_applies(const pfe_ctx *c, int v) {
     if (v == PFE_SPMM_STENCIL &&
         (c->kind != PFE_GRAPH_GRID || c->W < 1 || c->W % 4 != 0 || stencil_strip(c->d, c->g.row_len, kStencilSteps) == 0))
         return false;
+    // computed columns: one grid image
+    if ((v == PFE_SPMM_GRID1 || v == PFE_SPMM_GRID2) && (c->kind != PFE_GRAPH_GRID || c->W < 1)) return false;
     return c->g.row_len == 12 || c->g.row_len == 28;
+}
+
+// The FSAI column forms that apply: slot columns always; columns computed
+// from the stencil on one FP32 grid image of 12 or 28 slots a row with the
+// (learned or classical) FSAI factor set.
+static bool fsai_variant_applies(const pfe_ctx *c, int v) {
+    if (v == PFE_FSAI_SLOTS) return true;
+    return v == PFE_FSAI_STENCIL && c->mixed && c->nseg == 1 && c->kind == PFE_GRAPH_GRID && c->W > 0 &&
+           (c->g.row_len == 12 || c->g.row_len == 28);
+}
+
+static void set_fsai_variant(pfe_ctx *c, int v) {
+    c->fsai_variant = v;
+    for (int slot : {G_FSAI_TR, G_FSAI_T, G_FSAI_T1, G_FSAI_ZP}) c->kgrid[slot] = 0;  // occupancy differs
+    free_pcg_graph(c);
 }
 
 pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms) {
@@ -567,11 +584,52 @@ pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms) {
     c->spmm_variant = best;
     free_pcg_graph(c);  // the captured loop holds the previous variant
     if (choice) choice[0] = best;
+    // the FSAI kernels' column form, when the FSAI factor is in use: the time
+    // of one iteration's k_fsai_tr and k_fsai_zp (folding and holding launches)
+    if (c->fsai.enabled && !c->fsai.ic && fsai_variant_applies(c, PFE_FSAI_STENCIL)) {
+        float tv[2] = {0.f, 0.f};
+        for (int v = 0; v < 2; ++v) {
+            set_fsai_variant(c, v);
+            for (int which : {3, 4, 5}) {
+                float t = 0.f;
+                PFE_TRY(time_pcg_kernel(c, c->stream, which, reps, &t));
+                tv[v] += which == 3 ? t : 0.5f * t;
+            }
+        }
+        set_fsai_variant(c, tv[1] < tv[0] ? PFE_FSAI_STENCIL : PFE_FSAI_SLOTS);
+        c->fsai_tune_ms[0] = tv[0];
+        c->fsai_tune_ms[1] = tv[1];
+    }
+    return PFE_OK;
+}
+
+pfe_status pfe_get_variant(pfe_ctx *c, int32_t kernel, int32_t *variant, double *ms) {
+    if (!c || !variant) return PFE_EINVAL;
+    if (kernel == PFE_TUNE_SPMM) {
+        *variant = c->spmm_variant;
+    } else if (kernel == PFE_TUNE_FSAI) {
+        *variant = c->fsai_variant;
+        if (ms) {
+            ms[0] = c->fsai_tune_ms[0];
+            ms[1] = c->fsai_tune_ms[1];
+        }
+    } else {
+        return PFE_EINVAL;
+    }
     return PFE_OK;
 }
 
 pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant) {
-    if (!c || kernel != PFE_TUNE_SPMM || variant < 0 || variant >= PFE_SPMM_NVARIANTS) return PFE_EINVAL;
+    if (!c) return PFE_EINVAL;
+    if (kernel == PFE_TUNE_FSAI) {
+        if (variant < 0 || variant > PFE_FSAI_STENCIL) return PFE_EINVAL;
+        if (!fsai_variant_applies(c, variant))
+            return fail(c, PFE_EUNSUPPORTED, "FSAI column form does not apply here");
+        PFE_TRY(sync(c));
+        set_fsai_variant(c, variant);
+        return PFE_OK;
+    }
+    if (kernel != PFE_TUNE_SPMM || variant < 0 || variant >= PFE_SPMM_NVARIANTS) return PFE_EINVAL;
     if (!spmm_variant_applies(c, variant)) return fail(c, PFE_EUNSUPPORTED, "SpMM variant does not apply here");
     PFE_TRY(sync(c));
     c->spmm_variant = variant;

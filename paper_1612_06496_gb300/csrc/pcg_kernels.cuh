@@ -241,6 +241,77 @@ __device__ __forceinline__ void load_slot_range(const int *__restrict__ col, con
     }
 }
 
+// Values of slots [P0, P1) of a fixed-length row, as load_slot_range without
+// the columns.
+template <typename T, int P0, int P1, int K = P0>
+__device__ __forceinline__ void load_val_range(const T *__restrict__ val, int64_t base, T (&av)[P1 - P0]) {
+    static_assert(sizeof(T) == 4, "4-byte slot values");
+    if constexpr (K < P1) {
+        constexpr int W = (K % 4 == 0 && K + 4 <= P1) ? 4 : (K % 2 == 0 && K + 2 <= P1) ? 2 : 1;
+        constexpr int u = K - P0;
+        if constexpr (W == 4) {
+            const float4 vv = __ldg(reinterpret_cast<const float4 *>(val + base + K));
+            av[u] = vv.x; av[u + 1] = vv.y; av[u + 2] = vv.z; av[u + 3] = vv.w;
+        } else if constexpr (W == 2) {
+            const float2 vv = __ldg(reinterpret_cast<const float2 *>(val + base + K));
+            av[u] = vv.x; av[u + 1] = vv.y;
+        } else {
+            av[u] = __ldg(val + base + K);
+        }
+        load_val_range<T, P0, P1, K + W>(val, base, av);
+    }
+}
+
+// The stencil of the fixed-position rows of a grid graph: slot t of every
+// row is the pixel offset (dy_t, dx_t), the offsets with 0 < dx^2 + dy^2 <=
+// R^2 in (dy, dx) order -- the order the graph builder gives the slots.  12
+// slots are the radius-2 stencil and 28 the radius-3 one (no other radius
+// has these counts); the first LEN / 2 point backwards (lower neighbours).
+template <int LEN>
+struct StencilSlots {
+    static_assert(LEN == 12 || LEN == 28, "fixed rows of 12 or 28 slots");
+    static constexpr int R = LEN == 12 ? 2 : 3;
+    static constexpr int off(int t, bool want_dy) {
+        int k = 0;
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx)
+                if (dx * dx + dy * dy > 0 && dx * dx + dy * dy <= R * R) {
+                    if (k == t) return want_dy ? dy : dx;
+                    ++k;
+                }
+        return 0;
+    }
+    static constexpr int count() {
+        int k = 0;
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx) k += (dx * dx + dy * dy > 0 && dx * dx + dy * dy <= R * R) ? 1 : 0;
+        return k;
+    }
+    static_assert(count() == LEN, "stencil size");
+};
+
+// Column of slot T of row i of a one-image grid graph of width w and n
+// pixels, computed from the stencil instead of loaded: i + dy_T w + dx_T,
+// clamped into [0, n).  A slot whose neighbour is off the image has value 0
+// (padding), so any row serves there; clamping only keeps the address valid
+// (a backward slot can only fall below row 0, a forward one past row n - 1).
+template <int LEN, int T>
+__device__ __forceinline__ int stencil_col(int i, int w, int n) {
+    constexpr int dy = StencilSlots<LEN>::off(T, true), dx = StencilSlots<LEN>::off(T, false);
+    const int j = i + dy * w + dx;
+    if constexpr (T < LEN / 2)
+        return max(j, 0);
+    else
+        return min(j, n - 1);
+}
+template <int LEN, int P0, int K = P0, int N>
+__device__ __forceinline__ void stencil_cols(int i, int w, int n, int (&jj)[N]) {
+    if constexpr (K < P0 + N) {
+        jj[K - P0] = stencil_col<LEN, K>(i, w, n);
+        stencil_cols<LEN, P0, K + 1>(i, w, n, jj);
+    }
+}
+
 // ---- reductions -------------------------------------------------------------
 
 template <typename A, typename AT>
@@ -992,8 +1063,10 @@ __global__ void __launch_bounds__(kBlock) k_spmm(PcgArgs<T> a) {
 
 // k_spmm for graphs whose rows all have LEN slots (grid stencils; LEN a
 // compile-time constant): the slot loads of ROWS row groups are issued
-// together, then their gathers; at least MINB blocks per SM.
-template <typename T, int D, bool MS, int LEN, int ROWS, int MINB>
+// together, then their gathers; at least MINB blocks per SM.  GRID (one grid
+// image): only the slot values are loaded, the columns are computed from the
+// stencil (the same products in the same order).
+template <typename T, int D, bool MS, int LEN, int ROWS, int MINB, bool GRID = false>
 __global__ void __launch_bounds__(kBlock, MINB) k_spmm_fixed(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
@@ -1022,7 +1095,13 @@ __global__ void __launch_bounds__(kBlock, MINB) k_spmm_fixed(PcgArgs<T> a) {
             ii[h] = bsg.r0 + (g + h * warps_total) * SW::RPW + lm.r;
             ok[h] = lm.active && ii[h] < bsg.r1;
             const int64_t base = (ok[h] ? ii[h] : bsg.r0) * LEN;  // a valid row when idle
-            load_slots<T, LEN>(a.A.col, a.A.aoff, base, 0, LEN, (int)ii[h], jj[h], av[h]);
+            if constexpr (GRID) {
+                static_assert(!MS, "computed columns: one image");
+                load_val_range<T, 0, LEN>(a.A.aoff, base, av[h]);
+                stencil_cols<LEN, 0>((int)(ok[h] ? ii[h] : bsg.r0), a.grid_w, (int)a.A.n, jj[h]);
+            } else {
+                load_slots<T, LEN>(a.A.col, a.A.aoff, base, 0, LEN, (int)ii[h], jj[h], av[h]);
+            }
         }
 #pragma unroll
         for (int h = 0; h < ROWS; ++h) {
@@ -1436,6 +1515,20 @@ bool launch_spmm_fixed(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int v) {
             constexpr int MB = SubWarp<T, D>::V * (int)sizeof(T) >= 16 ? 4 : 6;  // 40 registers up to 2 columns a lane
             k_spmm_tma<T, D, LEN, S, MB><<<wave_grid(c, G_SPMM_TMA, k_spmm_tma<T, D, LEN, S, MB>, ntiles, 1, P::SMEM),
                                            kBlock, P::SMEM, s>>>(a);
+            return true;
+        }
+    }
+    if constexpr (!MS) {
+        if (v == PFE_SPMM_GRID1 && a.grid_w > 0) {
+            k_spmm_fixed<T, D, MS, LEN, 1, 6, true><<<wave_grid(c, G_SPMM_G1, k_spmm_fixed<T, D, MS, LEN, 1, 6, true>,
+                                                                rows_need<T, D>(c)),
+                                                      kBlock, 0, s>>>(a);
+            return true;
+        }
+        if (v == PFE_SPMM_GRID2 && a.grid_w > 0) {
+            k_spmm_fixed<T, D, MS, LEN, 2, 5, true><<<wave_grid(c, G_SPMM_G2, k_spmm_fixed<T, D, MS, LEN, 2, 5, true>,
+                                                                rows_need<T, D>(c)),
+                                                      kBlock, 0, s>>>(a);
             return true;
         }
     }
@@ -1862,13 +1955,44 @@ __device__ __forceinline__ void gslot_fixed(const int *__restrict__ col, const T
         for (int k = 0; k < V; ++k) acc[k] = fma(gv[u], vj[u][k], acc[k]);
 }
 
+// gslot_fixed on a one-image grid graph with the columns computed from the
+// stencil (stencil_col) instead of loaded: the same products in the same
+// order, 4 bytes a slot less traffic.
+template <typename T, int D, int V, int P0, int P1, int LEN, bool QS>
+__device__ __forceinline__ void gslot_grid(const T *__restrict__ gs, int64_t i, int w, int n, int c0,
+                                           const T *__restrict__ src, const T *__restrict__ qsrc, const T (&al)[V],
+                                           T (&acc)[V]) {
+    constexpr int NS = P1 - P0;
+    T gv[NS];
+    load_val_range<T, P0, P1>(gs, i * LEN, gv);
+    int jj[NS];
+    stencil_cols<LEN, P0>((int)i, w, n, jj);
+    T vj[NS][V];
+#pragma unroll
+    for (int u = 0; u < NS; ++u) ldv<T, V>(src + (int64_t)jj[u] * D + c0, vj[u]);
+    if constexpr (QS) {
+        T qj[NS][V];
+#pragma unroll
+        for (int u = 0; u < NS; ++u) ldv<T, V>(qsrc + (int64_t)jj[u] * D + c0, qj[u]);
+#pragma unroll
+        for (int u = 0; u < NS; ++u)
+#pragma unroll
+            for (int k = 0; k < V; ++k) vj[u][k] = fma(-al[k], qj[u][k], vj[u][k]);
+    }
+#pragma unroll
+    for (int u = 0; u < NS; ++u)
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[k] = fma(gv[u], vj[u][k], acc[k]);
+}
+
 // r' = r - alpha q and t = G r' in one pass: r' is recomputed at each
 // gathered lower neighbour from the old r and q (the same FMA its owner
 // uses), the owner writes its r' to the other buffer; then the dots t.t
 // (= r'.z') and r'.r' and the end of the iteration.  On refresh iterations
 // it does nothing (k_refresh_f and k_fsai_t<1> make r and t).
-// LEN > 0: uniform rows of LEN slots, lower slots at positions [0, LEN/2).
-template <typename T, int D, int LEN>
+// LEN > 0: uniform rows of LEN slots, lower slots at positions [0, LEN/2);
+// GRID: one grid image, the slot columns computed from the stencil.
+template <typename T, int D, int LEN, bool GRID>
 __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
@@ -1899,7 +2023,9 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr
         const T gd = a.gdiag[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = gd * ri[k];
-        if constexpr (LEN > 0)
+        if constexpr (GRID)
+            gslot_grid<T, D, V, 0, LEN / 2, LEN, true>(a.gslot, i, a.grid_w, (int)a.A.n, c0, rold, a.q, al, acc);
+        else if constexpr (LEN > 0)
             gslot_fixed<T, D, V, 0, LEN / 2, true>(a.A.col, a.gslot, i * LEN, c0, rold, a.q, al, acc);
         else
             gslot_range<T, D, V, true>(a.A.col, a.gslot, base, len, 0, a.kb[i], (int)i, c0, rold, a.q, al, acc);
@@ -1921,7 +2047,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr
 // the dots t.t (= r.z) and r.r.  MODE 0: the start of a solve (residual in
 // r2[0]); MODE 1: only after a residual refresh (residual in the new buffer),
 // ending the iteration.
-template <typename T, int D, int MODE, int LEN>
+template <typename T, int D, int MODE, int LEN, bool GRID>
 __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
     if (MODE == 1 && !*(volatile int *)&a.ctl->refresh_now) return;
@@ -1940,7 +2066,9 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(
         const T gd = a.gdiag[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = gd * ri[k];
-        if constexpr (LEN > 0)
+        if constexpr (GRID)
+            gslot_grid<T, D, V, 0, LEN / 2, LEN, false>(a.gslot, i, a.grid_w, (int)a.A.n, c0, rsrc, nullptr, nal, acc);
+        else if constexpr (LEN > 0)
             gslot_fixed<T, D, V, 0, LEN / 2, false>(a.A.col, a.gslot, i * LEN, c0, rsrc, nullptr, nal, acc);
         else
             gslot_range<T, D, V, false>(a.A.col, a.gslot, base, len, 0, a.kb[i], (int)i, c0, rsrc, nullptr, nal,
@@ -1966,7 +2094,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(
 // old content of the buffer p_new goes to); each thread reads and writes only
 // its row's own entries; z is never stored.  Block 0 also decides whether the
 // next iteration refreshes the residual.
-template <typename T, int D, int LEN>
+template <typename T, int D, int LEN, bool GRID>
 __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())) k_fsai_zp(PcgArgs<T> a) {
     PcgCtl *ctl = a.ctl;
     if (*(volatile int *)&ctl->done) return;
@@ -1999,7 +2127,9 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())
         const T gd = a.gdiag[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = gd * ti[k];
-        if constexpr (LEN > 0)
+        if constexpr (GRID)
+            gslot_grid<T, D, V, LEN / 2, LEN, LEN, false>(a.gslot, i, a.grid_w, (int)a.A.n, c0, a.t, nullptr, nal, acc);
+        else if constexpr (LEN > 0)
             gslot_fixed<T, D, V, LEN / 2, LEN, false>(a.A.col, a.gslot, i * LEN, c0, a.t, nullptr, nal, acc);
         else
             gslot_range<T, D, V, false>(a.A.col, a.gslot, base, len, a.kb[i], len, (int)i, c0, a.t, nullptr, nal,
@@ -2382,26 +2512,40 @@ pfe_status body_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, const PcgLau
 // The FSAI kernels with the compile-time row length of the layout (FP32 grid
 // graphs of radius 2 or 3; else the general kernels).
 // which: 0 = k_fsai_tr, 1 = k_fsai_t (start of a solve), 2 = k_fsai_t (after a refresh), 3 = k_fsai_zp
-template <typename T, int D, int LEN>
+template <typename T, int D, int LEN, bool GRID>
 void fsai_kernels_len(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int which) {
     if (which == 0)
-        k_fsai_tr<T, D, LEN><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D, LEN>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        k_fsai_tr<T, D, LEN, GRID><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D, LEN, GRID>, rows_need<T, D>(c)), kBlock, 0,
+                                     s>>>(a);
     else if (which == 1)
-        k_fsai_t<T, D, 0, LEN><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D, 0, LEN>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        k_fsai_t<T, D, 0, LEN, GRID><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D, 0, LEN, GRID>, rows_need<T, D>(c)), kBlock,
+                                       0, s>>>(a);
     else if (which == 2)
-        k_fsai_t<T, D, 1, LEN><<<wave_grid(c, G_FSAI_T1, k_fsai_t<T, D, 1, LEN>, rows_need<T, D>(c)), kBlock, 0, s>>>(
-            a);
+        k_fsai_t<T, D, 1, LEN, GRID><<<wave_grid(c, G_FSAI_T1, k_fsai_t<T, D, 1, LEN, GRID>, rows_need<T, D>(c)),
+                                       kBlock, 0, s>>>(a);
     else
-        k_fsai_zp<T, D, LEN><<<wave_grid(c, G_FSAI_ZP, k_fsai_zp<T, D, LEN>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        k_fsai_zp<T, D, LEN, GRID><<<wave_grid(c, G_FSAI_ZP, k_fsai_zp<T, D, LEN, GRID>, rows_need<T, D>(c)), kBlock, 0,
+                                     s>>>(a);
 }
+// The FSAI kernels on fixed-length rows (12 or 28 slots): slot columns loaded
+// (PFE_FSAI_SLOTS) or, on one grid image, computed from the stencil
+// (PFE_FSAI_STENCIL; the context's choice, made by pfe_autotune).
 template <typename T, int D>
 void launch_fsai(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int which) {
-    if (c->g.row_len == 12)
-        fsai_kernels_len<T, D, 12>(c, s, a, which);
-    else if (c->g.row_len == 28)
-        fsai_kernels_len<T, D, 28>(c, s, a, which);
-    else
-        fsai_kernels_len<T, D, 0>(c, s, a, which);
+    const bool grid = c->fsai_variant == PFE_FSAI_STENCIL && a.grid_w > 0;
+    if (c->g.row_len == 12) {
+        if (grid)
+            fsai_kernels_len<T, D, 12, true>(c, s, a, which);
+        else
+            fsai_kernels_len<T, D, 12, false>(c, s, a, which);
+    } else if (c->g.row_len == 28) {
+        if (grid)
+            fsai_kernels_len<T, D, 28, true>(c, s, a, which);
+        else
+            fsai_kernels_len<T, D, 28, false>(c, s, a, which);
+    } else {
+        fsai_kernels_len<T, D, 0, false>(c, s, a, which);
+    }
 }
 
 // The IC(0) triangular solves: one launch per level of the raster wavefront

@@ -29,8 +29,9 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
            "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_ic0", "pfe_get_segments",
            "pfe_get_segment_stats", "pfe_laplacian_eigenmap", "pfe_objective", "pfe_autotune",
-           "pfe_set_variant", "pfe_solve_two_stage", "pfe_kmeans", "pfe_residual"]
-SPMM_NVARIANTS = 6  # PFE_SPMM_GENERAL, _ROW1, _ROW2, _ROW2_4, _TMA, _STENCIL
+           "pfe_set_variant", "pfe_solve_two_stage", "pfe_kmeans", "pfe_residual", "pfe_get_variant"]
+SPMM_NVARIANTS = 8  # PFE_SPMM_GENERAL, _ROW1, _ROW2, _ROW2_4, _TMA, _STENCIL, _GRID1, _GRID2
+TUNE = {"spmm": 0, "fsai": 1}
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3, "fsai_tr": 4, "fsai_zp": 5, "fsai_zp_hold": 6,
           "pupdate_hold": 7}
 
@@ -113,6 +114,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_solve_two_stage.argtypes = [vp, i32, i32, i32, vp, vp, C.POINTER(SolveStats)]
     lib.pfe_kmeans.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp, C.POINTER(dbl), C.POINTER(i32)]
     lib.pfe_residual.argtypes = [vp, vp, vp, vp]
+    lib.pfe_get_variant.argtypes = [vp, i32, C.POINTER(i32), vp]
     for name in EXPORTS:
         if name not in ("pfe_default_params", "pfe_last_error", "pfe_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -284,8 +286,17 @@ class PFE:
         self._check(self.lib.pfe_autotune(self.ctx, int(reps), choice.ctypes.data, ms.ctypes.data), "pfe_autotune")
         return int(choice[0]), {v: float(t) for v, t in enumerate(ms) if t >= 0}
 
-    def set_variant(self, variant: int, kernel: int = 0):
+    def set_variant(self, variant: int, kernel: int | str = 0):
+        kernel = TUNE.get(kernel, kernel) if isinstance(kernel, str) else kernel
         self._check(self.lib.pfe_set_variant(self.ctx, int(kernel), int(variant)), "pfe_set_variant")
+
+    def get_variant(self, kernel: int | str = 0):
+        """(current variant, timings of the FSAI column forms from the last autotune or None)."""
+        kernel = TUNE.get(kernel, kernel) if isinstance(kernel, str) else kernel
+        v = C.c_int32()
+        ms = np.full(2, -1.0)
+        self._check(self.lib.pfe_get_variant(self.ctx, int(kernel), C.byref(v), ms.ctypes.data), "pfe_get_variant")
+        return v.value, (None if kernel == 0 else ms)
 
     def kmeans(self, k: int, X=None, C0=None, max_iter: int = 100):
         """k-means segmentation of X (n x d) or of the embedding: (labels,

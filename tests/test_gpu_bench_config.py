@@ -53,14 +53,18 @@ def _learned(spec, variant=None, tune=False):
 
 
 @pytest.mark.parametrize("crop_idx", [0, 1, 2, 3])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, "tuned"])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, "tuned", "stencil-fsai"])
 def test_c5_crops_learned_fsai_parity(crop_idx, variant):
     """Seeded 64x64 windows of the 2048x2048 image, d = 10, radius 2, the
-    learned factor, each SpMM variant forced (and the autotuner's pick)."""
+    learned factor, each SpMM variant forced, the autotuner's picks, and the
+    FSAI kernels with the columns computed from the stencil."""
     spec = _crop(crop_idx)
     assert spec.d == 10 and spec.radius == 2.0 and spec.tol == 1e-6
     g, ost, Yh_o = _oracle_crop(crop_idx)
-    p, Y0 = _learned(spec, None if variant == "tuned" else variant, tune=variant == "tuned")
+    forced = variant if isinstance(variant, int) else (7 if variant == "stencil-fsai" else None)
+    p, Y0 = _learned(spec, forced, tune=variant == "tuned")
+    if variant == "stencil-fsai":
+        p.set_variant(1, "fsai")
     Y = np.empty((spec.n, spec.d))
     Yhat = np.empty((spec.n, spec.d))
     st = p.solve(N_OUTER, N_INNER, Y, Yhat)
@@ -73,19 +77,19 @@ def test_c5_crops_learned_fsai_parity(crop_idx, variant):
 
 def test_c5_crop_learned_fsai_fixed_variants_bitwise():
     """The SpMM variants on fixed-length rows that take one row group per
-    step (the slot-loading kernel, its TMA-tile form and the stencil form)
-    add the same products in the same order: the learned-FSAI solves agree
-    bit for bit at d = 10."""
+    step (the slot-loading kernel, its TMA-tile form, the stencil form and
+    the computed-column form) add the same products in the same order: the
+    learned-FSAI solves agree bit for bit at d = 10."""
     spec = _crop(1)
     out = []
-    for variant in (1, 4, 5):
+    for variant in (1, 4, 5, 6):
         p, Y0 = _learned(spec, variant)
         Y = np.empty((spec.n, spec.d))
         p.solve(N_OUTER, N_INNER, Y, None)
         out.append(Y)
         p.close()
-    np.testing.assert_array_equal(out[0], out[1])
-    np.testing.assert_array_equal(out[0], out[2])
+    for k in range(1, len(out)):
+        np.testing.assert_array_equal(out[0], out[k])
 
 
 def test_c2_learned_fsai_matches_oracle():

@@ -10,7 +10,7 @@ from tests.gpu_common import gpu_problem, oracle_graph, relerr, small_spec
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_spmm_variants_match_oracle(variant):
     spec = CONFIGS["C1"]  # radius 2: 12 slots per row, the fixed-length kernels apply
     p, X, Y0 = gpu_problem(spec, "mixed")
@@ -29,7 +29,7 @@ def test_autotune_chooses_an_applicable_variant():
     p, X, Y0 = gpu_problem(spec, "mixed")
     p.init(Y0)
     choice, ms = p.autotune(5)
-    assert set(ms) == {0, 1, 2, 3, 4, 5} and all(t > 0 for t in ms.values())
+    assert set(ms) == {0, 1, 2, 3, 4, 5, 6, 7} and all(t > 0 for t in ms.values())
     assert ms[choice] == min(ms.values())
     st = p.solve(1, 2)
     assert st["n_unconverged"] == 0
@@ -43,26 +43,78 @@ def test_autotune_chooses_an_applicable_variant():
 
 
 @pytest.mark.parametrize("H,W,d,radius", [(23, 20, 3, 2.0), (29, 32, 4, 3.0), (64, 64, 10, 2.0), (7, 132, 10, 3.0),
-                                          (41, 100, 10, 2.0)])
+                                          (41, 100, 10, 2.0), (40, 3, 5, 3.0), (2, 50, 3, 2.0)])
 def test_stencil_spmm_equals_fixed_spmm_bitwise(H, W, d, radius):
     """The stencil-form SpMM (a ring of row bands of p and the rows' matrix
-    values staged by bulk copies; no column array) adds the same products in
-    the same order as the fixed-length kernel: whole solves agree bit for
-    bit (odd d: a left pad for 16-byte alignment; d = 4: four columns a
-    lane; a 7-row image: bands clipped at both ends; W = 100: a narrower
-    last strip)."""
+    values staged by bulk copies; no column array) and the fixed-length
+    kernels with the columns computed from the stencil add the same products
+    in the same order as the fixed-length kernels that read the columns:
+    whole solves agree bit for bit (odd d: a left pad for 16-byte alignment;
+    d = 4: four columns a lane; a 7-row image: bands clipped at both ends;
+    W = 100: a narrower last strip; W = 3 at radius 3 and a 2-row image:
+    stencil offsets that leave the image on both sides)."""
     spec = small_spec(H=H, W=W, d=d, radius=radius)
-    out = []
-    for variant in (1, 5):
+    out = {}
+    for variant in (1, 5, 6, 2, 7):
+        if variant == 5 and W % 4 != 0:  # the stencil form needs 16-byte aligned image rows
+            continue
         p, X, Y0 = gpu_problem(spec, "mixed")
         p.init(Y0)
         p.set_variant(variant)
         Y = np.empty_like(Y0)
         st = p.solve(2, 3, Y, None)
         assert st["n_unconverged"] == 0
+        out[variant] = Y
+        p.close()
+    for v in (5, 6):
+        if v in out:
+            np.testing.assert_array_equal(out[1], out[v])
+    np.testing.assert_array_equal(out[2], out[7])
+
+
+@pytest.mark.parametrize("H,W,d,radius", [(64, 64, 10, 2.0), (40, 3, 5, 3.0), (33, 47, 8, 3.0), (2, 50, 3, 2.0)])
+def test_fsai_stencil_columns_equal_slot_columns_bitwise(H, W, d, radius):
+    """The FSAI kernels with the columns computed from the stencil add the
+    same products in the same order as with the slot columns: learned-FSAI
+    solves agree bit for bit (images narrower and shorter than the stencil
+    included)."""
+    from paper_1612_06496_gb300.learned import load_weights
+    spec = small_spec(H=H, W=W, d=d, radius=radius)
+    out = []
+    for v in (0, 1):
+        p, X, Y0 = gpu_problem(spec, "mixed")
+        p.fsai_set(load_weights())
+        p.init(Y0)
+        p.set_variant(v, "fsai")
+        assert p.get_variant("fsai")[0] == v
+        Y = np.empty_like(Y0)
+        st = p.solve(2, 3, Y, None)
+        assert st["n_unconverged"] == 0
         out.append(Y)
         p.close()
     np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_autotune_picks_the_fsai_column_form():
+    """With the learned factor on one grid image the autotuner times both
+    column forms of the FSAI kernels and keeps the faster; on a batch only
+    the slot columns apply."""
+    from paper_1612_06496_gb300 import PFEError
+    from paper_1612_06496_gb300.learned import load_weights
+    spec = small_spec(H=48, W=52, d=10)
+    p, X, Y0 = gpu_problem(spec, "mixed")
+    p.fsai_set(load_weights())
+    p.init(Y0)
+    p.autotune(5)
+    v, ms = p.get_variant("fsai")
+    assert v in (0, 1) and np.all(ms > 0) and ms[v] == ms.min()
+    p.close()
+    q, _, Y0 = gpu_problem(spec, "fp64")
+    q.init(Y0)
+    with pytest.raises(PFEError) as ei:
+        q.set_variant(1, "fsai")
+    assert ei.value.status == 8
+    q.close()
 
 
 def test_stencil_spmm_needs_aligned_rows():
