@@ -416,8 +416,6 @@ def main():
         spec = spec0
     if args.n_inner:
         spec = replace(spec, n_inner=args.n_inner)
-    if batch and args.precond == "learned":
-        args.precond, args.no_alt = "jacobi", True  # the FSAI preconditioner is built for one problem
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -668,6 +666,8 @@ def main():
             "pcg_iters_mean": iters_total / max(n_solves, 1),
             "pcg_iters_max": max(s["pcg_iters_max"] for s in stats),
             "pcg_relres_max": max(s["relres_max"] for s in stats),
+            "pcg_replacements_per_solve": sum(s["replacements"] for s in stats) / max(n_solves, 1)
+                                          * (len(stats[0].get("seg_iters", [])) or 1),
             "true_relres_fp64_max": true_relres,
             "gnnz_rhs_per_s": nnz_iters * d / (ms / 1e3) / 1e9,
             "setup_s": setup_s, "lambda": info["lambda_"], "r": info["r"],

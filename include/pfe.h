@@ -488,7 +488,9 @@ PFE_API pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, doub
 PFE_API int32_t pfe_fsai_param_count(void);
 
 /* Evaluates the network on every pattern entry (G is built once per graph)
- * and makes later PCG solves use G^T G.  params == NULL switches back to
+ * and makes later PCG solves use G^T G.  On a batch every problem's entries
+ * read its own lambda (G is block diagonal like A) and every problem keeps
+ * its own PCG scalars and convergence.  params == NULL switches back to
  * Jacobi.  PFE_EUNSUPPORTED on an FP64 context.  Synchronises. */
 PFE_API pfe_status pfe_fsai_set(pfe_ctx *c, const float *params);
 
@@ -518,7 +520,8 @@ PFE_API pfe_status pfe_ic0(pfe_ctx *c);
  *   *loss = log(tr(G A G^T) / n) - (2/n) sum_i log G_ii,
  * and its gradient with respect to params (written to grad when non-NULL,
  * host or device).  Does not change which preconditioner the PCG uses, but
- * G is recomputed from params.  Synchronises. */
+ * G is recomputed from params.  One problem per context (PFE_EUNSUPPORTED
+ * on a batch).  Synchronises. */
 PFE_API pfe_status pfe_fsai_loss_grad(pfe_ctx *c, const float *params, float *grad, double *loss);
 
 /* The current G as FP64: gdiag[i] = G_ii (n values), gedge[k] = G_{b_k a_k}
@@ -539,12 +542,12 @@ PFE_API pfe_status pfe_adam_update(float *params, const float *grad, float *m, f
  * device memory allocated at all.  (There is no counterpart in the paper:
  * this entry point exists for callers, not for the method.)
  *
- * Who needs it: code that cannot call cudaMalloc -- a routine running while
- * its stream is being captured into a CUDA graph (allocation is illegal
- * there), a plug-in inside a host application that owns every device
- * allocation through its own memory pool, or a service that sizes device
- * memory once at start-up and must not grow it later.  Every other libpfe
- * entry point allocates its buffers itself.
+ * Who needs it: code that cannot call cudaMalloc -- a plug-in inside a host
+ * application that owns every device allocation through its own memory pool
+ * (a stray cudaMalloc would bypass the pool's accounting or fail against its
+ * reservation), or a service that sizes device memory once at start-up and
+ * must not grow it later.  Every other libpfe entry point allocates its
+ * buffers itself.
  *
  * Y (n x d) and deg (n, every d_i > 0) are FP64 device arrays the caller
  * owns; Yhat (n x d, FP64 device, may not alias Y) receives the result,
@@ -555,13 +558,17 @@ PFE_API pfe_status pfe_adam_update(float *params, const float *grad, float *m, f
  * pointers or NULL give PFE_EINVAL before any work is queued.
  *
  * All calls on a device share that array and it keeps the last call's
- * contents (the call resets what must start at zero), so calls that
- * overlap on the GPU -- two streams at once, or two threads -- race and
- * must be serialised by the caller.  The first call on each device looks
- * up the array's device address once (with that device current); make that
- * first call before any stream capture.  The call queues its work on
+ * contents (each call clears the ticket and error word it starts from and
+ * rewrites the rest before reading it), so calls that overlap on the GPU --
+ * two streams at once, or two threads -- race and must be serialised by the
+ * caller.  The first call on each device looks up the array's device
+ * address once (with that device current) and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not call
+ * the entry point again on a device after cudaDeviceReset (the kept address
+ * belongs to the context that was reset).  The call queues its work on
  * `stream` and synchronises it to report PFE_ESINGULAR when D^{1/2} Y is
- * numerically rank deficient.  It calls no allocating routine.
+ * numerically rank deficient (Yhat is then left as it was).  It calls no
+ * allocating routine.
  */
 PFE_API pfe_status pfe_orthonormalize_noalloc(const double *Y, const double *deg, int64_t n, int32_t d,
                                               double *Yhat, pfe_stream_t stream);

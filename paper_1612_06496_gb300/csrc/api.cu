@@ -1174,7 +1174,6 @@ int32_t pfe_fsai_param_count(void) { return kNParam; }
 pfe_status pfe_fsai_set(pfe_ctx *c, const float *params) {
     if (!c) return PFE_EINVAL;
     NvtxRange r("pfe learned FSAI set-up");
-    if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner is built for one problem, not a batch");
     PFE_TRY(sync(c));
     if (!params) {
         c->fsai.enabled = false;
@@ -1194,7 +1193,6 @@ pfe_status pfe_fsai_set(pfe_ctx *c, const float *params) {
 pfe_status pfe_fsai_classical(pfe_ctx *c) {
     if (!c) return PFE_EINVAL;
     NvtxRange r("pfe classical FSAI set-up");
-    if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner is built for one problem, not a batch");
     if (!c->mixed) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner runs on the mixed-precision path");
     PFE_TRY(sync(c));
     PFE_TRY(fsai_alloc(c));
@@ -1223,7 +1221,7 @@ pfe_status pfe_ic0(pfe_ctx *c) {
 
 pfe_status pfe_fsai_loss_grad(pfe_ctx *c, const float *params, float *grad, double *loss) {
     if (!c || !params || !loss) return PFE_EINVAL;
-    if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "the FSAI preconditioner is built for one problem, not a batch");
+    if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "the training loss is built for one problem, not a batch");
     PFE_TRY(fsai_alloc(c));
     PFE_CUDA_TRY(c, cudaMemcpyAsync(c->fsai.params, params, kNParam * sizeof(float), cudaMemcpyDefault, c->stream));
     PFE_TRY(fsai_loss_grad(c, loss));

@@ -387,7 +387,7 @@ inline Segs seg_view(const pfe_ctx *c) { return Segs{c->nseg, c->g.n, c->seg_off
 // arrays carved from a base pointer (doubles first, then ints).
 inline size_t segscal_bytes(int nseg, int d) {
     return sizeof(double) * 9 * (size_t)nseg * d + sizeof(long long) * (size_t)nseg +
-           sizeof(int) * (2 * (size_t)nseg * d + 2 * (size_t)nseg) + sizeof(unsigned) * 4 * (size_t)nseg;
+           sizeof(int) * (2 * (size_t)nseg * d + 3 * (size_t)nseg) + sizeof(unsigned) * 4 * (size_t)nseg;
 }
 inline SegScal segscal_carve(void *base, int nseg, int d) {
     SegScal sc;
@@ -408,7 +408,8 @@ inline SegScal segscal_carve(void *base, int nseg, int d) {
     sc.pending = ip + nd;
     sc.seg_active = ip + 2 * nd;
     sc.seg_iters = ip + 2 * nd + nseg;
-    sc.ticket = reinterpret_cast<unsigned *>(ip + 2 * nd + 2 * nseg);
+    sc.seg_live = ip + 2 * nd + 2 * nseg;
+    sc.ticket = reinterpret_cast<unsigned *>(ip + 2 * nd + 3 * nseg);
     return sc;
 }
 

@@ -39,6 +39,12 @@ struct View {
     const int *ea, *eb, *ext_slot;
     const double *ew, *deg, *adiag, *w64;
     double lam, r;
+    // a batch of problems: lambda of each problem, the problem of each row
+    int nseg;
+    const double *seg_lam;
+    const int *rseg;
+    // lambda of row i's problem
+    __device__ __forceinline__ double lam_of(int64_t i) const { return nseg > 1 ? seg_lam[rseg[i]] : lam; }
 };
 
 View view(pfe_ctx *c) {
@@ -58,6 +64,9 @@ View view(pfe_ctx *c) {
     v.w64 = c->g.w64;
     v.lam = c->lambda;
     v.r = c->r;
+    v.nseg = c->nseg;
+    v.seg_lam = c->seg_lam;
+    v.rseg = c->rseg;
     return v;
 }
 
@@ -87,7 +96,7 @@ __global__ void k_rowprep(View g, float *srow, int *kb, int *ent_of_slot) {
         }
         if (j == i || g.eid[idx] < 0) continue;  // padding
         const double w = g.w64[idx];
-        const double rho = g.lam * w * w / sqrt(aii * g.adiag[j]);
+        const double rho = g.lam_of(i) * w * w / sqrt(aii * g.adiag[j]);
         acc = fma(rho, rho, acc);
     }
     srow[i] = (float)acc;
@@ -116,7 +125,7 @@ __device__ __forceinline__ void features(const View &g, const float *srow, int64
         const int64_t k = e - g.n;
         const int a = g.ea[k], b = g.eb[k];
         const double aa = g.adiag[a], ab = g.adiag[b], w = g.ew[k];
-        f[0] = (float)(g.lam * w * w / sqrt(aa * ab));
+        f[0] = (float)(g.lam_of(a) * w * w / sqrt(aa * ab));
         f[1] = (float)(g.r * g.deg[b] / ab);
         f[2] = (float)(g.r * g.deg[a] / aa);
         f[3] = (float)w;
@@ -370,7 +379,7 @@ __global__ void k_kaporin_rows(View g, const int *kb, const float *gdiag, const 
                     break;
                 }
             const double w = g.w64[idx];
-            agj += g.lam * w * w * (gij - gik);
+            agj += g.lam_of(j) * w * w * (gij - gik);
         }
         q = fma(gij, agj, q);
         const float d = (float)(2.0 * agj);
@@ -655,7 +664,7 @@ __global__ void k_fsai_classical(View g, const int *kb, float *gdiag, float *gE,
                     const int64_t idx = bj + t;
                     if (g.eid[idx] >= 0 && g.col[idx] == k) {
                         const double w = g.w64[idx];
-                        v = -g.lam * w * w;
+                        v = -g.lam_of(j) * w * w;
                         break;
                     }
                 }

@@ -37,6 +37,7 @@ struct SegScal {
     int *active;                                  // nseg * d: column still iterating
     int *pending;                                 // nseg * d: reached tol on the recurrence, waiting for a replacement
     int *seg_active;                              // nseg: any column of the segment iterating
+    int *seg_live;                                // nseg: any column iterating or waiting to be confirmed
     int *seg_iters;                               // nseg: iterations of the segment in this solve
     long long *seg_iters_tot;                     // nseg: summed over solves until the host clears it
     unsigned *ticket;                             // nseg * 4: per-segment reduction tickets

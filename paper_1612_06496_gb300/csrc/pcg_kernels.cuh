@@ -262,42 +262,17 @@ __device__ __forceinline__ void load_val_range(const T *__restrict__ val, int64_
     }
 }
 
-// The stencil of the fixed-position rows of a grid graph: slot t of every
-// row is the pixel offset (dy_t, dx_t), the offsets with 0 < dx^2 + dy^2 <=
-// R^2 in (dy, dx) order -- the order the graph builder gives the slots.  12
-// slots are the radius-2 stencil and 28 the radius-3 one (no other radius
-// has these counts); the first LEN / 2 point backwards (lower neighbours).
-template <int LEN>
-struct StencilSlots {
-    static_assert(LEN == 12 || LEN == 28, "fixed rows of 12 or 28 slots");
-    static constexpr int R = LEN == 12 ? 2 : 3;
-    static constexpr int off(int t, bool want_dy) {
-        int k = 0;
-        for (int dy = -R; dy <= R; ++dy)
-            for (int dx = -R; dx <= R; ++dx)
-                if (dx * dx + dy * dy > 0 && dx * dx + dy * dy <= R * R) {
-                    if (k == t) return want_dy ? dy : dx;
-                    ++k;
-                }
-        return 0;
-    }
-    static constexpr int count() {
-        int k = 0;
-        for (int dy = -R; dy <= R; ++dy)
-            for (int dx = -R; dx <= R; ++dx) k += (dx * dx + dy * dy > 0 && dx * dx + dy * dy <= R * R) ? 1 : 0;
-        return k;
-    }
-    static_assert(count() == LEN, "stencil size");
-};
-
 // Column of slot T of row i of a one-image grid graph of width w and n
-// pixels, computed from the stencil instead of loaded: i + dy_T w + dx_T,
+// pixels, computed from the stencil (make_stencil: slot T is the T-th offset
+// in (dy, dx) order) instead of loaded: i + dy_T w + dx_T,
 // clamped into [0, n).  A slot whose neighbour is off the image has value 0
 // (padding), so any row serves there; clamping only keeps the address valid
 // (a backward slot can only fall below row 0, a forward one past row n - 1).
 template <int LEN, int T>
 __device__ __forceinline__ int stencil_col(int i, int w, int n) {
-    constexpr int dy = StencilSlots<LEN>::off(T, true), dx = StencilSlots<LEN>::off(T, false);
+    static_assert(stencil_count<LEN>() == LEN, "12 slots: radius 2, 28: radius 3");
+    constexpr Stencil<LEN> st = make_stencil<LEN>();
+    constexpr int dy = st.dy[T], dx = st.dx[T];
     const int j = i + dy * w + dx;
     if constexpr (T < LEN / 2)
         return max(j, 0);
@@ -521,8 +496,9 @@ constexpr unsigned kFull = 0xffffffffu;
 // has fallen kRefreshDrop below its value at the last one (the drift stays
 // below ~eps / kRefreshDrop of r).  A column whose recurrence residual
 // reaches tol stops (pending) and is confirmed on the next replacement's true
-// residual -- one is made as soon as no column is left iterating -- or, if
-// that residual is still above tol, resumes with a restarted direction.  A
+// residual -- one is made as soon as no column of any problem of a batch is
+// left iterating, so the problems of a batch share it -- or, if that
+// residual is still above tol, resumes with a restarted direction.  A
 // replacement that moved r by more than sqrt(kRestartDev) of its norm
 // restarts that column too (beta = 0).  Periodic replacements (every
 // `refresh` iterations) come on top; refresh = 0 turns replacement off and
@@ -580,13 +556,14 @@ static __device__ void finish_seg(PcgCtl *ctl, const SegScal &sc, int seg, const
     }
     live = __any_sync(kFull, live);
     iterating = __any_sync(kFull, iterating);
-    want = __any_sync(kFull, want) || (live && !iterating);  // only pending columns left: confirm them
+    want = __any_sync(kFull, want);
     if (lane == 0) {
         if (mode == 0)
             sc.seg_iters[seg] = 0;
-        else if (__ldcg(sc.seg_active + seg))
+        else if (__ldcg(sc.seg_live + seg))
             sc.seg_iters[seg] = it;
-        sc.seg_active[seg] = live;
+        sc.seg_active[seg] = iterating;  // the iteration kernels skip segments with no column iterating
+        sc.seg_live[seg] = live;         // the replacement kernels also visit waiting ones
         if (want && mode == 2) ctl->refresh_want = 1;
     }
     __syncwarp();
@@ -625,12 +602,18 @@ __device__ __forceinline__ V warp_sum(V v) {
 static __device__ void finish_all(PcgCtl *ctl, const SegScal &sc, int nseg, int D, cudaGraphConditionalHandle cond,
                                   int use_cond) {
     const int lane = threadIdx.x & 31;
-    int any = 0;
-    for (int s = lane; s < nseg; s += 32) any |= __ldcg(sc.seg_active + s);
+    int any = 0, iterating = 0;
+    for (int s = lane; s < nseg; s += 32) {
+        any |= __ldcg(sc.seg_live + s);
+        iterating |= __ldcg(sc.seg_active + s);
+    }
     any = __any_sync(kFull, any);
+    iterating = __any_sync(kFull, iterating);
     int done = 0;
     if (lane == 0) done = (!any) || *(volatile int *)&ctl->error || ctl->iter >= ctl->max_iter;
     done = __shfl_sync(kFull, done, 0);
+    // only columns waiting for confirmation left: the next iteration replaces
+    if (lane == 0 && !done && !iterating && ctl->refresh > 0) ctl->refresh_want = 1;
     if (done) {
         double mr = 0.0;
         long long tot = 0;
@@ -640,7 +623,7 @@ static __device__ void finish_all(PcgCtl *ctl, const SegScal &sc, int nseg, int 
             tot += it;
             sc.seg_iters_tot[s] += it;
             mx = max(mx, it);
-            nun += __ldcg(sc.seg_active + s) ? 1 : 0;
+            nun += __ldcg(sc.seg_live + s) ? 1 : 0;
             for (int c = 0; c < D; ++c) mr = fmax(mr, __ldcg(sc.relres + (int64_t)s * D + c));
         }
         tot = warp_sum(tot);
@@ -779,13 +762,17 @@ __device__ __forceinline__ void true_residual(const PcgArgs<T> &a, int64_t i, in
     const BlockSeg bsg = block_seg<MS_>(a.sg);                                                             \
     const int64_t warp_g = (int64_t)(blockIdx.x - bsg.b0) * kWarps + (threadIdx.x >> 5);                   \
     const int64_t warps_total = (int64_t)bsg.nb * kWarps;                                                  \
-    const int64_t seg_rows = ((MS_) && (LIVE_) && !__ldcg(a.sc.seg_active + bsg.seg)) ? 0 : bsg.r1 - bsg.r0; \
+    const int64_t seg_rows = ((MS_) && (LIVE_) && !__ldcg(((LIVE_) == 2 ? a.sc.seg_live : a.sc.seg_active) + bsg.seg)) \
+                                 ? 0                                                                                 \
+                                 : bsg.r1 - bsg.r0;                                                                  \
     for (int64_t g = warp_g; g * SW::RPW < seg_rows; g += warps_total)
 // one problem (FSAI kernels, y = A x)
 #define PFE_ROW_LOOP(T_, D_) PFE_ROW_LOOP_(T_, D_, false, false)
 // MS: batch (segments) or one problem; LIVE skips converged segments
 #define PFE_ROW_LOOP_MS(T_, D_, MS_) PFE_ROW_LOOP_(T_, D_, false, MS_)
-#define PFE_ROW_LOOP_LIVE(T_, D_, MS_) PFE_ROW_LOOP_(T_, D_, true, MS_)
+#define PFE_ROW_LOOP_LIVE(T_, D_, MS_) PFE_ROW_LOOP_(T_, D_, 1, MS_)
+// MS: batch, skipping segments with no column iterating or waiting to be confirmed
+#define PFE_ROW_LOOP_REPL(T_, D_, MS_) PFE_ROW_LOOP_(T_, D_, 2, MS_)
 #define PFE_ROW_I                                 \
     const int64_t i = bsg.r0 + g * SW::RPW + lm.r; \
     if (!lm.active || i >= bsg.r1) continue
@@ -1785,18 +1772,21 @@ __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush
 // replacement iterations).  It also measures how far the true residual lies
 // from the recurrence residual r - alpha q it replaces (|r - r_rec|^2 /
 // |r_rec|^2 per column -> sc.devr, for the restart test).
-template <typename T, int D, int LEN>
+template <typename T, int D, int LEN, bool MS>
 __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done || !*(volatile int *)&a.ctl->refresh_now) return;
     const int par = a.ctl->iter & 1;
     const T *__restrict__ rold = a.r2[par];
     T *__restrict__ rdst = a.r2[par ^ 1];
     __shared__ T salpha[D];
-    if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
+    {
+        const BlockSeg bs0 = block_seg<MS>(a.sg);
+        if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.sc.alpha[bs0.seg * D + threadIdx.x];
+    }
     __syncthreads();
     __shared__ DF sq_sh[sqsum_slots<T, 2, SubWarp<T, D>::V>()];
     SqSum<T, 2, SubWarp<T, D>::V> sq(sq_sh);  // |r - r_rec|^2 | |r_rec|^2
-    PFE_ROW_LOOP(T, D) {
+    PFE_ROW_LOOP_MS(T, D, MS) {
         PFE_ROW_I;
         const int c0 = lm.cg * V;
         T ri[V], ro[V], qi[V];
@@ -1819,7 +1809,7 @@ __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
         if (threadIdx.x < 32) {
             for (int c = threadIdx.x; c < D; c += 32) {
                 const double rec = tot[D + c];
-                a.sc.devr[c] = rec > 0.0 ? tot[c] / rec : (tot[c] > 0.0 ? INFINITY : 0.0);
+                a.sc.devr[bsg.seg * D + c] = rec > 0.0 ? tot[c] / rec : (tot[c] > 0.0 ? INFINITY : 0.0);
             }
             if (threadIdx.x == 0) a.ctl->xpending = 0;
         }
@@ -1886,11 +1876,14 @@ constexpr int gather_min_blocks() {
 // applied together with the next one (y += alpha_prev p_prev + alpha p in
 // one pass of k_fsai_zp, the directions in alternating buffers): the hi/lo
 // solution is read and written every other iteration.  Once the solve is
-// done the held state stays for the final k_xflush.
-template <typename T>
+// done the held state stays for the final k_xflush.  MS (a batch): each
+// segment's last block finishes its segment; the last segment to get there
+// finishes the iteration.
+template <typename T, bool MS = false>
 __device__ void fsai_finish(const PcgArgs<T> &a, const BlockSeg &bsg, const double *tot, int D, int mode) {
     PcgCtl *ctl = a.ctl;
     finish_seg(ctl, a.sc, bsg.seg, tot, tot + D, D, mode, ctl->iter + 1);
+    if (MS && !warp_last_segment(ctl, 1, a.sg.nseg)) return;
     if (threadIdx.x == 0 && mode != 0) ctl->iter += 1;
     if (threadIdx.x == 0 && mode == 1) ctl->refreshes += 1;
     __syncwarp();
@@ -1909,7 +1902,7 @@ __device__ void fsai_finish(const PcgArgs<T> &a, const BlockSeg &bsg, const doub
     }
     hold = __shfl_sync(kFull, hold, 0);
     if (hold)
-        for (int c = threadIdx.x; c < D; c += 32) a.sc.alpha_prev[c] = a.sc.alpha[c];
+        for (int c = threadIdx.x; c < a.sg.nseg * D; c += 32) a.sc.alpha_prev[c] = a.sc.alpha[c];
     __syncwarp();
 }
 
@@ -1991,21 +1984,26 @@ __device__ __forceinline__ void gslot_grid(const T *__restrict__ gs, int64_t i, 
 // (= r'.z') and r'.r' and the end of the iteration.  On refresh iterations
 // it does nothing (k_refresh_f and k_fsai_t<1> make r and t).
 // LEN > 0: uniform rows of LEN slots, lower slots at positions [0, LEN/2);
-// GRID: one grid image, the slot columns computed from the stencil.
-template <typename T, int D, int LEN, bool GRID>
+// GRID: one grid image, the slot columns computed from the stencil; MS: a
+// batch (each block in one segment, with its alpha; segments whose columns
+// have all converged are skipped).
+template <typename T, int D, int LEN, bool GRID, bool MS>
 __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr(PcgArgs<T> a) {
     const PcgCtl *ctl = a.ctl;
     if (*(volatile const int *)&ctl->done) return;
     if (ctl->refresh_now) return;
-    __shared__ T salpha[D];  // FSAI runs on one segment
-    if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
+    __shared__ T salpha[D];
+    {
+        const BlockSeg bs0 = block_seg<MS>(a.sg);
+        if (threadIdx.x < D) salpha[threadIdx.x] = (T)a.sc.alpha[bs0.seg * D + threadIdx.x];
+    }
     __syncthreads();
     __shared__ DF sq_sh[sqsum_slots<T, 2, SubWarp<T, D>::V>()];
     SqSum<T, 2, SubWarp<T, D>::V> sq(sq_sh);  // t.t (= r.z) | r.r
     const int par = ctl->iter & 1;
     const T *__restrict__ rold = a.r2[par];
     T *__restrict__ rnew = a.r2[1 - par];
-    PFE_ROW_LOOP(T, D) {
+    PFE_ROW_LOOP_LIVE(T, D, MS) {
         PFE_ROW_I;
         const int c0 = lm.cg * V;
         T al[V];
@@ -2040,21 +2038,21 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_tr
     sq.finish();
     __shared__ double tot[2 * D];
     if (grid_sum_cols<T, D, 2>(sq.acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot))
-        if (threadIdx.x < 32) fsai_finish(a, bsg, tot, D, 2);
+        if (threadIdx.x < 32) fsai_finish<T, MS>(a, bsg, tot, D, 2);
 }
 
 // t = G r: t_i = G_ii r_i + sum over the lower slots (j < i) of G_ij r_j, with
 // the dots t.t (= r.z) and r.r.  MODE 0: the start of a solve (residual in
 // r2[0]); MODE 1: only after a residual refresh (residual in the new buffer),
 // ending the iteration.
-template <typename T, int D, int MODE, int LEN, bool GRID>
+template <typename T, int D, int MODE, int LEN, bool GRID, bool MS>
 __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done) return;
     if (MODE == 1 && !*(volatile int *)&a.ctl->refresh_now) return;
     const T *__restrict__ rsrc = MODE == 0 ? a.r2[0] : a.r2[(a.ctl->iter + 1) & 1];
     __shared__ DF sq_sh[sqsum_slots<T, 2, SubWarp<T, D>::V>()];
     SqSum<T, 2, SubWarp<T, D>::V> sq(sq_sh);  // t.t (= r.z) | r.r
-    PFE_ROW_LOOP(T, D) {
+    PFE_ROW_LOOP_MS(T, D, MS) {
         PFE_ROW_I;
         const int c0 = lm.cg * V;
         int64_t base;
@@ -2084,7 +2082,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(
     sq.finish();
     __shared__ double tot[2 * D];
     if (grid_sum_cols<T, D, 2>(sq.acc, a.part, bsg, &a.sc.ticket[bsg.seg * 4 + 1], tot))
-        if (threadIdx.x < 32) fsai_finish(a, bsg, tot, D, MODE == 0 ? 0 : 1);
+        if (threadIdx.x < 32) fsai_finish<T, MS>(a, bsg, tot, D, MODE == 0 ? 0 : 1);
 }
 
 // z = G^T t (z_i = G_ii t_i + sum over the upper slots (j > i) of G_ji t_j)
@@ -2094,7 +2092,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D>())) k_fsai_t(
 // old content of the buffer p_new goes to); each thread reads and writes only
 // its row's own entries; z is never stored.  Block 0 also decides whether the
 // next iteration refreshes the residual.
-template <typename T, int D, int LEN, bool GRID>
+template <typename T, int D, int LEN, bool GRID, bool MS>
 __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())) k_fsai_zp(PcgArgs<T> a) {
     PcgCtl *ctl = a.ctl;
     if (*(volatile int *)&ctl->done) return;
@@ -2104,10 +2102,13 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())
     T *__restrict__ pdst = a.p[ctl->iter & 1];
     const T *__restrict__ psrc = a.p[(ctl->iter & 1) ^ 1];
     __shared__ T sbeta[D], salpha[D], salpha_prev[D];
-    if (threadIdx.x < D) {
-        sbeta[threadIdx.x] = p_ready ? T(0) : (T)a.sc.beta[threadIdx.x];
-        salpha[threadIdx.x] = (T)a.sc.alpha[threadIdx.x];
-        salpha_prev[threadIdx.x] = (T)a.sc.alpha_prev[threadIdx.x];
+    {
+        const int sk = block_seg<MS>(a.sg).seg * D + threadIdx.x;  // this block's segment
+        if (threadIdx.x < D) {
+            sbeta[threadIdx.x] = p_ready ? T(0) : (T)a.sc.beta[sk];
+            salpha[threadIdx.x] = (T)a.sc.alpha[sk];
+            salpha_prev[threadIdx.x] = (T)a.sc.alpha_prev[sk];
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // periodic, or asked for by a column in this iteration
         ctl->refresh_now = (ctl->refresh > 0 && (((ctl->iter + 1) % ctl->refresh) == 0 || ctl->refresh_want)) ? 1 : 0;
@@ -2115,7 +2116,7 @@ __global__ void __launch_bounds__(kBlock, (gather_min_blocks<T, D, LEN, true>())
         set_if(a, ctl->refresh_now);
     }
     __syncthreads();
-    PFE_ROW_LOOP(T, D) {
+    PFE_ROW_LOOP_MS(T, D, MS) {
         PFE_ROW_I;
         const int c0 = lm.cg * V;
         int64_t base;
@@ -2295,7 +2296,7 @@ __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
     for (int q = 0; q < 3; ++q)
 #pragma unroll
         for (int k = 0; k < SWt::V; ++k) acc[q][k] = A::zero();
-    PFE_ROW_LOOP_LIVE(T, D, MS) {
+    PFE_ROW_LOOP_REPL(T, D, MS) {
         PFE_ROW_I;
         const int c0 = lm.cg * V;
         T ri[V], rr[V];
@@ -2487,14 +2488,17 @@ void launch_refresh(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a) {
     else
         k_refresh<T, D, MS, 0><<<wave_grid(c, G_REFRESH, k_refresh<T, D, MS, 0>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
 }
-template <typename T, int D>
+template <typename T, int D, bool MS = false>
 void launch_refresh_f(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a) {
     if (c->g.row_len == 12)
-        k_refresh_f<T, D, 12><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 12>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        k_refresh_f<T, D, 12, MS><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 12, MS>, rows_need<T, D>(c)), kBlock, 0,
+                                    s>>>(a);
     else if (c->g.row_len == 28)
-        k_refresh_f<T, D, 28><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 28>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        k_refresh_f<T, D, 28, MS><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 28, MS>, rows_need<T, D>(c)), kBlock, 0,
+                                    s>>>(a);
     else
-        k_refresh_f<T, D, 0><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 0>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
+        k_refresh_f<T, D, 0, MS><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 0, MS>, rows_need<T, D>(c)), kBlock, 0,
+                                   s>>>(a);
 }
 
 template <typename T, int D, bool MS>
@@ -2512,39 +2516,41 @@ pfe_status body_ms(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, const PcgLau
 // The FSAI kernels with the compile-time row length of the layout (FP32 grid
 // graphs of radius 2 or 3; else the general kernels).
 // which: 0 = k_fsai_tr, 1 = k_fsai_t (start of a solve), 2 = k_fsai_t (after a refresh), 3 = k_fsai_zp
-template <typename T, int D, int LEN, bool GRID>
+template <typename T, int D, int LEN, bool GRID, bool MS>
 void fsai_kernels_len(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int which) {
     if (which == 0)
-        k_fsai_tr<T, D, LEN, GRID><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D, LEN, GRID>, rows_need<T, D>(c)), kBlock, 0,
-                                     s>>>(a);
+        k_fsai_tr<T, D, LEN, GRID, MS><<<wave_grid(c, G_FSAI_TR, k_fsai_tr<T, D, LEN, GRID, MS>, rows_need<T, D>(c)),
+                                         kBlock, 0, s>>>(a);
     else if (which == 1)
-        k_fsai_t<T, D, 0, LEN, GRID><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D, 0, LEN, GRID>, rows_need<T, D>(c)), kBlock,
-                                       0, s>>>(a);
+        k_fsai_t<T, D, 0, LEN, GRID, MS><<<wave_grid(c, G_FSAI_T, k_fsai_t<T, D, 0, LEN, GRID, MS>, rows_need<T, D>(c)),
+                                           kBlock, 0, s>>>(a);
     else if (which == 2)
-        k_fsai_t<T, D, 1, LEN, GRID><<<wave_grid(c, G_FSAI_T1, k_fsai_t<T, D, 1, LEN, GRID>, rows_need<T, D>(c)),
-                                       kBlock, 0, s>>>(a);
+        k_fsai_t<T, D, 1, LEN, GRID, MS><<<wave_grid(c, G_FSAI_T1, k_fsai_t<T, D, 1, LEN, GRID, MS>,
+                                                     rows_need<T, D>(c)),
+                                           kBlock, 0, s>>>(a);
     else
-        k_fsai_zp<T, D, LEN, GRID><<<wave_grid(c, G_FSAI_ZP, k_fsai_zp<T, D, LEN, GRID>, rows_need<T, D>(c)), kBlock, 0,
-                                     s>>>(a);
+        k_fsai_zp<T, D, LEN, GRID, MS><<<wave_grid(c, G_FSAI_ZP, k_fsai_zp<T, D, LEN, GRID, MS>, rows_need<T, D>(c)),
+                                         kBlock, 0, s>>>(a);
 }
 // The FSAI kernels on fixed-length rows (12 or 28 slots): slot columns loaded
 // (PFE_FSAI_SLOTS) or, on one grid image, computed from the stencil
-// (PFE_FSAI_STENCIL; the context's choice, made by pfe_autotune).
-template <typename T, int D>
+// (PFE_FSAI_STENCIL; the context's choice, made by pfe_autotune).  A batch
+// (MS) reads the slot columns.
+template <typename T, int D, bool MS = false>
 void launch_fsai(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, int which) {
-    const bool grid = c->fsai_variant == PFE_FSAI_STENCIL && a.grid_w > 0;
+    const bool grid = !MS && c->fsai_variant == PFE_FSAI_STENCIL && a.grid_w > 0;
     if (c->g.row_len == 12) {
         if (grid)
-            fsai_kernels_len<T, D, 12, true>(c, s, a, which);
+            fsai_kernels_len<T, D, 12, true, false>(c, s, a, which);
         else
-            fsai_kernels_len<T, D, 12, false>(c, s, a, which);
+            fsai_kernels_len<T, D, 12, false, MS>(c, s, a, which);
     } else if (c->g.row_len == 28) {
         if (grid)
-            fsai_kernels_len<T, D, 28, true>(c, s, a, which);
+            fsai_kernels_len<T, D, 28, true, false>(c, s, a, which);
         else
-            fsai_kernels_len<T, D, 28, false>(c, s, a, which);
+            fsai_kernels_len<T, D, 28, false, MS>(c, s, a, which);
     } else {
-        fsai_kernels_len<T, D, 0, false>(c, s, a, which);
+        fsai_kernels_len<T, D, 0, false, MS>(c, s, a, which);
     }
 }
 
@@ -2574,6 +2580,26 @@ void ic_solve(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, bool fwd, int sta
         ic_solve_len<T, D, 28>(c, s, a, fwd, start);
 }
 
+// One FSAI iteration of the loop body (position u of iters): q = A p, r -=
+// alpha q with t = G r, the replacement kernels (IF node), z = G^T t with the
+// direction and solution updates.
+template <typename T, int D, bool MS>
+pfe_status fsai_iter(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a, const PcgLaunch &L, int u, int iters,
+                     cudaStream_t &ks) {
+    launch_spmm<T, D, MS>(c, s, a);
+    launch_fsai<T, D, MS>(c, s, a, 0);
+    PFE_TRY(if_begin(c, s, L, u, ks));
+    k_xflush<T, D, MS><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, MS>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0,
+                         ks>>>(a, 0, 0);
+    launch_refresh_f<T, D, MS>(c, ks, a);
+    launch_fsai<T, D, MS>(c, ks, a, 2);
+    PFE_TRY(if_end(c, L));
+    PcgArgs<T> az = a;
+    az.if_pos = L.n_if > 0 ? (u + 1) % iters : -1;  // decides the next iteration's replacement
+    launch_fsai<T, D, MS>(c, s, az, 3);
+    return PFE_OK;
+}
+
 template <typename T, int D>
 pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
     PcgArgs<T> a = pcg_args<T>(c, L);
@@ -2592,12 +2618,19 @@ pfe_status init_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L) {
             return PFE_OK;
         }
         if (use_fsai<T>(c)) {
-            k_pcg_init<T, D, 1, false><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1, false>, rows_need<T, D>(c)), kBlock,
-                                         0, s>>>(a);
-            launch_fsai<T, D>(c, s, a, 1);
             PcgArgs<T> az = a;
             az.if_pos = L.n_if > 0 ? 0 : -1;  // decides the replacement of the body's first iteration
-            launch_fsai<T, D>(c, s, az, 3);
+            if (c->nseg > 1) {
+                k_pcg_init<T, D, 1, true><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1, true>, rows_need<T, D>(c)),
+                                            kBlock, 0, s>>>(a);
+                launch_fsai<T, D, true>(c, s, a, 1);
+                launch_fsai<T, D, true>(c, s, az, 3);
+            } else {
+                k_pcg_init<T, D, 1, false><<<wave_grid(c, G_INIT_F, k_pcg_init<T, D, 1, false>, rows_need<T, D>(c)),
+                                             kBlock, 0, s>>>(a);
+                launch_fsai<T, D>(c, s, a, 1);
+                launch_fsai<T, D>(c, s, az, 3);
+            }
             PFE_CUDA_TRY(c, cudaGetLastError());
             return PFE_OK;
         }
@@ -2635,17 +2668,10 @@ pfe_status body_T(pfe_ctx *c, cudaStream_t s, PcgLaunch L, int iters) {
         }
         if (use_fsai<T>(c)) {
             for (int u = 0; u < iters; ++u) {
-                launch_spmm<T, D, false>(c, s, a);
-                launch_fsai<T, D>(c, s, a, 0);
-                PFE_TRY(if_begin(c, s, L, u, ks));
-                k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c), flat_mult<T, D>()), kBlock, 0,
-                                        ks>>>(a, 0, 0);
-                launch_refresh_f<T, D>(c, ks, a);
-                launch_fsai<T, D>(c, ks, a, 2);
-                PFE_TRY(if_end(c, L));
-                PcgArgs<T> az = a;
-                az.if_pos = L.n_if > 0 ? (u + 1) % iters : -1;  // decides the next iteration's replacement
-                launch_fsai<T, D>(c, s, az, 3);
+                if (c->nseg > 1)
+                    PFE_TRY((fsai_iter<T, D, true>(c, s, a, L, u, iters, ks)));
+                else
+                    PFE_TRY((fsai_iter<T, D, false>(c, s, a, L, u, iters, ks)));
             }
             PFE_CUDA_TRY(c, cudaGetLastError());
             return PFE_OK;
@@ -2713,7 +2739,7 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
             hs.alpha[k] = 1e-30;
             hs.beta[k] = 0.5;
         }
-        for (int q = 0; q < nseg; ++q) hs.seg_active[q] = 1;
+        for (int q = 0; q < nseg; ++q) hs.seg_active[q] = hs.seg_live[q] = 1;
     }
     void *dsc = nullptr;
     const int64_t nd = c->g.n * (int64_t)D;
@@ -2789,7 +2815,10 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
                                                   flat_mult<T, D>()),
                                         kBlock, 0, s>>>(a);
         else if constexpr (std::is_same_v<T, float>) {
-            launch_fsai<T, D>(c, s, a, which == 3 ? 0 : 3);  // 4, 5: k_fsai_zp
+            if (multi)
+                launch_fsai<T, D, true>(c, s, a, which == 3 ? 0 : 3);  // 4, 5: k_fsai_zp
+            else
+                launch_fsai<T, D>(c, s, a, which == 3 ? 0 : 3);
         }
     };
     launch();  // warm-up

@@ -160,23 +160,97 @@ def test_edge_list_batch_and_cross_edges():
     assert ei.value.status == 1
 
 
-def test_batch_rejects_fsai():
+@pytest.mark.parametrize("precond", ["learned", "classical"])
+def test_batch_fsai_matches_oracle_per_image(precond):
+    """The FSAI preconditioner on a batch (one launch per kernel for every
+    image, each image's own lambda in the network features, its own PCG
+    scalars and convergence): every image against the oracle's exact
+    solves, FP32 path, 2e-4; and the factor of each image equals the one the
+    image gets alone."""
+    from paper_1612_06496_gb300.learned import load_weights
+    specs = _specs(d=4)
+    pf, probs, off, Y0 = _batch(specs, "mixed", tol=1e-6)
+    if precond == "learned":
+        pf.fsai_set(load_weights())
+    else:
+        pf.fsai_classical()
+    pf.init(Y0)
+    Y = np.empty_like(Y0)
+    Yh = np.empty_like(Y0)
+    st = pf.solve(2, 3, Y, Yh)
+    assert st["n_unconverged"] == 0
+    gd_b, ge_b = pf.fsai_get()
+    a_b, b_b, _ = pf.edges()
+    for k, (s, (X, Y0s)) in enumerate(zip(specs, probs)):
+        g, ost = _oracle(s, X, Y0s, 2, 3)
+        sl = slice(off[k], off[k + 1])
+        assert relerr(Y[sl], ost.Y) <= 2e-4, k
+        assert relerr(Yh[sl], O.embedding(g, ost)) <= 2e-4, k
+        # the same factor as the image alone
+        from paper_1612_06496_gb300 import PFE
+        H, W = s.shape
+        p1 = PFE(X, sigma=s.sigma, H=H, W=W, radius=s.radius, precision="mixed")
+        if precond == "learned":
+            p1.fsai_set(load_weights())
+        else:
+            p1.fsai_classical()
+        gd1, ge1 = p1.fsai_get()
+        a1, b1, _ = p1.edges()
+        p1.close()
+        np.testing.assert_allclose(gd_b[sl], gd1, rtol=1e-6)
+        # edges matched by their endpoints (the two lists need not share an order)
+        at = {(int(x), int(y)): v for x, y, v in zip(a1, b1, ge1)}
+        sel = np.nonzero((a_b >= off[k]) & (a_b < off[k + 1]))[0]
+        assert len(sel) == len(at)
+        ref = np.array([at[(int(a_b[e] - off[k]), int(b_b[e] - off[k]))] for e in sel])
+        np.testing.assert_allclose(ge_b[sel], ref, rtol=1e-5, atol=1e-7 * np.abs(ref).max())
+    pf.close()
+
+
+def test_batch_learned_fsai_cuts_iterations_and_images_converge_independently():
+    """With the learned factor each image of a batch needs fewer PCG
+    iterations than with Jacobi, and images stop on their own."""
+    from paper_1612_06496_gb300.learned import load_weights
+    specs = _specs(d=4, shapes=[(40, 48), (25, 31), (33, 29)], regions=4)
+    its = {}
+    for precond in ("jacobi", "learned"):
+        pf, probs, off, Y0 = _batch(specs, "mixed", tol=1e-6)
+        if precond == "learned":
+            pf.fsai_set(load_weights())
+        pf.init(Y0)
+        pf.solve(1, 2)
+        it, rr = pf.segment_stats()
+        assert np.all(rr <= 1e-6)
+        its[precond] = it
+        pf.close()
+    assert np.all(its["learned"] < its["jacobi"]), its
+
+
+def test_batch_rejects_ic0_and_training():
     from paper_1612_06496_gb300 import PFEError
     from paper_1612_06496_gb300.learned import init_params
     pf, probs, off, Y0 = _batch(_specs(), "mixed")
     with pytest.raises(PFEError) as ei:
-        pf.fsai_set(init_params(0))
+        pf.ic0()
+    assert ei.value.status == 8
+    with pytest.raises(PFEError) as ei:
+        pf.fsai_loss_grad(init_params(0))
     assert ei.value.status == 8
     pf.close()
 
 
-def test_c3_batch_full_size():
-    """The 64-image batch (96..481 x 96..321, 3-12 regions, radius 2, d = 5):
+@pytest.mark.parametrize("precond", ["jacobi", "learned"])
+def test_c3_batch_full_size(precond):
+    """The 64-image batch (96..481 x 96..321, 3-12 regions, radius 2, d = 5),
+    with Jacobi and with the learned factor (the benchmark's batch arms):
     one outer iteration of two inner steps; every image converged and
     D-orthonormal, the two smallest images against the oracle."""
+    from paper_1612_06496_gb300.learned import load_weights
     specs = batch_specs()
     pf, probs, off, Y0 = _batch(specs, "mixed", tol=1e-6)
     assert pf.info()["nseg"] == 64
+    if precond == "learned":
+        pf.fsai_set(load_weights())
     pf.init(Y0)
     Y = np.empty_like(Y0)
     Yh = np.empty_like(Y0)

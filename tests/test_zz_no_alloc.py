@@ -1,11 +1,10 @@
 """pfe_orthonormalize_noalloc: the allocation-free entry point.
 
-Some callers cannot call cudaMalloc at all: code that runs while a CUDA
-stream is being captured into a graph (allocation is not allowed there),
-plug-ins inside a host application that owns every device allocation
-through its own pool, or services that size device memory once at start-up.
-For them the library offers one entry point whose scratch memory is a fixed
-array compiled into the library.  This test calls it through the C ABI,
+Some callers cannot call cudaMalloc at all: plug-ins inside a host
+application that owns every device allocation through its own pool, or
+services that size device memory once at start-up.  For them the library
+offers one entry point whose scratch memory is a fixed array compiled into
+the library.  This test calls it through the C ABI,
 twice in a row, and checks it against the D-orthonormalisation that
 pfe_init performs (which allocates its own buffers), within the tolerance
 the other FP64 tests use.
@@ -68,3 +67,29 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     f = lib.pfe_orthonormalize_noalloc
     # host pointers are refused (the entry point copies nothing)
     assert f(Yh.ctypes.data, deg.data_ptr(), 64, 3, out.data_ptr(), None) == 1
+
+
+def test_noalloc_singular_call_then_a_good_one():
+    """A rank-deficient D^{1/2} Y (two equal columns) is PFE_ESINGULAR and
+    leaves Yhat as it was; the next call on the same device starts from the
+    shared array that call left behind and is exact again."""
+    torch = pytest.importorskip("torch")
+    from paper_1612_06496_gb300 import load_library
+    lib = load_library()
+    spec = small_spec(H=19, W=21, d=4, seed=14)
+    p, X, Y0 = gpu_problem(spec, "fp64", tol=1e-12)
+    p.init(Y0)
+    ref = p.get("Y")
+    deg = p.get("DEG")
+    p.close()
+    degd = torch.from_numpy(deg).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    bad = Y0.copy()
+    bad[:, 2] = bad[:, 1]
+    out = torch.full((spec.n, 4), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    assert _noalloc(lib, torch.from_numpy(bad).cuda(), degd, out, stream) == 6  # PFE_ESINGULAR
+    assert torch.isnan(out).all()
+    out2 = torch.full_like(out, float("nan"))
+    assert _noalloc(lib, torch.from_numpy(Y0).cuda(), degd, out2, stream) == 0
+    assert relerr(out2.cpu().numpy(), ref) <= 1e-12
