@@ -487,19 +487,16 @@ def main():
         nnz_iters = float(info["nnz_A"]) * iters_total
     launches = sum(s["kernel_launches"] for s in stats)
     sec_per_outer = job_seconds_per_outer(ms_max, args.steps, world)
-    # after the timed region: the next system of Eq. 13 solved from its warm
-    # start by the same path, and |b - A y| / |b| per column with A in FP64
-    # (pfe_residual), the problem's matrix rather than the FP32 rounding the
-    # iteration multiplies by
-    b_next, y_next = p.get("RHS"), p.get("Y")
-    p.solve_system(b_next, y_next)
-    true_relres = float(p.residual(b_next, y_next).max())
 
     # --- roofline of the dominant kernel: k_spmm (q = A p with the p.q dots)
     spmm_ms = p.time_kernel("spmm", 20)
     upd_ms = p.time_kernel("update", 20)
     pup_ms, puph_ms = p.time_kernel("pupdate", 20), p.time_kernel("pupdate_hold", 20)
     edge_ms = p.time_kernel("edge", 10)
+    # the kernels of a replacement iteration (every 50 iterations, after a
+    # 1e3-fold fall of a residual, and to confirm convergence): the
+    # replacement residual, the update flush, and (FSAI) t = G r with the dots
+    repl_ms, xfl_ms = p.time_kernel("replace", 10), p.time_kernel("xflush", 10)
     n, d, nnz, ne = info["n"], info["d"], info["nnz_A"], info["n_edges"]
     fsai_k = {}
     fsai_arm = args.precond in ("learned", "classical")  # the FSAI kernels run (any factor G)
@@ -512,11 +509,13 @@ def main():
         # lo) in, y out
         tr_ms = p.time_kernel("fsai_tr", 20)
         zf_ms, zh_ms = p.time_kernel("fsai_zp", 20), p.time_kernel("fsai_zp_hold", 20)
+        ft_ms = p.time_kernel("fsai_t", 10)
         slot_b = (2 if fsai_cols == 1 else 4) * (nnz - n)
         tr_b = slot_b + 4 * n + 16 * n * d
         zh_b = slot_b + 4 * n + 12 * n * d
         zf_b = zh_b + 20 * n * d
-        fsai_k = {"k_fsai_tr_ms": round(tr_ms, 5), "k_fsai_tr_GBps": round(tr_b / (tr_ms * 1e-3) / 1e9, 1),
+        fsai_k = {"k_fsai_t_ms": round(ft_ms, 5),
+                  "k_fsai_tr_ms": round(tr_ms, 5), "k_fsai_tr_GBps": round(tr_b / (tr_ms * 1e-3) / 1e9, 1),
                   "k_fsai_zp_fold_ms": round(zf_ms, 5), "k_fsai_zp_fold_GBps": round(zf_b / (zf_ms * 1e-3) / 1e9, 1),
                   "k_fsai_zp_hold_ms": round(zh_ms, 5), "k_fsai_zp_hold_GBps": round(zh_b / (zh_ms * 1e-3) / 1e9, 1)}
     # the SpMM variant the autotuner chose for this arm
@@ -572,7 +571,16 @@ def main():
                                   "k_edge_ms": round(edge_ms, 5),
                                   # b read + written (FP32), w, column + edge id per directed slot, Y, C in, RHS out
                                   "k_edge_GBps": round((8 * d * ne + 4 * ne + 8 * 2 * ne + 12 * n * d)
-                                                       / (edge_ms * 1e-3) / 1e9, 1), **fsai_k}}
+                                                       / (edge_ms * 1e-3) / 1e9, 1),
+                                  "replacement_residual_ms": round(repl_ms, 5), "k_xflush_ms": round(xfl_ms, 5),
+                                  **fsai_k}}
+    # after the timings: the next system of Eq. 13 solved from its warm start
+    # by the same path, and |b - A y| / |b| per column with A in FP64
+    # (pfe_residual), the problem's matrix rather than the FP32 rounding the
+    # iteration multiplies by
+    b_next, y_next = p.get("RHS"), p.get("Y")
+    p.solve_system(b_next, y_next)
+    true_relres = float(p.residual(b_next, y_next).max())
     p.close()
 
     # --- the FP32 path with the other preconditioner

@@ -449,6 +449,13 @@ PFE_API pfe_status pfe_solve_system(pfe_ctx *c, const double *RHS, double *Y, pf
  *                       (FSAI preconditioner set)
  *   PFE_KERNEL_FSAI_ZP_HOLD  the same launch on the other iterations, which
  *                       hold the solution update (no pass over y)
+ *   PFE_KERNEL_REPLACE  the residual replacement r = b - A y with A's FP64
+ *                       values (k_refresh; k_refresh_f with an FSAI factor),
+ *                       run on replacement iterations only
+ *   PFE_KERNEL_XFLUSH   y += alpha_prev p_prev + alpha p, applying the pending
+ *                       solution updates ahead of a replacement
+ *   PFE_KERNEL_FSAI_T   t = G r with the column dots after a replacement
+ *                       (FSAI factor set)
  * The iteration state is not modified (scratch copies and a scratch control
  * block are used; the edge pass rewrites the same right-hand side).  Only
  * the PCG direction p and product q, which every solve re-initialises, are
@@ -464,7 +471,10 @@ enum {
     PFE_KERNEL_FSAI_TR = 4,
     PFE_KERNEL_FSAI_ZP = 5,
     PFE_KERNEL_FSAI_ZP_HOLD = 6,
-    PFE_KERNEL_PUPDATE_HOLD = 7
+    PFE_KERNEL_PUPDATE_HOLD = 7,
+    PFE_KERNEL_REPLACE = 8,
+    PFE_KERNEL_XFLUSH = 9,
+    PFE_KERNEL_FSAI_T = 10
 };
 PFE_API pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_ms);
 

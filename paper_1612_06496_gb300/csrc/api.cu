@@ -1154,12 +1154,18 @@ pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_
         ms /= (float)reps;
     } else if (which == PFE_KERNEL_SPMM || which == PFE_KERNEL_UPDATE || which == PFE_KERNEL_PUPDATE ||
                which == PFE_KERNEL_FSAI_TR || which == PFE_KERNEL_FSAI_ZP || which == PFE_KERNEL_FSAI_ZP_HOLD ||
-               which == PFE_KERNEL_PUPDATE_HOLD) {
+               which == PFE_KERNEL_PUPDATE_HOLD || which == PFE_KERNEL_REPLACE || which == PFE_KERNEL_XFLUSH ||
+               which == PFE_KERNEL_FSAI_T) {
+        if (which == PFE_KERNEL_FSAI_T && (!c->fsai.enabled || c->fsai.ic))
+            return fail(c, PFE_EUNSUPPORTED, "pfe_time_kernel: k_fsai_t needs an FSAI factor");
         const int k = which == PFE_KERNEL_PUPDATE        ? 2
                       : which == PFE_KERNEL_FSAI_TR      ? 3
                       : which == PFE_KERNEL_FSAI_ZP      ? 4
                       : which == PFE_KERNEL_FSAI_ZP_HOLD ? 5
                       : which == PFE_KERNEL_PUPDATE_HOLD ? 6
+                      : which == PFE_KERNEL_REPLACE      ? 7
+                      : which == PFE_KERNEL_XFLUSH       ? 8
+                      : which == PFE_KERNEL_FSAI_T       ? 9
                                                          : which;
         PFE_TRY(time_pcg_kernel(c, c->stream, k, reps, &ms));
     } else {

@@ -2715,7 +2715,9 @@ pfe_status apply_T(pfe_ctx *c, cudaStream_t s, const void *x, void *y) {
 // the direction buffers, so the iteration state is left as it was.
 // which: 0 = k_spmm, 1 = k_update, 2 = k_pupdate folding two solution
 // updates, 3 = k_fsai_tr, 4 = k_fsai_zp folding, 5 = k_fsai_zp holding one,
-// 6 = k_pupdate holding.
+// 6 = k_pupdate holding; on a replacement iteration: 7 = the replacement
+// residual (k_refresh, or k_refresh_f with an FSAI factor), 8 = k_xflush
+// applying two pending solution updates, 9 = k_fsai_t (t = G r with the dots).
 template <typename T, int D>
 pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, int variant) {
     PcgCtl h;
@@ -2726,6 +2728,9 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
     h.p_ready = 0;
     h.xpending = 1;
     h.xfold = (which == 2 || which == 4) ? 1 : 0;  // 2, 4: the folding launch; 5, 6: the holding one
+    h.xheld = which == 8 ? 1 : 0;
+    h.refresh_now = which >= 7 ? 1 : 0;
+    h.refresh = 1 << 30;  // residual replacement on (confirmation logic), never periodic
     // scratch per-segment scalars: every column active
     const int nseg = c->nseg;
     const size_t sc_bytes = segscal_bytes(nseg, D);
@@ -2743,7 +2748,7 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
     }
     void *dsc = nullptr;
     const int64_t nd = c->g.n * (int64_t)D;
-    const bool fsai = which >= 3 && which <= 5;
+    const bool fsai = (which >= 3 && which <= 5) || which == 9 || (which == 7 && use_fsai<T>(c) && !c->fsai.ic);
     if (fsai && (!use_fsai<T>(c) || c->fsai.ic)) {
         c->err = "pfe_time_kernel: the FSAI kernels need the FSAI preconditioner on the mixed path";
         return PFE_EUNSUPPORTED;
@@ -2814,11 +2819,30 @@ pfe_status time_T(pfe_ctx *c, cudaStream_t s, int which, int reps, float *ms, in
             k_pupdate<T, D, false><<<wave_grid(c, G_PUPD, k_pupdate<T, D, false>, flat_need<T, D>(c),
                                                   flat_mult<T, D>()),
                                         kBlock, 0, s>>>(a);
-        else if constexpr (std::is_same_v<T, float>) {
+        else if (which == 7 && !fsai) {
+            // k_refresh's finisher ends the replacement: mark the next launch as one again
+            cudaMemsetAsync(&dctl->refresh_now, 1, sizeof(int), s);
             if (multi)
-                launch_fsai<T, D, true>(c, s, a, which == 3 ? 0 : 3);  // 4, 5: k_fsai_zp
+                launch_refresh<T, D, true>(c, s, a);
             else
-                launch_fsai<T, D>(c, s, a, which == 3 ? 0 : 3);
+                launch_refresh<T, D, false>(c, s, a);
+        } else if (which == 8 && multi)
+            k_xflush<T, D, true><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, true>, flat_need<T, D>(c), flat_mult<T, D>()),
+                                   kBlock, 0, s>>>(a, 0, 0);
+        else if (which == 8)
+            k_xflush<T, D, false><<<wave_grid(c, G_XFLUSH, k_xflush<T, D, false>, flat_need<T, D>(c),
+                                                 flat_mult<T, D>()),
+                                       kBlock, 0, s>>>(a, 0, 0);
+        else if constexpr (std::is_same_v<T, float>) {
+            const int kf = which == 3 ? 0 : which == 9 ? 2 : 3;  // 4, 5: k_fsai_zp
+            if (which == 7 && multi)
+                launch_refresh_f<T, D, true>(c, s, a);
+            else if (which == 7)
+                launch_refresh_f<T, D>(c, s, a);
+            else if (multi)
+                launch_fsai<T, D, true>(c, s, a, kf);
+            else
+                launch_fsai<T, D>(c, s, a, kf);
         }
     };
     launch();  // warm-up
