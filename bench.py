@@ -71,8 +71,9 @@ def parse():
 
 
 def cpu_sample_worker(arg: str):
-    """One outer iteration of the oracle (Jacobi-PCG mode) on a seeded window
-    of the workload's image, with the full image's lambda; prints JSON."""
+    """One outer iteration per step of the oracle (Jacobi-PCG mode), single
+    threaded, on one window of the workload's image with the full image's
+    lambda (or, for the batch, on one of its images); prints JSON."""
     import numpy as np
 
     from oracle import pfe_oracle as O
@@ -81,15 +82,13 @@ def cpu_sample_worker(arg: str):
     cfg = json.loads(arg)
     if cfg["workload"] == "C3":
         from synth import batch_specs
-        specs = batch_specs()
-        spec = min(specs, key=lambda s: s.n)  # the smallest image, with its own lambda
+        specs = sorted(batch_specs(), key=lambda s: s.n)
+        spec = specs[cfg["index"] % len(specs)]  # the smallest images first, each with its own lambda
         X, Y0 = make_problem(spec)
         g = O.build_grid_graph(X, spec.H, spec.W, spec.radius, spec.sigma)
     else:
         spec = CONFIGS[cfg["workload"]]
-        win_w, win_h = min(cfg["window"], spec.W), min(cfg["window"], spec.H)  # the whole image when smaller
-        x0 = (spec.W - win_w) // 2
-        y0 = (spec.H - win_h) // 2
+        x0, y0, win_w, win_h = cfg["window"]
         wspec = replace(spec, crop=(x0, y0, win_w, win_h))
         X, Y0 = make_problem(wspec)
         g = O.build_grid_graph(X, win_h, win_w, spec.radius, spec.sigma, lam=cfg["lambda"])
@@ -110,20 +109,57 @@ def cpu_sample_worker(arg: str):
     print(json.dumps({"times": times, "iters": iters, "nnz": int(nnz), "n": int(g.n)}))
 
 
+def cpu_windows(spec, window: int, count: int) -> list:
+    """`count` windows of window x window pixels (the whole image when it is
+    smaller) spread over the image on a regular grid, distinct when they fit."""
+    ww, wh = min(window, spec.W), min(window, spec.H)
+    k = 1
+    while k * k < count:
+        k += 1
+    out = []
+    for q in range(count):
+        gx, gy = q % k, q // k
+        x0 = ((spec.W - ww) * (2 * gx + 1)) // (2 * k)
+        y0 = ((spec.H - wh) * (2 * gy + 1)) // (2 * k)
+        out.append((x0, y0, ww, wh))
+    return out
+
+
+def cpu_cores() -> int:
+    return max(1, min(16, os.cpu_count() or 1))
+
+
 def run_cpu_sample(workload: str, lam: float, steps: int, window: int, nnz_full: int) -> dict:
+    """The oracle, as it stands and single threaded, on one window (the batch:
+    one image) per host core, all at once: the seconds a step of the
+    slowest one took, times nnz_A of the whole workload over the nnz_A the
+    cores processed together, estimates the seconds per outer iteration of
+    the whole workload on these cores."""
+    from synth import CONFIGS
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    arg = json.dumps({"workload": workload, "lambda": lam, "steps": steps, "window": window})
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-worker", arg],
-                       capture_output=True, text=True, env=env, cwd=ROOT)
-    if r.returncode != 0:
-        raise RuntimeError("CPU oracle sample failed:\n" + r.stderr[-2000:])
-    out = json.loads(r.stdout.strip().splitlines()[-1])
-    scale = nnz_full / out["nnz"]
-    out["scale"] = scale
-    out["per_step_scaled"] = [t * scale for t in out["times"]]
-    return out
+    spec = CONFIGS[workload]
+    whole = workload != "C3" and window >= spec.W and window >= spec.H
+    cores = 1 if whole else cpu_cores()  # an image that fits one window runs whole, on one core
+    wins = cpu_windows(spec, window, cores) if workload != "C3" else [None] * cores
+    procs = []
+    for q in range(cores):
+        arg = json.dumps({"workload": workload, "lambda": lam, "steps": steps, "window": wins[q], "index": q})
+        procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-sample-worker", arg],
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT))
+    outs = []
+    for pr in procs:
+        so, se = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError("CPU oracle sample failed:\n" + se[-2000:])
+        outs.append(json.loads(so.strip().splitlines()[-1]))
+    nnz_done = sum(o["nnz"] for o in outs)
+    scale = nnz_full / nnz_done
+    per_step = [max(o["times"][k] for o in outs) for k in range(steps)]
+    return {"times": per_step, "iters": [sum(o["iters"][k] for o in outs) / cores for k in range(steps)],
+            "nnz": nnz_done, "n": sum(o["n"] for o in outs), "scale": scale, "cores": cores,
+            "window": wins[0][2:] if wins[0] else None, "per_step_scaled": [t * scale for t in per_step]}
 
 
 # --------------------------------------------------------------------------
@@ -257,7 +293,7 @@ def run_reference(args, rank: int, world: int):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(spec, args.gpus),
         "pcg_iters_mean": sum(out["iters"][args.warmup:]) / len(timed),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": out["cores"], "kind": "oracle",
                          "sample": cpu_sample_text(spec, args.cpu_window, out)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -265,16 +301,19 @@ def run_reference(args, rank: int, world: int):
 
 
 def cpu_sample_text(spec, window: int, out: dict) -> str:
+    pcg = f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}, single threaded per process)"
     if spec.name == "C3":
-        return (f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration per step on the smallest image "
-                f"of the batch ({out['n']} pixels, its own lambda, {out['iters'][0]:.0f} PCG iterations per solve), "
-                f"scaled to the whole batch by the nnz_A ratio {out['scale']:.1f}")
-    if window >= spec.W and window >= spec.H:
-        return (f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration per step on the whole image "
-                f"({out['iters'][0]:.0f} PCG iterations per solve)")
-    return (f"oracle (FP64, Jacobi-PCG tol {spec.tol:g}) one outer iteration per step on the central "
-            f"{min(window, spec.W)}x{min(window, spec.H)} window of the same image with the full image's lambda "
-            f"({out['iters'][0]:.0f} PCG iterations per solve), scaled by nnz_A ratio {out['scale']:.1f}")
+        return (f"{pcg}, one outer iteration per step on {out['cores']} images of the batch at once (the smallest, "
+                f"each with its own lambda; {out['iters'][0]:.0f} PCG iterations per solve on average), extrapolated "
+                f"to the whole batch by nnz_A ({out['scale']:.1f}x the nonzeros the {out['cores']} cores processed)")
+    if out["scale"] <= 1.0 + 1e-12:
+        return (f"{pcg}, one outer iteration per step on the whole image ({out['iters'][0]:.0f} PCG iterations "
+                f"per solve)")
+    w, h = out["window"]
+    return (f"{pcg}, one outer iteration per step on {out['cores']} {w}x{h} windows of the same image at once (one "
+            f"per host core, spread over the image, the full image's lambda; {out['iters'][0]:.0f} PCG iterations "
+            f"per solve on average); the slowest window's time extrapolated to the whole image by nnz_A "
+            f"({out['scale']:.1f}x the nonzeros the {out['cores']} cores processed)")
 
 
 def problem_inputs(spec, rank: int, world: int):
@@ -653,10 +692,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
             out = run_cpu_sample(args.workload, info["lambda_"], 1, args.cpu_window, nnz)
-            cpu = {"value": out["per_step_scaled"][0], "unit": UNIT, "cores": 1, "kind": "oracle",
+            cpu = {"value": out["per_step_scaled"][0], "unit": UNIT, "cores": out["cores"], "kind": "oracle",
                    "sample": cpu_sample_text(spec, args.cpu_window, out) + f" ({out['times'][0]:.1f} s measured)"}
         except Exception as ex:  # report, do not hide
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+            cpu = {"value": None, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": f"failed: {ex}"}
 
     if rank == 0:
         line = {
