@@ -480,7 +480,8 @@ def main():
         elif precond == "ic0":
             p.ic0()
         p.init(Y0d)
-        tuned[precision + "/" + precond] = p.autotune(10) + p.get_variant("fsai")  # kernel variants (setup)
+        # kernel variants (setup): SpMM, FSAI column form, edge-pass column form
+        tuned[precision + "/" + precond] = p.autotune(10) + p.get_variant("fsai") + p.get_variant("edge")
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         for _ in range(warmup):
@@ -540,6 +541,7 @@ def main():
     fsai_k = {}
     fsai_arm = args.precond in ("learned", "classical")  # the FSAI kernels run (any factor G)
     fsai_cols = tuned.get("mixed/" + args.precond, (0, {}, 0, None))[2]  # 1: columns computed from the stencil
+    edge_cols = tuned.get("mixed/" + args.precond, (0, {}, 0, None, 0, None))[4]  # 1: edge pass from the stencil
     if fsai_arm:
         # lower (upper) slots: FP32 G value (+ int32 column unless computed
         # from the stencil) each, G_ii per row; t = G r': r, q in, r', t out;
@@ -608,9 +610,11 @@ def main():
                                   "k_pupdate_hold_ms": round(puph_ms, 5),
                                   "k_pupdate_hold_GBps": round(puph_b / (puph_ms * 1e-3) / 1e9, 1),
                                   "k_edge_ms": round(edge_ms, 5),
-                                  # b read + written (FP32), w, column + edge id per directed slot, Y, C in, RHS out
-                                  "k_edge_GBps": round((8 * d * ne + 4 * ne + 8 * 2 * ne + 12 * n * d)
-                                                       / (edge_ms * 1e-3) / 1e9, 1),
+                                  # b read + written (FP32), w, column + edge id per directed slot (none
+                                  # when computed from the stencil), Y, C in, RHS out
+                                  "k_edge_columns": "stencil" if edge_cols == 1 else "slots",
+                                  "k_edge_GBps": round((8 * d * ne + 4 * ne + (0 if edge_cols == 1 else 8 * 2 * ne)
+                                                        + 12 * n * d) / (edge_ms * 1e-3) / 1e9, 1),
                                   "replacement_residual_ms": round(repl_ms, 5), "k_xflush_ms": round(xfl_ms, 5),
                                   **fsai_k}}
     # after the timings: the next system of Eq. 13 solved from its warm start
@@ -726,6 +730,9 @@ def main():
                              "fsai_columns": {0: "slots", 1: "stencil"}[v[2]] if v[3] is not None and v[3][0] > 0
                              else None,
                              "fsai_ms": [round(float(x), 5) for x in v[3]] if v[3] is not None and v[3][0] > 0
+                             else None,
+                             "edge_columns": {0: "slots", 1: "stencil"}[v[4]],
+                             "edge_ms": [round(float(x), 5) for x in v[5]] if v[5] is not None and v[5][0] > 0
                              else None}
                          for k, v in tuned.items()},
             "gpu_launches": launches,

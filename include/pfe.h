@@ -214,7 +214,10 @@ PFE_API pfe_status pfe_init(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY
  *    batch only PFE_SPMM_ROW1 at radius 2);
  *  - with an FSAI factor set (pfe_fsai_set, pfe_fsai_classical) on one FP32
  *    grid image of radius 2 or 3: the column form of the FSAI kernels
- *    (PFE_TUNE_FSAI), timed as one iteration's k_fsai_tr and k_fsai_zp.
+ *    (PFE_TUNE_FSAI), timed as one iteration's k_fsai_tr and k_fsai_zp;
+ *  - on one FP32 grid image of radius 2: the edge pass's column form
+ *    (PFE_TUNE_EDGE), slot arrays or the stencil (Sec. III's memory
+ *    argument: the structured grid needs no stored columns).
  * Every variant of a kernel adds the same products in the same order, so
  * the choice changes the time, not the results.  choice[0] receives the
  * chosen SpMM variant and ms[v] (at least PFE_SPMM_NVARIANTS entries; either
@@ -241,16 +244,23 @@ enum {
     PFE_SPMM_GRID2 = 7,   /* the same, two row groups per step */
     PFE_SPMM_NVARIANTS = 8
 };
-enum { PFE_TUNE_SPMM = 0, PFE_TUNE_FSAI = 1 };
+enum { PFE_TUNE_SPMM = 0, PFE_TUNE_FSAI = 1, PFE_TUNE_EDGE = 2 };
 enum {
     PFE_FSAI_SLOTS = 0,   /* FSAI kernels read each slot's column */
     PFE_FSAI_STENCIL = 1  /* one grid image: the columns are computed from the stencil */
 };
+enum {
+    PFE_EDGE_SLOTS = 0,   /* edge pass reads each slot's column and edge id */
+    PFE_EDGE_STENCIL = 1  /* one FP32 grid image of radius 2: the neighbour and the edge's Bregman
+                             slot of every slot are computed from the stencil (only the weights
+                             are read) */
+};
 PFE_API pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms);
 PFE_API pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant);
-/* pfe_get_variant -- the current choice for `kernel` (PFE_TUNE_SPMM or
- * PFE_TUNE_FSAI); for PFE_TUNE_FSAI, ms (2 entries, may be NULL) receives the
- * two column forms' times from the last pfe_autotune (-1 if not tuned). */
+/* pfe_get_variant -- the current choice for `kernel` (PFE_TUNE_SPMM,
+ * PFE_TUNE_FSAI or PFE_TUNE_EDGE); for PFE_TUNE_FSAI and PFE_TUNE_EDGE, ms
+ * (2 entries, may be NULL) receives the two column forms' times from the
+ * last pfe_autotune (-1 if not tuned). */
 PFE_API pfe_status pfe_get_variant(pfe_ctx *c, int32_t kernel, int32_t *variant, double *ms);
 
 /*
@@ -457,7 +467,8 @@ PFE_API pfe_status pfe_solve_system(pfe_ctx *c, const double *RHS, double *Y, pf
  *   PFE_KERNEL_FSAI_T   t = G r with the column dots after a replacement
  *                       (FSAI factor set)
  * The iteration state is not modified (scratch copies and a scratch control
- * block are used; the edge pass rewrites the same right-hand side).  Only
+ * block are used; the timed edge passes write the spare b buffer and a
+ * scratch right-hand side).  Only
  * the PCG direction p and product q, which every solve re-initialises, are
  * overwritten.  Synchronises; allocates temporary device memory.  Returns
  * PFE_EUNSUPPORTED for an FSAI kernel without the FSAI preconditioner set,

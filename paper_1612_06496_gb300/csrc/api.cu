@@ -556,6 +556,48 @@ static bool fsai_variant_applies(const pfe_ctx *c, int v) {
            (c->g.row_len == 12 || c->g.row_len == 28);
 }
 
+// The edge-pass column forms that apply: slot arrays always; the stencil on
+// one FP32 grid image of 12 slots a row.
+static bool edge_variant_applies(const pfe_ctx *c, int v) {
+    if (v == PFE_EDGE_SLOTS) return true;
+    return v == PFE_EDGE_STENCIL && c->mixed && c->nseg == 1 && c->kind == PFE_GRAPH_GRID && c->W > 0 &&
+           c->g.row_len == 12;
+}
+
+// Average time of `reps` edge passes on the current state.  The passes write
+// the spare b buffer (which the next edge pass rewrites) and, instead of the
+// right-hand side of the next solve, the FP64 staging buffer (n x d, large
+// enough for either precision), so the iteration state is left as it was.
+static pfe_status time_edge(pfe_ctx *c, int reps, float *ms) {
+    cudaEvent_t e0, e1;
+    PFE_CUDA_TRY(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, PFE_ECUDA, "cudaEventCreate failed");
+    }
+    const int cur = c->bs_cur;
+    void *rhs = c->wk.RHS;
+    c->wk.RHS = c->wk.stage;
+    pfe_status st = launch_edge(c, c->stream);
+    c->bs_cur = cur;
+    cudaEventRecord(e0, c->stream);
+    for (int k = 0; k < reps && st == PFE_OK; ++k) {
+        st = launch_edge(c, c->stream);
+        c->bs_cur = cur;
+    }
+    c->wk.RHS = rhs;
+    cudaEventRecord(e1, c->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PFE_OK) return st;
+    if (e != cudaSuccess) return fail(c, PFE_ECUDA, cudaGetErrorString(e));
+    *ms = t / (float)reps;
+    return PFE_OK;
+}
+
 static void set_fsai_variant(pfe_ctx *c, int v) {
     c->fsai_variant = v;
     for (int slot : {G_FSAI_TR, G_FSAI_T, G_FSAI_T1, G_FSAI_ZP}) c->kgrid[slot] = 0;  // occupancy differs
@@ -600,6 +642,14 @@ pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms) {
         c->fsai_tune_ms[0] = tv[0];
         c->fsai_tune_ms[1] = tv[1];
     }
+    // the edge pass's column form
+    if (edge_variant_applies(c, PFE_EDGE_STENCIL)) {
+        for (int v = 0; v < 2; ++v) {
+            c->edge_variant = v;
+            PFE_TRY(time_edge(c, reps, &c->edge_tune_ms[v]));
+        }
+        c->edge_variant = c->edge_tune_ms[1] < c->edge_tune_ms[0] ? PFE_EDGE_STENCIL : PFE_EDGE_SLOTS;
+    }
     return PFE_OK;
 }
 
@@ -613,6 +663,12 @@ pfe_status pfe_get_variant(pfe_ctx *c, int32_t kernel, int32_t *variant, double 
             ms[0] = c->fsai_tune_ms[0];
             ms[1] = c->fsai_tune_ms[1];
         }
+    } else if (kernel == PFE_TUNE_EDGE) {
+        *variant = c->edge_variant;
+        if (ms) {
+            ms[0] = c->edge_tune_ms[0];
+            ms[1] = c->edge_tune_ms[1];
+        }
     } else {
         return PFE_EINVAL;
     }
@@ -621,6 +677,14 @@ pfe_status pfe_get_variant(pfe_ctx *c, int32_t kernel, int32_t *variant, double 
 
 pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant) {
     if (!c) return PFE_EINVAL;
+    if (kernel == PFE_TUNE_EDGE) {
+        if (variant < 0 || variant > PFE_EDGE_STENCIL) return PFE_EINVAL;
+        if (!edge_variant_applies(c, variant))
+            return fail(c, PFE_EUNSUPPORTED, "edge-pass column form does not apply here");
+        PFE_TRY(sync(c));
+        c->edge_variant = variant;
+        return PFE_OK;
+    }
     if (kernel == PFE_TUNE_FSAI) {
         if (variant < 0 || variant > PFE_FSAI_STENCIL) return PFE_EINVAL;
         if (!fsai_variant_applies(c, variant))
@@ -1131,27 +1195,7 @@ pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_
     PFE_TRY(sync(c));
     float ms = 0.f;
     if (which == PFE_KERNEL_EDGE) {
-        // the edge pass is idempotent while its inputs (Y, old b, C) are unchanged:
-        // repeated launches rewrite the same right-hand side and spare b buffer
-        cudaEvent_t e0, e1;
-        PFE_CUDA_TRY(c, cudaEventCreate(&e0));
-        PFE_CUDA_TRY(c, cudaEventCreate(&e1));
-        const int cur = c->bs_cur;
-        pfe_status st = launch_edge(c, c->stream);
-        c->bs_cur = cur;
-        cudaEventRecord(e0, c->stream);
-        for (int k = 0; k < reps && st == PFE_OK; ++k) {
-            st = launch_edge(c, c->stream);
-            c->bs_cur = cur;
-        }
-        cudaEventRecord(e1, c->stream);
-        cudaError_t e = cudaEventSynchronize(e1);
-        cudaEventElapsedTime(&ms, e0, e1);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        if (st != PFE_OK) return st;
-        if (e != cudaSuccess) return fail(c, PFE_ECUDA, cudaGetErrorString(e));
-        ms /= (float)reps;
+        PFE_TRY(time_edge(c, reps, &ms));
     } else if (which == PFE_KERNEL_SPMM || which == PFE_KERNEL_UPDATE || which == PFE_KERNEL_PUPDATE ||
                which == PFE_KERNEL_FSAI_TR || which == PFE_KERNEL_FSAI_ZP || which == PFE_KERNEL_FSAI_ZP_HOLD ||
                which == PFE_KERNEL_PUPDATE_HOLD || which == PFE_KERNEL_REPLACE || which == PFE_KERNEL_XFLUSH ||

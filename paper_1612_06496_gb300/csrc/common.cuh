@@ -297,7 +297,7 @@ __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
 enum GridSlot {
     G_INIT = 0, G_INIT_F, G_PUPD, G_SPMM, G_UPDATE, G_FSAI_TR, G_XFLUSH, G_REFRESH, G_REFRESH_F,
     G_FSAI_T, G_FSAI_T1, G_FSAI_ZP, G_APPLY, G_EDGE, G_PAPPLY, G_TIME_SPMM, G_TIME_UPDATE, G_SPMM_F1, G_SPMM_F2,
-    G_SPMM_F3, G_SPMM_TMA, G_SPMM_STENCIL, G_IC_R, G_IC_DOTS, G_SPMM_G1, G_SPMM_G2, G_NSLOTS
+    G_SPMM_F3, G_SPMM_TMA, G_SPMM_STENCIL, G_IC_R, G_IC_DOTS, G_SPMM_G1, G_SPMM_G2, G_EDGE_GRID, G_NSLOTS
 };
 // Strip width of the stencil SpMM pipeline for d columns, rows of len
 // slots (radius 2: 12, radius 3: 28) and p steps in flight: the widest

@@ -35,6 +35,7 @@ struct EdgeArgs {
     T lambda, gamma;
     Segs sg;                // batch: lambda of each row's segment
     const double *seg_lam;  // nseg
+    int grid_w, grid_h;     // one grid image: its width and height (0 otherwise)
 };
 
 template <typename T, int V>
@@ -208,9 +209,69 @@ __device__ __forceinline__ void edge_half(const EdgeArgs<T> &a, int64_t base, in
     }
 }
 
+// edge_half on one grid image without the column and edge-id arrays: slot t
+// of row i = (x, y) is stencil offset (dx_t, dy_t), its neighbour j = i +
+// dy_t W + dx_t when (x + dx_t, y + dy_t) lies in the image (else a padding
+// slot), and the edge's b slot follows from the fixed forward positions of
+// the graph builder: i K/2 + (t - K/2) for a forward slot (i owns the edge),
+// j K/2 + (K - 1 - t - K/2) for a backward one (j owns it through the
+// reverse offset K - 1 - t).  Only the weights are loaded; the products are
+// those of edge_half, in the same order.
+template <typename T, int D, int V, int P0, int P1, bool FIRST, int LEN>
+__device__ __forceinline__ void edge_half_grid(const EdgeArgs<T> &a, int i, int x, int y, int c0,
+                                               const T (&yi)[V], T gam, T (&acc)[V]) {
+    static_assert(sizeof(T) == 4, "the float path");
+    constexpr Stencil<LEN> st = make_stencil<LEN>();
+    constexpr int KH = LEN / 2;
+    constexpr int A0 = P0 & ~3, A1 = (P1 + 3) & ~3, NG = A1 - A0, NS = P1 - P0;
+    const int64_t base = (int64_t)i * LEN;
+    T ww[NG];
+#pragma unroll
+    for (int g4 = 0; g4 < NG / 4; ++g4) {
+        const float4 w4 = __ldg(reinterpret_cast<const float4 *>(a.w + base + A0 + 4 * g4));
+        ww[4 * g4] = w4.x; ww[4 * g4 + 1] = w4.y; ww[4 * g4 + 2] = w4.z; ww[4 * g4 + 3] = w4.w;
+    }
+    int jj[NS], ee[NS];
+    bool ok[NS];
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+        const int t = P0 + u;
+        const int dx = st.dx[t], dy = st.dy[t];
+        ok[u] = (unsigned)(x + dx) < (unsigned)a.grid_w && (unsigned)(y + dy) < (unsigned)a.grid_h;
+        const int j = i + dy * a.grid_w + dx;
+        jj[u] = ok[u] ? j : i;
+        ee[u] = ok[u] ? (FIRST ? i * KH + (t - KH) : j * KH + (LEN - 1 - t - KH)) : 0;  // padding: a valid dummy
+    }
+    T yj[NS][V], bo[NS][V];
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+        eldv<T, V>(a.y + (int64_t)jj[u] * D + c0, yj[u]);
+        eldv<T, V>(a.bs_old + (int64_t)ee[u] * D + c0, bo[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+        const int q = P0 - A0 + u;
+        if (!ok[u]) continue;  // padding slot
+        T bn[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const T diff = FIRST ? (yi[k] - yj[u][k]) : (yj[u][k] - yi[k]);  // y_a - y_b
+            const T t = ww[q] * diff + bo[u][k];                              // (M Y + b)_e
+            const T z = shrink<T>(t, gam);                                    // d_e
+            bn[k] = t - z;                                                    // b'_e
+            const T v = ww[q] * (z - bn[k]);
+            acc[k] = FIRST ? acc[k] + v : acc[k] - v;
+        }
+        if (FIRST) estv<T, V>(a.bs_new + (int64_t)ee[u] * D + c0, bn);
+    }
+}
+
 // The edge pass on fixed-position rows of LEN slots (grid graphs): the same
-// arithmetic as k_edge, each half of a row as straight-line code.
-template <typename T, int D, bool MS, int LEN>
+// arithmetic as k_edge, each half of a row as straight-line code.  GRID (one
+// grid image, the float path): the columns and edge ids come from the
+// stencil (edge_half_grid), so only the weights, y, b, C and the right-hand
+// side move.
+template <typename T, int D, bool MS, int LEN, bool GRID = false>
 __global__ void __launch_bounds__(kBlock, 4) k_edge_fixed(EdgeArgs<T> a) {
     constexpr int V = (sizeof(T) == 4 && D % 4 == 0) ? 4 : (D % 2 == 0 ? 2 : 1);
     constexpr int L = D / V, RPW = 32 / L;
@@ -233,8 +294,15 @@ __global__ void __launch_bounds__(kBlock, 4) k_edge_fixed(EdgeArgs<T> a) {
         eldv<T, V>(a.y + i * D + c0, yi);
 #pragma unroll
         for (int k = 0; k < V; ++k) acc[k] = T(0);
-        edge_half<T, D, V, 0, LEN / 2, false>(a, base, c0, yi, gam, acc);
-        edge_half<T, D, V, LEN / 2, LEN, true>(a, base, c0, yi, gam, acc);
+        if constexpr (GRID) {
+            static_assert(!MS, "computed columns: one image");
+            const int ii = (int)i, y = ii / a.grid_w, x = ii - y * a.grid_w;
+            edge_half_grid<T, D, V, 0, LEN / 2, false, LEN>(a, ii, x, y, c0, yi, gam, acc);
+            edge_half_grid<T, D, V, LEN / 2, LEN, true, LEN>(a, ii, x, y, c0, yi, gam, acc);
+        } else {
+            edge_half<T, D, V, 0, LEN / 2, false>(a, base, c0, yi, gam, acc);
+            edge_half<T, D, V, LEN / 2, LEN, true>(a, base, c0, yi, gam, acc);
+        }
         T ci[V];
         eldv<T, V>(a.cw + i * D + c0, ci);
 #pragma unroll
@@ -265,6 +333,9 @@ pfe_status edge_T(pfe_ctx *c, cudaStream_t s) {
     a.gamma = (T)(1.0 / c->lambda);
     a.sg = seg_view(c);
     a.seg_lam = c->seg_lam;
+    const bool one_grid = c->kind == PFE_GRAPH_GRID && c->nseg == 1;
+    a.grid_w = one_grid ? (int)c->W : 0;
+    a.grid_h = one_grid ? (int)(c->g.n / c->W) : 0;
     constexpr int V = (sizeof(T) == 4 && D % 4 == 0) ? 4 : (D % 2 == 0 ? 2 : 1);
     constexpr int RPW = 32 / (D / V);
     const int64_t need = ((c->g.n + RPW - 1) / RPW + kWarps - 1) / kWarps;
@@ -277,6 +348,16 @@ pfe_status edge_T(pfe_ctx *c, cudaStream_t s) {
         else
             k_edge<T, D, true><<<wave_grid(c, G_EDGE, k_edge<T, D, true>, need), kBlock, 0, s>>>(a);
     } else {
+        if constexpr (std::is_same_v<T, float>) {
+            if (rl == 12 && one_grid && c->edge_variant == PFE_EDGE_STENCIL) {
+                k_edge_fixed<T, D, false, 12, true><<<wave_grid(c, G_EDGE_GRID, k_edge_fixed<T, D, false, 12, true>,
+                                                                need),
+                                                      kBlock, 0, s>>>(a);
+                PFE_CUDA_TRY(c, cudaGetLastError());
+                c->bs_cur = 1 - c->bs_cur;
+                return PFE_OK;
+            }
+        }
         if (rl == 12)
             k_edge_fixed<T, D, false, 12><<<wave_grid(c, G_EDGE, k_edge_fixed<T, D, false, 12>, need), kBlock, 0,
                                             s>>>(a);

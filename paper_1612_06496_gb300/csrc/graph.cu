@@ -76,13 +76,16 @@ __global__ void k_grid_count(int64_t n, int64_t n_slices, GridSegs gs, Offsets o
         nf_row[i] = nf;
     }
     (void)nb;
-    int mf = __reduce_max_sync(0xffffffffu, nf);
     if ((threadIdx.x & 31) == 0) {
         int64_t s = i >> 5;
         // fixed positions: slot t of every row is stencil offset t (K is a
-        // multiple of 4: the offsets come in orbits of the 90-degree rotation)
+        // multiple of 4: the offsets come in orbits of the 90-degree rotation),
+        // and so is the Bregman slot of each forward edge: forward offset t of
+        // row i owns b slot i K/2 + (t - K/2) (a slot whose offset leaves the
+        // image is unused), so a kernel finds any edge's b slot from the
+        // stencil alone
         slice_len[s] = off.K * 32;
-        fslice_len[s] = mf * 32;
+        fslice_len[s] = (off.K / 2) * 32;
     }
 }
 
@@ -116,25 +119,19 @@ __global__ void k_grid_fill(int64_t n, int64_t n_slices, GridSegs gs, Offsets of
             int64_t j = vo + (int64_t)y2 * W + x2;
             double w = (j > i) ? heat_weight(X, m, i, j, inv2s2) : heat_weight(X, m, j, i, inv2s2);
             int e;
-            if (t >= off.K / 2) {  // forward: i owns the edge
-                e = (int)(fslice_ptr[s] + (int64_t)lane * flen + kf);
-                int64_t ext = fw_off[i] + kf;
+            if (t >= off.K / 2) {  // forward: i owns the edge, at its slot for offset t
+                e = (int)(fslice_ptr[s] + (int64_t)lane * flen + (t - off.K / 2));
+                int64_t ext = fw_off[i] + kf;  // external numbering: i's valid forward edges in order
                 ext_slot[ext] = e;
                 ea[ext] = (int)i;
                 eb[ext] = (int)j;
                 ew[ext] = w;
                 ++kf;
-            } else {  // backward: j owns it; its rank among j's forward edges
-                int tr = off.K - 1 - t;  // index of the reverse offset
-                int rank = 0;
-                int xj = x2, yj = y2;
-                for (int u = off.K / 2; u < tr; ++u) {
-                    int x3 = xj + off.dx[u], y3 = yj + off.dy[u];
-                    if (x3 >= 0 && x3 < W && y3 >= 0 && y3 < H) ++rank;
-                }
+            } else {  // backward: j owns it, at j's slot for the reverse offset
+                const int tr = off.K - 1 - t;  // index of the reverse offset
                 const int64_t sj = j >> 5;
                 const int flj = (int)((fslice_ptr[sj + 1] - fslice_ptr[sj]) >> 5);
-                e = (int)(fslice_ptr[sj] + (int64_t)(j & 31) * flj + rank);
+                e = (int)(fslice_ptr[sj] + (int64_t)(j & 31) * flj + (tr - off.K / 2));
             }
             col[idx] = (int)j;
             eid[idx] = e;

@@ -174,6 +174,8 @@ struct pfe_ctx {
     int64_t work_bytes = 0;  // the part of it in work_allocs
     int spmm_variant = PFE_SPMM_ROW1;  // SpMM kernel variant (pfe_autotune)
     int fsai_variant = PFE_FSAI_SLOTS; // FSAI kernels' column form (pfe_autotune)
+    int edge_variant = PFE_EDGE_SLOTS; // edge pass: slot columns and edge ids, or from the stencil (pfe_autotune)
+    float edge_tune_ms[2] = {-1.f, -1.f};
     float fsai_tune_ms[2] = {-1.f, -1.f};
     int le_iters = 0;                 // last Laplacian-eigenmap computation
     double le_residual = 0.0;

@@ -677,7 +677,7 @@ __device__ __forceinline__ void df_add_prod2(DF &acc, float ah, float al, float 
 // FP64 system matrix (not of the FP32 rounding the iteration's q = A p uses)
 // to about 2^-44 of |A||y|.  FP64 path: plain FP64.  LEN > 0: uniform rows
 // of LEN slots (row i's at i * LEN), loaded as vectors.
-template <typename T, int D, int V, int LEN = 0>
+template <typename T, int D, int V, int LEN = 0, bool GRID = false>
 __device__ __forceinline__ void true_residual(const PcgArgs<T> &a, int64_t i, int c0, T (&out)[V]) {
     T bi[V];
     ldv_rw<T, V>(a.b + i * D + c0, bi);
@@ -697,9 +697,15 @@ __device__ __forceinline__ void true_residual(const PcgArgs<T> &a, int64_t i, in
             const int4 *c4 = reinterpret_cast<const int4 *>(a.A.col + i * LEN);
             const float4 *h4 = reinterpret_cast<const float4 *>(a.A.aoff + i * LEN);
             const float4 *l4 = reinterpret_cast<const float4 *>(a.A.aofflo + i * LEN);
+            int jall[GRID ? LEN : 1];  // GRID: every slot's column from the stencil (one grid image)
+            if constexpr (GRID) stencil_cols<LEN, 0>((int)i, a.grid_w, (int)a.A.n, jall);
 #pragma unroll
             for (int q = 0; q < LEN / 4; ++q) {
-                const int4 jc = __ldg(c4 + q);
+                int4 jc;
+                if constexpr (GRID)
+                    jc = make_int4(jall[4 * q], jall[4 * q + 1], jall[4 * q + 2], jall[4 * q + 3]);
+                else
+                    jc = __ldg(c4 + q);
                 const float4 vh = __ldg(h4 + q), vl = __ldg(l4 + q);
                 const int jj[4] = {jc.x, jc.y, jc.z, jc.w};
                 const float sh[4] = {vh.x, vh.y, vh.z, vh.w}, sl[4] = {vl.x, vl.y, vl.z, vl.w};
@@ -1772,7 +1778,7 @@ __global__ void __launch_bounds__(kBlock) k_xflush(PcgArgs<T> a, int final_flush
 // replacement iterations).  It also measures how far the true residual lies
 // from the recurrence residual r - alpha q it replaces (|r - r_rec|^2 /
 // |r_rec|^2 per column -> sc.devr, for the restart test).
-template <typename T, int D, int LEN, bool MS>
+template <typename T, int D, int LEN, bool MS, bool GRID = false>
 __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
     if (*(volatile int *)&a.ctl->done || !*(volatile int *)&a.ctl->refresh_now) return;
     const int par = a.ctl->iter & 1;
@@ -1792,7 +1798,7 @@ __global__ void __launch_bounds__(kBlock) k_refresh_f(PcgArgs<T> a) {
         T ri[V], ro[V], qi[V];
         ldv<T, V>(rold + i * D + c0, ro);
         ldv<T, V>(a.q + i * D + c0, qi);
-        true_residual<T, D, V, LEN>(a, i, c0, ri);
+        true_residual<T, D, V, LEN, GRID>(a, i, c0, ri);
         stv<T, V>(rdst + i * D + c0, ri);
 #pragma unroll
         for (int k = 0; k < V; ++k) {
@@ -2285,7 +2291,7 @@ __global__ void __launch_bounds__(kBlock) k_ic_bwd(PcgArgs<T> a, int64_t level, 
 // iteration with the true residual.  Also |r - r_rec|^2, the squared
 // distance of the true residual from the recurrence residual k_update left
 // in r (its |r_rec|^2 is in sc.rec2), for the restart test.
-template <typename T, int D, bool MS, int LEN>
+template <typename T, int D, bool MS, int LEN, bool GRID = false>
 __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
     if (!*(volatile int *)&a.ctl->refresh_now) return;
     using A = Acc<T>;
@@ -2301,7 +2307,7 @@ __global__ void __launch_bounds__(kBlock) k_refresh(PcgArgs<T> a) {
         const int c0 = lm.cg * V;
         T ri[V], rr[V];
         ldv_rw<T, V>(a.r + i * D + c0, rr);
-        true_residual<T, D, V, LEN>(a, i, c0, ri);
+        true_residual<T, D, V, LEN, GRID>(a, i, c0, ri);
         const T dv = a.A.dinv[i];
 #pragma unroll
         for (int k = 0; k < V; ++k) {
@@ -2479,8 +2485,23 @@ static pfe_status if_end(pfe_ctx *c, const PcgLaunch &L) {
 
 // The replacement kernels with the compile-time row length of fixed-length
 // layouts (12 or 28 slots), else the general slot loop.
+// On one FP32 grid image the replacement residual computes the slot columns
+// from the stencil (the same products in the same order as with the column
+// array), so no per-iteration kernel of that path reads the column array.
 template <typename T, int D, bool MS>
 void launch_refresh(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a) {
+    if constexpr (!MS && std::is_same_v<T, float>) {
+        if (a.grid_w > 0 && c->g.row_len == 12) {
+            k_refresh<T, D, MS, 12, true><<<wave_grid(c, G_REFRESH, k_refresh<T, D, MS, 12, true>, rows_need<T, D>(c)),
+                                            kBlock, 0, s>>>(a);
+            return;
+        }
+        if (a.grid_w > 0 && c->g.row_len == 28) {
+            k_refresh<T, D, MS, 28, true><<<wave_grid(c, G_REFRESH, k_refresh<T, D, MS, 28, true>, rows_need<T, D>(c)),
+                                            kBlock, 0, s>>>(a);
+            return;
+        }
+    }
     if (c->g.row_len == 12)
         k_refresh<T, D, MS, 12><<<wave_grid(c, G_REFRESH, k_refresh<T, D, MS, 12>, rows_need<T, D>(c)), kBlock, 0, s>>>(a);
     else if (c->g.row_len == 28)
@@ -2490,6 +2511,20 @@ void launch_refresh(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a) {
 }
 template <typename T, int D, bool MS = false>
 void launch_refresh_f(pfe_ctx *c, cudaStream_t s, const PcgArgs<T> &a) {
+    if constexpr (!MS) {
+        if (a.grid_w > 0 && c->g.row_len == 12) {
+            k_refresh_f<T, D, 12, MS, true><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 12, MS, true>,
+                                                        rows_need<T, D>(c)),
+                                              kBlock, 0, s>>>(a);
+            return;
+        }
+        if (a.grid_w > 0 && c->g.row_len == 28) {
+            k_refresh_f<T, D, 28, MS, true><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 28, MS, true>,
+                                                        rows_need<T, D>(c)),
+                                              kBlock, 0, s>>>(a);
+            return;
+        }
+    }
     if (c->g.row_len == 12)
         k_refresh_f<T, D, 12, MS><<<wave_grid(c, G_REFRESH_F, k_refresh_f<T, D, 12, MS>, rows_need<T, D>(c)), kBlock, 0,
                                     s>>>(a);

@@ -31,7 +31,7 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_get_segment_stats", "pfe_laplacian_eigenmap", "pfe_objective", "pfe_autotune",
            "pfe_set_variant", "pfe_solve_two_stage", "pfe_kmeans", "pfe_residual", "pfe_get_variant"]
 SPMM_NVARIANTS = 8  # PFE_SPMM_GENERAL, _ROW1, _ROW2, _ROW2_4, _TMA, _STENCIL, _GRID1, _GRID2
-TUNE = {"spmm": 0, "fsai": 1}
+TUNE = {"spmm": 0, "fsai": 1, "edge": 2}
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3, "fsai_tr": 4, "fsai_zp": 5, "fsai_zp_hold": 6,
           "pupdate_hold": 7, "replace": 8, "xflush": 9, "fsai_t": 10}
 
@@ -291,7 +291,8 @@ class PFE:
         self._check(self.lib.pfe_set_variant(self.ctx, int(kernel), int(variant)), "pfe_set_variant")
 
     def get_variant(self, kernel: int | str = 0):
-        """(current variant, timings of the FSAI column forms from the last autotune or None)."""
+        """(current variant, timings of the column forms from the last autotune
+        (the FSAI kernels or the edge pass), or None for the SpMM)."""
         kernel = TUNE.get(kernel, kernel) if isinstance(kernel, str) else kernel
         v = C.c_int32()
         ms = np.full(2, -1.0)

@@ -131,3 +131,72 @@ def test_stencil_spmm_needs_aligned_rows():
     choice, ms = p.autotune(3)
     assert 5 not in ms and choice != 5
     p.close()
+
+
+@pytest.mark.parametrize("H,W,d", [(64, 64, 10), (41, 100, 10), (2, 50, 3), (40, 3, 5), (19, 530, 4), (23, 29, 7)])
+def test_edge_pass_from_the_stencil_equals_slot_arrays_bitwise(H, W, d):
+    """The edge pass with each slot's neighbour and its edge's Bregman slot
+    computed from the stencil (no column or edge-id array read) forms the
+    same products in the same order as with the slot arrays: three inner
+    steps give bit-identical Y, b and right-hand sides (an image shorter and
+    one narrower than the stencil, ragged widths, odd d)."""
+    spec = small_spec(H=H, W=W, d=d)
+    out = []
+    for v in (0, 1):
+        p, X, Y0 = gpu_problem(spec, "mixed")
+        p.init(Y0)
+        p.set_variant(v, "edge")
+        assert p.get_variant("edge")[0] == v
+        for _ in range(3):
+            p.inner_step()
+        out.append((p.get("Y"), p.get("BS"), p.get("RHS")))
+        p.close()
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_edge_column_form_applies_to_one_fp32_radius2_image():
+    """The stencil form of the edge pass needs one FP32 grid image of radius
+    2 (12 slots a row): elsewhere choosing it is PFE_EUNSUPPORTED and the
+    autotuner keeps the slot arrays; there it times both and keeps the
+    faster."""
+    from paper_1612_06496_gb300 import PFEError
+    for precision, radius in (("fp64", 2.0), ("mixed", 3.0)):
+        spec = small_spec(H=20, W=24, d=4, radius=radius)
+        p, X, Y0 = gpu_problem(spec, precision)
+        p.init(Y0)
+        with pytest.raises(PFEError) as ei:
+            p.set_variant(1, "edge")
+        assert ei.value.status == 8
+        p.autotune(3)
+        assert p.get_variant("edge")[0] == 0
+        p.close()
+    spec = small_spec(H=40, W=44, d=6)
+    p, X, Y0 = gpu_problem(spec, "mixed")
+    p.init(Y0)
+    p.autotune(3)
+    v, ms = p.get_variant("edge")
+    assert v in (0, 1) and np.all(ms > 0) and ms[v] == ms.min()
+    p.close()
+
+
+def test_timing_the_edge_pass_leaves_the_iteration_state():
+    """Timing the edge pass (pfe_time_kernel, and the autotuner's edge-form
+    choice) right after pfe_init writes neither the first solve's
+    right-hand side nor b: the solve that follows is bit for bit the one
+    without the timing."""
+    spec = small_spec(H=30, W=34, d=6)
+    out = []
+    for timed in (False, True):
+        p, X, Y0 = gpu_problem(spec, "mixed")
+        p.init(Y0)
+        if timed:
+            p.time_kernel("edge", 3)
+            p.set_variant(1, "edge")
+            p.time_kernel("edge", 3)
+            p.set_variant(0, "edge")
+        Y = np.empty_like(Y0)
+        p.solve(1, 3, Y, None)
+        out.append(Y)
+        p.close()
+    np.testing.assert_array_equal(out[0], out[1])
