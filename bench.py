@@ -468,6 +468,7 @@ def main():
     Y0d = torch.from_numpy(Y0).cuda()
 
     tuned = {}
+    shapes = {}  # launch shapes chosen by the autotuner, per arm
 
     def run_arm(precision: str, warmup: int, steps: int, clocks: bool, precond: str = "jacobi"):
         t0 = time.perf_counter()
@@ -482,6 +483,10 @@ def main():
         p.init(Y0d)
         # kernel variants (setup): SpMM, FSAI column form, edge-pass column form
         tuned[precision + "/" + precond] = p.autotune(10) + p.get_variant("fsai") + p.get_variant("edge")
+        shapes[precision + "/" + precond] = {
+            k: p.get_shape(k) for k in ["spmm", "edge"] + (
+                ["fsai_tr", "fsai_zp"] if precond in ("learned", "classical") else
+                ["update", "pupdate"] if precond == "jacobi" else [])}
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         for _ in range(warmup):
@@ -732,6 +737,9 @@ def main():
                              "fsai_ms": [round(float(x), 5) for x in v[3]] if v[3] is not None and v[3][0] > 0
                              else None,
                              "edge_columns": {0: "slots", 1: "stencil"}[v[4]],
+                             # blocks per SM of each row kernel (0: its occupancy) and the times tried
+                             "blocks_per_sm": {kk: {"chosen": b, "ms": {str(bb): round(t, 5) for bb, t in m.items()}}
+                                               for kk, (b, m) in shapes.get(k, {}).items()},
                              "edge_ms": [round(float(x), 5) for x in v[5]] if v[5] is not None and v[5][0] > 0
                              else None}
                          for k, v in tuned.items()},

@@ -264,6 +264,30 @@ PFE_API pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant);
 PFE_API pfe_status pfe_get_variant(pfe_ctx *c, int32_t kernel, int32_t *variant, double *ms);
 
 /*
+ * Launch shapes.  Besides the variants above, pfe_autotune chooses the grid
+ * of each row kernel that the configured iteration runs -- the SpMM (its
+ * current variant, except the stencil form, which sizes its own grid), and
+ * k_update and k_pupdate (Jacobi) or k_fsai_tr and k_fsai_zp (an FSAI
+ * factor), and the edge pass -- as a number of resident blocks per SM: the
+ * kernel's occupancy (the default) and up to three fewer, each timed like
+ * the variants, a smaller count kept only when it is at least 2 % faster.
+ * The grid groups the rows of a kernel's dot products into block partials,
+ * so a tuned shape changes the solves by rounding (each is reproducible).
+ *
+ * pfe_get_shape -- for `kernel` (PFE_KERNEL_SPMM, _UPDATE, _PUPDATE,
+ * _FSAI_TR, _FSAI_ZP or _EDGE): *blocks_per_sm receives the chosen count (0:
+ * the kernel's occupancy), and ms (8 entries, may be NULL) the time of one
+ * launch at b = 1..8 blocks per SM in ms[b - 1] from the last pfe_autotune
+ * (-1 where not timed; k_pupdate and k_fsai_zp: the average of the launches
+ * that fold and that hold the solution update).  pfe_set_shape sets the
+ * count directly (0 restores the occupancy; counts above it act as it);
+ * PFE_EINVAL for another kernel or a count outside 0..8.  pfe_init resets
+ * every shape to the default.
+ */
+PFE_API pfe_status pfe_get_shape(pfe_ctx *c, int32_t kernel, int32_t *blocks_per_sm, double *ms);
+PFE_API pfe_status pfe_set_shape(pfe_ctx *c, int32_t kernel, int32_t blocks_per_sm);
+
+/*
  * pfe_kmeans -- the segmentation stage of Sec. IV: k-means clustering of the
  * rows of X (n x d row-major FP64, host or device; NULL = the context's
  * embedding D^{-1/2} P, d = its dimension), in FP64.  Start: C0 (k x d, host

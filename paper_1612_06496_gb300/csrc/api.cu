@@ -604,6 +604,93 @@ static void set_fsai_variant(pfe_ctx *c, int v) {
     free_pcg_graph(c);
 }
 
+// The wave_grid slot of a tunable row kernel in the current configuration
+// (-1: the kernel has no tunable shape here).
+static int shape_slot(const pfe_ctx *c, int kernel) {
+    switch (kernel) {
+        case PFE_KERNEL_SPMM: {
+            static const int sl[PFE_SPMM_NVARIANTS] = {G_SPMM,     G_SPMM_F1, G_SPMM_F2, G_SPMM_F3,
+                                                       G_SPMM_TMA, -1,        G_SPMM_G1, G_SPMM_G2};
+            return c->spmm_variant >= 0 && c->spmm_variant < PFE_SPMM_NVARIANTS ? sl[c->spmm_variant] : -1;
+        }
+        case PFE_KERNEL_UPDATE: return G_UPDATE;
+        case PFE_KERNEL_PUPDATE: return G_PUPD;
+        case PFE_KERNEL_FSAI_TR: return G_FSAI_TR;
+        case PFE_KERNEL_FSAI_ZP: return G_FSAI_ZP;
+        case PFE_KERNEL_EDGE: return c->edge_variant == PFE_EDGE_STENCIL ? G_EDGE_GRID : G_EDGE;
+        default: return -1;
+    }
+}
+// row of c->shape_ms for a tunable kernel
+static int shape_row(int kernel) {
+    switch (kernel) {
+        case PFE_KERNEL_SPMM: return 0;
+        case PFE_KERNEL_UPDATE: return 1;
+        case PFE_KERNEL_PUPDATE: return 2;
+        case PFE_KERNEL_FSAI_TR: return 3;
+        case PFE_KERNEL_FSAI_ZP: return 4;
+        case PFE_KERNEL_EDGE: return 5;
+        default: return -1;
+    }
+}
+
+// One launch of a tunable kernel on scratch state (time_pcg_kernel; the
+// edge pass by time_edge): the folding and holding launches averaged for
+// k_pupdate and k_fsai_zp.
+static pfe_status time_shape(pfe_ctx *c, int kernel, int reps, float *ms) {
+    float t = 0.f, u = 0.f;
+    switch (kernel) {
+        case PFE_KERNEL_SPMM: PFE_TRY(time_pcg_kernel(c, c->stream, 0, reps, &t)); break;
+        case PFE_KERNEL_UPDATE: PFE_TRY(time_pcg_kernel(c, c->stream, 1, reps, &t)); break;
+        case PFE_KERNEL_PUPDATE:
+            PFE_TRY(time_pcg_kernel(c, c->stream, 2, reps, &t));
+            PFE_TRY(time_pcg_kernel(c, c->stream, 6, reps, &u));
+            t = 0.5f * (t + u);
+            break;
+        case PFE_KERNEL_FSAI_TR: PFE_TRY(time_pcg_kernel(c, c->stream, 3, reps, &t)); break;
+        case PFE_KERNEL_FSAI_ZP:
+            PFE_TRY(time_pcg_kernel(c, c->stream, 4, reps, &t));
+            PFE_TRY(time_pcg_kernel(c, c->stream, 5, reps, &u));
+            t = 0.5f * (t + u);
+            break;
+        case PFE_KERNEL_EDGE: PFE_TRY(time_edge(c, reps, &t)); break;
+        default: return PFE_EINVAL;
+    }
+    *ms = t;
+    return PFE_OK;
+}
+
+// Launch-shape tuning of one kernel: its occupancy (the default) and up to
+// three fewer blocks per SM; a smaller count is kept only when >= 2 % faster.
+static pfe_status tune_shape(pfe_ctx *c, int kernel, int reps) {
+    const int slot = shape_slot(c, kernel), row = shape_row(kernel);
+    if (slot < 0 || row < 0) return PFE_OK;
+    for (int b = 0; b < 8; ++b) c->shape_ms[row][b] = -1.f;
+    c->kbps[slot] = 0;
+    c->kgrid[slot] = 0;
+    float t0 = 0.f;
+    PFE_TRY(time_shape(c, kernel, reps, &t0));
+    const int g0 = c->kgrid[slot];  // the default grid (the kernel's occupancy, or the work if smaller)
+    const int occ = std::min(8, std::max(1, (g0 + c->num_sms - 1) / c->num_sms));
+    c->shape_ms[row][occ - 1] = t0;
+    int best = 0;
+    float tbest = t0;
+    for (int b = occ - 1; b >= std::max(1, occ - 3); --b) {
+        c->kbps[slot] = b;
+        c->kgrid[slot] = 0;
+        float t = 0.f;
+        PFE_TRY(time_shape(c, kernel, reps, &t));
+        c->shape_ms[row][b - 1] = t;
+        if (t < 0.98f * t0 && t < tbest) {
+            tbest = t;
+            best = b;
+        }
+    }
+    c->kbps[slot] = best;
+    c->kgrid[slot] = 0;
+    return PFE_OK;
+}
+
 pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms) {
     if (!c || reps < 1) return PFE_EINVAL;
     if (!c->inited) return fail(c, PFE_ESTATE, "pfe_autotune before pfe_init");
@@ -650,6 +737,21 @@ pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms) {
         }
         c->edge_variant = c->edge_tune_ms[1] < c->edge_tune_ms[0] ? PFE_EDGE_STENCIL : PFE_EDGE_SLOTS;
     }
+    // launch shapes of the kernels the configured iteration runs (single
+    // problems: a batch keeps one block or more per segment at occupancy)
+    if (c->nseg == 1) {
+        const bool fsai = c->fsai.enabled && !c->fsai.ic;
+        PFE_TRY(tune_shape(c, PFE_KERNEL_SPMM, reps));
+        if (fsai) {
+            PFE_TRY(tune_shape(c, PFE_KERNEL_FSAI_TR, reps));
+            PFE_TRY(tune_shape(c, PFE_KERNEL_FSAI_ZP, reps));
+        } else if (!c->fsai.enabled) {
+            PFE_TRY(tune_shape(c, PFE_KERNEL_UPDATE, reps));
+            PFE_TRY(tune_shape(c, PFE_KERNEL_PUPDATE, reps));
+        }
+        PFE_TRY(tune_shape(c, PFE_KERNEL_EDGE, reps));
+        free_pcg_graph(c);  // the captured loop holds the grids
+    }
     return PFE_OK;
 }
 
@@ -672,6 +774,28 @@ pfe_status pfe_get_variant(pfe_ctx *c, int32_t kernel, int32_t *variant, double 
     } else {
         return PFE_EINVAL;
     }
+    return PFE_OK;
+}
+
+pfe_status pfe_get_shape(pfe_ctx *c, int32_t kernel, int32_t *blocks_per_sm, double *ms) {
+    if (!c || !blocks_per_sm) return PFE_EINVAL;
+    const int slot = shape_slot(c, kernel), row = shape_row(kernel);
+    if (slot < 0 || row < 0) return fail(c, PFE_EINVAL, "pfe_get_shape: not a tunable kernel");
+    *blocks_per_sm = c->kbps[slot];
+    if (ms)
+        for (int b = 0; b < 8; ++b) ms[b] = c->shape_ms[row][b] > 0.f ? c->shape_ms[row][b] : -1.0;
+    return PFE_OK;
+}
+
+pfe_status pfe_set_shape(pfe_ctx *c, int32_t kernel, int32_t blocks_per_sm) {
+    if (!c) return PFE_EINVAL;
+    const int slot = shape_slot(c, kernel);
+    if (slot < 0 || shape_row(kernel) < 0 || blocks_per_sm < 0 || blocks_per_sm > 8)
+        return fail(c, PFE_EINVAL, "pfe_set_shape: not a tunable kernel, or blocks per SM outside 0..8");
+    PFE_TRY(sync(c));
+    c->kbps[slot] = blocks_per_sm;
+    c->kgrid[slot] = 0;
+    free_pcg_graph(c);
     return PFE_OK;
 }
 
@@ -843,6 +967,9 @@ static pfe_status init_impl(pfe_ctx *c, int32_t d, const double *Y0, int64_t ldY
     free_work(c);
     c->d = d;
     memset(c->kgrid, 0, sizeof(c->kgrid));  // kernels are sized again for this d
+    memset(c->kbps, 0, sizeof(c->kbps));    // with their default shapes
+    for (auto &r : c->shape_ms)
+        for (float &t : r) t = -1.f;
     const int64_t nd = c->n * (int64_t)d;
     const int64_t ed = c->g.fslots * (int64_t)d;
     auto &w = c->wk;

@@ -292,8 +292,9 @@ __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
 
 // Grid of a grid-stride kernel: exactly one wave of the kernel's own
 // occupancy (a second, partial wave would leave most SMs idle while it
-// runs), capped at `need` blocks and rounded down to a multiple of `mult`.
-// Cached per context in c->kgrid[slot].
+// runs), or of the blocks per SM the autotuner chose for the kernel
+// (c->kbps[slot]), capped at `need` blocks and rounded down to a multiple of
+// `mult`.  Cached per context in c->kgrid[slot].
 enum GridSlot {
     G_INIT = 0, G_INIT_F, G_PUPD, G_SPMM, G_UPDATE, G_FSAI_TR, G_XFLUSH, G_REFRESH, G_REFRESH_F,
     G_FSAI_T, G_FSAI_T1, G_FSAI_ZP, G_APPLY, G_EDGE, G_PAPPLY, G_TIME_SPMM, G_TIME_UPDATE, G_SPMM_F1, G_SPMM_F2,
@@ -424,6 +425,7 @@ inline int wave_grid(pfe_ctx *c, int slot, K kernel, int64_t need, int mult = 1,
         }
         int64_t grid = (int64_t)occ * c->num_sms;
         if (c->prm.blocks_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)c->prm.blocks_per_sm * c->num_sms);
+        if (c->kbps[slot] > 0) grid = std::min<int64_t>(grid, (int64_t)c->kbps[slot] * c->num_sms);  // pfe_autotune
         grid = std::min<int64_t>(grid, std::max<int64_t>(need, 1));
         if (mult > 1) grid = std::max<int64_t>(mult, grid / mult * mult);
         // every segment owns at least one block of a row kernel

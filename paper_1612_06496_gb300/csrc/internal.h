@@ -164,6 +164,8 @@ struct pfe_ctx {
     int *h_flag = nullptr;            // pinned host scratch
     int grid_rows = 0;                // blocks of the persistent row kernels (upper bound)
     int kgrid[32] = {0};              // per-kernel grid cache (wave_grid), reset by pfe_init
+    int kbps[32] = {0};               // blocks per SM chosen by pfe_autotune per kernel slot (0: occupancy)
+    float shape_ms[8][8] = {};        // pfe_autotune: time of each tuned kernel at 1..8 blocks per SM (<= 0: not timed)
     cudaGraph_t pcg_graph = nullptr;
     cudaGraphExec_t pcg_exec = nullptr;
     pfe::FsaiState fsai;

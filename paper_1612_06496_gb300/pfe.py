@@ -29,7 +29,8 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
            "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
            "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_ic0", "pfe_get_segments",
            "pfe_get_segment_stats", "pfe_laplacian_eigenmap", "pfe_objective", "pfe_autotune",
-           "pfe_set_variant", "pfe_solve_two_stage", "pfe_kmeans", "pfe_residual", "pfe_get_variant"]
+           "pfe_set_variant", "pfe_solve_two_stage", "pfe_kmeans", "pfe_residual", "pfe_get_variant",
+           "pfe_get_shape", "pfe_set_shape"]
 SPMM_NVARIANTS = 8  # PFE_SPMM_GENERAL, _ROW1, _ROW2, _ROW2_4, _TMA, _STENCIL, _GRID1, _GRID2
 TUNE = {"spmm": 0, "fsai": 1, "edge": 2}
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3, "fsai_tr": 4, "fsai_zp": 5, "fsai_zp_hold": 6,
@@ -115,6 +116,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_kmeans.argtypes = [vp, vp, i32, i32, vp, i32, vp, vp, C.POINTER(dbl), C.POINTER(i32)]
     lib.pfe_residual.argtypes = [vp, vp, vp, vp]
     lib.pfe_get_variant.argtypes = [vp, i32, C.POINTER(i32), vp]
+    lib.pfe_get_shape.argtypes = [vp, i32, C.POINTER(i32), vp]
+    lib.pfe_set_shape.argtypes = [vp, i32, i32]
     for name in EXPORTS:
         if name not in ("pfe_default_params", "pfe_last_error", "pfe_status_string"):
             getattr(lib, name).restype = C.c_int
@@ -298,6 +301,17 @@ class PFE:
         ms = np.full(2, -1.0)
         self._check(self.lib.pfe_get_variant(self.ctx, int(kernel), C.byref(v), ms.ctypes.data), "pfe_get_variant")
         return v.value, (None if kernel == 0 else ms)
+
+    def get_shape(self, kernel: str):
+        """(blocks per SM chosen for a row kernel (0: its occupancy), {blocks
+        per SM: ms} timed by the last autotune)."""
+        b = C.c_int32()
+        ms = np.full(8, -1.0)
+        self._check(self.lib.pfe_get_shape(self.ctx, KERNEL[kernel], C.byref(b), ms.ctypes.data), "pfe_get_shape")
+        return b.value, {k + 1: float(t) for k, t in enumerate(ms) if t > 0}
+
+    def set_shape(self, kernel: str, blocks_per_sm: int):
+        self._check(self.lib.pfe_set_shape(self.ctx, KERNEL[kernel], int(blocks_per_sm)), "pfe_set_shape")
 
     def kmeans(self, k: int, X=None, C0=None, max_iter: int = 100):
         """k-means segmentation of X (n x d) or of the embedding: (labels,

@@ -200,3 +200,52 @@ def test_timing_the_edge_pass_leaves_the_iteration_state():
         out.append(Y)
         p.close()
     np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "learned"])
+def test_autotuned_launch_shapes(precond):
+    """pfe_autotune also chooses the blocks per SM of each row kernel the
+    iteration runs (the SpMM, k_update and k_pupdate or k_fsai_tr and
+    k_fsai_zp, the edge pass): the default (occupancy) is timed with up to
+    three smaller counts.  Every shape solves within the FP32 path's 2e-4 of
+    the oracle, and a shape's solve is reproducible bit for bit; other
+    kernels and counts outside 0..8 are refused."""
+    from paper_1612_06496_gb300 import PFEError
+    from paper_1612_06496_gb300.learned import load_weights
+    spec = small_spec(H=96, W=90, d=6)
+    kernels = ["spmm", "edge"] + (["fsai_tr", "fsai_zp"] if precond == "learned" else ["update", "pupdate"])
+
+    def problem():
+        p, X, Y0 = gpu_problem(spec, "mixed")
+        if precond == "learned":
+            p.fsai_set(load_weights())
+        p.init(Y0)
+        return p, X, Y0
+
+    p, X, Y0 = problem()
+    p.autotune(3)
+    shapes = {k: p.get_shape(k) for k in kernels}
+    for k, (b, ms) in shapes.items():
+        assert 0 <= b <= 8 and len(ms) >= 1 and all(t > 0 for t in ms.values()), (k, b, ms)
+        assert b == 0 or b in ms, (k, b, ms)
+    with pytest.raises(PFEError):
+        p.get_shape("xflush")
+    with pytest.raises(PFEError):
+        p.set_shape("spmm", 9)
+    p.close()
+    g = oracle_graph(spec, X)
+    ref = O.soc_pfe(g, Y0, 2, 3, solver="direct").Y
+    for k in kernels:
+        for b in sorted(shapes[k][1])[:2]:
+            out = []
+            for _ in range(2):
+                p, _, _ = problem()
+                p.set_shape(k, b)
+                assert p.get_shape(k)[0] == b
+                Y = np.empty_like(Y0)
+                st = p.solve(2, 3, Y, None)
+                assert st["n_unconverged"] == 0
+                out.append(Y)
+                p.close()
+            np.testing.assert_array_equal(out[0], out[1])
+            assert relerr(out[0], ref) <= 2e-4, (k, b, relerr(out[0], ref))
