@@ -19,7 +19,10 @@ M^{-1} = G^T G with G lower triangular on the pattern of tril(A):
   with s_i = sum over i's lower neighbours j of rho_ij^2.
 * Training criterion: Kaporin's condition number of G A G^T,
       L = log(tr(G A G^T) / n) - (2/n) sum_i log G_ii   (+ log det A / n, constant),
-  which classical FSAI minimises over the same pattern.
+  which classical FSAI minimises over the same pattern, optionally plus
+  mu times the mean relative residual of the preconditioner on right-hand
+  sides b_c the method itself produced (Eq. 13's right-hand sides),
+      R = (1/m) sum_c |A G^T G b_c - b_c|^2 / |b_c|^2  (``rhs_residual``).
 
 Training takes Adam steps (Kingma and Ba, ICLR 2015, Algorithm 1) on the
 loss averaged over a mini-batch of images: ``adam_step``.
@@ -152,14 +155,42 @@ def kaporin(g, G):
     return L, dG, T
 
 
-def loss_and_grad(theta, g, bf16: bool = False):
+def rhs_residual(g, G, B):
+    """R = (1/m) sum_c |A G^T G b_c - b_c|^2 / |b_c|^2 over the m columns of
+    B (n x m) and dR/dG on G's pattern (lower triangle with the diagonal).
+    With u = G b, v = G^T u, w = A v - b and s = dR/dv = 2 A w / (m |b|^2)
+    (A symmetric): v_j = sum_i G_ij u_i gives dR/dG_ij = u_i s_j, and u_i =
+    sum_j G_ij b_j gives dR/dG_ij = (G s)_i b_j; both are kept where G has
+    an entry."""
+    m = B.shape[1]
+    A = g.A.tocsr()
+    bn = np.sum(B * B, axis=0)
+    U = G @ B
+    V = G.T @ U
+    Wr = A @ V - B
+    R = float(np.sum(np.sum(Wr * Wr, axis=0) / bn) / m)
+    S = (A @ Wr) * (2.0 / (m * bn))
+    GS = G @ S
+    Gc = G.tocoo()
+    i, j = Gc.row, Gc.col
+    vals = np.sum(U[i] * S[j] + GS[i] * B[j], axis=1)
+    return R, sp.csr_matrix((vals, (i, j)), shape=G.shape)
+
+
+def loss_and_grad(theta, g, bf16: bool = False, B=None, mu: float = 0.0):
     """Kaporin loss of the network's G on graph g and its gradient w.r.t.
-    theta (bf16: the hidden layer's operands rounded as on the GPU)."""
+    theta (bf16: the hidden layer's operands rounded as on the GPU); with
+    right-hand sides B (n x m) and mu > 0, plus mu times rhs_residual."""
     Fd, Fe = entry_features(g)
     od, cd = mlp_forward(theta, Fd, bf16)
     oe, ce = mlp_forward(theta, Fe, bf16)
     G, gd, ge = assemble_G(g, od, oe)
     L, dG, T = kaporin(g, G)
+    Rr = None
+    if B is not None and mu > 0.0:
+        Rr, dR = rhs_residual(g, G, B)
+        L = L + mu * Rr
+        dG = dG.tocsr() + mu * dR
     Ad = g.A.diagonal()
     dG = dG.tocsr()
     dgd = np.asarray(dG[np.arange(g.n), np.arange(g.n)]).ravel()
@@ -169,7 +200,7 @@ def loss_and_grad(theta, g, bf16: bool = False):
     dout_e = np.zeros_like(oe)
     dout_e[:, 0] = dge / np.sqrt(Ad[g.a])
     grad = mlp_backward(theta, cd, dout_d, bf16) + mlp_backward(theta, ce, dout_e, bf16)
-    return L, grad, {"T": T, "gd": gd, "ge": ge, "G": G}
+    return L, grad, {"T": T, "gd": gd, "ge": ge, "G": G, "R": Rr}
 
 
 def classical_fsai(A) -> sp.csr_matrix:

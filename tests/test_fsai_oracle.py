@@ -306,3 +306,63 @@ def test_bf16_network_stays_within_bf16_rounding_of_fp64():
     o16, _ = F.mlp_forward(theta, Fm, bf16=True)
     rel = np.linalg.norm(o16 - o64) / np.linalg.norm(o64)
     assert 1e-5 < rel < 2e-2, rel
+
+
+# ---- the right-hand-side residual term of the training criterion
+
+def test_rhs_residual_one_by_one_closed_form():
+    """n = 1: A = [a], G = [g], b = [beta] give R = (a g^2 - 1)^2 and
+    dR/dg = 4 a g (a g^2 - 1), whatever beta."""
+    from types import SimpleNamespace
+    for a, gv, beta in ((3.0, 0.4, 2.0), (0.5, 1.7, -0.3), (2.0, 2 ** -0.5, 5.0)):
+        g = SimpleNamespace(A=sp.csr_matrix([[a]]))
+        R, dR = F.rhs_residual(g, sp.csr_matrix([[gv]]), np.array([[beta]]))
+        assert R == pytest.approx((a * gv * gv - 1) ** 2, rel=1e-14, abs=1e-30)
+        assert dR[0, 0] == pytest.approx(4 * a * gv * (a * gv * gv - 1), rel=1e-13, abs=1e-15)
+
+
+def test_rhs_residual_vanishes_at_the_exact_inverse_factor():
+    """With G the inverse of the Cholesky factor of A (a full lower pattern),
+    G^T G = A^{-1}: R = 0 and its gradient vanishes."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(8)
+    M = rng.standard_normal((7, 7))
+    A = M @ M.T + 7 * np.eye(7)
+    G = np.linalg.inv(np.linalg.cholesky(A))
+    R, dR = F.rhs_residual(SimpleNamespace(A=sp.csr_matrix(A)), sp.csr_matrix(np.tril(G)),
+                           rng.standard_normal((7, 3)))
+    assert R < 1e-28
+    assert np.max(np.abs(dR.toarray())) < 1e-12
+
+
+def test_rhs_residual_gradient_matches_finite_differences():
+    g = _tiny_graph(5, 6)
+    rng = np.random.default_rng(9)
+    G = F.classical_fsai(g.A)
+    G.data = G.data * (1 + 0.2 * rng.standard_normal(G.data.shape))
+    B = rng.standard_normal((g.n, 3)) + 2.0
+    R, dR = F.rhs_residual(g, G, B)
+    Gc = G.tocoo()
+    for t in rng.choice(Gc.nnz, 15, replace=False):
+        i, j = Gc.row[t], Gc.col[t]
+        h = 1e-6 * max(abs(Gc.data[t]), 1e-3)
+        Gp = G.tolil(); Gp[i, j] += h
+        Gm = G.tolil(); Gm[i, j] -= h
+        fd = (F.rhs_residual(g, Gp.tocsr(), B)[0] - F.rhs_residual(g, Gm.tocsr(), B)[0]) / (2 * h)
+        assert fd == pytest.approx(dR[i, j], rel=1e-5, abs=1e-10)
+
+
+def test_network_gradient_with_the_rhs_term_matches_finite_differences():
+    g = _tiny_graph(6, 5)
+    rng = np.random.default_rng(10)
+    th = F.init_params(7) + 0.05 * rng.standard_normal(F.NPARAM)
+    B = rng.standard_normal((g.n, 2))
+    L0 = F.loss_and_grad(th, g)[0]
+    L, grad, info = F.loss_and_grad(th, g, B=B, mu=0.7)
+    assert L == pytest.approx(L0 + 0.7 * info["R"], rel=1e-14)
+    for k in rng.choice(F.NPARAM, 20, replace=False):
+        h = 1e-6
+        tp = th.copy(); tp[k] += h
+        tm = th.copy(); tm[k] -= h
+        fd = (F.loss_and_grad(tp, g, B=B, mu=0.7)[0] - F.loss_and_grad(tm, g, B=B, mu=0.7)[0]) / (2 * h)
+        assert fd == pytest.approx(grad[k], rel=1e-5, abs=1e-9), k
