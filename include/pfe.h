@@ -569,6 +569,19 @@ PFE_API pfe_status pfe_ic0(pfe_ctx *c);
  * on a batch).  Synchronises. */
 PFE_API pfe_status pfe_fsai_loss_grad(pfe_ctx *c, const float *params, float *grad, double *loss);
 
+/* pfe_fsai_loss_grad_rhs -- pfe_fsai_loss_grad plus mu times the mean
+ * relative residual of the preconditioner on m right-hand sides B of Eq. 13
+ * that the method produced (n x m FP64, row-major, host or device; 1 <= m
+ * <= 32, every column nonzero):
+ *   R = (1/m) sum_c |A G^T G b_c - b_c|^2 / |b_c|^2,   loss = K(G) + mu R,
+ * with A in FP64 and the gradient of both terms w.r.t. params (dR/dG_ij =
+ * u_i s_j + (G s)_i b_j with u = G b, s = 2 A (A G^T G b - b) / (m |b|^2),
+ * on G's pattern).  *rterm (may be NULL) receives R.  mu = 0 or B = NULL
+ * is pfe_fsai_loss_grad.  Allocates its scratch vectors (five n x m FP64)
+ * for the call.  Synchronises. */
+PFE_API pfe_status pfe_fsai_loss_grad_rhs(pfe_ctx *c, const float *params, const double *B, int32_t m, double mu,
+                                          float *grad, double *loss, double *rterm);
+
 /* The current G as FP64: gdiag[i] = G_ii (n values), gedge[k] = G_{b_k a_k}
  * for edge k of pfe_get_edges (n_edges values); either may be NULL. */
 PFE_API pfe_status pfe_fsai_get(pfe_ctx *c, double *gdiag, double *gedge);

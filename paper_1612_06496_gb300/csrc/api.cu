@@ -1407,6 +1407,37 @@ pfe_status pfe_fsai_loss_grad(pfe_ctx *c, const float *params, float *grad, doub
     return sync(c);
 }
 
+pfe_status pfe_fsai_loss_grad_rhs(pfe_ctx *c, const float *params, const double *B, int32_t m, double mu,
+                                  float *grad, double *loss, double *rterm) {
+    if (!c || !params || !loss) return PFE_EINVAL;
+    if (c->nseg > 1) return fail(c, PFE_EUNSUPPORTED, "the training loss is built for one problem, not a batch");
+    const bool rhs = B && mu > 0.0;
+    if (rhs && (m < 1 || m > 32)) return fail(c, PFE_EINVAL, "pfe_fsai_loss_grad_rhs: needs 1 <= m <= 32");
+    if (!(mu >= 0.0)) return fail(c, PFE_EINVAL, "pfe_fsai_loss_grad_rhs: mu must be >= 0");
+    PFE_TRY(fsai_alloc(c));
+    PFE_CUDA_TRY(c, cudaMemcpyAsync(c->fsai.params, params, kNParam * sizeof(float), cudaMemcpyDefault, c->stream));
+    const double *dB = B;
+    double *tmp = nullptr;
+    if (rhs && !is_device_ptr(B)) {
+        const size_t bytes = sizeof(double) * (size_t)c->n * m;
+        if (cudaMalloc((void **)&tmp, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PFE_ENOMEM, "pfe_fsai_loss_grad_rhs: device copy of B");
+        }
+        if (cudaMemcpyAsync(tmp, B, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+            cudaFree(tmp);
+            return fail(c, PFE_ECUDA, "pfe_fsai_loss_grad_rhs: copy of B");
+        }
+        dB = tmp;
+    }
+    pfe_status st = fsai_loss_grad(c, loss, rhs ? dB : nullptr, rhs ? m : 0, rhs ? mu : 0.0, rterm);
+    if (tmp) cudaFree(tmp);
+    PFE_TRY(st);
+    if (grad)
+        PFE_CUDA_TRY(c, cudaMemcpyAsync(grad, c->fsai.grad, kNParam * sizeof(float), cudaMemcpyDefault, c->stream));
+    return sync(c);
+}
+
 pfe_status pfe_fsai_get(pfe_ctx *c, double *gdiag, double *gedge) {
     if (!c) return PFE_EINVAL;
     if (!c->fsai.gdiag) return fail(c, PFE_ESTATE, "no FSAI factor: call pfe_fsai_set or pfe_fsai_loss_grad first");

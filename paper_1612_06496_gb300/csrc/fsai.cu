@@ -37,7 +37,7 @@ struct View {
     int64_t n, n_edges, n_slices;
     const int *slice_ptr, *col, *eid;
     const int *ea, *eb, *ext_slot;
-    const double *ew, *deg, *adiag, *w64;
+    const double *ew, *deg, *adiag, *w64, *aoff;
     double lam, r;
     // a batch of problems: lambda of each problem, the problem of each row
     int nseg;
@@ -62,6 +62,7 @@ View view(pfe_ctx *c) {
     v.deg = c->g.deg;
     v.adiag = c->g.adiag64;
     v.w64 = c->g.w64;
+    v.aoff = c->g.aoff64;
     v.lam = c->lambda;
     v.r = c->r;
     v.nseg = c->nseg;
@@ -413,13 +414,100 @@ __global__ void k_sum2(int64_t n, const double *a, const double *b, double *part
     }
 }
 
-// dL/dh per entry from dq (in place): L = log(Q/n) - (2/n) sum log G_ii.
-__global__ void k_dloss(View g, const double *sums, const float *gdiag, const float *hraw, float *dq) {
+// ---- right-hand-side residual term: R = (1/m) sum_c |A G^T G b_c - b_c|^2 / |b_c|^2
+// over m right-hand sides the method produced (n x m, row-major, FP64).
+// u = G b, v = G^T u, w = A v - b, s = 2 mu A w / (m |b|^2) (A symmetric); the
+// gradient on G's pattern is dR/dG_ij = u_i s_j + (G s)_i b_j.
+constexpr int kMaxRhs = 32;
+
+// out = G x (MODE 0: G_ii and the lower slots [0, kb_i)), G^T x (MODE 1: G_ii
+// and the upper slots [kb_i, len), which hold the transposed entries), or
+// A x in FP64 (MODE 2); one thread per (row, column).  Padding slots carry 0.
+template <int MODE>
+__global__ void k_rg_apply(View g, const int *kb, const float *gdiag, const float *gslot, const double *x, int m,
+                           double *out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n * m) return;
+    const int64_t i = k / m;
+    const int c = (int)(k - i * m);
+    const int64_t sl = i >> 5;
+    const int s0 = g.slice_ptr[sl];
+    const int len = (g.slice_ptr[sl + 1] - s0) >> 5;
+    const int64_t base = s0 + (i & 31) * (int64_t)len;
+    const int lo = MODE == 1 ? kb[i] : 0, hi = MODE == 0 ? kb[i] : len;
+    double acc = (MODE == 2 ? g.adiag[i] : (double)gdiag[i]) * x[k];
+    for (int t = lo; t < hi; ++t) {
+        const double v = MODE == 2 ? g.aoff[base + t] : (double)gslot[base + t];
+        acc = fma(v, x[(int64_t)g.col[base + t] * m + c], acc);
+    }
+    out[k] = acc;
+}
+
+// w -= b, and the column sums |w_c|^2 (out[c]) and |b_c|^2 (out[m + c]):
+// block partials, the last block adds them in block order.
+__global__ void k_rg_resid(int64_t n, int m, const double *b, double *w, double *part, unsigned *ticket, double *out) {
+    double acc[2 * kMaxRhs];
+    for (int c = 0; c < 2 * m; ++c) acc[c] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int c = 0; c < m; ++c) {
+            const double bv = b[i * m + c], wv = w[i * m + c] - bv;
+            w[i * m + c] = wv;
+            acc[c] = fma(wv, wv, acc[c]);
+            acc[m + c] = fma(bv, bv, acc[m + c]);
+        }
+    __shared__ double red[256];
+    for (int c = 0; c < 2 * m; ++c) {
+        red[threadIdx.x] = acc[c];
+        __syncthreads();
+        for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+            if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * 2 * m + c] = red[0];
+        __syncthreads();
+    }
+    if (last_block_arrives(ticket)) {
+        for (int c = threadIdx.x; c < 2 * m; c += blockDim.x) {
+            double t = 0.0;
+            for (unsigned k = 0; k < gridDim.x; ++k) t += __ldcg(part + (int64_t)k * 2 * m + c);
+            out[c] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+}
+
+// s (= A w on entry) *= 2 mu / (m |b_c|^2)
+__global__ void k_rg_scale(int64_t n, int m, const double *sq, double mu, double *s) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n * m) return;
+    const int c = (int)(k % m);
+    s[k] *= 2.0 * mu / ((double)m * sq[m + c]);
+}
+
+// Gradient of the term per pattern entry (the entry order of dq): diagonal
+// entry i, then edge k = (a_k, b_k), a < b, entry G_{b a}:
+//   dR/dG_ij = sum_c u_ic s_jc + (G s)_ic b_jc.
+__global__ void k_rg_entries(View g, int m, const double *u, const double *s, const double *gs, const double *b,
+                             float *drhs) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= g.n + g.n_edges) return;
+    const int64_t i = e < g.n ? e : g.eb[e - g.n], j = e < g.n ? e : g.ea[e - g.n];
+    double t = 0.0;
+    for (int c = 0; c < m; ++c) t += u[i * m + c] * s[j * m + c] + gs[i * m + c] * b[j * m + c];
+    drhs[e] = (float)t;
+}
+
+// dL/dh per entry from dq (in place): L = log(Q/n) - (2/n) sum log G_ii
+// (+ the right-hand-side term's dL/dG_ij, drhs, when given).
+__global__ void k_dloss(View g, const double *sums, const float *gdiag, const float *hraw, float *dq,
+                        const float *drhs) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t N = g.n + g.n_edges;
     if (e >= N) return;
     const double Q = sums[0];
     double dG = dq[e] / Q;
+    if (drhs) dG += drhs[e];
     if (e < g.n) {
         dG -= 2.0 / ((double)g.n * gdiag[e]);
         const double h = hraw[e];
@@ -787,21 +875,73 @@ pfe_status fsai_infer(pfe_ctx *c) {
 }
 
 // Kaporin loss of the current G and its gradient w.r.t. f.params -> f.grad.
-pfe_status fsai_loss_grad(pfe_ctx *c, double *loss) {
+pfe_status fsai_loss_grad(pfe_ctx *c, double *loss, const double *B, int m, double mu, double *rterm) {
     auto &f = c->fsai;
     cudaStream_t s = c->stream;
     View v = view(c);
     const int64_t n = c->g.n, N = n + c->g.n_edges;
+    const bool rhs = B && m > 0 && mu > 0.0;
+    if (rhs && m > kMaxRhs) {
+        c->err = "pfe_fsai_loss_grad_rhs: at most 32 right-hand sides";
+        return PFE_EINVAL;
+    }
     PFE_TRY(fsai_infer(c));
     k_kaporin_rows<<<nblk(n, 128), 128, 0, s>>>(v, f.kb, f.gdiag, f.gslot, f.ent_of_slot, f.dq, f.qrow, f.logd);
     k_sum2<<<256, kBlock, 0, s>>>(n, f.qrow, f.logd, f.part, f.tick, f.sums);
-    k_dloss<<<nblk(N, 256), 256, 0, s>>>(v, f.sums, f.gdiag, f.hraw, f.dq);
+    // the right-hand-side term: five n x m FP64 vectors, N entry gradients,
+    // block partials and the 2m column sums (training only, allocated here)
+    double *u = nullptr, *vv = nullptr, *w = nullptr, *sv = nullptr, *gs = nullptr, *rpart = nullptr, *sq = nullptr;
+    float *drhs = nullptr;
+    unsigned *rtick = nullptr;
+    struct Free {
+        void **ps[9];
+        ~Free() {
+            for (void **p : ps)
+                if (*p) cudaFree(*p);
+        }
+    } fr{{(void **)&u, (void **)&vv, (void **)&w, (void **)&sv, (void **)&gs, (void **)&rpart, (void **)&sq,
+          (void **)&drhs, (void **)&rtick}};
+    constexpr int kRgBlocks = 256;
+    if (rhs) {
+        const size_t nm = sizeof(double) * (size_t)n * m;
+        if (cudaMalloc((void **)&u, nm) != cudaSuccess || cudaMalloc((void **)&vv, nm) != cudaSuccess ||
+            cudaMalloc((void **)&w, nm) != cudaSuccess || cudaMalloc((void **)&sv, nm) != cudaSuccess ||
+            cudaMalloc((void **)&gs, nm) != cudaSuccess ||
+            cudaMalloc((void **)&rpart, sizeof(double) * kRgBlocks * 2 * m) != cudaSuccess ||
+            cudaMalloc((void **)&sq, sizeof(double) * 2 * m) != cudaSuccess ||
+            cudaMalloc((void **)&drhs, sizeof(float) * N) != cudaSuccess ||
+            cudaMalloc((void **)&rtick, sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            c->err = "pfe_fsai_loss_grad_rhs: device allocation failed";
+            return PFE_ENOMEM;
+        }
+        PFE_CUDA_TRY(c, cudaMemsetAsync(rtick, 0, sizeof(unsigned), s));
+        const unsigned gnm = nblk(n * m, 256);
+        k_rg_apply<0><<<gnm, 256, 0, s>>>(v, f.kb, f.gdiag, f.gslot, B, m, u);     // u = G b
+        k_rg_apply<1><<<gnm, 256, 0, s>>>(v, f.kb, f.gdiag, f.gslot, u, m, vv);    // v = G^T u
+        k_rg_apply<2><<<gnm, 256, 0, s>>>(v, f.kb, f.gdiag, f.gslot, vv, m, w);    // A v
+        k_rg_resid<<<kRgBlocks, 256, 0, s>>>(n, m, B, w, rpart, rtick, sq);        // w = A v - b, norms
+        k_rg_apply<2><<<gnm, 256, 0, s>>>(v, f.kb, f.gdiag, f.gslot, w, m, sv);    // A w
+        k_rg_scale<<<gnm, 256, 0, s>>>(n, m, sq, mu, sv);                          // s
+        k_rg_apply<0><<<gnm, 256, 0, s>>>(v, f.kb, f.gdiag, f.gslot, sv, m, gs);   // G s
+        k_rg_entries<<<nblk(N, 256), 256, 0, s>>>(v, m, u, sv, gs, B, drhs);
+    }
+    k_dloss<<<nblk(N, 256), 256, 0, s>>>(v, f.sums, f.gdiag, f.hraw, f.dq, drhs);
     k_mlp_bwd<<<f.mlp_blocks, kMlpThreads, smem_bwd(), s>>>(v, f.srow, f.params, f.dq, f.gpart, f.tick + 1, f.grad);
     PFE_CUDA_TRY(c, cudaGetLastError());
     double h[2];
+    double hs[2 * kMaxRhs] = {};
     PFE_CUDA_TRY(c, cudaMemcpyAsync(h, f.sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (rhs) PFE_CUDA_TRY(c, cudaMemcpyAsync(hs, sq, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, s));
     PFE_CUDA_TRY(c, cudaStreamSynchronize(s));
     *loss = std::log(h[0] / (double)n) - 2.0 / (double)n * h[1];
+    double R = 0.0;
+    if (rhs) {
+        for (int k = 0; k < m; ++k) R += hs[k] / hs[m + k];
+        R /= (double)m;
+        *loss += mu * R;
+    }
+    if (rterm) *rterm = R;
     return PFE_OK;
 }
 

@@ -39,7 +39,8 @@ struct FsaiState {
 
 pfe_status fsai_alloc(pfe_ctx *c);
 pfe_status fsai_infer(pfe_ctx *c);
-pfe_status fsai_loss_grad(pfe_ctx *c, double *loss);
+pfe_status fsai_loss_grad(pfe_ctx *c, double *loss, const double *B = nullptr, int m = 0, double mu = 0.0,
+                          double *rterm = nullptr);
 pfe_status fsai_export(pfe_ctx *c, double *od, double *oe);
 pfe_status fsai_classical(pfe_ctx *c);
 pfe_status ic0_factor(pfe_ctx *c);

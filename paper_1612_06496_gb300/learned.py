@@ -62,21 +62,33 @@ def load_weights(path: str = WEIGHTS) -> np.ndarray:
         return z["params"].astype(np.float32)
 
 
-def train(images: int, epochs: int, batch: int, lr: float, out: str, seed: int = 0, log=print) -> dict:
+def method_rhs(p, Y0, steps: int):
+    """A right-hand side of Eq. 13 the method produces on this image: the
+    next system's after `steps` inner iterations from Y0 (Jacobi PCG), as a
+    device tensor (n x d FP64)."""
+    import torch
+    p.init(torch.from_numpy(Y0).cuda())
+    for _ in range(steps):
+        p.inner_step()
+    return torch.from_numpy(np.ascontiguousarray(p.get("RHS"))).cuda()
+
+
+def train(images: int, epochs: int, batch: int, lr: float, out: str, seed: int = 0, log=print,
+          mu: float = 0.0, rhs_steps: int = 1, init: np.ndarray | None = None, first_image: int = 0) -> dict:
     import torch
 
     from paper_1612_06496_gb300 import PFE
     from paper_1612_06496_gb300.pfe import adam_update, fsai_param_count
-    from synth import make_image, features_from_image
+    from synth import make_image, features_from_image, make_problem
 
     dev = torch.device("cuda")
     npar = fsai_param_count()
-    params = torch.from_numpy(init_params(seed)).to(dev)
+    params = torch.from_numpy(init_params(seed) if init is None else init.astype(np.float32)).to(dev)
     m = torch.zeros(npar, dtype=torch.float32, device=dev)
     v = torch.zeros_like(m)
     gsum = torch.zeros_like(m)
     gtmp = torch.zeros_like(m)
-    specs = training_specs(images)
+    specs = training_specs(first_image + images)[first_image:]
     step, hist = 0, []
     t0 = time.time()
     for ep in range(epochs):
@@ -87,10 +99,17 @@ def train(images: int, epochs: int, batch: int, lr: float, out: str, seed: int =
             nb = 0
             for k in order[bi:bi + batch]:
                 s = specs[k]
-                X = features_from_image(make_image(s))
-                p = PFE(torch.from_numpy(X).to(dev), sigma=s.sigma, H=s.H, W=s.W, radius=s.radius,
-                        precision="mixed")
-                loss, _ = p.fsai_loss_grad(params, gtmp)
+                if mu > 0.0:  # Kaporin + mu x the residual on a right-hand side the method produced
+                    X, Y0 = make_problem(s)
+                    p = PFE(torch.from_numpy(X).to(dev), sigma=s.sigma, H=s.H, W=s.W, radius=s.radius,
+                            precision="mixed")
+                    B = method_rhs(p, Y0, rhs_steps)
+                    loss, _, _ = p.fsai_loss_grad_rhs(params, B, mu, gtmp)
+                else:
+                    X = features_from_image(make_image(s))
+                    p = PFE(torch.from_numpy(X).to(dev), sigma=s.sigma, H=s.H, W=s.W, radius=s.radius,
+                            precision="mixed")
+                    loss, _ = p.fsai_loss_grad(params, gtmp)
                 p.close()
                 gsum += gtmp
                 losses.append(loss)
@@ -102,7 +121,8 @@ def train(images: int, epochs: int, batch: int, lr: float, out: str, seed: int =
         hist.append({"epoch": ep, "mean_loss": float(np.mean(losses)), "seconds": time.time() - t0})
         log(json.dumps(hist[-1]))
     theta = params.cpu().numpy()
-    meta = {"images": images, "epochs": epochs, "batch": batch, "lr": lr, "seed": seed, "history": hist}
+    meta = {"images": images, "first_image": first_image, "epochs": epochs, "batch": batch, "lr": lr, "seed": seed,
+            "mu": mu, "rhs_steps": rhs_steps, "history": hist}
     if out:
         np.savez(out, params=theta, meta=json.dumps(meta))
     return {"params": theta, "meta": meta}

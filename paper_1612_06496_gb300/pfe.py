@@ -26,7 +26,7 @@ ARR = {"Y": 0, "P": 1, "B": 2, "BS": 3, "RHS": 4, "DEG": 5, "DIAG": 6}
 EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step", "pfe_pstep", "pfe_solve",
            "pfe_destroy", "pfe_last_error", "pfe_status_string", "pfe_get_info", "pfe_set_stream",
            "pfe_get_array", "pfe_set_array", "pfe_get_edges", "pfe_apply_A", "pfe_solve_system",
-           "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_get",
+           "pfe_time_kernel", "pfe_fsai_param_count", "pfe_fsai_set", "pfe_fsai_loss_grad", "pfe_fsai_loss_grad_rhs", "pfe_fsai_get",
            "pfe_adam_update", "pfe_orthonormalize_noalloc", "pfe_fsai_classical", "pfe_ic0", "pfe_get_segments",
            "pfe_get_segment_stats", "pfe_laplacian_eigenmap", "pfe_objective", "pfe_autotune",
            "pfe_set_variant", "pfe_solve_two_stage", "pfe_kmeans", "pfe_residual", "pfe_get_variant",
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.pfe_fsai_set.argtypes = [vp, vp]
     lib.pfe_fsai_classical.argtypes = [vp]
     lib.pfe_fsai_loss_grad.argtypes = [vp, vp, vp, C.POINTER(dbl)]
+    lib.pfe_fsai_loss_grad_rhs.argtypes = [vp, vp, vp, i32, dbl, vp, C.POINTER(dbl), C.POINTER(dbl)]
     lib.pfe_fsai_get.argtypes = [vp, vp, vp]
     lib.pfe_adam_update.argtypes = [vp, vp, vp, vp, i64, i32, dbl, dbl, dbl, dbl, vp]
     lib.pfe_get_segments.argtypes = [vp, vp, vp]
@@ -463,6 +464,19 @@ class PFE:
         loss = C.c_double()
         self._check(self.lib.pfe_fsai_loss_grad(self.ctx, pp, pg, C.byref(loss)), "pfe_fsai_loss_grad")
         return loss.value, grad
+
+    def fsai_loss_grad_rhs(self, params, B, mu: float, grad=None):
+        """Kaporin loss plus mu times the mean relative residual of G^T G on
+        the right-hand sides B (n x m FP64, host or device): (loss, grad, R)."""
+        pp, kp = _ptr_f32(params)
+        if grad is None:
+            grad = np.empty(self.lib.pfe_fsai_param_count(), dtype=np.float32)
+        pg, kg = _ptr_f32(grad)
+        pb, kb = _ptr(B)
+        loss, rt = C.c_double(), C.c_double()
+        self._check(self.lib.pfe_fsai_loss_grad_rhs(self.ctx, pp, pb, int(B.shape[1]), float(mu), pg, C.byref(loss),
+                                                    C.byref(rt)), "pfe_fsai_loss_grad_rhs")
+        return loss.value, grad, rt.value
 
     def fsai_get(self):
         info = self.info()

@@ -194,3 +194,32 @@ def test_adam_kernel_matches_oracle():
     u_terms = lr * (m_terms / (1 - b1 ** step)) / (np.sqrt(v / (1 - b2 ** step)) + eps)
     err = np.abs(P.cpu().numpy().astype(np.float64) - th)
     assert np.all(err <= u32 * np.abs(th) + 16 * u32 * u_terms)
+
+
+@pytest.mark.parametrize("H,W,d,radius", [(12, 13, 2, 2.0), (23, 19, 3, 3.0)])
+def test_fsai_rhs_term_matches_oracle(H, W, d, radius):
+    """The training criterion with the right-hand-side term, mu times the
+    mean of |A G^T G b - b|^2 / |b|^2 over a right-hand side of Eq. 13 that
+    the method produced (after one inner step), through the GPU's forward,
+    Kaporin and right-hand-side kernels and the network's backward, against
+    the oracle with the same BF16 roundings: R to 1e-3, the loss to 1e-4,
+    the gradient to 1e-3 (FP32 network output and accumulation); mu = 0
+    gives the Kaporin loss and gradient bit for bit."""
+    spec = small_spec(H=H, W=W, d=d, radius=radius)
+    p, X, Y0 = gpu_problem(spec, "mixed")
+    g = oracle_graph(spec, X)
+    p.init(Y0)
+    p.inner_step()
+    B = np.ascontiguousarray(p.get("RHS"))
+    th = _perturbed_params(5, 0.05).astype(np.float32)
+    mu = 0.5
+    L_ref, grad_ref, info = F.loss_and_grad(th.astype(np.float64), g, bf16=True, B=B, mu=mu)
+    L, grad, R = p.fsai_loss_grad_rhs(th, B, mu)
+    assert abs(R - info["R"]) <= 1e-3 * info["R"], (R, info["R"])
+    assert abs(L - L_ref) <= 1e-4 * max(1.0, abs(L_ref)), (L, L_ref)
+    assert relerr(grad, grad_ref) <= 1e-3, relerr(grad, grad_ref)
+    L0, g0, R0 = p.fsai_loss_grad_rhs(th, B, 0.0)
+    L1, g1 = p.fsai_loss_grad(th)
+    assert L0 == L1 and R0 == 0.0
+    np.testing.assert_array_equal(g0, g1)
+    p.close()
