@@ -281,7 +281,9 @@ PFE_API pfe_status pfe_get_variant(pfe_ctx *c, int32_t kernel, int32_t *variant,
  * (-1 where not timed; k_pupdate and k_fsai_zp: the average of the launches
  * that fold and that hold the solution update).  pfe_set_shape sets the
  * count directly (0 restores the occupancy; counts above it act as it);
- * PFE_EINVAL for another kernel or a count outside 0..8.  pfe_init resets
+ * PFE_EINVAL for another kernel or a count outside 0..8.  The stencil-form
+ * SpMM (PFE_SPMM_STENCIL) sizes its own grid: pfe_get_shape reports 0 and
+ * no timings for it, pfe_set_shape gives PFE_EUNSUPPORTED.  pfe_init resets
  * every shape to the default.
  */
 PFE_API pfe_status pfe_get_shape(pfe_ctx *c, int32_t kernel, int32_t *blocks_per_sm, double *ms);

@@ -779,19 +779,22 @@ pfe_status pfe_get_variant(pfe_ctx *c, int32_t kernel, int32_t *variant, double 
 
 pfe_status pfe_get_shape(pfe_ctx *c, int32_t kernel, int32_t *blocks_per_sm, double *ms) {
     if (!c || !blocks_per_sm) return PFE_EINVAL;
-    const int slot = shape_slot(c, kernel), row = shape_row(kernel);
-    if (slot < 0 || row < 0) return fail(c, PFE_EINVAL, "pfe_get_shape: not a tunable kernel");
-    *blocks_per_sm = c->kbps[slot];
+    const int row = shape_row(kernel);
+    if (row < 0) return fail(c, PFE_EINVAL, "pfe_get_shape: not a tunable kernel");
+    // the stencil-form SpMM sizes its own grid: the default, nothing timed
+    const int slot = shape_slot(c, kernel);
+    *blocks_per_sm = slot >= 0 ? c->kbps[slot] : 0;
     if (ms)
-        for (int b = 0; b < 8; ++b) ms[b] = c->shape_ms[row][b] > 0.f ? c->shape_ms[row][b] : -1.0;
+        for (int b = 0; b < 8; ++b) ms[b] = (slot >= 0 && c->shape_ms[row][b] > 0.f) ? c->shape_ms[row][b] : -1.0;
     return PFE_OK;
 }
 
 pfe_status pfe_set_shape(pfe_ctx *c, int32_t kernel, int32_t blocks_per_sm) {
     if (!c) return PFE_EINVAL;
     const int slot = shape_slot(c, kernel);
-    if (slot < 0 || shape_row(kernel) < 0 || blocks_per_sm < 0 || blocks_per_sm > 8)
+    if (shape_row(kernel) < 0 || blocks_per_sm < 0 || blocks_per_sm > 8)
         return fail(c, PFE_EINVAL, "pfe_set_shape: not a tunable kernel, or blocks per SM outside 0..8");
+    if (slot < 0) return fail(c, PFE_EUNSUPPORTED, "pfe_set_shape: the stencil-form SpMM sizes its own grid");
     PFE_TRY(sync(c));
     c->kbps[slot] = blocks_per_sm;
     c->kgrid[slot] = 0;

@@ -6,6 +6,7 @@ import pytest
 
 from oracle import fsai_oracle as F
 from oracle import pfe_oracle as O
+from synth import make_problem
 from tests.gpu_common import gpu_problem, oracle_graph, relerr, small_spec
 
 pytestmark = pytest.mark.gpu
@@ -223,3 +224,38 @@ def test_fsai_rhs_term_matches_oracle(H, W, d, radius):
     assert L0 == L1 and R0 == 0.0
     np.testing.assert_array_equal(g0, g1)
     p.close()
+
+
+@pytest.mark.parametrize("lam_scale,r", [(0.2, 1.0), (5.0, 1.0), (1.0, 4.0), (1.0, 0.25)])
+def test_trained_network_away_from_its_training_lambda_and_r(lam_scale, r):
+    """The network was trained with lambda = sqrt(vol W), r = 1.  Its inputs
+    are scale-free quantities of A (the Jacobi-scaled coupling lam w^2 /
+    sqrt(A_aa A_bb) and the share r d_i / A_ii of the constraint term), so
+    other lambda and r change its inputs, not their meaning.  At lambda
+    scaled by 0.2 and 5 and at r = 4 and 0.25 the learned factor still gives
+    the oracle's solution of the whole nested loop (FP32 path, 2e-4) and
+    still needs fewer PCG iterations than Jacobi, within 30 % of the
+    classical FSAI (the pattern's Kaporin optimum)."""
+    from paper_1612_06496_gb300.learned import load_weights
+    spec = small_spec(H=48, W=52, d=4, seed=13, regions=4)
+    X, Y0 = make_problem(spec)
+    g0 = oracle_graph(spec, X)
+    lam = lam_scale * g0.lam
+    g = O.build_grid_graph(X, spec.H, spec.W, spec.radius, spec.sigma, lam=lam, r=r)
+    ref = O.soc_pfe(g, Y0, 1, 3, solver="direct")
+    its = {}
+    for kind in ("jacobi", "classical", "learned"):
+        p, _, _ = gpu_problem(spec, "mixed", tol=1e-6, lam=lam, r=r)
+        p.init(Y0)
+        if kind == "classical":
+            p.fsai_classical()
+        elif kind == "learned":
+            p.fsai_set(load_weights())
+        Y = np.empty_like(Y0)
+        st = p.solve(1, 3, Y, None)
+        assert st["n_unconverged"] == 0
+        assert relerr(Y, ref.Y) <= 2e-4, (kind, relerr(Y, ref.Y))
+        its[kind] = st["pcg_iters_total"]
+        p.close()
+    assert its["learned"] < its["jacobi"], its
+    assert its["learned"] <= 1.3 * its["classical"], its

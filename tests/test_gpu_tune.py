@@ -249,3 +249,19 @@ def test_autotuned_launch_shapes(precond):
                 p.close()
             np.testing.assert_array_equal(out[0], out[1])
             assert relerr(out[0], ref) <= 2e-4, (k, b, relerr(out[0], ref))
+
+
+def test_shape_of_the_stencil_spmm_is_its_own():
+    """With the stencil-form SpMM in use (it sizes its own grid) the SpMM's
+    launch shape reads as the default with nothing timed, and setting one is
+    PFE_EUNSUPPORTED."""
+    from paper_1612_06496_gb300 import PFEError
+    spec = small_spec(H=40, W=44, d=6)
+    p, X, Y0 = gpu_problem(spec, "mixed")
+    p.init(Y0)
+    p.set_variant(5)
+    assert p.get_shape("spmm") == (0, {})
+    with pytest.raises(PFEError) as ei:
+        p.set_shape("spmm", 3)
+    assert ei.value.status == 8
+    p.close()
