@@ -124,3 +124,21 @@ def test_reference_arm_runs_on_rank_zero_only(bench, capsys):
     args = argparse.Namespace(workload="C1", steps=1, warmup=1, gpus=2, cpu_window=192)
     assert bench.run_reference(args, rank=1, world=2) is None
     assert capsys.readouterr().out == ""
+
+
+def test_computed_column_traffic_files(bench, monkeypatch):
+    """The captures of the computed-column SpMM variants (6, 7) and of
+    k_fsai_tr with computed columns (variant 1) come from one run; the
+    computed-column SpMM moves fewer bytes per nonzero than the slot form."""
+    prof = os.path.join(bench.ROOT, "profiles")
+    kv6 = _kv(os.path.join(prof, "spmm_v6_traffic.txt"))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: kv6["kernel_sha"])
+    for v in (6, 7):
+        kv = _kv(os.path.join(prof, f"spmm_v{v}_traffic.txt"))
+        assert kv["kernel_sha"] == kv6["kernel_sha"] and kv["variant"] == str(v)
+        assert bench.ncu_traffic("C5", "spmm", float(kv["units"]), v) == pytest.approx(
+            float(kv["dram_bytes_per_launch"]))
+    kt = _kv(os.path.join(prof, "fsai_tr_v1_traffic.txt"))
+    assert kt["kernel_sha"] == kv6["kernel_sha"] and kt["variant"] == "1"
+    assert bench.ncu_traffic("C5", "fsai_tr", 2 * float(kt["units"]), 1) == pytest.approx(
+        2 * float(kt["dram_bytes_per_launch"]))
