@@ -244,10 +244,15 @@ enum {
     PFE_SPMM_GRID2 = 7,   /* the same, two row groups per step */
     PFE_SPMM_NVARIANTS = 8
 };
-enum { PFE_TUNE_SPMM = 0, PFE_TUNE_FSAI = 1, PFE_TUNE_EDGE = 2 };
+enum { PFE_TUNE_SPMM = 0, PFE_TUNE_FSAI = 1, PFE_TUNE_EDGE = 2, PFE_TUNE_MLP = 3 };
 enum {
     PFE_FSAI_SLOTS = 0,   /* FSAI kernels read each slot's column */
     PFE_FSAI_STENCIL = 1  /* one grid image: the columns are computed from the stencil */
+};
+enum {
+    PFE_MLP_MMA_SYNC = 0, /* the network's 64 x 64 layer as warp-level mma.sync m16n8k16 tiles */
+    PFE_MLP_TCGEN05 = 1   /* the default: 128 x 64 x 64 tcgen05.mma per 128 entries, FP32 accumulator in
+                             tensor memory (inference; training's backward runs mma.sync) */
 };
 enum {
     PFE_EDGE_SLOTS = 0,   /* edge pass reads each slot's column and edge id */
@@ -258,9 +263,12 @@ enum {
 PFE_API pfe_status pfe_autotune(pfe_ctx *c, int32_t reps, int32_t *choice, double *ms);
 PFE_API pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant);
 /* pfe_get_variant -- the current choice for `kernel` (PFE_TUNE_SPMM,
- * PFE_TUNE_FSAI or PFE_TUNE_EDGE); for PFE_TUNE_FSAI and PFE_TUNE_EDGE, ms
- * (2 entries, may be NULL) receives the two column forms' times from the
- * last pfe_autotune (-1 if not tuned). */
+ * PFE_TUNE_FSAI, PFE_TUNE_EDGE or PFE_TUNE_MLP); for PFE_TUNE_FSAI and
+ * PFE_TUNE_EDGE, ms (2 entries, may be NULL) receives the two column forms'
+ * times from the last pfe_autotune (-1 if not tuned).  PFE_TUNE_MLP (not
+ * tuned: the network runs once per image) selects the tensor-core path of the
+ * learned factor's inference; it takes effect at the next pfe_fsai_set or
+ * pfe_fsai_loss_grad. */
 PFE_API pfe_status pfe_get_variant(pfe_ctx *c, int32_t kernel, int32_t *variant, double *ms);
 
 /*

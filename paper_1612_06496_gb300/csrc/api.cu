@@ -765,6 +765,8 @@ pfe_status pfe_get_variant(pfe_ctx *c, int32_t kernel, int32_t *variant, double 
             ms[0] = c->fsai_tune_ms[0];
             ms[1] = c->fsai_tune_ms[1];
         }
+    } else if (kernel == PFE_TUNE_MLP) {
+        *variant = c->fsai.mlp_tc ? PFE_MLP_TCGEN05 : PFE_MLP_MMA_SYNC;
     } else if (kernel == PFE_TUNE_EDGE) {
         *variant = c->edge_variant;
         if (ms) {
@@ -804,6 +806,12 @@ pfe_status pfe_set_shape(pfe_ctx *c, int32_t kernel, int32_t blocks_per_sm) {
 
 pfe_status pfe_set_variant(pfe_ctx *c, int32_t kernel, int32_t variant) {
     if (!c) return PFE_EINVAL;
+    if (kernel == PFE_TUNE_MLP) {
+        if (variant != PFE_MLP_MMA_SYNC && variant != PFE_MLP_TCGEN05) return PFE_EINVAL;
+        PFE_TRY(sync(c));
+        c->fsai.mlp_tc = variant == PFE_MLP_TCGEN05;
+        return PFE_OK;
+    }
     if (kernel == PFE_TUNE_EDGE) {
         if (variant < 0 || variant > PFE_EDGE_STENCIL) return PFE_EINVAL;
         if (!edge_variant_applies(c, variant))

@@ -317,6 +317,182 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_fwd(View g, const float *sr
     }
 }
 
+// ---- the network's inference on the 5th-generation tensor cores (tcgen05) -----
+// One CTA of 128 threads takes 128 pattern entries at a time.  Layer 1 (4 ->
+// 64, FP32) and the ReLU run one entry per thread and write h1 as BF16 into
+// shared memory; the 64 x 64 layer is one 128 x 64 x 64 MMA (tcgen05.mma
+// kind::f16, BF16 operands, FP32 accumulator in tensor memory, issued by one
+// thread as four K = 16 steps); thread t reads its entry's 64 accumulators
+// back from TMEM lane t (tcgen05.ld 32x32b) for the bias, ReLU and the two
+// heads.  Operands use the no-swizzle K-major layout: 8-row x 16-byte core
+// matrices, the K-adjacent ones 128 bytes apart (leading-dimension offset),
+// the next 8 rows 1024 bytes on (stride offset).
+constexpr int kTcRows = 128;   // entries per tile: the MMA's M
+constexpr int kTcCols = 64;    // TMEM columns of the FP32 accumulator (N = 64)
+
+struct SmemTc {
+    __nv_bfloat16 A[kTcRows * HW];  // h1, 16 KB (1024-byte aligned)
+    __nv_bfloat16 B[HW * HW];       // W2 as N x K (n = h2 unit, k = h1 unit), 8 KB
+    float W1[4 * HW], b1[HW], b2[HW], W3[HW * 2], b3[4];
+    unsigned long long mbar;
+    unsigned tmem_base;
+    int ok;
+};
+constexpr size_t kSmemTc = sizeof(SmemTc) + 1024;  // + the alignment slack
+
+// byte offset of element (r, k) of an R x 64 BF16 operand in the layout above
+__device__ __forceinline__ int tc_off(int r, int k) { return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor (tcgen05): start address, leading- and
+// stride-dimension byte offsets (all >> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = 64, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(HW >> 3) << 17) |
+                              ((uint32_t)(kTcRows >> 4) << 24);
+
+__device__ __forceinline__ bool tc_mbar_wait(uint32_t mbar, uint32_t parity) {
+    // bounded: give up after about a second of device time
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 1000000000ull) return false;
+    }
+}
+
+__global__ void __launch_bounds__(kTcRows, 4) k_mlp_fwd_tc(View g, const float *srow, const float *__restrict__ P,
+                                                          float *gdiag, float *gE, float *hraw, unsigned *err) {
+    extern __shared__ unsigned char smem_raw[];
+    SmemTc &S = *reinterpret_cast<SmemTc *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    unsigned char *Ab = reinterpret_cast<unsigned char *>(S.A);
+    unsigned char *Bb = reinterpret_cast<unsigned char *>(S.B);
+    for (int t = tid; t < 4 * HW; t += blockDim.x) S.W1[t] = P[OW1 + t];
+    for (int t = tid; t < HW; t += blockDim.x) {
+        S.b1[t] = P[OB1 + t];
+        S.b2[t] = P[OB2 + t];
+    }
+    for (int t = tid; t < 2 * HW; t += blockDim.x) S.W3[t] = P[OW3 + t];
+    if (tid < 2) S.b3[tid] = P[OB3 + tid];
+    for (int t = tid; t < HW * HW; t += blockDim.x) {
+        const int k = t / HW, n = t % HW;  // W2[k][n]
+        *reinterpret_cast<__nv_bfloat16 *>(Bb + tc_off(n, k)) = __float2bfloat16_rn(P[OW2 + t]);
+    }
+    const uint32_t mbar = smem_u32(&S.mbar);
+    if (tid == 0) {
+        S.ok = 1;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {  // 64 TMEM columns for the accumulator
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // W2 written by the generic proxy
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = S.tmem_base;
+    const uint32_t abase = smem_u32(S.A), bbase = smem_u32(S.B);
+    const int64_t N = g.n + g.n_edges, ntiles = (N + kTcRows - 1) / kTcRows;
+    uint32_t parity = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t e = tile * kTcRows + tid;
+        float f[4] = {0.f, 0.f, 0.f, 0.f}, scale = 0.f;
+        int head = 0;
+        if (e < N) features(g, srow, e, f, head, scale);
+        // layer 1 (FP32) into the A operand
+#pragma unroll 8
+        for (int u = 0; u < HW; ++u) {
+            float a = S.b1[u];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a = fmaf(f[k], S.W1[k * HW + u], a);
+            *reinterpret_cast<__nv_bfloat16 *>(Ab + tc_off(tid, u)) = __float2bfloat16_rn(fmaxf(a, 0.f));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int ks = 0; ks < HW / 16; ++ks) {  // K = 16 a step: two core matrices along K
+                const uint64_t ad = tc_desc(abase + ks * 256, 128, 1024);
+                const uint64_t bd = tc_desc(bbase + ks * 256, 128, 1024);
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+                    "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(ks)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                         : "memory");
+        }
+        const bool ok = __syncthreads_and(tc_mbar_wait(mbar, parity)) != 0;
+        parity ^= 1u;
+        if (!ok) {  // the accumulator never arrived: report, leave (block-uniform)
+            if (tid == 0) {
+                atomicExch(err, 1u);
+                S.ok = 0;
+            }
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: this thread's entry is TMEM lane 32 warp + lane = row tid
+        float s = 0.f;
+#pragma unroll
+        for (int c = 0; c < HW / 16; ++c) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * c)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int u = 16 * c + j;
+                s = fmaf(fmaxf(__uint_as_float(r[j]) + S.b2[u], 0.f), S.W3[u * 2 + head], s);
+            }
+        }
+        if (e < N) {
+            const float h = s + S.b3[head];
+            hraw[e] = h;
+            if (e < g.n)
+                gdiag[e] = softplusf(h) * scale;
+            else
+                gE[g.ext_slot[e - g.n]] = h * scale;
+        }
+        // every thread's TMEM reads are done before the next tile's MMA overwrites
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    // an MMA still in flight after a time-out gets a second bounded wait
+    if (!S.ok && tid == 0) tc_mbar_wait(mbar, parity ^ 1u);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kTcCols) : "memory");
+}
+
 // G values per SELL slot (both orientations of an edge carry G_ba) so that
 // the PCG apply kernels read them coalesced.
 __global__ void k_gslots(View g, const float *gE, float *gslot) {
@@ -859,6 +1035,7 @@ pfe_status fsai_alloc(pfe_ctx *c) {
     k_entmap<<<nblk(std::max<int64_t>(ne, 1), 256), 256, 0, s>>>(v, f.ent_of_slot);
     PFE_CUDA_TRY(c, cudaGetLastError());
     PFE_CUDA_TRY(c, cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fwd()));
+    PFE_CUDA_TRY(c, cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTc));
     PFE_CUDA_TRY(c, cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bwd()));
     return PFE_OK;
 }
@@ -868,7 +1045,25 @@ pfe_status fsai_infer(pfe_ctx *c) {
     auto &f = c->fsai;
     cudaStream_t s = c->stream;
     View v = view(c);
-    k_mlp_fwd<<<f.mlp_blocks, kMlpThreads, smem_fwd(), s>>>(v, f.srow, f.params, f.gdiag, f.gE, f.hraw);
+    if (f.mlp_tc) {
+        // 5th-generation tensor cores: one 128-entry tile per CTA step, at
+        // most four CTAs (256 TMEM columns) per SM
+        unsigned *err = f.tick + 3;
+        PFE_CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+        const int64_t ntiles = (c->g.n + c->g.n_edges + kTcRows - 1) / kTcRows;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)c->num_sms * 4));
+        k_mlp_fwd_tc<<<grid, kTcRows, kSmemTc, s>>>(v, f.srow, f.params, f.gdiag, f.gE, f.hraw, err);
+        PFE_CUDA_TRY(c, cudaGetLastError());
+        unsigned h = 0;
+        PFE_CUDA_TRY(c, cudaMemcpyAsync(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        PFE_CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (h) {
+            c->err = "learned FSAI: the tensor-core accumulator did not arrive";
+            return PFE_ETIMEOUT;
+        }
+    } else {
+        k_mlp_fwd<<<f.mlp_blocks, kMlpThreads, smem_fwd(), s>>>(v, f.srow, f.params, f.gdiag, f.gE, f.hraw);
+    }
     k_gslots<<<nblk(c->g.n_slices * 32, 256), 256, 0, s>>>(v, f.gE, f.gslot);
     PFE_CUDA_TRY(c, cudaGetLastError());
     return PFE_OK;

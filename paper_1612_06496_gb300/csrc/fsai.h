@@ -30,6 +30,7 @@ struct FsaiState {
     unsigned *tick = nullptr;
     float *params = nullptr;   // network parameters in use (device copy)
     float *grad = nullptr;     // last gradient
+    bool mlp_tc = true;        // network inference on tcgen05 (TMEM accumulator); false: mma.sync
     bool ic = false;           // the factor is IC(0)'s L: M^{-1} = L^{-T} L^{-1} (triangular solves)
     int ic_cl = 0;             // IC level schedule: pixel (x, y) has level x + ic_cl y
     int64_t ic_levels = 0;

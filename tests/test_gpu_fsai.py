@@ -259,3 +259,32 @@ def test_trained_network_away_from_its_training_lambda_and_r(lam_scale, r):
         p.close()
     assert its["learned"] < its["jacobi"], its
     assert its["learned"] <= 1.3 * its["classical"], its
+
+
+@pytest.mark.parametrize("H,W,d,radius", [(21, 23, 3, 3.0), (37, 41, 4, 2.0), (64, 64, 5, 2.0)])
+def test_tcgen05_inference_matches_mma_sync_and_oracle(H, W, d, radius):
+    """The learned factor's inference on the 5th-generation tensor cores
+    (128 x 64 x 64 tcgen05.mma per 128 pattern entries, FP32 accumulator in
+    tensor memory, the default) against the mma.sync form and the oracle:
+    both take the same BF16 operands and accumulate in FP32 (in another
+    order), so G agrees to 1e-5 between them, and to the oracle with the
+    same BF16 roundings within 1e-4 (FP32 features and accumulation);
+    entry counts that leave a ragged last tile of 128."""
+    spec = small_spec(H=H, W=W, d=d, radius=radius)
+    p, X, Y0 = gpu_problem(spec, "mixed")
+    g = oracle_graph(spec, X)
+    th = _perturbed_params().astype(np.float32)
+    assert p.get_variant("mlp")[0] == 1
+    p.fsai_set(th)
+    gd1, ge1 = p.fsai_get()
+    p.set_variant(0, "mlp")
+    p.fsai_set(th)
+    gd0, ge0 = p.fsai_get()
+    assert relerr(gd1, gd0) < 1e-5 and relerr(ge1, ge0) < 1e-5, (relerr(gd1, gd0), relerr(ge1, ge0))
+    Fd, Fe = F.entry_features(g)
+    th32 = th.astype(np.float64)
+    od, _ = F.mlp_forward(th32, Fd, True)
+    oe, _ = F.mlp_forward(th32, Fe, True)
+    _, gd_ref, ge_ref = F.assemble_G(g, od, oe)
+    assert relerr(gd1, gd_ref) < 1e-4 and relerr(ge1, ge_ref) < 1e-4
+    p.close()
