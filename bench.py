@@ -560,7 +560,19 @@ def main():
         tr_b = slot_b + 4 * n + 16 * n * d
         zh_b = slot_b + 4 * n + 12 * n * d
         zf_b = zh_b + 20 * n * d
-        fsai_k = {"k_fsai_t_ms": round(ft_ms, 5),
+        # the network's inference (once per image, in the setup): the 64 x 64
+        # layer's 2 * 64 * 64 flops per pattern entry on the tensor cores
+        mlp = {}
+        if args.precond == "learned":
+            n_ent = n + ne
+            for name, v in (("tcgen05", 1), ("mma_sync", 0)):
+                p.set_variant(v, "mlp")
+                t_ms = p.time_kernel("mlp", 5)
+                mlp[name] = {"ms": round(t_ms, 4),
+                             "tensor_TFLOPs": round(2 * 64 * 64 * n_ent / (t_ms * 1e-3) / 1e12, 1)}
+            p.set_variant(1, "mlp")
+            mlp["entries"] = n_ent
+        fsai_k = {"k_fsai_t_ms": round(ft_ms, 5), "mlp_inference": mlp,
                   "k_fsai_tr_ms": round(tr_ms, 5), "k_fsai_tr_GBps": round(tr_b / (tr_ms * 1e-3) / 1e9, 1),
                   "k_fsai_zp_fold_ms": round(zf_ms, 5), "k_fsai_zp_fold_GBps": round(zf_b / (zf_ms * 1e-3) / 1e9, 1),
                   "k_fsai_zp_hold_ms": round(zh_ms, 5), "k_fsai_zp_hold_GBps": round(zh_b / (zh_ms * 1e-3) / 1e9, 1)}

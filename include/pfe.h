@@ -500,6 +500,9 @@ PFE_API pfe_status pfe_solve_system(pfe_ctx *c, const double *RHS, double *Y, pf
  *                       solution updates ahead of a replacement
  *   PFE_KERNEL_FSAI_T   t = G r with the column dots after a replacement
  *                       (FSAI factor set)
+ *   PFE_KERNEL_MLP      the learned factor's network inference over every
+ *                       pattern entry, on the path PFE_TUNE_MLP selects
+ *                       (after pfe_fsai_set; rewrites G with the same values)
  * The iteration state is not modified (scratch copies and a scratch control
  * block are used; the timed edge passes write the spare b buffer and a
  * scratch right-hand side).  Only
@@ -519,7 +522,8 @@ enum {
     PFE_KERNEL_PUPDATE_HOLD = 7,
     PFE_KERNEL_REPLACE = 8,
     PFE_KERNEL_XFLUSH = 9,
-    PFE_KERNEL_FSAI_T = 10
+    PFE_KERNEL_FSAI_T = 10,
+    PFE_KERNEL_MLP = 11
 };
 PFE_API pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_ms);
 

@@ -1334,6 +1334,10 @@ pfe_status pfe_time_kernel(pfe_ctx *c, int32_t which, int32_t reps, double *avg_
     float ms = 0.f;
     if (which == PFE_KERNEL_EDGE) {
         PFE_TRY(time_edge(c, reps, &ms));
+    } else if (which == PFE_KERNEL_MLP) {
+        if (!c->fsai.enabled || c->fsai.ic || !c->fsai.params)
+            return fail(c, PFE_EUNSUPPORTED, "pfe_time_kernel: the network needs a learned FSAI factor (pfe_fsai_set)");
+        PFE_TRY(fsai_time_infer(c, reps, &ms));
     } else if (which == PFE_KERNEL_SPMM || which == PFE_KERNEL_UPDATE || which == PFE_KERNEL_PUPDATE ||
                which == PFE_KERNEL_FSAI_TR || which == PFE_KERNEL_FSAI_ZP || which == PFE_KERNEL_FSAI_ZP_HOLD ||
                which == PFE_KERNEL_PUPDATE_HOLD || which == PFE_KERNEL_REPLACE || which == PFE_KERNEL_XFLUSH ||

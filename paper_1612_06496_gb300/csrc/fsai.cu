@@ -1069,6 +1069,53 @@ pfe_status fsai_infer(pfe_ctx *c) {
     return PFE_OK;
 }
 
+// Average device time of `reps` launches of the network's inference kernel
+// (the current path: tcgen05 or mma.sync) on f.params, CUDA events on the
+// context's stream (the outputs are rewritten with the same values).
+pfe_status fsai_time_infer(pfe_ctx *c, int reps, float *ms) {
+    auto &f = c->fsai;
+    cudaStream_t s = c->stream;
+    View v = view(c);
+    const int64_t ntiles = (c->g.n + c->g.n_edges + kTcRows - 1) / kTcRows;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)c->num_sms * 4));
+    unsigned *err = f.tick + 3;
+    auto launch = [&]() {
+        if (f.mlp_tc)
+            k_mlp_fwd_tc<<<grid, kTcRows, kSmemTc, s>>>(v, f.srow, f.params, f.gdiag, f.gE, f.hraw, err);
+        else
+            k_mlp_fwd<<<f.mlp_blocks, kMlpThreads, smem_fwd(), s>>>(v, f.srow, f.params, f.gdiag, f.gE, f.hraw);
+    };
+    cudaEvent_t e0, e1;
+    PFE_CUDA_TRY(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        c->err = "cudaEventCreate failed";
+        return PFE_ECUDA;
+    }
+    PFE_CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+    launch();
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < reps; ++k) launch();
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        c->err = "pfe_time_kernel: network inference failed";
+        return PFE_ECUDA;
+    }
+    unsigned h = 0;
+    PFE_CUDA_TRY(c, cudaMemcpy(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (h) {
+        c->err = "learned FSAI: the tensor-core accumulator did not arrive";
+        return PFE_ETIMEOUT;
+    }
+    *ms = t / (float)reps;
+    return PFE_OK;
+}
+
 // Kaporin loss of the current G and its gradient w.r.t. f.params -> f.grad.
 pfe_status fsai_loss_grad(pfe_ctx *c, double *loss, const double *B, int m, double mu, double *rterm) {
     auto &f = c->fsai;

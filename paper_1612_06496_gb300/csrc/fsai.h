@@ -40,6 +40,7 @@ struct FsaiState {
 
 pfe_status fsai_alloc(pfe_ctx *c);
 pfe_status fsai_infer(pfe_ctx *c);
+pfe_status fsai_time_infer(pfe_ctx *c, int reps, float *ms);
 pfe_status fsai_loss_grad(pfe_ctx *c, double *loss, const double *B = nullptr, int m = 0, double mu = 0.0,
                           double *rterm = nullptr);
 pfe_status fsai_export(pfe_ctx *c, double *od, double *oe);

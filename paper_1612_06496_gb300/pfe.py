@@ -34,7 +34,7 @@ EXPORTS = ["pfe_default_params", "pfe_build_graph", "pfe_init", "pfe_inner_step"
 SPMM_NVARIANTS = 8  # PFE_SPMM_GENERAL, _ROW1, _ROW2, _ROW2_4, _TMA, _STENCIL, _GRID1, _GRID2
 TUNE = {"spmm": 0, "fsai": 1, "edge": 2, "mlp": 3}
 KERNEL = {"spmm": 0, "update": 1, "edge": 2, "pupdate": 3, "fsai_tr": 4, "fsai_zp": 5, "fsai_zp_hold": 6,
-          "pupdate_hold": 7, "replace": 8, "xflush": 9, "fsai_t": 10}
+          "pupdate_hold": 7, "replace": 8, "xflush": 9, "fsai_t": 10, "mlp": 11}
 
 
 class GraphDesc(C.Structure):
