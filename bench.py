@@ -71,9 +71,10 @@ def parse():
 
 
 def cpu_sample_worker(arg: str):
-    """One outer iteration per step of the oracle (Jacobi-PCG mode), single
-    threaded, on one window of the workload's image with the full image's
-    lambda (or, for the batch, on one of its images); prints JSON."""
+    """One outer iteration per step of the oracle (Jacobi-PCG mode, or with
+    "solver": "direct" its sparse-LU mode, A factored once before the steps),
+    single threaded, on one window of the workload's image with the full
+    image's lambda (or, for the batch, on one of its images); prints JSON."""
     import numpy as np
 
     from oracle import pfe_oracle as O
@@ -93,7 +94,13 @@ def cpu_sample_worker(arg: str):
         X, Y0 = make_problem(wspec)
         g = O.build_grid_graph(X, win_h, win_w, spec.radius, spec.sigma, lam=cfg["lambda"])
     st = O.init_state(g, Y0)
-    solve = O.PCGSolver(g.A, spec.tol, 5000, 50)
+    factor_s = 0.0
+    if cfg.get("solver", "pcg") == "direct":
+        t0 = time.perf_counter()
+        solve = O.DirectSolver(g.A)
+        factor_s = time.perf_counter() - t0
+    else:
+        solve = O.PCGSolver(g.A, spec.tol, 5000, 50)
     times, iters = [], []
     for _ in range(cfg["steps"]):
         t0 = time.perf_counter()
@@ -106,7 +113,7 @@ def cpu_sample_worker(arg: str):
         times.append(time.perf_counter() - t0)
         iters.append(its / spec.n_inner)
     nnz = g.A.nnz
-    print(json.dumps({"times": times, "iters": iters, "nnz": int(nnz), "n": int(g.n)}))
+    print(json.dumps({"times": times, "iters": iters, "nnz": int(nnz), "n": int(g.n), "factor_s": factor_s}))
 
 
 def cpu_windows(spec, window: int, count: int) -> list:
@@ -129,7 +136,7 @@ def cpu_cores() -> int:
     return max(1, min(16, os.cpu_count() or 1))
 
 
-def run_cpu_sample(workload: str, lam: float, steps: int, window: int, nnz_full: int) -> dict:
+def run_cpu_sample(workload: str, lam: float, steps: int, window: int, nnz_full: int, solver: str = "pcg") -> dict:
     """The oracle, as it stands and single threaded, on one window (the batch:
     one image) per host core, all at once: the seconds a step of the
     slowest one took, times nnz_A of the whole workload over the nnz_A the
@@ -145,7 +152,8 @@ def run_cpu_sample(workload: str, lam: float, steps: int, window: int, nnz_full:
     wins = cpu_windows(spec, window, cores) if workload != "C3" else [None] * cores
     procs = []
     for q in range(cores):
-        arg = json.dumps({"workload": workload, "lambda": lam, "steps": steps, "window": wins[q], "index": q})
+        arg = json.dumps({"workload": workload, "lambda": lam, "steps": steps, "window": wins[q], "index": q,
+                          "solver": solver})
         procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-sample-worker", arg],
                                       stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT))
     outs = []
@@ -159,7 +167,8 @@ def run_cpu_sample(workload: str, lam: float, steps: int, window: int, nnz_full:
     per_step = [max(o["times"][k] for o in outs) for k in range(steps)]
     return {"times": per_step, "iters": [sum(o["iters"][k] for o in outs) / cores for k in range(steps)],
             "nnz": nnz_done, "n": sum(o["n"] for o in outs), "scale": scale, "cores": cores,
-            "window": wins[0][2:] if wins[0] else None, "per_step_scaled": [t * scale for t in per_step]}
+            "window": wins[0][2:] if wins[0] else None, "per_step_scaled": [t * scale for t in per_step],
+            "factor_s": max(o.get("factor_s", 0.0) for o in outs)}
 
 
 # --------------------------------------------------------------------------
@@ -715,6 +724,14 @@ def main():
             out = run_cpu_sample(args.workload, info["lambda_"], 1, args.cpu_window, nnz)
             cpu = {"value": out["per_step_scaled"][0], "unit": UNIT, "cores": out["cores"], "kind": "oracle",
                    "sample": cpu_sample_text(spec, args.cpu_window, out) + f" ({out['times'][0]:.1f} s measured)"}
+            if args.workload in ("C1", "C2"):
+                # the oracle's direct mode beside it: sparse LU of A once, then exact solves
+                od = run_cpu_sample(args.workload, info["lambda_"], 1, args.cpu_window, nnz, solver="direct")
+                cpu["direct"] = {"value": od["per_step_scaled"][0], "unit": UNIT, "cores": od["cores"],
+                                 "factor_s_measured": round(od["factor_s"], 3),
+                                 "sample": "the same windows, sparse-LU solves (A factored once before the step, "
+                                           "not counted) instead of Jacobi-PCG, scaled the same way "
+                                           f"({od['times'][0]:.2f} s measured)"}
         except Exception as ex:  # report, do not hide
             cpu = {"value": None, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": f"failed: {ex}"}
 

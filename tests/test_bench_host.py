@@ -142,3 +142,15 @@ def test_computed_column_traffic_files(bench, monkeypatch):
     assert kt["kernel_sha"] == kv6["kernel_sha"] and kt["variant"] == "1"
     assert bench.ncu_traffic("C5", "fsai_tr", 2 * float(kt["units"]), 1) == pytest.approx(
         2 * float(kt["dram_bytes_per_launch"]))
+
+
+def test_cpu_sample_direct_mode(bench):
+    """The oracle's direct mode (sparse LU of A once, exact solves) beside its
+    Jacobi-PCG mode on the 32x32 image (one window: the whole image): no PCG
+    iterations and a factorisation time in the direct mode, PCG iterations
+    and none in the other."""
+    d = bench.run_cpu_sample("C1", 0.0, 1, 192, 12676, solver="direct")
+    p = bench.run_cpu_sample("C1", 0.0, 1, 192, 12676)
+    assert d["cores"] == 1 and d["scale"] == pytest.approx(1.0)
+    assert d["iters"] == [0.0] and d["factor_s"] > 0.0
+    assert p["iters"][0] > 0 and p["factor_s"] == 0.0
